@@ -1,0 +1,274 @@
+"""Seeded synthetic inputs for the element volume term: mesh, metric terms,
+hydrostatic reference state and perturbed state.
+
+This module is shared by the tests, the benchmark and the oracle checks. It
+holds none of the volume term's arithmetic: no differentiation matrix, no
+equation of state of the model and no flux. It places GLL points (using
+scipy's Gauss-Jacobi root finder) and evaluates closed-form geometry and
+thermodynamics.
+
+The workload follows the paper's setting (Sec. 2): a dry atmosphere on a
+curvilinear hexahedral mesh of tensor-product elements with Nq^3 points each.
+The benchmark adds a sine warp of a 10 km box, an isothermal hydrostatic
+reference state and small seeded perturbations:
+
+* Box [0, L]^3 split into nx*ny*nz elements. Element e = ex + nx*(ey + ny*ez).
+  Within an element, point (i, j, k) sits at the GLL node (xi_i, xi_j, xi_k).
+* Warp, applied to all three axes at once from the unwarped coordinates:
+  x = xh + A s(yh) s(zh), y = yh + A s(zh) s(xh), z = zh + A s(xh) s(yh),
+  where s(u) = sin(pi u / L) and A = warp * L. The box boundary stays fixed.
+* Metric terms are analytic, g_{a,d} = J dxi_d/dx_a. With a_d = dx/dxi_d, the
+  three vectors are J grad(xi_r) = a_s x a_t, J grad(xi_s) = a_t x a_r and
+  J grad(xi_t) = a_r x a_s, and J = a_r . (a_s x a_t). They are stored as
+  g[3*d + a].
+* The reference state is isothermal (T = 300 K) and hydrostatic:
+  p_h = p0 exp(-grav z / (R T)), rho_ref = p_h / (R T),
+  theta_ref = T (p0 / p_h)^(R / cp) and Theta_ref = rho_ref * theta_ref.
+  Here z is the warped height of the point.
+* The state is rho = rho_ref (1 + eps B_rho), theta = theta_ref (1 + eps B_theta)
+  and Theta = rho * theta. Velocities u, v and w are i.i.d. uniform(-vmax, vmax)
+  at every point, and U_a = rho u_a. Each B is a sum of four Gaussian bumps
+  a exp(-|x - c|^2 / w^2), with centres uniform in the box, widths uniform in
+  [0.1 L, 0.3 L] and amplitudes uniform in [-1, 1]. The draws come from
+  numpy's PCG64 in this order: the bumps of B_rho, the bumps of B_theta, then
+  the velocities (3 x M values, field-major).
+
+Per-point arrays use [e][k][j][i] order with i fastest. State fields are
+planes in the order (rho, U1, U2, U3, Theta).
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+
+import numpy as np
+
+NFIELDS = 5
+FIELD_NAMES = ("rho", "U1", "U2", "U3", "Theta")
+
+
+@dataclass(frozen=True)
+class Constants:
+    """Dry-air constants of the benchmark (SI units)."""
+    p0: float = 1.0e5
+    R: float = 287.17
+    cp: float = 1004.67
+    grav: float = 9.80616
+
+    def as_dict(self) -> dict:
+        return {"p0": self.p0, "R": self.R, "cp": self.cp, "grav": self.grav}
+
+
+DRY_AIR = Constants()
+# The paper's nondimensional set (p_p0 = 1, p_Gamma = 1.4, p_R = 1), with cp
+# chosen so that cp / (cp - R) = 1.4, and no gravity.
+PAPER_UNITS = Constants(p0=1.0, R=1.0, cp=3.5, grav=0.0)
+
+
+def gll_points(N: int) -> np.ndarray:
+    """GLL points on [-1, 1]: the endpoints and the roots of P_N'.
+
+    The interior points are the Gauss-Jacobi(1, 1) points of degree N - 1
+    (P_N' is proportional to P^(1,1)_{N-1}). They come from scipy's
+    ``roots_jacobi``, which is independent of the Newton iterations in the
+    oracle and in the library."""
+    if N < 1:
+        raise ValueError("N must be >= 1")
+    from scipy.special import roots_jacobi
+    inner = roots_jacobi(N - 1, 1.0, 1.0)[0] if N > 1 else np.zeros(0)
+    pts = np.concatenate(([-1.0], np.sort(inner), [1.0]))
+    return pts
+
+
+@dataclass
+class Mesh:
+    N: int
+    shape: tuple            # (nx, ny, nz)
+    L: float
+    x: np.ndarray           # (3, M) physical coordinates
+    g: np.ndarray           # (9, M) metric terms, g[3*d + a] = g_{a+1, d+1}
+    Jinv: np.ndarray        # (M,)
+
+    @property
+    def Nq(self) -> int:
+        return self.N + 1
+
+    @property
+    def Ne(self) -> int:
+        return int(np.prod(self.shape))
+
+    @property
+    def M(self) -> int:
+        return self.Ne * self.Nq ** 3
+
+
+def _node_axes(N: int, shape, L: float):
+    """Unwarped coordinates, broadcastable to (nz, ny, nx, Nq, Nq, Nq)."""
+    nx, ny, nz = shape
+    Nq = N + 1
+    r = (gll_points(N) + 1.0) * 0.5
+    hx, hy, hz = L / nx, L / ny, L / nz
+    xh = (np.arange(nx)[:, None] + r[None, :]) * hx   # (nx, Nq)
+    yh = (np.arange(ny)[:, None] + r[None, :]) * hy
+    zh = (np.arange(nz)[:, None] + r[None, :]) * hz
+    xh = xh.reshape(1, 1, nx, 1, 1, Nq)
+    yh = yh.reshape(1, ny, 1, 1, Nq, 1)
+    zh = zh.reshape(nz, 1, 1, Nq, 1, 1)
+    return xh, yh, zh, (hx, hy, hz)
+
+
+def _cross(a, b):
+    return (a[1] * b[2] - a[2] * b[1], a[2] * b[0] - a[0] * b[2], a[0] * b[1] - a[1] * b[0])
+
+
+def _finish(N, shape, L, X, a_r, a_s, a_t) -> Mesh:
+    full = (shape[2], shape[1], shape[0], N + 1, N + 1, N + 1)
+    M = int(np.prod(full))
+    bc = lambda v: np.broadcast_to(v, full)
+    a_r = [bc(c) for c in a_r]
+    a_s = [bc(c) for c in a_s]
+    a_t = [bc(c) for c in a_t]
+    gr = _cross(a_s, a_t)
+    gs = _cross(a_t, a_r)
+    gt = _cross(a_r, a_s)
+    J = a_r[0] * gr[0] + a_r[1] * gr[1] + a_r[2] * gr[2]
+    if np.any(J <= 0):
+        raise ValueError("mapping is not orientation preserving")
+    g = np.empty((9, M))
+    for d, gd in enumerate((gr, gs, gt)):
+        for a in range(3):
+            g[3 * d + a] = np.ascontiguousarray(gd[a]).reshape(M)
+    x = np.empty((3, M))
+    for a in range(3):
+        x[a] = np.ascontiguousarray(bc(X[a])).reshape(M)
+    return Mesh(N=N, shape=tuple(shape), L=L, x=x, g=g,
+                Jinv=np.ascontiguousarray(1.0 / J).reshape(M))
+
+
+def warped_box(N: int, shape=(8, 8, 8), L: float = 10_000.0, warp: float = 0.05) -> Mesh:
+    """The benchmark mesh: the sine-warped box described in the module docstring."""
+    xh, yh, zh, (hx, hy, hz) = _node_axes(N, shape, L)
+    A = warp * L
+    k = math.pi / L
+    sx, sy, sz = np.sin(k * xh), np.sin(k * yh), np.sin(k * zh)
+    cx, cy, cz = np.cos(k * xh), np.cos(k * yh), np.cos(k * zh)
+    X = (xh + A * sy * sz, yh + A * sz * sx, zh + A * sx * sy)
+    # a_d = dx/dxi_d. Each xi_d moves only its own unwarped coordinate, by h_d / 2.
+    Ak = A * k
+    a_r = (0.5 * hx + 0 * sx, 0.5 * hx * Ak * sz * cx, 0.5 * hx * Ak * cx * sy)
+    a_s = (0.5 * hy * Ak * cy * sz, 0.5 * hy + 0 * sy, 0.5 * hy * Ak * sx * cy)
+    a_t = (0.5 * hz * Ak * sy * cz, 0.5 * hz * Ak * cz * sx, 0.5 * hz + 0 * sz)
+    return _finish(N, shape, L, X, a_r, a_s, a_t)
+
+
+def affine_box(N: int, shape=(2, 2, 2), L: float = 1.0, B=None) -> Mesh:
+    """An affine mesh x = B xh of the box (a constant, generally non-orthogonal
+    map). Each element is affine, so the metric terms are constant."""
+    if B is None:
+        B = np.array([[1.0, 0.3, -0.2], [0.1, 0.9, 0.25], [-0.15, 0.2, 1.1]])
+    B = np.asarray(B, dtype=np.float64)
+    xh, yh, zh, (hx, hy, hz) = _node_axes(N, shape, L)
+    X = tuple(B[a, 0] * xh + B[a, 1] * yh + B[a, 2] * zh for a in range(3))
+    a_r = tuple(np.float64(0.5 * hx * B[a, 0]) for a in range(3))
+    a_s = tuple(np.float64(0.5 * hy * B[a, 1]) for a in range(3))
+    a_t = tuple(np.float64(0.5 * hz * B[a, 2]) for a in range(3))
+    return _finish(N, shape, L, X, a_r, a_s, a_t)
+
+
+def hydrostatic_reference(z: np.ndarray, c: Constants = DRY_AIR, T: float = 300.0):
+    """Isothermal hydrostatic reference state at heights z: (rho_ref, Theta_ref)."""
+    p_h = c.p0 * np.exp(-c.grav * z / (c.R * T))
+    rho = p_h / (c.R * T)
+    theta = T * (c.p0 / p_h) ** (c.R / c.cp)
+    return rho, rho * theta
+
+
+def _bumps(rng: np.random.Generator, L: float, count: int = 4):
+    centres = rng.uniform(0.0, L, size=(count, 3))
+    widths = rng.uniform(0.1 * L, 0.3 * L, size=count)
+    amps = rng.uniform(-1.0, 1.0, size=count)
+    return centres, widths, amps
+
+
+def _eval_bumps(x: np.ndarray, bumps) -> np.ndarray:
+    centres, widths, amps = bumps
+    out = np.zeros(x.shape[1])
+    for c, w, a in zip(centres, widths, amps):
+        r2 = (x[0] - c[0]) ** 2 + (x[1] - c[1]) ** 2 + (x[2] - c[2]) ** 2
+        out += a * np.exp(-r2 / (w * w))
+    return out
+
+
+def perturbed_state(mesh: Mesh, rho_ref, rhotheta_ref, seed: int,
+                    eps: float = 1e-3, vmax: float = 10.0) -> np.ndarray:
+    """Seeded state (5, M): Gaussian-bump perturbations of rho and theta and
+    per-point uniform random velocities (see module docstring)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    b_rho = _bumps(rng, mesh.L)
+    b_theta = _bumps(rng, mesh.L)
+    vel = rng.uniform(-vmax, vmax, size=(3, mesh.M))
+    rho = rho_ref * (1.0 + eps * _eval_bumps(mesh.x, b_rho))
+    theta = (rhotheta_ref / rho_ref) * (1.0 + eps * _eval_bumps(mesh.x, b_theta))
+    q = np.empty((NFIELDS, mesh.M))
+    q[0] = rho
+    q[1:4] = rho[None, :] * vel
+    q[4] = rho * theta
+    return q
+
+
+@dataclass
+class Workload:
+    """Everything one evaluation of the volume term needs."""
+    mesh: Mesh
+    consts: Constants
+    rho_ref: np.ndarray
+    rhotheta_ref: np.ndarray
+    q: np.ndarray
+    seed: int
+    name: str = ""
+    meta: dict = field(default_factory=dict)
+
+    @property
+    def N(self):
+        return self.mesh.N
+
+    @property
+    def Ne(self):
+        return self.mesh.Ne
+
+    @property
+    def M(self):
+        return self.mesh.M
+
+    def problem(self) -> dict:
+        """Geometry and constants in the dict form the oracle and the binding take."""
+        d = {"N": self.mesh.N, "Ne": self.mesh.Ne, "g": self.mesh.g, "Jinv": self.mesh.Jinv,
+             "rho_ref": self.rho_ref, "rhotheta_ref": self.rhotheta_ref}
+        d.update(self.consts.as_dict())
+        return d
+
+
+def make_workload(N: int, n: int, seed: int, L: float = 10_000.0, warp: float = 0.05,
+                  consts: Constants = DRY_AIR, T: float = 300.0, eps: float = 1e-3,
+                  vmax: float = 10.0, name: str = "") -> Workload:
+    """Warped n x n x n box of order N with the seeded perturbed hydrostatic state."""
+    mesh = warped_box(N, (n, n, n), L=L, warp=warp)
+    rho_ref, rt_ref = hydrostatic_reference(mesh.x[2], consts, T)
+    q = perturbed_state(mesh, rho_ref, rt_ref, seed, eps=eps, vmax=vmax)
+    return Workload(mesh=mesh, consts=consts, rho_ref=rho_ref, rhotheta_ref=rt_ref,
+                    q=q, seed=seed, name=name,
+                    meta={"L": L, "warp": warp, "T": T, "eps": eps, "vmax": vmax, "n": n})
+
+
+# The two single-GPU workloads: the small parity case and the timed case.
+PARITY_SMALL = dict(N=4, n=8, seed=0, name="N=4 (Nq=5), 8^3=512 elements, warped 10 km box")
+BENCH_FULL = dict(N=7, n=32, seed=1,
+                  name="N=7 (Nq=8), 32^3=32768 elements (16.8M nodes), warped 10 km box")
+
+
+def parity_small() -> Workload:
+    return make_workload(**PARITY_SMALL)
+
+
+def bench_full() -> Workload:
+    return make_workload(**BENCH_FULL)
