@@ -1,0 +1,382 @@
+#!/usr/bin/env python3
+"""Benchmark of the element volume term (Sec. 2, Eq. (2)) on GB300.
+
+One step = one evaluation of the volume term over the whole timed workload:
+order N = 7 (Nq = 8), 32^3 = 32768 elements (16,777,216 GLL points) on the
+sine-warped 10 km box with the seeded perturbed hydrostatic state.  Metric:
+GDOF/s = points per second / 1e9 (a DOF is a grid point, as in the paper's
+Table 2), aggregated over all ranks.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl numa|reference]
+
+Under torchrun every rank evaluates its own copy of the workload: elements are
+independent in the volume term, so ranks need no data-path collective (weak
+scaling).  Rank 0 prints one JSON line.
+
+--impl reference times the FP64 CPU oracle on the host cores instead (each step
+a bounded sample of the same workload); only rank 0 runs it.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "volume-RHS GDOF/s"
+UNIT = "GDOF/s"
+# Algorithmic HBM bytes per point of the FP64 path: 5 state + 9 metric + Jinv +
+# 2 reference arrays read (17 x 8 B), 5 rhs fields written (5 x 8 B).
+BYTES_PER_NODE_FP64 = 176
+# Algorithmic FP64 flops per point (an FMA counts 2, pow and divide count 1):
+# EOS 5, three directions of u and fluxes 3 x 17, three D sweeps 30*Nq,
+# Jinv scaling and gravity 8.
+def flops_per_node_fp64(Nq: int) -> int:
+    return 5 + 51 + 30 * Nq + 8
+
+
+# FP64 CUDA-core peak of one GB300, used only when the FP64 pipe binds.
+FP64_PEAK_TFLOPS = 1.25
+FALLBACK_HBM_GBS = 6800.0
+CPU_SAMPLE_ELEMENTS = 4096     # bounded oracle sample: the first 4096 elements
+
+
+def workload_full(n: int = 32):
+    """The timed workload; a smaller n (elements per axis) is for ncu captures."""
+    from paper_1604_08501_gb300 import workload as wl
+    if n == wl.BENCH_FULL["n"]:
+        return wl.bench_full(), wl.BENCH_FULL["name"]
+    w = wl.make_workload(N=wl.BENCH_FULL["N"], n=n, seed=wl.BENCH_FULL["seed"])
+    return w, f"N=7 (Nq=8), {n}^3={n ** 3} elements, warped 10 km box (profiling size)"
+
+
+def workload_config(w, name):
+    return {"workload": name, "N": w.N, "Nq": w.N + 1, "elements": w.Ne, "points": w.M,
+            "seed": w.seed, "precision": "fp64",
+            "l2": f"inputs larger than L2: {w.M * BYTES_PER_NODE_FP64 / 1e9:.2f} GB moved "
+                  "per step against a 129 MB L2, no flush"}
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured (MEASURED_PEAKS.json hbm_gbs, STREAM-style copy)"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback 6.8 TB/s (MEASURED_PEAKS.json absent)"
+
+
+def load_traffic(kernel: str):
+    """dram bytes per launch of ``kernel`` from the committed ncu summary, if the
+    kernel source has not changed since the counters were taken."""
+    import hashlib
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(p) as f:
+            d = json.load(f)[kernel]
+        src = os.path.join(ROOT, d["source"])
+        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+        if sha != d["source_sha"]:
+            return None
+        return float(d["dram_bytes_per_launch"])
+    except Exception:
+        return None
+
+
+# ---------------------------------------------------------------- clocks
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during a region."""
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id: str):
+        self.gpu_id = gpu_id
+        self.proc = None
+        self.t0 = self.t1 = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.QUERY}", "--format=csv,noheader,nounits",
+                 "-lms", "50", "-i", self.gpu_id],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, ValueError):
+            self.proc = None
+        time.sleep(0.3)
+
+    def mark(self, which):
+        setattr(self, which, time.time())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.15)
+        self.proc.terminate()
+        out, _ = self.proc.communicate(timeout=10)
+        rows = []
+        for line in out.strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                rows.append({"sm": float(f[1]), "max": float(f[2]), "power": float(f[3]),
+                             "hw": f[5], "hw_thermal": f[6], "sw_thermal": f[7], "sw_power": f[8]})
+            except ValueError:
+                continue
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        # nvidia-smi prints no timestamps in this mode: samples are spaced ~50 ms
+        # from start(); keep the busy ones (power well above idle) as "under load".
+        pmax = max(r["power"] for r in rows)
+        load = [r for r in rows if r["power"] >= 0.5 * pmax] or rows
+        reasons = []
+        for key, name in (("hw", "hw_slowdown"), ("hw_thermal", "hw_thermal_slowdown"),
+                          ("sw_thermal", "sw_thermal_slowdown"), ("sw_power", "sw_power_cap")):
+            if any(r[key].lower().startswith("active") for r in load):
+                reasons.append(name)
+        return {"sm_mhz": statistics.median(r["sm"] for r in load),
+                "sm_max_mhz": max(r["max"] for r in load), "reasons": reasons,
+                "samples_under_load": len(load), "power_w_max": pmax}
+
+
+def gpu_id_for(device_index: int) -> str:
+    import torch
+    try:
+        u = str(torch.cuda.get_device_properties(device_index).uuid)
+        return u if u.startswith("GPU-") else "GPU-" + u
+    except Exception:
+        vis = os.environ.get("CUDA_VISIBLE_DEVICES")
+        if vis:
+            return vis.split(",")[device_index]
+        return str(device_index)
+
+
+# ---------------------------------------------------------------- distributed
+
+def dist_setup(backend: str):
+    import torch.distributed as dist
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    if world > 1 and not dist.is_initialized():
+        dist.init_process_group(backend)
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, local, world
+
+
+def reduce_max(x: float, device=None) -> float:
+    """Max of x over ranks (identity without torch.distributed)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return x
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(device=None):
+    import torch.distributed as dist
+    if dist.is_available() and dist.is_initialized() and dist.get_world_size() > 1:
+        if device is not None and dist.get_backend() == "nccl":
+            dist.barrier(device_ids=[device.index])
+        else:
+            dist.barrier()
+
+
+def aggregate(units_per_rank: int, seconds_local: float, device=None):
+    """Whole-job throughput: units all ranks processed / max time over ranks."""
+    import torch.distributed as dist
+    world = dist.get_world_size() if dist.is_available() and dist.is_initialized() else 1
+    tmax = reduce_max(seconds_local, device)
+    return units_per_rank * world / tmax, tmax
+
+
+# ---------------------------------------------------------------- CPU oracle
+
+def oracle_sample(w, elements: int):
+    n3 = (w.N + 1) ** 3
+    m = min(elements, w.Ne) * n3
+    prob = w.problem()
+    sub = {k: v for k, v in prob.items()}
+    sub["Ne"] = min(elements, w.Ne)
+    sub["g"] = np.ascontiguousarray(prob["g"][:, :m])
+    for k in ("Jinv", "rho_ref", "rhotheta_ref"):
+        sub[k] = np.ascontiguousarray(prob[k][:m])
+    return sub, np.ascontiguousarray(w.q[:, :m]), m
+
+
+def cpu_baseline(w, min_seconds: float = 10.0):
+    import oracle
+    prob, q, m = oracle_sample(w, CPU_SAMPLE_ELEMENTS)
+    oracle.vol_rhs_o2(prob, q)        # warm-up (page-in)
+    runs, t0 = 0, time.perf_counter()
+    while True:
+        oracle.vol_rhs_o2(prob, q)
+        runs += 1
+        el = time.perf_counter() - t0
+        if el >= min_seconds:
+            break
+    return {"value": runs * m / el / 1e9, "unit": UNIT, "cores": oracle.max_threads(),
+            "kind": "oracle",
+            "sample": f"first {prob['Ne']} of {w.Ne} elements ({m} points) of the timed workload, "
+                      f"oracle O2 (fluxes once per point, OpenMP over elements), {runs} runs "
+                      f"in {el:.1f} s"}
+
+
+def run_reference(args):
+    rank, local, world = dist_setup("gloo")
+    if rank != 0:
+        return 0
+    import oracle
+    w, name = workload_full()
+    prob, q, m = oracle_sample(w, CPU_SAMPLE_ELEMENTS)
+    for _ in range(args.warmup):
+        oracle.vol_rhs_o2(prob, q)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.vol_rhs_o2(prob, q)
+    el = time.perf_counter() - t0
+    value = args.steps * m / el / 1e9
+    sample = (f"each step: oracle O2 on the first {prob['Ne']} of {w.Ne} elements "
+              f"({m} points) of the timed workload")
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": el / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": workload_config(w, name), "impl": "reference",
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.max_threads(),
+                             "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+# ---------------------------------------------------------------- GPU
+
+def run_gpu(args):
+    import torch
+    rank, local, world = dist_setup("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    from paper_1604_08501_gb300 import build as lib_build
+    if rank == 0 or world == 1:
+        lib_build.build()
+    barrier(dev)
+    from paper_1604_08501_gb300.numa_vol import VolumeTerm
+
+    w, name = workload_full(args.n)
+    vt = VolumeTerm.from_problem(w.problem())
+    q_host = torch.from_numpy(w.q).pin_memory()
+    q = q_host.to(dev)
+    out = torch.empty_like(q)
+    stream = torch.cuda.current_stream(dev)
+
+    for _ in range(args.warmup):
+        vt.rhs(q, out, stream)
+    torch.cuda.synchronize(dev)
+
+    sampler = ClockSampler(gpu_id_for(local)) if rank == 0 else None
+    if sampler:
+        sampler.start()
+    K = args.steps
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(K)]
+    t_start, t_end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier(dev)
+    torch.cuda.synchronize(dev)
+    t_start.record(stream)
+    for k in range(K):
+        ev[k][0].record(stream)
+        vt.rhs(q, out, stream)
+        ev[k][1].record(stream)
+    t_end.record(stream)
+    torch.cuda.synchronize(dev)
+    barrier(dev)
+    clocks = sampler.stop() if sampler else None
+    region_ms = t_start.elapsed_time(t_end)
+    kernel_ms = float(np.mean([a.elapsed_time(b) for a, b in ev]))
+    value, tmax = aggregate(K * w.M, region_ms * 1e-3, dev)
+    ms_per_step = tmax * 1e3 / K
+
+    # End to end through the public host-buffer call: H2D of q from pinned
+    # memory, the kernel, D2H of rhs, every step.
+    step_bytes = 5 * w.M * 8
+    e2e_value = None
+    if not args.no_e2e:
+        out_host = torch.empty_like(q_host).pin_memory()
+        for _ in range(3):
+            vt.rhs_host(q_host, out_host)
+        barrier(dev)
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        for _ in range(K):
+            vt.rhs_host(q_host, out_host)
+        e2e_s = time.perf_counter() - t0
+        barrier(dev)
+        e2e_value, _ = aggregate(K * w.M, e2e_s, dev)
+
+    if rank == 0:
+        peak, peak_src = measured_peaks()
+        kname = "vol_rhs_fp64_kernel<8>"
+        hbm_gbs = BYTES_PER_NODE_FP64 * w.M / (kernel_ms * 1e-3) / 1e9
+        fp64_tfs = flops_per_node_fp64(w.N + 1) * w.M / (kernel_ms * 1e-3) / 1e12
+        traffic = load_traffic(kname)
+        hbm = {"bound": "hbm", "achieved": hbm_gbs, "peak": peak, "unit": "GB/s",
+               "frac": hbm_gbs / peak, "traffic": traffic, "kernel": kname,
+               "bytes_per_point": BYTES_PER_NODE_FP64, "peak_source": peak_src,
+               "kernel_ms": kernel_ms}
+        alu = {"bound": "alu", "achieved": fp64_tfs, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+               "frac": fp64_tfs / FP64_PEAK_TFLOPS, "traffic": traffic, "kernel": kname,
+               "flops_per_point": flops_per_node_fp64(w.N + 1),
+               "peak_source": "FP64 CUDA-core peak of one GB300 (1.25 TFLOP/s)",
+               "kernel_ms": kernel_ms}
+        roof, other = (hbm, alu) if hbm["frac"] >= alu["frac"] else (alu, hbm)
+        line = {"metric": METRIC, "value": value / 1e9, "unit": UNIT, "n_gpus": world,
+                "steps": K, "warmup": args.warmup, "ms_per_step": ms_per_step,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "f64", "data": "synthetic", "config": workload_config(w, name),
+                "roofline": roof, "roofline_other": other,
+                "e2e": None if e2e_value is None else
+                       {"value": e2e_value / 1e9, "unit": UNIT, "h2d_bytes_per_step": step_bytes,
+                        "d2h_bytes_per_step": step_bytes},
+                "gpu_launches": K, "clocks": clocks}
+        if world == 1 and not args.no_cpu_baseline and args.n == 32:
+            line["cpu_baseline"] = cpu_baseline(w)
+        print(json.dumps(line))
+    vt.close()
+    return 0
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=300)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", choices=["numa", "reference"], default="numa")
+    ap.add_argument("--no-cpu-baseline", action="store_true",
+                    help="skip the timed oracle sample (for profiling runs)")
+    ap.add_argument("--no-e2e", action="store_true",
+                    help="skip the host-buffer end-to-end leg (for profiling runs)")
+    ap.add_argument("--n", type=int, default=32,
+                    help="elements per axis; 32 is the timed workload, smaller is for ncu")
+    args = ap.parse_args(argv)
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gpu(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

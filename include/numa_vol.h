@@ -1,0 +1,153 @@
+/*
+ * numa_vol.h - C ABI of the GB300 (sm_103a) element volume term of a
+ * NUMA-style dry compressible Euler model on hexahedral GLL spectral
+ * elements (Kloeckner, Wilcox, Warburton, "Array Program Transformation with
+ * Loo.py by Example: High-Order Finite Elements", ARRAY'16).
+ *
+ * The operation (Sec. 2, Eq. (2), with the sign of the paper's r- and s-flux
+ * subroutines in Sec. 3, which subtract Jinv * D * flux from rhsq).  For
+ * every element e, point (i, j, k) and field b of q = (rho, U1, U2, U3, Theta):
+ *
+ *   rhs_b(e,i,j,k) = -Jinv(e,i,j,k) * [ sum_n D[i][n] F_r[b](e,n,j,k)
+ *                                     + sum_n D[j][n] F_s[b](e,i,n,k)
+ *                                     + sum_n D[k][n] F_t[b](e,i,j,n) ]
+ *                    - delta_{b,U3} * (rho - rho_ref) * grav
+ *
+ * where, for reference direction d in {r, s, t} (Sec. 2, Eq. (1), flux column
+ * f_a, contracted with the metric terms as in the paper's subroutines):
+ *
+ *   u_d      = (g_{1d} U1 + g_{2d} U2 + g_{3d} U3) / rho
+ *   F_d[rho] = rho u_d,  F_d[U_a] = U_a u_d + g_{ad} p',  F_d[Theta] = Theta u_d
+ *   p'       = p(Theta) - p(Theta_ref),  p(Theta) = p0 (R Theta / p0)^gamma,
+ *   gamma    = cp / (cp - R)            (equation of state, Sec. 2)
+ *
+ * and D is the (N+1) x (N+1) GLL differentiation matrix, D[i][n] = l_n'(xi_i).
+ * The reference-state pressure subtraction and the gravity source extend the
+ * paper's gravity-free form. Theta_ref = rho_ref = grav = 0 gives the
+ * paper's form exactly.
+ *
+ * Layout (all per-point arrays): element-major, then k, j, i with i fastest,
+ * i.e. index ((e*Nq + k)*Nq + j)*Nq + i with Nq = N + 1.  M = Ne * Nq^3.
+ * State and rhs: five planes of M values each, contiguous, in the order
+ * (rho, U1, U2, U3, Theta); plane b starts at element offset b*M.
+ *
+ * Errors: every int-returning call returns NUMA_OK (0) or a negative code;
+ * numa_vol_last_error() then returns a message for the calling thread.  No
+ * call aborts the process, and invalid arguments are rejected on the host
+ * before anything is launched.
+ *
+ * Threading: a handle must not be used from two threads at once.  Distinct
+ * handles are independent.
+ */
+#ifndef NUMA_VOL_H
+#define NUMA_VOL_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define NUMA_OK 0
+#define NUMA_EINVAL (-1)        /* null pointer, N out of range, bad size or misalignment */
+#define NUMA_ENOMEM (-2)        /* device allocation failed                               */
+#define NUMA_ECUDA (-3)         /* a CUDA call or kernel launch failed                    */
+#define NUMA_EUNSUPPORTED (-4)  /* valid request this build does not implement            */
+
+#define NUMA_MAX_N 7            /* orders N = 1 .. 7 (Nq = 2 .. 8)                        */
+
+/* Physical constants: EOS reference pressure p0, gas constant R, specific heat
+ * at constant pressure cp (gamma = cp / (cp - R), Sec. 2), gravity grav. */
+typedef struct {
+    double p0, R, cp, grav;
+} numa_constants;
+
+/* Mesh size: num_elements hexahedra of order N (Nq = N + 1 points per axis). */
+typedef struct {
+    int64_t num_elements;
+    int N;
+} numa_mesh;
+
+/* Per-point geometry and reference state, FP64, M values each, in the layout
+ * above.  Host or device pointers (the library copies them).
+ *   g[3*d + a] = g_{a+1,d+1} = J * d(xi_d)/d(x_a) for reference direction d
+ *                (0 = r, 1 = s, 2 = t) and physical axis a (0 = x, 1 = y,
+ *                2 = z): the paper's geometric-factor slots 1-3 (r) and 4-6
+ *                (s), a fastest, extended by slots 7-9 for t.
+ *   Jinv       = 1 / J (the paper's slot 10).
+ *   rho_ref, rhotheta_ref = reference density and reference Theta. */
+typedef struct {
+    const double *g[9];
+    const double *Jinv;
+    const double *rho_ref;
+    const double *rhotheta_ref;
+} numa_geometry;
+
+typedef enum {
+    NUMA_FP64 = 0,   /* state, geometry and rhs in FP64                  */
+    NUMA_MIXED = 1   /* reserved for the mixed-precision form            */
+} numa_precision;
+
+typedef struct numa_vol numa_vol;
+
+/*
+ * Create a handle for one mesh on the current CUDA device.
+ *
+ * Copies the geometry and reference arrays into device memory owned by the
+ * handle (the caller's arrays may be freed afterwards).  It builds the GLL
+ * differentiation matrix for N, and it evaluates p(Theta_ref) once per point
+ * on the device, with the same function the rhs kernel uses for p(Theta).
+ * So p' is exactly zero wherever Theta == Theta_ref.  Synchronous.
+ *
+ * mesh->N in [1, NUMA_MAX_N]; mesh->num_elements >= 0; every pointer of geo
+ * non-null; c->cp > c->R > 0 and c->p0 > 0.  On success *out receives the
+ * handle (release with numa_vol_destroy).  Errors: NUMA_EINVAL,
+ * NUMA_ENOMEM, NUMA_ECUDA, NUMA_EUNSUPPORTED (prec other than NUMA_FP64).
+ */
+int numa_vol_create(const numa_mesh *mesh, const numa_geometry *geo,
+                    const numa_constants *c, numa_precision prec, numa_vol **out);
+
+/*
+ * Enqueue one evaluation of the volume term on a CUDA stream.
+ *
+ * q:   device pointer, 5 planes of M doubles (read only).
+ * rhs: device pointer, 5 planes of M doubles (overwritten; the paper's
+ *      kernel accumulates into rhsq, this call stores the volume term).
+ * Both must be 16-byte aligned and must not overlap.  stream is a
+ * cudaStream_t (NULL = the legacy default stream).  The call returns once
+ * the kernel is enqueued; rhs is complete when the stream reaches that
+ * point.  Errors: NUMA_EINVAL (null handle/pointer, misalignment,
+ * overlap), NUMA_ECUDA (launch failure).  Ne = 0 enqueues nothing.
+ */
+int numa_vol_rhs(numa_vol *h, const void *q, void *rhs, void *stream);
+
+/*
+ * Evaluate the volume term from HOST memory: copies q to the device, runs the
+ * kernel, copies rhs back and waits for completion.  Device staging buffers
+ * (2 x 5 x M doubles) are allocated on the first call and owned by the
+ * handle.  q and rhs are host pointers to 5 planes of M doubles (pinned
+ * memory gives full copy bandwidth).  Errors: NUMA_EINVAL, NUMA_ENOMEM,
+ * NUMA_ECUDA.
+ */
+int numa_vol_rhs_host(numa_vol *h, const double *q, double *rhs);
+
+/* Release a handle and its device memory.  NULL is a no-op.  Synchronises
+ * the device before freeing. */
+void numa_vol_destroy(numa_vol *h);
+
+/* Message for the last error on the calling thread ("" if none).  The
+ * pointer stays valid until the thread's next numa_vol call. */
+const char *numa_vol_last_error(void);
+
+/*
+ * Host-only: write the (N+1) x (N+1) GLL differentiation matrix the kernels
+ * apply, row-major, D[i*(N+1) + n] = l_n'(xi_i) (the paper's D(i,n)), into
+ * D_out.  Needs no GPU.  Errors: NUMA_EINVAL.
+ */
+int numa_vol_diff_matrix(int N, double *D_out);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* NUMA_VOL_H */

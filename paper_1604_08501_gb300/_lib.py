@@ -1,0 +1,75 @@
+"""ctypes declarations of the C ABI in ``include/numa_vol.h``.
+
+The library is the in-tree ``libnumavol.so`` built by ``build.py``.  There is
+no fallback: if the library is missing or does not load, every entry point
+raises."""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+from .build import LIB
+
+NUMA_OK, NUMA_EINVAL, NUMA_ENOMEM, NUMA_ECUDA, NUMA_EUNSUPPORTED = 0, -1, -2, -3, -4
+NUMA_MAX_N = 7
+NUMA_FP64, NUMA_MIXED = 0, 1
+
+_ERRNAMES = {NUMA_EINVAL: "NUMA_EINVAL", NUMA_ENOMEM: "NUMA_ENOMEM",
+             NUMA_ECUDA: "NUMA_ECUDA", NUMA_EUNSUPPORTED: "NUMA_EUNSUPPORTED"}
+
+_DP = C.POINTER(C.c_double)
+
+
+class numa_constants(C.Structure):
+    _fields_ = [("p0", C.c_double), ("R", C.c_double), ("cp", C.c_double), ("grav", C.c_double)]
+
+
+class numa_mesh(C.Structure):
+    _fields_ = [("num_elements", C.c_int64), ("N", C.c_int)]
+
+
+class numa_geometry(C.Structure):
+    _fields_ = [("g", C.c_void_p * 9), ("Jinv", C.c_void_p), ("rho_ref", C.c_void_p),
+                ("rhotheta_ref", C.c_void_p)]
+
+
+class NumaError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{_ERRNAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+_lib = None
+
+
+def load() -> C.CDLL:
+    """Load ``libnumavol.so``; raise if it has not been built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB):
+        raise RuntimeError(
+            f"{LIB} is not built: call __graft_entry__.build() (or "
+            "paper_1604_08501_gb300.build.build()) first; there is no CPU fallback")
+    lib = C.CDLL(LIB)
+    lib.numa_vol_create.argtypes = [C.POINTER(numa_mesh), C.POINTER(numa_geometry),
+                                    C.POINTER(numa_constants), C.c_int, C.POINTER(C.c_void_p)]
+    lib.numa_vol_create.restype = C.c_int
+    lib.numa_vol_rhs.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
+    lib.numa_vol_rhs.restype = C.c_int
+    lib.numa_vol_rhs_host.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p]
+    lib.numa_vol_rhs_host.restype = C.c_int
+    lib.numa_vol_destroy.argtypes = [C.c_void_p]
+    lib.numa_vol_destroy.restype = None
+    lib.numa_vol_last_error.argtypes = []
+    lib.numa_vol_last_error.restype = C.c_char_p
+    lib.numa_vol_diff_matrix.argtypes = [C.c_int, _DP]
+    lib.numa_vol_diff_matrix.restype = C.c_int
+    _lib = lib
+    return lib
+
+
+def check(code: int) -> None:
+    if code != NUMA_OK:
+        msg = load().numa_vol_last_error().decode(errors="replace")
+        raise NumaError(code, msg)

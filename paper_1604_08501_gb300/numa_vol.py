@@ -1,0 +1,154 @@
+"""Python binding of the element volume term (argument marshalling only).
+
+Every step of the computation runs in the CUDA kernels of ``libnumavol.so``.
+This module passes pointers, sizes and a stream through the C ABI of
+``include/numa_vol.h``.  PyTorch provides device memory and streams.
+
+    vt = VolumeTerm.from_problem(prob)     # numa_vol_create
+    rhs = vt.rhs(q)                        # numa_vol_rhs on the current stream
+    rhs_host = vt.rhs_host(q_host)         # numa_vol_rhs_host (copies included)
+    vt.close()                             # numa_vol_destroy
+"""
+from __future__ import annotations
+
+import ctypes as C
+
+import numpy as np
+
+from . import _lib
+from ._lib import NUMA_FP64, NUMA_MIXED, NumaError, check
+
+NFIELDS = 5
+
+
+def _host_or_device_ptr(a, M: int, keep: list) -> int:
+    """Pointer to M contiguous doubles from a numpy array or torch tensor."""
+    try:
+        import torch
+        if isinstance(a, torch.Tensor):
+            if a.dtype != torch.float64:
+                raise TypeError("geometry tensors must be float64")
+            a = a.contiguous()
+            if a.numel() != M:
+                raise ValueError(f"geometry array has {a.numel()} entries, expected {M}")
+            keep.append(a)
+            return a.data_ptr()
+    except ImportError:  # pragma: no cover
+        pass
+    arr = np.ascontiguousarray(a, dtype=np.float64)
+    if arr.size != M:
+        raise ValueError(f"geometry array has {arr.size} entries, expected {M}")
+    keep.append(arr)
+    return arr.ctypes.data
+
+
+def diff_matrix(N: int) -> np.ndarray:
+    """The GLL differentiation matrix the kernels apply (numa_vol_diff_matrix)."""
+    D = np.zeros((N + 1, N + 1))
+    check(_lib.load().numa_vol_diff_matrix(int(N), D.ctypes.data_as(C.POINTER(C.c_double))))
+    return D
+
+
+class VolumeTerm:
+    """One mesh on the current CUDA device (numa_vol_create ... numa_vol_destroy)."""
+
+    def __init__(self, N: int, num_elements: int, g, Jinv, rho_ref, rhotheta_ref,
+                 p0: float, R: float, cp: float, grav: float, precision: str = "fp64"):
+        lib = _lib.load()
+        self.N = int(N)
+        self.Ne = int(num_elements)
+        self.Nq = self.N + 1
+        self.M = self.Ne * self.Nq ** 3
+        self.precision = precision
+        keep: list = []
+        geo = _lib.numa_geometry()
+        g = list(g)
+        if len(g) != 9:
+            raise ValueError("g must hold 9 metric arrays")
+        for s in range(9):
+            geo.g[s] = _host_or_device_ptr(g[s], self.M, keep)
+        geo.Jinv = _host_or_device_ptr(Jinv, self.M, keep)
+        geo.rho_ref = _host_or_device_ptr(rho_ref, self.M, keep)
+        geo.rhotheta_ref = _host_or_device_ptr(rhotheta_ref, self.M, keep)
+        mesh = _lib.numa_mesh(self.Ne, self.N)
+        consts = _lib.numa_constants(float(p0), float(R), float(cp), float(grav))
+        prec = {"fp64": NUMA_FP64, "mixed": NUMA_MIXED}[precision]
+        h = C.c_void_p()
+        check(lib.numa_vol_create(C.byref(mesh), C.byref(geo), C.byref(consts), prec, C.byref(h)))
+        self._h = h
+
+    @classmethod
+    def from_problem(cls, prob: dict, precision: str = "fp64") -> "VolumeTerm":
+        return cls(prob["N"], prob["Ne"], prob["g"], prob["Jinv"], prob["rho_ref"],
+                   prob["rhotheta_ref"], prob["p0"], prob["R"], prob["cp"], prob["grav"],
+                   precision=precision)
+
+    @property
+    def handle(self) -> int:
+        if self._h is None or not self._h.value:
+            raise RuntimeError("VolumeTerm is closed")
+        return self._h.value
+
+    def rhs(self, q, out=None, stream=None):
+        """Enqueue rhs = volume term of q on ``stream`` (default: torch's current
+        stream).  q and out are (5, M) float64 CUDA tensors."""
+        import torch
+        if not (isinstance(q, torch.Tensor) and q.is_cuda and q.dtype == torch.float64):
+            raise TypeError("q must be a float64 CUDA tensor")
+        if q.numel() != NFIELDS * self.M or not q.is_contiguous():
+            raise ValueError(f"q must be contiguous with {NFIELDS} x {self.M} entries")
+        if out is None:
+            out = torch.empty((NFIELDS, self.M), dtype=torch.float64, device=q.device)
+        elif not (out.is_cuda and out.dtype == torch.float64 and out.is_contiguous()
+                  and out.numel() == NFIELDS * self.M):
+            raise ValueError("out must be a contiguous float64 CUDA tensor like q")
+        if stream is None:
+            stream = torch.cuda.current_stream(q.device)
+        s = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+        check(_lib.load().numa_vol_rhs(self.handle, C.c_void_p(q.data_ptr()),
+                                       C.c_void_p(out.data_ptr()), C.c_void_p(s)))
+        return out
+
+    def rhs_host(self, q, out=None):
+        """Volume term of a host state through numa_vol_rhs_host (host-to-device
+        copy, kernel, device-to-host copy; synchronous).  Accepts numpy arrays or
+        CPU torch tensors (pinned memory copies fastest) and returns ``out``."""
+        import torch
+        if isinstance(q, torch.Tensor):
+            if q.is_cuda or q.dtype != torch.float64 or not q.is_contiguous():
+                raise TypeError("q must be a contiguous float64 CPU tensor")
+            qp = q.data_ptr()
+            if out is None:
+                out = torch.empty((NFIELDS, self.M), dtype=torch.float64,
+                                  pin_memory=q.is_pinned())
+            op = out.data_ptr()
+        else:
+            q = np.ascontiguousarray(q, dtype=np.float64)
+            qp = q.ctypes.data
+            if out is None:
+                out = np.empty((NFIELDS, self.M))
+            op = out.ctypes.data if isinstance(out, np.ndarray) else out.data_ptr()
+        if int(np.prod(q.shape)) != NFIELDS * self.M:
+            raise ValueError(f"q must have {NFIELDS} x {self.M} entries")
+        check(_lib.load().numa_vol_rhs_host(self.handle, C.c_void_p(qp), C.c_void_p(op)))
+        return out
+
+    def close(self) -> None:
+        if getattr(self, "_h", None) is not None and self._h.value:
+            _lib.load().numa_vol_destroy(self._h)
+        self._h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+__all__ = ["VolumeTerm", "diff_matrix", "NumaError"]

@@ -248,11 +248,13 @@ class Workload:
         return d
 
 
-def make_workload(N: int, n: int, seed: int, L: float = 10_000.0, warp: float = 0.05,
+def make_workload(N: int, n, seed: int, L: float = 10_000.0, warp: float = 0.05,
                   consts: Constants = DRY_AIR, T: float = 300.0, eps: float = 1e-3,
                   vmax: float = 10.0, name: str = "") -> Workload:
-    """Warped n x n x n box of order N with the seeded perturbed hydrostatic state."""
-    mesh = warped_box(N, (n, n, n), L=L, warp=warp)
+    """Warped box of order N with the seeded perturbed hydrostatic state.
+    ``n`` is the number of elements per axis, or a tuple (nx, ny, nz)."""
+    shape = (n, n, n) if np.isscalar(n) else tuple(int(v) for v in n)
+    mesh = warped_box(N, shape, L=L, warp=warp)
     rho_ref, rt_ref = hydrostatic_reference(mesh.x[2], consts, T)
     q = perturbed_state(mesh, rho_ref, rt_ref, seed, eps=eps, vmax=vmax)
     return Workload(mesh=mesh, consts=consts, rho_ref=rho_ref, rhotheta_ref=rt_ref,
