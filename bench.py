@@ -264,32 +264,19 @@ def run_reference(args):
 
 # ---------------------------------------------------------------- GPU
 
-def run_gpu(args):
+def time_variant(vt, q, q_host, dev, K, W, rank, e2e=True):
+    """Device time of K launches (CUDA events on the launching stream, per
+    launch and over the region), clocks sampled meanwhile, then the same K
+    steps end to end through the host-buffer call."""
     import torch
-    rank, local, world = dist_setup("nccl")
-    torch.cuda.set_device(local)
-    dev = torch.device("cuda", local)
-    from paper_1604_08501_gb300 import build as lib_build
-    if rank == 0 or world == 1:
-        lib_build.build()
-    barrier(dev)
-    from paper_1604_08501_gb300.numa_vol import VolumeTerm
-
-    w, name = workload_full(args.n)
-    vt = VolumeTerm.from_problem(w.problem())
-    q_host = torch.from_numpy(w.q).pin_memory()
-    q = q_host.to(dev)
     out = torch.empty_like(q)
     stream = torch.cuda.current_stream(dev)
-
-    for _ in range(args.warmup):
+    for _ in range(W):
         vt.rhs(q, out, stream)
     torch.cuda.synchronize(dev)
-
-    sampler = ClockSampler(gpu_id_for(local)) if rank == 0 else None
+    sampler = ClockSampler(gpu_id_for(dev.index)) if rank == 0 else None
     if sampler:
         sampler.start()
-    K = args.steps
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
           for _ in range(K)]
     t_start, t_end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -304,16 +291,11 @@ def run_gpu(args):
     torch.cuda.synchronize(dev)
     barrier(dev)
     clocks = sampler.stop() if sampler else None
-    region_ms = t_start.elapsed_time(t_end)
-    kernel_ms = float(np.mean([a.elapsed_time(b) for a, b in ev]))
-    value, tmax = aggregate(K * w.M, region_ms * 1e-3, dev)
-    ms_per_step = tmax * 1e3 / K
-
-    # End to end through the public host-buffer call: H2D of q from pinned
-    # memory, the kernel, D2H of rhs, every step.
-    step_bytes = 5 * w.M * 8
-    e2e_value = None
-    if not args.no_e2e:
+    res = {"region_ms": t_start.elapsed_time(t_end),
+           "kernel_ms": float(np.mean([a.elapsed_time(b) for a, b in ev])),
+           "clocks": clocks, "e2e_s": None}
+    if e2e:
+        # H2D of q from pinned memory, the kernel, D2H of rhs, every step.
         out_host = torch.empty_like(q_host).pin_memory()
         for _ in range(3):
             vt.rhs_host(q_host, out_host)
@@ -322,39 +304,89 @@ def run_gpu(args):
         t0 = time.perf_counter()
         for _ in range(K):
             vt.rhs_host(q_host, out_host)
-        e2e_s = time.perf_counter() - t0
+        res["e2e_s"] = time.perf_counter() - t0
         barrier(dev)
-        e2e_value, _ = aggregate(K * w.M, e2e_s, dev)
+    return res
+
+
+def roofline_entries(kname, kernel_ms, w):
+    peak, peak_src = measured_peaks()
+    hbm_gbs = BYTES_PER_NODE_FP64 * w.M / (kernel_ms * 1e-3) / 1e9
+    fp64_tfs = flops_per_node_fp64(w.N + 1) * w.M / (kernel_ms * 1e-3) / 1e12
+    hbm = {"bound": "hbm", "achieved": hbm_gbs, "peak": peak, "unit": "GB/s",
+           "frac": hbm_gbs / peak, "traffic": load_traffic(kname), "kernel": kname,
+           "bytes_per_point": BYTES_PER_NODE_FP64, "peak_source": peak_src,
+           "kernel_ms": kernel_ms}
+    # FP64-equivalent flop rate against the FP64 pipe of one GB300 (152 SMs x
+    # 2 DFMA/clk x 2 flop x 2.07 GHz = 1.26 TFLOP/s nominal).  It binds the
+    # native kernel; the double-float kernel runs on the FP32 pipes.
+    alu = {"bound": "alu", "achieved": fp64_tfs, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+           "frac": fp64_tfs / FP64_PEAK_TFLOPS, "traffic": load_traffic(kname), "kernel": kname,
+           "flops_per_point": flops_per_node_fp64(w.N + 1),
+           "peak_source": "FP64 pipe of one GB300, nominal 1.25 TFLOP/s "
+                          "(microbenchmark: 1.056 TFLOP/s)",
+           "kernel_ms": kernel_ms}
+    return (alu, hbm) if kname.startswith("vol_rhs_fp64") else (hbm, alu)
+
+
+def run_gpu(args):
+    import torch
+    rank, local, world = dist_setup("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    from paper_1604_08501_gb300 import build as lib_build
+    if rank == 0 or world == 1:
+        lib_build.build()
+    barrier(dev)
+    from paper_1604_08501_gb300.numa_vol import VolumeTerm
+
+    w, name = workload_full(args.n)
+    q_host = torch.from_numpy(w.q).pin_memory()
+    q = q_host.to(dev)
+    K, W = args.steps, args.warmup
+    step_bytes = 5 * w.M * 8
+
+    results = {}
+    for prec in args.precisions:
+        vt = VolumeTerm.from_problem(w.problem(), precision=prec)
+        r = time_variant(vt, q, q_host, dev, K, W, rank, e2e=not args.no_e2e)
+        r["kernel"] = vt.kernel_name
+        vt.close()
+        value, tmax = aggregate(K * w.M, r["region_ms"] * 1e-3, dev)
+        r["value"], r["ms_per_step"] = value / 1e9, tmax * 1e3 / K
+        if r["e2e_s"] is not None:
+            e2e_value, _ = aggregate(K * w.M, r["e2e_s"], dev)
+            r["e2e"] = {"value": e2e_value / 1e9, "unit": UNIT,
+                        "h2d_bytes_per_step": step_bytes, "d2h_bytes_per_step": step_bytes}
+        else:
+            r["e2e"] = None
+        results[prec] = r
 
     if rank == 0:
-        peak, peak_src = measured_peaks()
-        kname = "vol_rhs_fp64_kernel<8>"
-        hbm_gbs = BYTES_PER_NODE_FP64 * w.M / (kernel_ms * 1e-3) / 1e9
-        fp64_tfs = flops_per_node_fp64(w.N + 1) * w.M / (kernel_ms * 1e-3) / 1e12
-        traffic = load_traffic(kname)
-        hbm = {"bound": "hbm", "achieved": hbm_gbs, "peak": peak, "unit": "GB/s",
-               "frac": hbm_gbs / peak, "traffic": traffic, "kernel": kname,
-               "bytes_per_point": BYTES_PER_NODE_FP64, "peak_source": peak_src,
-               "kernel_ms": kernel_ms}
-        alu = {"bound": "alu", "achieved": fp64_tfs, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-               "frac": fp64_tfs / FP64_PEAK_TFLOPS, "traffic": traffic, "kernel": kname,
-               "flops_per_point": flops_per_node_fp64(w.N + 1),
-               "peak_source": "FP64 CUDA-core peak of one GB300 (1.25 TFLOP/s)",
-               "kernel_ms": kernel_ms}
-        roof, other = (hbm, alu) if hbm["frac"] >= alu["frac"] else (alu, hbm)
-        line = {"metric": METRIC, "value": value / 1e9, "unit": UNIT, "n_gpus": world,
-                "steps": K, "warmup": args.warmup, "ms_per_step": ms_per_step,
+        head_prec = args.precisions[0]
+        head = results[head_prec]
+        roof, other = roofline_entries(head["kernel"], head["kernel_ms"], w)
+        dtypes = {"fp64": "f64", "df64": "df64 (FP32 hi+lo pairs, 48-bit)"}
+        line = {"metric": METRIC, "value": head["value"], "unit": UNIT, "n_gpus": world,
+                "steps": K, "warmup": W, "ms_per_step": head["ms_per_step"],
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-                "dtype": "f64", "data": "synthetic", "config": workload_config(w, name),
-                "roofline": roof, "roofline_other": other,
-                "e2e": None if e2e_value is None else
-                       {"value": e2e_value / 1e9, "unit": UNIT, "h2d_bytes_per_step": step_bytes,
-                        "d2h_bytes_per_step": step_bytes},
-                "gpu_launches": K, "clocks": clocks}
+                "dtype": dtypes.get(head_prec, head_prec), "data": "synthetic",
+                "config": workload_config(w, name), "roofline": roof, "roofline_other": other,
+                "e2e": head["e2e"], "gpu_launches": K, "clocks": head["clocks"],
+                "precision": head_prec}
+        variants = {}
+        for prec in args.precisions[1:]:
+            r = results[prec]
+            vr, vo = roofline_entries(r["kernel"], r["kernel_ms"], w)
+            variants[prec] = {"value": r["value"], "unit": UNIT, "ms_per_step": r["ms_per_step"],
+                              "dtype": dtypes.get(prec, prec), "roofline": vr,
+                              "roofline_other": vo, "e2e": r["e2e"], "gpu_launches": K,
+                              "clocks": r["clocks"]}
+        if variants:
+            line["variants"] = variants
         if world == 1 and not args.no_cpu_baseline and args.n == 32:
             line["cpu_baseline"] = cpu_baseline(w)
         print(json.dumps(line))
-    vt.close()
     return 0
 
 
@@ -370,9 +402,12 @@ def main(argv=None):
                     help="skip the host-buffer end-to-end leg (for profiling runs)")
     ap.add_argument("--n", type=int, default=32,
                     help="elements per axis; 32 is the timed workload, smaller is for ncu")
+    ap.add_argument("--precision", default="fp64,df64",
+                    help="comma-separated precision modes; the first is the headline value")
     args = ap.parse_args(argv)
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
+    args.precisions = [p for p in args.precision.split(",") if p]
     if args.impl == "reference":
         return run_reference(args)
     return run_gpu(args)

@@ -84,8 +84,10 @@ typedef struct {
 } numa_geometry;
 
 typedef enum {
-    NUMA_FP64 = 0,   /* state, geometry and rhs in FP64                  */
-    NUMA_MIXED = 1   /* reserved for the mixed-precision form            */
+    NUMA_FP64 = 0,   /* FP64 state and rhs, every operation on the FP64 pipe           */
+    NUMA_MIXED = 1,  /* reserved for the mixed-precision form                           */
+    NUMA_DF64 = 2    /* FP64 state and rhs, double-float arithmetic (hi + lo FP32 pairs,
+                        about 48 significant bits) on the FP32 pipes; N = 7 only      */
 } numa_precision;
 
 typedef struct numa_vol numa_vol;
@@ -95,14 +97,28 @@ typedef struct numa_vol numa_vol;
  *
  * Copies the geometry and reference arrays into device memory owned by the
  * handle (the caller's arrays may be freed afterwards).  It builds the GLL
- * differentiation matrix for N, and it evaluates p(Theta_ref) once per point
- * on the device, with the same function the rhs kernel uses for p(Theta).
- * So p' is exactly zero wherever Theta == Theta_ref.  Synchronous.
+ * differentiation matrix for N and evaluates, once per point on the device,
+ * 1/Theta_ref and p(Theta_ref)/Theta_ref.  p' is exactly zero wherever
+ * Theta == Theta_ref.  Synchronous.
  *
  * mesh->N in [1, NUMA_MAX_N]; mesh->num_elements >= 0; every pointer of geo
  * non-null; c->cp > c->R > 0 and c->p0 > 0.  On success *out receives the
  * handle (release with numa_vol_destroy).  Errors: NUMA_EINVAL,
- * NUMA_ENOMEM, NUMA_ECUDA, NUMA_EUNSUPPORTED (prec other than NUMA_FP64).
+ * NUMA_ENOMEM, NUMA_ECUDA, NUMA_EUNSUPPORTED (NUMA_MIXED; NUMA_DF64 with N != 7).
+ *
+ * NUMA_FP64 and NUMA_DF64 compute the same operation.  Both evaluate
+ * p(Theta) - p(Theta_ref) as p_ref ((1 + x)^gamma - 1) by its binomial series
+ * in x = (Theta - Theta_ref)/Theta_ref where |x| <= 1/64, and by pow
+ * elsewhere.  The error of NUMA_FP64 against an exact evaluation is a few
+ * units of 2^-53 times the condition number of the D sweeps (the ratio of
+ * sum |Jinv D F| to |rhs|).  The factor for NUMA_DF64 is about 2^-48, so
+ * NUMA_DF64 suits states with well-conditioned sweeps, such as the benchmark's
+ * per-point random velocities.  Smooth fields with a large mean (a uniform wind)
+ * need NUMA_FP64.  NUMA_DF64 falls back to native FP64: for the whole handle
+ * when a geometry array (after values below 2^-50 of the array's largest
+ * magnitude are set to zero) holds a magnitude outside [2^-40, 2^41); and for
+ * one element when its state holds such a value or its double-float result
+ * overflows.  N != 7 with NUMA_DF64 gives NUMA_EUNSUPPORTED.
  */
 int numa_vol_create(const numa_mesh *mesh, const numa_geometry *geo,
                     const numa_constants *c, numa_precision prec, numa_vol **out);
@@ -134,6 +150,11 @@ int numa_vol_rhs_host(numa_vol *h, const double *q, double *rhs);
 /* Release a handle and its device memory.  NULL is a no-op.  Synchronises
  * the device before freeing. */
 void numa_vol_destroy(numa_vol *h);
+
+/* Name of the kernel numa_vol_rhs launches for this handle:
+ * "vol_rhs_fp64_kernel<Nq>" (NUMA_FP64, or NUMA_DF64 after a geometry
+ * fallback) or "vol_rhs_df64_kernel".  Static string; "" for a NULL handle. */
+const char *numa_vol_kernel_name(const numa_vol *h);
 
 /* Message for the last error on the calling thread ("" if none).  The
  * pointer stays valid until the thread's next numa_vol call. */

@@ -18,6 +18,8 @@ pressure(Theta, c)      p0 (R Theta / p0)^gamma, gamma = cp / (cp - R).
 vol_rhs_o1(prob, q)     brute force, one pass per reference direction.
 vol_rhs_o2(prob, q)     fluxes once per node, then the D contractions.
 vol_rhs_points(prob, q, ids)  Eq. (2) at selected nodes only.
+vol_rhs_abs(prob, q)    running error bound |Jinv| sum |D| |F| per point.
+condition_numbers(prob, q)  per field max(bound) / max|rhs|.
 
 ``prob`` is a dict with keys N, Ne, g (9 x M), Jinv, rho_ref, rhotheta_ref
 (each M = Ne*(N+1)^3 doubles, [e][k][j][i] order) and constants p0, R, cp,
@@ -63,6 +65,7 @@ def _configure(lib):
     lib.oracle_vol_rhs_o2.argtypes = [C.POINTER(_Problem), _DP, _DP, C.c_int]
     lib.oracle_vol_rhs_points.argtypes = [C.POINTER(_Problem), _DP, C.c_int64,
                                           C.POINTER(C.c_int64), _DP]
+    lib.oracle_vol_rhs_abs.argtypes = [C.POINTER(_Problem), _DP, _DP]
     lib.oracle_max_threads.restype = C.c_int
     return lib
 
@@ -168,6 +171,23 @@ def vol_rhs_o2(prob: dict, q, nthreads: int = 0) -> np.ndarray:
     return out
 
 
+def vol_rhs_abs(prob: dict, q) -> np.ndarray:
+    """Running error bound: |Jinv| sum_d sum_n |D| |F| (+ |gravity term|) per point."""
+    b = _Bound(prob)
+    q = b.state(q)
+    out = np.empty((5, b.M))
+    if _load().oracle_vol_rhs_abs(C.byref(b.s), _ptr(q), _ptr(out)) != 0:
+        raise RuntimeError("oracle error bound rejected its arguments")
+    return out
+
+
+def condition_numbers(prob: dict, q, rhs=None) -> np.ndarray:
+    """Per field: max of the running error bound over max |rhs|."""
+    ab = vol_rhs_abs(prob, q)
+    rhs = vol_rhs_o2(prob, q) if rhs is None else np.asarray(rhs).reshape(5, -1)
+    return np.array([ab[f].max() / max(np.abs(rhs[f]).max(), 1e-300) for f in range(5)])
+
+
 def vol_rhs_points(prob: dict, q, node_ids) -> np.ndarray:
     b = _Bound(prob)
     q = b.state(q)
@@ -181,4 +201,4 @@ def vol_rhs_points(prob: dict, q, node_ids) -> np.ndarray:
 
 
 __all__ = ["gll_nodes", "diff_matrix", "pressure", "vol_rhs_o1", "vol_rhs_o2",
-           "vol_rhs_points", "max_threads", "build_oracle"]
+           "vol_rhs_points", "vol_rhs_abs", "condition_numbers", "max_threads", "build_oracle"]

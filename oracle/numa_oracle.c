@@ -328,6 +328,49 @@ int oracle_vol_rhs_points(const oracle_problem *P, const double *q, int64_t npts
     return 0;
 }
 
+/* ------------------------------------------------------------------------- */
+/* Running error bound of Eq. (2): the same sums with every term replaced by  */
+/* its magnitude, |Jinv| * sum_d sum_n |D| |F_d[b]| (plus |(rho - rho_ref)    */
+/* grav| on U3).  The ratio of its maximum to the maximum |rhs_b| is the       */
+/* condition number of field b; rounding errors of any evaluation of Eq. (2)   */
+/* scale with it.                                                              */
+/* ------------------------------------------------------------------------- */
+
+int oracle_vol_rhs_abs(const oracle_problem *P, const double *q, double *out)
+{
+    if (check_problem(P) || !q || !out) return -1;
+    const int Nq = P->N + 1;
+    const int64_t n3 = (int64_t)Nq * Nq * Nq;
+    const int64_t M = P->Ne * n3;
+#ifdef _OPENMP
+#pragma omp parallel for schedule(static)
+#endif
+    for (int64_t node = 0; node < M; ++node) {
+        int64_t e = node / n3, l = node % n3;
+        int i = (int)(l % Nq), j = (int)((l / Nq) % Nq), k = (int)(l / (Nq * Nq));
+        double s[ORACLE_NFIELDS] = {0, 0, 0, 0, 0};
+        for (int d = 0; d < 3; ++d) {
+            int iota = d == 0 ? i : (d == 1 ? j : k);
+            for (int n = 0; n < Nq; ++n) {
+                int64_t m;
+                if (d == 0) m = ((e * Nq + k) * Nq + j) * Nq + n;
+                else if (d == 1) m = ((e * Nq + k) * Nq + n) * Nq + i;
+                else m = ((e * Nq + n) * Nq + j) * Nq + i;
+                double F[ORACLE_NFIELDS];
+                node_flux(P, q, M, m, d, F);
+                for (int b = 0; b < ORACLE_NFIELDS; ++b)
+                    s[b] += fabs(P->D[iota * Nq + n]) * fabs(F[b]);
+            }
+        }
+        for (int b = 0; b < ORACLE_NFIELDS; ++b) {
+            double v = fabs(P->Jinv[node]) * s[b];
+            if (b == 3) v = v + fabs((q[0 * M + node] - P->rho_ref[node]) * P->grav);
+            out[b * M + node] = v;
+        }
+    }
+    return 0;
+}
+
 /* Number of threads O2 will use for nthreads <= 0 (1 without OpenMP). */
 int oracle_max_threads(void)
 {

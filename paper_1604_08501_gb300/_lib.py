@@ -12,7 +12,7 @@ from .build import LIB
 
 NUMA_OK, NUMA_EINVAL, NUMA_ENOMEM, NUMA_ECUDA, NUMA_EUNSUPPORTED = 0, -1, -2, -3, -4
 NUMA_MAX_N = 7
-NUMA_FP64, NUMA_MIXED = 0, 1
+NUMA_FP64, NUMA_MIXED, NUMA_DF64 = 0, 1, 2
 
 _ERRNAMES = {NUMA_EINVAL: "NUMA_EINVAL", NUMA_ENOMEM: "NUMA_ENOMEM",
              NUMA_ECUDA: "NUMA_ECUDA", NUMA_EUNSUPPORTED: "NUMA_EUNSUPPORTED"}
@@ -63,6 +63,8 @@ def load() -> C.CDLL:
     lib.numa_vol_destroy.restype = None
     lib.numa_vol_last_error.argtypes = []
     lib.numa_vol_last_error.restype = C.c_char_p
+    lib.numa_vol_kernel_name.argtypes = [C.c_void_p]
+    lib.numa_vol_kernel_name.restype = C.c_char_p
     lib.numa_vol_diff_matrix.argtypes = [C.c_int, _DP]
     lib.numa_vol_diff_matrix.restype = C.c_int
     _lib = lib

@@ -13,25 +13,83 @@ constexpr int kFields = 5;
 // Device-side geometry of one handle. Every per-point array has M entries,
 // padded so that each starts on a 256-byte boundary.
 struct DeviceGeometry {
-    const double *g[9];     // metric terms g[3*d + a]
-    const double *Jinv;     // 1 / J
-    const double *rho_ref;  // reference density
-    const double *p_ref;    // p(Theta_ref), evaluated once at create time
-    const double *D;        // (N+1)^2, row-major D[i*Nq + n]
+    const double *g[9];      // metric terms g[3*d + a]
+    const double *Jinv;      // 1 / J
+    const double *rho_ref;   // reference density
+    const double *theta_ref; // reference Theta
+    const double *w;         // 1 / Theta_ref
+    const double *A;         // p(Theta_ref) / Theta_ref
+    const double *D;         // (N+1)^2, row-major D[i*Nq + n]
 };
 
 struct EosConstants {
     double p0, R, gamma, grav;
 };
 
+// Parameters of the native kernel: EOS constants, c[k] = binom(gamma, k+1)
+// (k = 0..8, the coefficients of the p' series), and the even-odd pieces of D
+// for r, m < Nq/2: De = (D[r][m] + D[r][N-m])/2, Do = (D[r][m] - D[r][N-m])/2,
+// Dc[r] = D[r][c] and Dcr[m] = D[c][m] (centre column and row, odd Nq).
+// Uniform across threads, so the kernel reads them as constant-bank operands.
+struct NativeParams {
+    EosConstants eos;
+    double c[9];
+    double De[16], Do[16], Dc[4], Dcr[4];
+};
+
+// Per-point arrays of the double-float path (N = 7): float2 (h, l) pairs, and
+// the reference state in FP64, so that rho - rho_ref and Theta - Theta_ref are
+// exact FP64 differences before they are split.
+struct DfGeometry {
+    const float2 *g[9];      // metric terms
+    const float2 *Jinv;      // 1 / J
+    const double *rho_ref;   // reference density
+    const double *theta_ref; // reference Theta
+    const float2 *w;         // 1 / Theta_ref
+    const float2 *A;         // p(Theta_ref) / Theta_ref
+};
+
+// Kernel parameters of the double-float path.
+struct DfParams;  // defined below
+
 // Launchers (vol_fp64.cu). They return a cudaError_t from the launch.
-cudaError_t launch_pref_fp64(const double *rhotheta_ref, double *p_ref, int64_t M,
-                             EosConstants c, cudaStream_t s);
-cudaError_t launch_vol_rhs_fp64(int N, int64_t Ne, const DeviceGeometry &geo, EosConstants c,
+// reference_eos: w = 1/Theta_ref, A = p(Theta_ref)/Theta_ref per point.
+cudaError_t launch_reference_eos(const double *theta_ref, double *w, double *A, int64_t M,
+                                 EosConstants c, cudaStream_t s);
+cudaError_t launch_vol_rhs_fp64(int N, int64_t Ne, const DeviceGeometry &geo,
+                                const NativeParams &P, const double *q, double *rhs,
+                                cudaStream_t s);
+
+// Launchers of the double-float path (vol_df64.cu).  abs_max: max |src| into
+// *amax_bits (the bit pattern of a nonnegative double).  to_df: split src
+// into (h, l) pairs, flushing |x| < thresh to zero and flagging values left
+// outside the fast-path range in *bad.
+cudaError_t launch_abs_max(const double *src, int64_t M, unsigned long long *amax_bits,
+                           cudaStream_t s);
+cudaError_t launch_to_df(const double *src, float2 *dst, int64_t M, double thresh, int *bad,
+                         cudaStream_t s);
+cudaError_t launch_vol_rhs_df64(int64_t Ne, const DfGeometry &geo, const DfParams &P,
                                 const double *q, double *rhs, cudaStream_t s);
 
 // GLL points and differentiation matrix on the host (gll.cpp).
 int gll_diff_matrix(int N, double *D);
+
+// Double-float value: the unevaluated sum h + l of two floats.
+struct df {
+    float h, l;
+};
+
+struct DfParams {
+    df De[4][4];       // (D[i][m] + D[i][7-m]) / 2, i, m < 4
+    df Do[4][4];       // (D[i][m] - D[i][7-m]) / 2
+    df c1, c2, c3;     // binom(gamma, k), k = 1..3
+    float ct[6];       // binom(gamma, k), k = 4..9
+    df grav_df;        // gravity
+    double grav, p0, R, gamma;
+    double D[64];      // D for the native fallback
+};
+
+enum class Kernel { Native, DoubleFloat };
 
 }  // namespace numa
 
@@ -45,7 +103,11 @@ struct numa_vol {
     numa::EosConstants eos{};
     void *d_block = nullptr;        // one allocation: geometry, reference state, D
     size_t block_bytes = 0;
-    numa::DeviceGeometry geo{};
+    numa::Kernel kernel = numa::Kernel::Native;
+    numa::DeviceGeometry geo{};     // native path
+    numa::DfGeometry dgeo{};        // double-float path
+    numa::DfParams dparams{};
+    numa::NativeParams nparams{};
     double *d_stage = nullptr;      // host entry point: q and rhs staging, 2 * 5 * M
     cudaStream_t host_stream = nullptr;
 };

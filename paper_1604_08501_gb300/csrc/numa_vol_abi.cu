@@ -1,0 +1,374 @@
+// C ABI of the element volume term: argument checks, device memory of a
+// handle, and dispatch to the kernels.  See include/numa_vol.h.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <new>
+#include <string>
+
+#include "numa_internal.h"
+#include "numa_vol.h"
+
+namespace {
+
+thread_local std::string g_last_error;
+
+int fail(int code, const std::string &msg) {
+    g_last_error = msg;
+    return code;
+}
+
+int fail_cuda(cudaError_t e, const char *where) {
+    int code = (e == cudaErrorMemoryAllocation) ? NUMA_ENOMEM : NUMA_ECUDA;
+    return fail(code, std::string(where) + ": " + cudaGetErrorName(e) + " (" +
+                          cudaGetErrorString(e) + ")");
+}
+
+// Per-point arrays start on 256-byte boundaries inside the handle's block.
+int64_t padded(int64_t M) { return (M + 31) / 32 * 32; }
+
+bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
+bool overlap(const void *a, const void *b, size_t bytes) {
+    auto x = reinterpret_cast<uintptr_t>(a), y = reinterpret_cast<uintptr_t>(b);
+    return x < y + bytes && y < x + bytes;
+}
+
+// Device (or managed) memory the current device can address directly.
+bool is_device_pointer(const void *p) {
+    cudaPointerAttributes attr;
+    if (cudaPointerGetAttributes(&attr, p) != cudaSuccess) {
+        cudaGetLastError();  // clear the sticky-free error of an unknown pointer
+        return false;
+    }
+    return attr.type == cudaMemoryTypeDevice || attr.type == cudaMemoryTypeManaged;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *numa_vol_last_error(void) { return g_last_error.c_str(); }
+
+const char *numa_vol_kernel_name(const numa_vol *h) {
+    static const char *native[] = {"", "vol_rhs_fp64_kernel<2>", "vol_rhs_fp64_kernel<3>",
+                                   "vol_rhs_fp64_kernel<4>", "vol_rhs_fp64_kernel<5>",
+                                   "vol_rhs_fp64_kernel<6>", "vol_rhs_fp64_kernel<7>",
+                                   "vol_rhs_fp64_kernel<8>"};
+    if (!h) return "";
+    if (h->kernel == numa::Kernel::DoubleFloat) return "vol_rhs_df64_kernel";
+    return native[h->N];
+}
+
+int numa_vol_diff_matrix(int N, double *D_out) {
+    g_last_error.clear();
+    if (!D_out) return fail(NUMA_EINVAL, "numa_vol_diff_matrix: D_out is NULL");
+    if (N < 1 || N > NUMA_MAX_N)
+        return fail(NUMA_EINVAL, "numa_vol_diff_matrix: N must be in [1, 7]");
+    return numa::gll_diff_matrix(N, D_out);
+}
+
+}  // extern "C"
+
+namespace {
+
+// Host split of a double into a df constant (round-to-nearest pieces).
+numa::df split_host(long double x) {
+    const float h = static_cast<float>(x);
+    const float l = static_cast<float>(x - static_cast<long double>(h));
+    return numa::df{h, l};
+}
+
+// binom(gamma, k) for k = 0..9, in long double.
+void binomial_coefficients(double gamma, long double c[10]) {
+    c[0] = 1.0L;
+    for (int k = 1; k < 10; ++k) c[k] = c[k - 1] * ((long double)gamma - (k - 1)) / k;
+}
+
+void build_params(numa_vol *h, const double *D) {
+    long double c[10];
+    binomial_coefficients(h->eos.gamma, c);
+    h->nparams.eos = h->eos;
+    for (int k = 0; k < 9; ++k) h->nparams.c[k] = static_cast<double>(c[k + 1]);
+    {
+        const int Nq = h->Nq, half = Nq / 2, ctr = Nq / 2;
+        for (int r = 0; r < half; ++r) {
+            for (int m = 0; m < half; ++m) {
+                const long double a = D[r * Nq + m], b = D[r * Nq + (Nq - 1 - m)];
+                h->nparams.De[r * half + m] = static_cast<double>((a + b) / 2);
+                h->nparams.Do[r * half + m] = static_cast<double>((a - b) / 2);
+            }
+            if (Nq & 1) {
+                h->nparams.Dc[r] = D[r * Nq + ctr];
+                h->nparams.Dcr[r] = D[ctr * Nq + r];
+            }
+        }
+    }
+    if (h->N != 7) return;
+    numa::DfParams &P = h->dparams;
+    for (int i = 0; i < 4; ++i)
+        for (int m = 0; m < 4; ++m) {
+            const long double a = D[i * 8 + m], b = D[i * 8 + 7 - m];
+            P.De[i][m] = split_host((a + b) / 2);
+            P.Do[i][m] = split_host((a - b) / 2);
+        }
+    P.c1 = split_host(c[1]);
+    P.c2 = split_host(c[2]);
+    P.c3 = split_host(c[3]);
+    for (int k = 4; k < 10; ++k) P.ct[k - 4] = static_cast<float>(c[k]);
+    P.grav_df = split_host(h->eos.grav);
+    P.grav = h->eos.grav;
+    P.p0 = h->eos.p0;
+    P.R = h->eos.R;
+    P.gamma = h->eos.gamma;
+    for (int t = 0; t < 64; ++t) P.D[t] = D[t];
+}
+
+// Per-point arrays of a handle, in order: g[0..8], Jinv, rho_ref, theta_ref,
+// w = 1/theta_ref, A = p(theta_ref)/theta_ref.
+constexpr int kArrays = 14;
+
+// Stage the caller's arrays and the derived reference arrays as FP64 in
+// `dst` (kArrays slots of P doubles each).
+cudaError_t stage_fp64(numa_vol *h, const numa_geometry *geo, double *const *dst) {
+    const size_t bytes = sizeof(double) * h->M;
+    const double *src[12] = {geo->g[0], geo->g[1], geo->g[2], geo->g[3], geo->g[4], geo->g[5],
+                             geo->g[6], geo->g[7], geo->g[8], geo->Jinv, geo->rho_ref,
+                             geo->rhotheta_ref};
+    cudaError_t e = cudaSuccess;
+    for (int s = 0; s < 12 && e == cudaSuccess; ++s)
+        if (bytes) e = cudaMemcpy(dst[s], src[s], bytes, cudaMemcpyDefault);
+    if (e == cudaSuccess) e = numa::launch_reference_eos(dst[11], dst[12], dst[13], h->M, h->eos, 0);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(0);
+    return e;
+}
+
+// Native layout: kArrays FP64 arrays (each padded(M)), then D.
+cudaError_t create_native(numa_vol *h, const numa_geometry *geo, const double *D) {
+    const int64_t P = padded(h->M);
+    h->block_bytes = sizeof(double) * (kArrays * P + h->Nq * h->Nq);
+    cudaError_t e = cudaMalloc(&h->d_block, h->block_bytes);
+    if (e != cudaSuccess) {
+        h->d_block = nullptr;
+        return e;
+    }
+    double *base = static_cast<double *>(h->d_block);
+    double *slots[kArrays];
+    for (int s = 0; s < kArrays; ++s) slots[s] = base + s * P;
+    double *dD = base + kArrays * P;
+    e = stage_fp64(h, geo, slots);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(dD, D, sizeof(double) * h->Nq * h->Nq, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return e;
+    for (int s = 0; s < 9; ++s) h->geo.g[s] = slots[s];
+    h->geo.Jinv = slots[9];
+    h->geo.rho_ref = slots[10];
+    h->geo.theta_ref = slots[11];
+    h->geo.w = slots[12];
+    h->geo.A = slots[13];
+    h->geo.D = dD;
+    h->kernel = numa::Kernel::Native;
+    return cudaSuccess;
+}
+
+// Double-float layout: kArrays float2 arrays.  Sets *in_range = false (and
+// keeps nothing) if a value stays outside the fast-path range after the
+// relative flush of rounding noise.
+cudaError_t create_df(numa_vol *h, const numa_geometry *geo, bool *in_range) {
+    *in_range = true;
+    const int64_t P = padded(h->M);
+    h->block_bytes = sizeof(float2) * kArrays * P;
+    cudaError_t e = cudaMalloc(&h->d_block, h->block_bytes);
+    if (e != cudaSuccess) {
+        h->d_block = nullptr;
+        return e;
+    }
+    void *tmp = nullptr;
+    e = cudaMalloc(&tmp, sizeof(double) * kArrays * P + 256);
+    if (e != cudaSuccess) {
+        cudaFree(h->d_block);
+        h->d_block = nullptr;
+        return e;
+    }
+    double *staged[kArrays];
+    for (int s = 0; s < kArrays; ++s) staged[s] = static_cast<double *>(tmp) + s * P;
+    unsigned long long *d_amax = reinterpret_cast<unsigned long long *>(
+        static_cast<double *>(tmp) + kArrays * P);
+    int *d_bad = reinterpret_cast<int *>(d_amax + kArrays);
+    float2 *base = static_cast<float2 *>(h->d_block);
+    float2 *slots[kArrays];
+    for (int s = 0; s < kArrays; ++s) slots[s] = base + s * P;
+    e = stage_fp64(h, geo, staged);
+    if (e == cudaSuccess) e = cudaMemset(d_amax, 0, sizeof(unsigned long long) * kArrays + sizeof(int));
+    for (int s = 0; s < kArrays && e == cudaSuccess; ++s)
+        e = numa::launch_abs_max(staged[s], h->M, d_amax + s, 0);
+    unsigned long long amax[kArrays] = {};
+    if (e == cudaSuccess)
+        e = cudaMemcpy(amax, d_amax, sizeof(amax), cudaMemcpyDeviceToHost);
+    for (int s = 0; s < kArrays && e == cudaSuccess; ++s) {
+        if (s == 10 || s == 11) {   // rho_ref and theta_ref stay FP64
+            if (h->M) e = cudaMemcpy(slots[s], staged[s], sizeof(double) * h->M,
+                                     cudaMemcpyDeviceToDevice);
+            continue;
+        }
+        double mx;
+        std::memcpy(&mx, &amax[s], sizeof(double));
+        e = numa::launch_to_df(staged[s], slots[s], h->M, std::ldexp(mx, -50), d_bad, 0);
+    }
+    int bad = 0;
+    if (e == cudaSuccess) e = cudaMemcpy(&bad, d_bad, sizeof(int), cudaMemcpyDeviceToHost);
+    cudaFree(tmp);
+    if (e != cudaSuccess || bad) {
+        cudaFree(h->d_block);
+        h->d_block = nullptr;
+        *in_range = (e != cudaSuccess) || !bad;
+        return e;
+    }
+    for (int s = 0; s < 9; ++s) h->dgeo.g[s] = slots[s];
+    h->dgeo.Jinv = slots[9];
+    h->dgeo.rho_ref = reinterpret_cast<const double *>(slots[10]);
+    h->dgeo.theta_ref = reinterpret_cast<const double *>(slots[11]);
+    h->dgeo.w = slots[12];
+    h->dgeo.A = slots[13];
+    h->kernel = numa::Kernel::DoubleFloat;
+    return cudaSuccess;
+}
+
+}  // namespace
+
+extern "C" {
+
+int numa_vol_create(const numa_mesh *mesh, const numa_geometry *geo, const numa_constants *c,
+                    numa_precision prec, numa_vol **out) {
+    g_last_error.clear();
+    if (!out) return fail(NUMA_EINVAL, "numa_vol_create: out is NULL");
+    *out = nullptr;
+    if (!mesh || !geo || !c) return fail(NUMA_EINVAL, "numa_vol_create: NULL argument");
+    if (mesh->N < 1 || mesh->N > NUMA_MAX_N)
+        return fail(NUMA_EINVAL, "numa_vol_create: N must be in [1, 7]");
+    if (mesh->num_elements < 0)
+        return fail(NUMA_EINVAL, "numa_vol_create: num_elements must be >= 0");
+    if (mesh->num_elements > (int64_t)INT32_MAX)
+        return fail(NUMA_EINVAL, "numa_vol_create: num_elements exceeds 2^31 - 1");
+    if (!(c->p0 > 0) || !(c->R > 0) || !(c->cp > c->R))
+        return fail(NUMA_EINVAL, "numa_vol_create: need p0 > 0 and cp > R > 0");
+    for (int s = 0; s < 9; ++s)
+        if (!geo->g[s]) return fail(NUMA_EINVAL, "numa_vol_create: NULL metric array");
+    if (!geo->Jinv || !geo->rho_ref || !geo->rhotheta_ref)
+        return fail(NUMA_EINVAL, "numa_vol_create: NULL Jinv or reference array");
+    if (prec == NUMA_MIXED)
+        return fail(NUMA_EUNSUPPORTED, "numa_vol_create: NUMA_MIXED is not implemented");
+    if (prec != NUMA_FP64 && prec != NUMA_DF64)
+        return fail(NUMA_EINVAL, "numa_vol_create: unknown precision");
+    if (prec == NUMA_DF64 && mesh->N != 7)
+        return fail(NUMA_EUNSUPPORTED, "numa_vol_create: NUMA_DF64 is implemented for N = 7 only");
+
+    numa_vol *h = new (std::nothrow) numa_vol();
+    if (!h) return fail(NUMA_ENOMEM, "numa_vol_create: host allocation failed");
+    h->N = mesh->N;
+    h->Nq = mesh->N + 1;
+    h->Ne = mesh->num_elements;
+    h->M = h->Ne * h->Nq * h->Nq * h->Nq;
+    h->prec = prec;
+    h->eos = numa::EosConstants{c->p0, c->R, c->cp / (c->cp - c->R), c->grav};
+
+    cudaError_t e = cudaGetDevice(&h->device);
+    if (e != cudaSuccess) {
+        delete h;
+        return fail_cuda(e, "numa_vol_create: cudaGetDevice");
+    }
+    double D[(NUMA_MAX_N + 1) * (NUMA_MAX_N + 1)];
+    numa::gll_diff_matrix(h->N, D);
+
+    build_params(h, D);
+    bool use_native = prec == NUMA_FP64;
+    if (!use_native) {
+        bool in_range = true;
+        e = create_df(h, geo, &in_range);
+        if (e == cudaSuccess && !in_range) use_native = true;   // geometry out of range
+    }
+    if (use_native && e == cudaSuccess) e = create_native(h, geo, D);
+    if (e != cudaSuccess) {
+        cudaFree(h->d_block);
+        delete h;
+        return fail_cuda(e, "numa_vol_create: upload of geometry");
+    }
+    *out = h;
+    return NUMA_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+cudaError_t launch(numa_vol *h, const double *q, double *rhs, cudaStream_t s) {
+    if (h->kernel == numa::Kernel::DoubleFloat)
+        return numa::launch_vol_rhs_df64(h->Ne, h->dgeo, h->dparams, q, rhs, s);
+    return numa::launch_vol_rhs_fp64(h->N, h->Ne, h->geo, h->nparams, q, rhs, s);
+}
+
+}  // namespace
+
+extern "C" {
+
+int numa_vol_rhs(numa_vol *h, const void *q, void *rhs, void *stream) {
+    g_last_error.clear();
+    if (!h) return fail(NUMA_EINVAL, "numa_vol_rhs: NULL handle");
+    if (h->Ne == 0) return NUMA_OK;
+    if (!q || !rhs) return fail(NUMA_EINVAL, "numa_vol_rhs: NULL q or rhs");
+    if (!aligned16(q) || !aligned16(rhs))
+        return fail(NUMA_EINVAL, "numa_vol_rhs: q and rhs must be 16-byte aligned");
+    const size_t bytes = sizeof(double) * numa::kFields * h->M;
+    if (overlap(q, rhs, bytes)) return fail(NUMA_EINVAL, "numa_vol_rhs: q and rhs overlap");
+    if (!is_device_pointer(q) || !is_device_pointer(rhs))
+        return fail(NUMA_EINVAL, "numa_vol_rhs: q and rhs must be device pointers");
+    cudaError_t e = launch(h, static_cast<const double *>(q), static_cast<double *>(rhs),
+                           static_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return fail_cuda(e, "numa_vol_rhs: launch");
+    return NUMA_OK;
+}
+
+int numa_vol_rhs_host(numa_vol *h, const double *q, double *rhs) {
+    g_last_error.clear();
+    if (!h) return fail(NUMA_EINVAL, "numa_vol_rhs_host: NULL handle");
+    if (h->Ne == 0) return NUMA_OK;
+    if (!q || !rhs) return fail(NUMA_EINVAL, "numa_vol_rhs_host: NULL q or rhs");
+    const size_t bytes = sizeof(double) * numa::kFields * h->M;
+    if (overlap(q, rhs, bytes)) return fail(NUMA_EINVAL, "numa_vol_rhs_host: q and rhs overlap");
+    cudaError_t e = cudaSuccess;
+    if (!h->host_stream) e = cudaStreamCreateWithFlags(&h->host_stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) return fail_cuda(e, "numa_vol_rhs_host: stream");
+    if (!h->d_stage) {
+        e = cudaMalloc(&h->d_stage, 2 * bytes);
+        if (e != cudaSuccess) {
+            h->d_stage = nullptr;
+            return fail_cuda(e, "numa_vol_rhs_host: staging allocation");
+        }
+    }
+    double *dq = h->d_stage;
+    double *dr = h->d_stage + numa::kFields * h->M;
+    e = cudaMemcpyAsync(dq, q, bytes, cudaMemcpyHostToDevice, h->host_stream);
+    if (e == cudaSuccess)
+        e = launch(h, dq, dr, h->host_stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(rhs, dr, bytes, cudaMemcpyDeviceToHost, h->host_stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->host_stream);
+    if (e != cudaSuccess) return fail_cuda(e, "numa_vol_rhs_host");
+    return NUMA_OK;
+}
+
+void numa_vol_destroy(numa_vol *h) {
+    if (!h) return;
+    int cur = 0;
+    cudaGetDevice(&cur);
+    if (cur != h->device) cudaSetDevice(h->device);
+    cudaDeviceSynchronize();
+    if (h->host_stream) cudaStreamDestroy(h->host_stream);
+    cudaFree(h->d_stage);
+    cudaFree(h->d_block);
+    if (cur != h->device) cudaSetDevice(cur);
+    delete h;
+}
+
+}  // extern "C"

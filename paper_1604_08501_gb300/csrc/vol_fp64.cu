@@ -1,17 +1,28 @@
-// FP64 element volume term on sm_103a.
+// Native FP64 element volume term on sm_103a, orders N = 1..7.
 //
 // Computes, per element and point, the pressure perturbation from the Theta
 // equation of state, the contravariant fluxes of the five fields in the three
 // reference directions, the three D sweeps, the Jinv scaling and the gravity
 // source (Sec. 2, Eq. (2); sign and flux form of the paper's r/s subroutines,
-// Sec. 3).
+// Sec. 3).  Every floating-point operation is an FP64 operation.
 //
-// Kernel structure: one CTA per element, one thread per point.  Each thread
-// computes the fifteen fluxes of its own point once (the paper's "precompute
-// fluxes" step, Sec. 3 opt. level 5) into shared memory.  After a barrier it
-// applies the three D sweeps from shared memory, keeps the sum in registers
-// and applies Jinv once at write-back (opt. levels 7 and 8).  State and
-// geometry are read once from HBM, and rhs is written once.
+// On GB300 the FP64 pipe (about 0.53 T DFMA/s) binds this kernel, so the
+// design minimises FP64 instructions per point:
+//  * p' = p(Theta) - p(Theta_ref) is evaluated as p_ref ((1+x)^gamma - 1) by
+//    its binomial series in x = (Theta - Theta_ref)/Theta_ref for |x| <= 1/64
+//    (12 FP64 operations, and no cancellation), and by pow elsewhere.
+//  * 1/rho is formed once; u_d = (g_d . U) * (1/rho).
+//  * The fluxes are computed once per point into shared memory (the paper's
+//    flux precompute, Sec. 3, opt. level 5).
+//  * Each line of each (direction, field) is swept by one thread with the
+//    even-odd split of the GLL D (D[N-i][N-n] = -D[i][n]): E_m = F_m + F_{N-m},
+//    O_m = F_m - F_{N-m}, and S_i = a_i + b_i, S_{N-i} = b_i - a_i with
+//    a_i = sum_m De[i][m] E_m (+ D[i][c] F_c for odd Nq), b_i = sum_m Do[i][m] O_m.
+//    That is half the multiplies of the direct sweep.
+//  * Jinv is applied once to the sum of the three sweeps (opt. level 8).
+//
+// One CTA of Nq^3 threads per element, in three phases: fluxes by point,
+// sweeps by line (in place), combination by point.
 #include <cuda_runtime.h>
 
 #include "numa_internal.h"
@@ -20,74 +31,141 @@ namespace numa {
 
 namespace {
 
-// p0 (R Theta / p0)^gamma, the equation of state of Sec. 2.  Each step is
-// rounded explicitly, so the create-time evaluation of p(Theta_ref) and the
-// per-call evaluation of p(Theta) agree bit for bit for equal arguments.
-__device__ __forceinline__ double eos_pressure(double Th, const EosConstants &c) {
-    return __dmul_rn(c.p0, pow(__ddiv_rn(__dmul_rn(c.R, Th), c.p0), c.gamma));
-}
-
-__global__ void pref_kernel(double *p, int64_t M, EosConstants c) {
-    for (int64_t m = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; m < M;
-         m += (int64_t)gridDim.x * blockDim.x)
-        p[m] = eos_pressure(p[m], c);
+// Shared-memory slot of position n on line `line` (lines of Nq points).  For
+// Nq = 8 an XOR swizzle keeps the 8-byte accesses of all three phases free of
+// bank conflicts; other orders use the plain layout.
+template <int NQ>
+__device__ __forceinline__ int slot(int line, int n) {
+    if constexpr (NQ == 8) return line * 8 + (n ^ ((line & 6) | ((line >> 3) & 1)));
+    else return line * NQ + n;
 }
 
 template <int NQ>
-__global__ void __launch_bounds__(NQ * NQ * NQ)
-vol_rhs_fp64_kernel(DeviceGeometry geo, EosConstants c, const double *__restrict__ q,
+__device__ __forceinline__ int dir_slot(int d, int i, int j, int k) {
+    if (d == 0) return slot<NQ>(NQ * k + j, i);
+    if (d == 1) return slot<NQ>(NQ * k + i, j);
+    return slot<NQ>(NQ * j + i, k);
+}
+
+// p0 (R Theta / p0)^gamma, the equation of state of Sec. 2.  Not inlined:
+// the rhs kernel calls it only where the series does not apply, and keeping
+// pow out of line keeps its registers out of the kernel's budget.
+__device__ __noinline__ double eos_pressure(double Th, const EosConstants &c) {
+    return __dmul_rn(c.p0, pow(__ddiv_rn(__dmul_rn(c.R, Th), c.p0), c.gamma));
+}
+
+// p' from the binomial series where it converges fast, pow elsewhere.
+__device__ __forceinline__ double pressure_perturbation(double Th, double th0, double w, double A,
+                                                        const NativeParams &P) {
+    const double thp = Th - th0;              // Theta'
+    const double x = thp * w;                 // Theta' / Theta_ref
+    if (fabs(x) <= 0.015625) {
+        double g = P.c[8];
+#pragma unroll
+        for (int k = 7; k >= 0; --k) g = fma(g, x, P.c[k]);   // sum_k c_{k+1} x^k
+        return (A * thp) * g;
+    }
+    // Outside the series range (or Theta_ref = 0, where w and A are not finite
+    // and x is inf or NaN): the definition, two evaluations of the equation of state.
+    return eos_pressure(Th, P.eos) - eos_pressure(th0, P.eos);
+}
+
+// Resident CTAs per SM the register budget is sized for: 1024 threads per SM,
+// at most 32 CTAs.
+template <int NQ>
+constexpr int min_ctas() {
+    constexpr int n = 1024 / (NQ * NQ * NQ);
+    return n < 1 ? 1 : (n > 32 ? 32 : n);
+}
+
+template <int NQ>
+__global__ void __launch_bounds__(NQ * NQ * NQ, min_ctas<NQ>())
+vol_rhs_fp64_kernel(DeviceGeometry geo, NativeParams P, const double *__restrict__ q,
                     double *__restrict__ rhs, int64_t M) {
     constexpr int N3 = NQ * NQ * NQ;
-    __shared__ double sD[NQ * NQ];
-    extern __shared__ double sF[];  // [direction][field][point], 15 * N3
+    constexpr int NL = NQ * NQ;               // lines per (direction, field)
+    constexpr int HALF = NQ / 2;
+    constexpr bool ODD = (NQ & 1) != 0;
+    constexpr int C = NQ / 2;                 // centre index for odd Nq
+    extern __shared__ double sF[];            // [direction*5 + field][slot]
 
     const int l = threadIdx.x;
+    const int i = l % NQ, j = (l / NQ) % NQ, k = l / (NQ * NQ);
     const int64_t node = (int64_t)blockIdx.x * N3 + l;
-    for (int t = l; t < NQ * NQ; t += N3) sD[t] = geo.D[t];
 
+    // ---- phase 1: p', fluxes ----------------------------------------
     const double rho = q[node];
-    const double U1 = q[M + node], U2 = q[2 * M + node], U3 = q[3 * M + node];
+    const double U[3] = {q[M + node], q[2 * M + node], q[3 * M + node]};
     const double Th = q[4 * M + node];
-    const double pp = eos_pressure(Th, c) - geo.p_ref[node];
-
+    const double pp = pressure_perturbation(Th, geo.theta_ref[node], geo.w[node], geo.A[node], P);
+    const double rinv = __drcp_rn(rho);
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
         const double g1 = geo.g[3 * d][node], g2 = geo.g[3 * d + 1][node],
                      g3 = geo.g[3 * d + 2][node];
-        const double u = (g1 * U1 + g2 * U2 + g3 * U3) / rho;
-        double *F = sF + d * kFields * N3 + l;
-        F[0 * N3] = rho * u;
-        F[1 * N3] = U1 * u + g1 * pp;
-        F[2 * N3] = U2 * u + g2 * pp;
-        F[3 * N3] = U3 * u + g3 * pp;
+        const double v = fma(g3, U[2], fma(g2, U[1], g1 * U[0]));
+        const double u = v * rinv;
+        const int s = dir_slot<NQ>(d, i, j, k);
+        double *F = sF + d * kFields * N3 + s;
+        F[0 * N3] = v;
+        F[1 * N3] = fma(U[0], u, g1 * pp);
+        F[2 * N3] = fma(U[1], u, g2 * pp);
+        F[3 * N3] = fma(U[2], u, g3 * pp);
         F[4 * N3] = Th * u;
     }
     __syncthreads();
 
-    const int i = l % NQ, j = (l / NQ) % NQ, k = l / (NQ * NQ);
+    // ---- phase 2: even-odd sweeps, one line per task, in place --------
+    for (int item = l; item < 3 * kFields * NL; item += N3) {
+        double *buf = sF + (item / NL) * N3;
+        const int line = item % NL;
+        double F[NQ];
+#pragma unroll
+        for (int n = 0; n < NQ; ++n) F[n] = buf[slot<NQ>(line, n)];
+        double E[HALF > 0 ? HALF : 1], O[HALF > 0 ? HALF : 1];
+#pragma unroll
+        for (int m = 0; m < HALF; ++m) {
+            E[m] = F[m] + F[NQ - 1 - m];
+            O[m] = F[m] - F[NQ - 1 - m];
+        }
+        double Sc = 0.0;
+#pragma unroll
+        for (int r = 0; r < HALF; ++r) {
+            double a = ODD ? P.Dc[r] * F[C] : 0.0, b = 0.0;
+#pragma unroll
+            for (int m = 0; m < HALF; ++m) {
+                a = fma(P.De[r * HALF + m], E[m], a);
+                b = fma(P.Do[r * HALF + m], O[m], b);
+            }
+            buf[slot<NQ>(line, r)] = b + a;
+            buf[slot<NQ>(line, NQ - 1 - r)] = b - a;
+        }
+        if (ODD) {
+            // centre row: D[c][N-m] = -D[c][m] and D[c][c] = 0, so S_c = sum_m D[c][m] O_m
+#pragma unroll
+            for (int m = 0; m < HALF; ++m) Sc = fma(P.Dcr[m], O[m], Sc);
+            buf[slot<NQ>(line, C)] = Sc;
+        }
+    }
+    __syncthreads();
+
+    // ---- phase 3: combine, scale, gravity, store ----------------------
     const double Jinv = geo.Jinv[node];
     const double drho = rho - geo.rho_ref[node];
 #pragma unroll
     for (int b = 0; b < kFields; ++b) {
-        const double *Fr = sF + (0 * kFields + b) * N3;
-        const double *Fs = sF + (1 * kFields + b) * N3;
-        const double *Ft = sF + (2 * kFields + b) * N3;
-        double s = 0.0;
-#pragma unroll
-        for (int n = 0; n < NQ; ++n) s += sD[i * NQ + n] * Fr[(k * NQ + j) * NQ + n];
-#pragma unroll
-        for (int n = 0; n < NQ; ++n) s += sD[j * NQ + n] * Fs[(k * NQ + n) * NQ + i];
-#pragma unroll
-        for (int n = 0; n < NQ; ++n) s += sD[k * NQ + n] * Ft[(n * NQ + j) * NQ + i];
-        double v = -Jinv * s;
-        if (b == 3) v -= drho * c.grav;
+        const double R = sF[(0 * kFields + b) * N3 + dir_slot<NQ>(0, i, j, k)] +
+                         sF[(1 * kFields + b) * N3 + dir_slot<NQ>(1, i, j, k)] +
+                         sF[(2 * kFields + b) * N3 + dir_slot<NQ>(2, i, j, k)];
+        double v = -Jinv * R;
+        if (b == 3) v = fma(-drho, P.eos.grav, v);
         rhs[b * M + node] = v;
     }
 }
 
 template <int NQ>
-cudaError_t launch_nq(int64_t Ne, const DeviceGeometry &geo, EosConstants c, const double *q,
-                      double *rhs, cudaStream_t s) {
+cudaError_t launch_nq(int64_t Ne, const DeviceGeometry &geo, const NativeParams &P,
+                      const double *q, double *rhs, cudaStream_t s) {
     constexpr int N3 = NQ * NQ * NQ;
     const size_t smem = sizeof(double) * kFields * 3 * N3;
     // The opt-in above 48 KB is per device; setting it on every launch keeps
@@ -95,36 +173,42 @@ cudaError_t launch_nq(int64_t Ne, const DeviceGeometry &geo, EosConstants c, con
     cudaError_t e = cudaFuncSetAttribute(vol_rhs_fp64_kernel<NQ>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    const int64_t M = Ne * N3;
-    vol_rhs_fp64_kernel<NQ><<<(unsigned)Ne, N3, smem, s>>>(geo, c, q, rhs, M);
+    vol_rhs_fp64_kernel<NQ><<<(unsigned)Ne, N3, smem, s>>>(geo, P, q, rhs, Ne * N3);
     return cudaGetLastError();
+}
+
+// w = 1/Theta_ref and A = p(Theta_ref)/Theta_ref, in place of a copy of Theta_ref.
+__global__ void reference_eos_kernel(const double *__restrict__ theta_ref, double *__restrict__ w,
+                                     double *__restrict__ A, int64_t M, EosConstants c) {
+    for (int64_t m = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; m < M;
+         m += (int64_t)gridDim.x * blockDim.x) {
+        const double th = theta_ref[m];
+        w[m] = 1.0 / th;
+        A[m] = eos_pressure(th, c) / th;
+    }
 }
 
 }  // namespace
 
-cudaError_t launch_pref_fp64(const double *rhotheta_ref, double *p_ref, int64_t M,
-                             EosConstants c, cudaStream_t s) {
+cudaError_t launch_reference_eos(const double *theta_ref, double *w, double *A, int64_t M,
+                                 EosConstants c, cudaStream_t s) {
     if (M == 0) return cudaSuccess;
-    if (rhotheta_ref != p_ref) {
-        cudaError_t e = cudaMemcpyAsync(p_ref, rhotheta_ref, sizeof(double) * M,
-                                        cudaMemcpyDefault, s);
-        if (e != cudaSuccess) return e;
-    }
-    pref_kernel<<<1216, 256, 0, s>>>(p_ref, M, c);
+    reference_eos_kernel<<<1216, 256, 0, s>>>(theta_ref, w, A, M, c);
     return cudaGetLastError();
 }
 
-cudaError_t launch_vol_rhs_fp64(int N, int64_t Ne, const DeviceGeometry &geo, EosConstants c,
-                                const double *q, double *rhs, cudaStream_t s) {
+cudaError_t launch_vol_rhs_fp64(int N, int64_t Ne, const DeviceGeometry &geo,
+                                const NativeParams &P, const double *q, double *rhs,
+                                cudaStream_t s) {
     if (Ne == 0) return cudaSuccess;
     switch (N) {
-        case 1: return launch_nq<2>(Ne, geo, c, q, rhs, s);
-        case 2: return launch_nq<3>(Ne, geo, c, q, rhs, s);
-        case 3: return launch_nq<4>(Ne, geo, c, q, rhs, s);
-        case 4: return launch_nq<5>(Ne, geo, c, q, rhs, s);
-        case 5: return launch_nq<6>(Ne, geo, c, q, rhs, s);
-        case 6: return launch_nq<7>(Ne, geo, c, q, rhs, s);
-        case 7: return launch_nq<8>(Ne, geo, c, q, rhs, s);
+        case 1: return launch_nq<2>(Ne, geo, P, q, rhs, s);
+        case 2: return launch_nq<3>(Ne, geo, P, q, rhs, s);
+        case 3: return launch_nq<4>(Ne, geo, P, q, rhs, s);
+        case 4: return launch_nq<5>(Ne, geo, P, q, rhs, s);
+        case 5: return launch_nq<6>(Ne, geo, P, q, rhs, s);
+        case 6: return launch_nq<7>(Ne, geo, P, q, rhs, s);
+        case 7: return launch_nq<8>(Ne, geo, P, q, rhs, s);
         default: return cudaErrorInvalidValue;
     }
 }

@@ -16,7 +16,7 @@ import ctypes as C
 import numpy as np
 
 from . import _lib
-from ._lib import NUMA_FP64, NUMA_MIXED, NumaError, check
+from ._lib import NUMA_DF64, NUMA_FP64, NUMA_MIXED, NumaError, check
 
 NFIELDS = 5
 
@@ -50,7 +50,10 @@ def diff_matrix(N: int) -> np.ndarray:
 
 
 class VolumeTerm:
-    """One mesh on the current CUDA device (numa_vol_create ... numa_vol_destroy)."""
+    """One mesh on the current CUDA device (numa_vol_create ... numa_vol_destroy).
+
+    precision: "fp64" (every operation on the FP64 pipe), "df64" (double-float
+    arithmetic on the FP32 pipes, N = 7) or "mixed"."""
 
     def __init__(self, N: int, num_elements: int, g, Jinv, rho_ref, rhotheta_ref,
                  p0: float, R: float, cp: float, grav: float, precision: str = "fp64"):
@@ -72,7 +75,7 @@ class VolumeTerm:
         geo.rhotheta_ref = _host_or_device_ptr(rhotheta_ref, self.M, keep)
         mesh = _lib.numa_mesh(self.Ne, self.N)
         consts = _lib.numa_constants(float(p0), float(R), float(cp), float(grav))
-        prec = {"fp64": NUMA_FP64, "mixed": NUMA_MIXED}[precision]
+        prec = {"fp64": NUMA_FP64, "df64": NUMA_DF64, "mixed": NUMA_MIXED}[precision]
         h = C.c_void_p()
         check(lib.numa_vol_create(C.byref(mesh), C.byref(geo), C.byref(consts), prec, C.byref(h)))
         self._h = h
@@ -88,6 +91,11 @@ class VolumeTerm:
         if self._h is None or not self._h.value:
             raise RuntimeError("VolumeTerm is closed")
         return self._h.value
+
+    @property
+    def kernel_name(self) -> str:
+        """The kernel numa_vol_rhs launches for this handle."""
+        return _lib.load().numa_vol_kernel_name(self.handle).decode()
 
     def rhs(self, q, out=None, stream=None):
         """Enqueue rhs = volume term of q on ``stream`` (default: torch's current

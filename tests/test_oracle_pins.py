@@ -213,6 +213,30 @@ def test_paper_units_by_hand_n1():
                 assert abs(out[b, node] - want) < 1e-15, (f, node, out[b, node], want)
 
 
+def test_error_bound_by_hand_and_triangle_inequality():
+    # By hand (the N=1 paper-units case): only the r-direction carries rho and
+    # Theta fluxes, so the bound is (|F(0)| + |F(1)|)/2 = |rhs| there; U2 has
+    # F_s[U2] = p on both points of each s-line, bound (p + p)/2 = p(k).
+    gold = load_golden("paper_units_n1_by_hand.json")
+    mesh = wl.affine_box(1, (1, 1, 1), L=2.0, B=np.eye(3))
+    q = np.zeros((5, 8))
+    for node in range(8):
+        env = {"i": node % 2, "j": (node // 2) % 2, "k": node // 4}
+        q[:, node] = [eval(gold["state"][f], env) for f in ("rho", "U1", "U2", "U3", "Theta")]
+    prob = problem(mesh, wl.PAPER_UNITS, 0.0, 0.0)
+    ab = oracle.vol_rhs_abs(prob, q)
+    rhs = oracle.vol_rhs_o2(prob, q)
+    np.testing.assert_allclose(ab[0], np.abs(rhs[0]), rtol=1e-15)
+    np.testing.assert_allclose(ab[4], np.abs(rhs[4]), rtol=1e-15)
+    p = np.where(np.arange(8) // 4 == 0, 1.0, 2.0 ** 1.4)
+    np.testing.assert_allclose(ab[2], p, rtol=1e-15)
+    # triangle inequality on a warped workload
+    w = wl.make_workload(4, 2, seed=2)
+    ab = oracle.vol_rhs_abs(w.problem(), w.q)
+    rhs = oracle.vol_rhs_o2(w.problem(), w.q)
+    assert np.all(ab >= np.abs(rhs) * (1 - 1e-14))
+
+
 # --------------------------------------------------------------------------
 # Structure
 # --------------------------------------------------------------------------
