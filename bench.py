@@ -240,7 +240,7 @@ def run_reference(args):
     if rank != 0:
         return 0
     import oracle
-    w, name = workload_full()
+    w, name = workload_full(args.n)
     prob, q, m = oracle_sample(w, CPU_SAMPLE_ELEMENTS)
     for _ in range(args.warmup):
         oracle.vol_rhs_o2(prob, q)

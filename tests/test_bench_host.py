@@ -1,0 +1,65 @@
+"""Host-side logic of bench.py: multi-rank aggregation over gloo (world size 2,
+CPU), the reference arm's JSON line, and the roofline bookkeeping."""
+import json
+import os
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+import bench  # noqa: E402
+
+
+def _rank_main(rank, world, port, out):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank),
+                      WORLD_SIZE=str(world), LOCAL_RANK=str(rank))
+    import torch.distributed as dist
+    bench.dist_setup("gloo")
+    # rank r "took" 1 + r seconds for 1000 units
+    thr, tmax = bench.aggregate(1000, 1.0 + rank)
+    bench.barrier()
+    with open(os.path.join(out, f"r{rank}.json"), "w") as f:
+        json.dump({"thr": thr, "tmax": tmax, "max": bench.reduce_max(float(rank * 10))}, f)
+    dist.destroy_process_group()
+
+
+def test_aggregate_over_two_gloo_ranks(tmp_path):
+    import torch.multiprocessing as mp
+    port = 29500 + os.getpid() % 1000
+    mp.spawn(_rank_main, args=(2, port, str(tmp_path)), nprocs=2, join=True)
+    for r in range(2):
+        d = json.load(open(tmp_path / f"r{r}.json"))
+        # whole-job throughput: units of all ranks over the slowest rank's time
+        assert d["tmax"] == 2.0
+        assert d["thr"] == pytest.approx(2000 / 2.0)
+        assert d["max"] == 10.0
+
+
+def test_single_process_aggregate_is_identity():
+    thr, tmax = bench.aggregate(500, 2.0)
+    assert (thr, tmax) == (250.0, 2.0)
+
+
+def test_reference_arm_prints_one_json_line():
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference",
+                        "--n", "3", "--steps", "2", "--warmup", "3"],
+                       capture_output=True, text=True, timeout=600, cwd=ROOT)
+    assert r.returncode == 0, r.stderr
+    lines = [l for l in r.stdout.splitlines() if l.strip()]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["unit"] == "GDOF/s" and d["value"] > 0
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] >= 1
+    assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["higher_is_better"] is True
+
+
+def test_roofline_entries_pick_the_binding_bound():
+    from paper_1604_08501_gb300 import workload as wl
+    w = wl.make_workload(7, 1, seed=0)
+    roof, other = bench.roofline_entries("vol_rhs_fp64_kernel<8>", 1.0, w)
+    assert roof["bound"] == "alu" and other["bound"] == "hbm"
+    roof, other = bench.roofline_entries("vol_rhs_df64_kernel", 1.0, w)
+    assert roof["bound"] == "hbm"
+    assert roof["achieved"] == pytest.approx(176 * w.M / 1e-3 / 1e9)
