@@ -34,9 +34,10 @@ if ROOT not in sys.path:
 
 METRIC = "volume-RHS GDOF/s"
 UNIT = "GDOF/s"
-# Algorithmic HBM bytes per point of the FP64 path: 5 state + 9 metric + Jinv +
-# 2 reference arrays read (17 x 8 B), 5 rhs fields written (5 x 8 B).
+# Algorithmic HBM bytes per point: 5 state + 9 metric + Jinv + 2 reference arrays
+# read, 5 rhs fields written; 8 bytes each in FP64 (176), 4 in FP32 (88).
 BYTES_PER_NODE_FP64 = 176
+BYTES_PER_NODE_MIXED = 88
 # Algorithmic FP64 flops per point (an FMA counts 2, pow and divide count 1):
 # EOS 5, three directions of u and fluxes 3 x 17, three D sweeps 30*Nq,
 # Jinv scaling and gravity 8.
@@ -311,12 +312,14 @@ def time_variant(vt, q, q_host, dev, K, W, rank, e2e=True):
 
 def roofline_entries(kname, kernel_ms, w):
     peak, peak_src = measured_peaks()
-    hbm_gbs = BYTES_PER_NODE_FP64 * w.M / (kernel_ms * 1e-3) / 1e9
-    fp64_tfs = flops_per_node_fp64(w.N + 1) * w.M / (kernel_ms * 1e-3) / 1e12
+    bpp = BYTES_PER_NODE_MIXED if "mixed" in kname else BYTES_PER_NODE_FP64
+    hbm_gbs = bpp * w.M / (kernel_ms * 1e-3) / 1e9
     hbm = {"bound": "hbm", "achieved": hbm_gbs, "peak": peak, "unit": "GB/s",
            "frac": hbm_gbs / peak, "traffic": load_traffic(kname), "kernel": kname,
-           "bytes_per_point": BYTES_PER_NODE_FP64, "peak_source": peak_src,
-           "kernel_ms": kernel_ms}
+           "bytes_per_point": bpp, "peak_source": peak_src, "kernel_ms": kernel_ms}
+    if "mixed" in kname:
+        return hbm, None
+    fp64_tfs = flops_per_node_fp64(w.N + 1) * w.M / (kernel_ms * 1e-3) / 1e12
     # FP64-equivalent flop rate against the FP64 pipe of one GB300 (152 SMs x
     # 2 DFMA/clk x 2 flop x 2.07 GHz = 1.26 TFLOP/s nominal).  It binds the
     # native kernel; the double-float kernel runs on the FP32 pipes.
@@ -341,13 +344,16 @@ def run_gpu(args):
     from paper_1604_08501_gb300.numa_vol import VolumeTerm
 
     w, name = workload_full(args.n)
-    q_host = torch.from_numpy(w.q).pin_memory()
-    q = q_host.to(dev)
     K, W = args.steps, args.warmup
-    step_bytes = 5 * w.M * 8
 
     results = {}
     for prec in args.precisions:
+        # the mixed mode takes the FP32 perturbation state (input preparation,
+        # outside the timed regions)
+        q_np = w.q_mixed() if prec == "mixed" else w.q
+        q_host = torch.from_numpy(q_np).pin_memory()
+        q = q_host.to(dev)
+        step_bytes = q_np.nbytes
         vt = VolumeTerm.from_problem(w.problem(), precision=prec)
         r = time_variant(vt, q, q_host, dev, K, W, rank, e2e=not args.no_e2e)
         r["kernel"] = vt.kernel_name
@@ -366,7 +372,8 @@ def run_gpu(args):
         head_prec = args.precisions[0]
         head = results[head_prec]
         roof, other = roofline_entries(head["kernel"], head["kernel_ms"], w)
-        dtypes = {"fp64": "f64", "df64": "df64 (FP32 hi+lo pairs, 48-bit)"}
+        dtypes = {"fp64": "f64", "df64": "df64 (FP32 hi+lo pairs, 48-bit)",
+                  "mixed": "f32 (perturbation state)"}
         line = {"metric": METRIC, "value": head["value"], "unit": UNIT, "n_gpus": world,
                 "steps": K, "warmup": W, "ms_per_step": head["ms_per_step"],
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -402,7 +409,7 @@ def main(argv=None):
                     help="skip the host-buffer end-to-end leg (for profiling runs)")
     ap.add_argument("--n", type=int, default=32,
                     help="elements per axis; 32 is the timed workload, smaller is for ncu")
-    ap.add_argument("--precision", default="fp64,df64",
+    ap.add_argument("--precision", default="fp64,df64,mixed",
                     help="comma-separated precision modes; the first is the headline value")
     args = ap.parse_args(argv)
     if args.warmup < 3:

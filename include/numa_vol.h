@@ -53,6 +53,7 @@ extern "C" {
 #define NUMA_ENOMEM (-2)        /* device allocation failed                               */
 #define NUMA_ECUDA (-3)         /* a CUDA call or kernel launch failed                    */
 #define NUMA_EUNSUPPORTED (-4)  /* valid request this build does not implement            */
+#define NUMA_ETIMEOUT (-5)      /* a kernel's bounded wait on its own staged copies ran out */
 
 #define NUMA_MAX_N 7            /* orders N = 1 .. 7 (Nq = 2 .. 8)                        */
 
@@ -85,7 +86,8 @@ typedef struct {
 
 typedef enum {
     NUMA_FP64 = 0,   /* FP64 state and rhs, every operation on the FP64 pipe           */
-    NUMA_MIXED = 1,  /* reserved for the mixed-precision form                           */
+    NUMA_MIXED = 1,  /* FP32 perturbation state (rho', U1, U2, U3, Theta'), FP32 rhs,
+                        FP32 geometry and arithmetic                                    */
     NUMA_DF64 = 2    /* FP64 state and rhs, double-float arithmetic (hi + lo FP32 pairs,
                         about 48 significant bits) on the FP32 pipes; N = 7 only      */
 } numa_precision;
@@ -104,7 +106,14 @@ typedef struct numa_vol numa_vol;
  * mesh->N in [1, NUMA_MAX_N]; mesh->num_elements >= 0; every pointer of geo
  * non-null; c->cp > c->R > 0 and c->p0 > 0.  On success *out receives the
  * handle (release with numa_vol_destroy).  Errors: NUMA_EINVAL,
- * NUMA_ENOMEM, NUMA_ECUDA, NUMA_EUNSUPPORTED (NUMA_MIXED; NUMA_DF64 with N != 7).
+ * NUMA_ENOMEM, NUMA_ECUDA, NUMA_EUNSUPPORTED (NUMA_DF64 with N != 7).
+ *
+ * NUMA_MIXED takes the state as FP32 perturbations from the reference state:
+ * plane 0 holds rho - rho_ref, plane 4 holds Theta - Theta_ref, and planes 1-3
+ * hold U1..U3.  It writes the (same) rhs in FP32.  The geometry is rounded to
+ * FP32 once.  p' is evaluated from Theta - Theta_ref without cancellation
+ * (series in x, or expm1(gamma log1p(x))).  Error against the FP64 volume term
+ * of the full state: about 1e-7 times the sweep condition number, normwise.
  *
  * NUMA_FP64 and NUMA_DF64 compute the same operation.  Both evaluate
  * p(Theta) - p(Theta_ref) as p_ref ((1 + x)^gamma - 1) by its binomial series
@@ -126,9 +135,10 @@ int numa_vol_create(const numa_mesh *mesh, const numa_geometry *geo,
 /*
  * Enqueue one evaluation of the volume term on a CUDA stream.
  *
- * q:   device pointer, 5 planes of M doubles (read only).
- * rhs: device pointer, 5 planes of M doubles (overwritten; the paper's
- *      kernel accumulates into rhsq, this call stores the volume term).
+ * q:   device pointer, 5 planes of M values (read only): doubles for NUMA_FP64
+ *      and NUMA_DF64, floats (perturbation form) for NUMA_MIXED.
+ * rhs: device pointer, 5 planes of M values of the same type (overwritten; the
+ *      paper's kernel accumulates into rhsq, this call stores the volume term).
  * Both must be 16-byte aligned and must not overlap.  stream is a
  * cudaStream_t (NULL = the legacy default stream).  The call returns once
  * the kernel is enqueued; rhs is complete when the stream reaches that
@@ -139,13 +149,27 @@ int numa_vol_rhs(numa_vol *h, const void *q, void *rhs, void *stream);
 
 /*
  * Evaluate the volume term from HOST memory: copies q to the device, runs the
- * kernel, copies rhs back and waits for completion.  Device staging buffers
+ * kernel, copies rhs back and waits for completion.  The mesh is processed in
+ * up to 8 chunks of elements on three internal streams, so the copy-in of one
+ * chunk, the kernel on the previous one and the copy-out of the one before
+ * overlap.  Device staging buffers
  * (2 x 5 x M doubles) are allocated on the first call and owned by the
- * handle.  q and rhs are host pointers to 5 planes of M doubles (pinned
- * memory gives full copy bandwidth).  Errors: NUMA_EINVAL, NUMA_ENOMEM,
- * NUMA_ECUDA.
+ * handle.  q and rhs are host pointers to 5 planes of M values of the
+ * handle's state type (pinned memory gives full copy bandwidth).  Errors:
+ * NUMA_EINVAL, NUMA_ENOMEM, NUMA_ECUDA.
  */
-int numa_vol_rhs_host(numa_vol *h, const double *q, double *rhs);
+int numa_vol_rhs_host(numa_vol *h, const void *q, void *rhs);
+
+/*
+ * Status of the kernels enqueued so far on a handle.  Reads and clears the
+ * handle's device status word on `stream` and waits for the stream.  Returns
+ * NUMA_ETIMEOUT if a kernel gave up a bounded wait on its own staged
+ * shared-memory copies; that kernel returned early, so the rhs of the elements
+ * it still owed is incomplete.  No timeout is expected in operation: each wait
+ * is bounded far above its normal duration.  Returns NUMA_OK otherwise.
+ * numa_vol_rhs_host checks it itself.
+ */
+int numa_vol_status(numa_vol *h, void *stream);
 
 /* Release a handle and its device memory.  NULL is a no-op.  Synchronises
  * the device before freeing. */
@@ -153,7 +177,8 @@ void numa_vol_destroy(numa_vol *h);
 
 /* Name of the kernel numa_vol_rhs launches for this handle:
  * "vol_rhs_fp64_kernel<Nq>" (NUMA_FP64, or NUMA_DF64 after a geometry
- * fallback) or "vol_rhs_df64_kernel".  Static string; "" for a NULL handle. */
+ * fallback), "vol_rhs_df64_kernel" or "vol_rhs_mixed_kernel<Nq>".  Static
+ * string; "" for a NULL handle. */
 const char *numa_vol_kernel_name(const numa_vol *h);
 
 /* Message for the last error on the calling thread ("" if none).  The

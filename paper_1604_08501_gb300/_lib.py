@@ -10,12 +10,13 @@ import os
 
 from .build import LIB
 
-NUMA_OK, NUMA_EINVAL, NUMA_ENOMEM, NUMA_ECUDA, NUMA_EUNSUPPORTED = 0, -1, -2, -3, -4
+NUMA_OK, NUMA_EINVAL, NUMA_ENOMEM, NUMA_ECUDA, NUMA_EUNSUPPORTED, NUMA_ETIMEOUT = 0, -1, -2, -3, -4, -5
 NUMA_MAX_N = 7
 NUMA_FP64, NUMA_MIXED, NUMA_DF64 = 0, 1, 2
 
 _ERRNAMES = {NUMA_EINVAL: "NUMA_EINVAL", NUMA_ENOMEM: "NUMA_ENOMEM",
-             NUMA_ECUDA: "NUMA_ECUDA", NUMA_EUNSUPPORTED: "NUMA_EUNSUPPORTED"}
+             NUMA_ECUDA: "NUMA_ECUDA", NUMA_EUNSUPPORTED: "NUMA_EUNSUPPORTED",
+             NUMA_ETIMEOUT: "NUMA_ETIMEOUT"}
 
 _DP = C.POINTER(C.c_double)
 
@@ -59,6 +60,8 @@ def load() -> C.CDLL:
     lib.numa_vol_rhs.restype = C.c_int
     lib.numa_vol_rhs_host.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p]
     lib.numa_vol_rhs_host.restype = C.c_int
+    lib.numa_vol_status.argtypes = [C.c_void_p, C.c_void_p]
+    lib.numa_vol_status.restype = C.c_int
     lib.numa_vol_destroy.argtypes = [C.c_void_p]
     lib.numa_vol_destroy.restype = None
     lib.numa_vol_last_error.argtypes = []

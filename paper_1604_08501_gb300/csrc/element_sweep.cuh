@@ -1,0 +1,79 @@
+// Shared-memory layout and the even-odd D sweep of one line, shared by the
+// native FP64 and the mixed-precision kernels.
+//
+// Fluxes of one element are kept per (direction, field) in line-major order:
+// direction r has lines (k, j) with position i, s has lines (k, i) with
+// position j, t has lines (j, i) with position k.  For Nq = 8 an XOR swizzle
+// slot(line, n) = 8 line + (n ^ h(line)) keeps the accesses free of bank
+// conflicts when points write, lines read and write, and points read back:
+//   8-byte values: h(line) = (line & 6) | ((line >> 3) & 1)
+//     (a half-warp wavefront: the 16 lanes need distinct (line & 1, n ^ h) pairs);
+//   4-byte values: h(line) = bit2 << 2 | bit4 << 1 | bit3 of line
+//     (a warp wavefront: lanes of equal line % 4 need distinct n ^ h, and h must
+//     flip bit 2 with line bit 2 for the s-direction writes).
+//
+// The sweep uses the centro-antisymmetry of the GLL D, D[N-i][N-n] = -D[i][n]:
+// with E_m = F_m + F_{N-m} and O_m = F_m - F_{N-m} (m < Nq/2),
+//   S_i = a_i + b_i,  S_{N-i} = b_i - a_i,
+//   a_i = sum_m De[i][m] E_m (+ D[i][c] F_c for odd Nq),  b_i = sum_m Do[i][m] O_m,
+// De = (D[i][m] + D[i][N-m])/2, Do = (D[i][m] - D[i][N-m])/2, and for odd Nq the
+// centre row S_c = sum_m D[c][m] O_m.  That is half the multiplies of
+// S_i = sum_n D[i][n] F_n.
+#pragma once
+
+namespace numa {
+
+template <int NQ, typename T>
+__device__ __forceinline__ int slot(int line, int n) {
+    if constexpr (NQ == 8 && sizeof(T) == 8)
+        return line * 8 + (n ^ ((line & 6) | ((line >> 3) & 1)));
+    else if constexpr (NQ == 8 && sizeof(T) == 4)
+        return line * 8 + (n ^ ((((line >> 2) & 1) << 2) | (((line >> 4) & 1) << 1) | ((line >> 3) & 1)));
+    else
+        return line * NQ + n;
+}
+
+template <int NQ, typename T>
+__device__ __forceinline__ int dir_slot(int d, int i, int j, int k) {
+    if (d == 0) return slot<NQ, T>(NQ * k + j, i);
+    if (d == 1) return slot<NQ, T>(NQ * k + i, j);
+    return slot<NQ, T>(NQ * j + i, k);
+}
+
+// Sweep line `line` of buf in place.  De, Do: (Nq/2)^2 row-major; Dc[r] =
+// D[r][c] and Dcr[m] = D[c][m] for odd Nq.  The tables live in kernel
+// parameter space, so every thread reads the same constant-bank operand.
+template <int NQ, typename T, typename Tab>
+__device__ __forceinline__ void sweep_line(T *buf, int line, const Tab &tab) {
+    constexpr int HALF = NQ / 2;
+    constexpr bool ODD = (NQ & 1) != 0;
+    constexpr int C = NQ / 2;
+    T F[NQ];
+#pragma unroll
+    for (int n = 0; n < NQ; ++n) F[n] = buf[slot<NQ, T>(line, n)];
+    T E[HALF > 0 ? HALF : 1], O[HALF > 0 ? HALF : 1];
+#pragma unroll
+    for (int m = 0; m < HALF; ++m) {
+        E[m] = F[m] + F[NQ - 1 - m];
+        O[m] = F[m] - F[NQ - 1 - m];
+    }
+#pragma unroll
+    for (int r = 0; r < HALF; ++r) {
+        T a = ODD ? tab.Dc[r] * F[C] : T(0), b = T(0);
+#pragma unroll
+        for (int m = 0; m < HALF; ++m) {
+            a = fma(tab.De[r * HALF + m], E[m], a);
+            b = fma(tab.Do[r * HALF + m], O[m], b);
+        }
+        buf[slot<NQ, T>(line, r)] = b + a;
+        buf[slot<NQ, T>(line, NQ - 1 - r)] = b - a;
+    }
+    if (ODD) {
+        T Sc = T(0);
+#pragma unroll
+        for (int m = 0; m < HALF; ++m) Sc = fma(tab.Dcr[m], O[m], Sc);
+        buf[slot<NQ, T>(line, C)] = Sc;
+    }
+}
+
+}  // namespace numa

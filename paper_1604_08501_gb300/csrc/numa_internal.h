@@ -10,6 +10,11 @@ namespace numa {
 
 constexpr int kFields = 5;
 
+// Elements [e0, e0 + count) of a mesh whose per-point planes hold M values.
+struct ElemRange {
+    int64_t e0, count, M;
+};
+
 // Device-side geometry of one handle. Every per-point array has M entries,
 // padded so that each starts on a 256-byte boundary.
 struct DeviceGeometry {
@@ -49,6 +54,23 @@ struct DfGeometry {
     const float2 *A;         // p(Theta_ref) / Theta_ref
 };
 
+// Per-point arrays of the mixed-precision path, FP32.
+struct MixedGeometry {
+    const float *g[9];
+    const float *Jinv;
+    const float *rho_ref;
+    const float *theta_ref;
+};
+
+// Parameters of the mixed-precision kernel: even-odd pieces of D (as in
+// NativeParams), c[k] = binom(gamma, k+1) for k = 0..4, K = p0^(1-gamma) R^gamma
+// (so p(Theta) = K Theta^gamma), gamma - 1, gamma and gravity.
+struct MixedParams {
+    float De[16], Do[16], Dc[4], Dcr[4];
+    float c[5];
+    float K, gm1, gamma, grav;
+};
+
 // Kernel parameters of the double-float path.
 struct DfParams;  // defined below
 
@@ -56,7 +78,7 @@ struct DfParams;  // defined below
 // reference_eos: w = 1/Theta_ref, A = p(Theta_ref)/Theta_ref per point.
 cudaError_t launch_reference_eos(const double *theta_ref, double *w, double *A, int64_t M,
                                  EosConstants c, cudaStream_t s);
-cudaError_t launch_vol_rhs_fp64(int N, int64_t Ne, const DeviceGeometry &geo,
+cudaError_t launch_vol_rhs_fp64(int N, ElemRange r, const DeviceGeometry &geo,
                                 const NativeParams &P, const double *q, double *rhs,
                                 cudaStream_t s);
 
@@ -68,8 +90,16 @@ cudaError_t launch_abs_max(const double *src, int64_t M, unsigned long long *ama
                            cudaStream_t s);
 cudaError_t launch_to_df(const double *src, float2 *dst, int64_t M, double thresh, int *bad,
                          cudaStream_t s);
-cudaError_t launch_vol_rhs_df64(int64_t Ne, const DfGeometry &geo, const DfParams &P,
+cudaError_t launch_vol_rhs_df64(ElemRange r, const DfGeometry &geo, const DfParams &P,
                                 const double *q, double *rhs, cudaStream_t s);
+
+// Launchers of the mixed-precision path (vol_mixed.cu).
+cudaError_t launch_to_f32(const double *src, float *dst, int64_t M, cudaStream_t s);
+// N = 7 launches the persistent bulk-copy kernel (2 CTAs per SM); it sets
+// bit 0 of *err if a bounded wait on its copies times out.
+cudaError_t launch_vol_rhs_mixed(int N, ElemRange r, const MixedGeometry &geo,
+                                 const MixedParams &P, const float *q, float *rhs, int *err,
+                                 int num_sms, cudaStream_t s);
 
 // GLL points and differentiation matrix on the host (gll.cpp).
 int gll_diff_matrix(int N, double *D);
@@ -89,7 +119,7 @@ struct DfParams {
     double D[64];      // D for the native fallback
 };
 
-enum class Kernel { Native, DoubleFloat };
+enum class Kernel { Native, DoubleFloat, Mixed };
 
 }  // namespace numa
 
@@ -99,6 +129,8 @@ struct numa_vol {
     int64_t Ne = 0;
     int64_t M = 0;
     int device = 0;
+    int num_sms = 0;
+    int *d_err = nullptr;           // device status word: bit 0 = a bounded wait timed out
     numa_precision prec = NUMA_FP64;
     numa::EosConstants eos{};
     void *d_block = nullptr;        // one allocation: geometry, reference state, D
@@ -108,6 +140,12 @@ struct numa_vol {
     numa::DfGeometry dgeo{};        // double-float path
     numa::DfParams dparams{};
     numa::NativeParams nparams{};
-    double *d_stage = nullptr;      // host entry point: q and rhs staging, 2 * 5 * M
-    cudaStream_t host_stream = nullptr;
+    numa::MixedGeometry mgeo{};     // mixed-precision path
+    numa::MixedParams mparams{};
+    size_t elem = sizeof(double);   // bytes per state/rhs value (4 for NUMA_MIXED)
+    void *d_stage = nullptr;        // host entry point: q and rhs staging, 2 * 5 * M values
+    // host entry point: copy-in, compute and copy-out streams, per-chunk events
+    cudaStream_t host_stream = nullptr, h2d_stream = nullptr, d2h_stream = nullptr;
+    static constexpr int kChunks = 8;
+    cudaEvent_t ev_in[kChunks] = {}, ev_out[kChunks] = {};
 };

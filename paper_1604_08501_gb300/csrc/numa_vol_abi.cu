@@ -2,6 +2,7 @@
 // handle, and dispatch to the kernels.  See include/numa_vol.h.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdint>
 #include <cstring>
@@ -58,7 +59,12 @@ const char *numa_vol_kernel_name(const numa_vol *h) {
                                    "vol_rhs_fp64_kernel<6>", "vol_rhs_fp64_kernel<7>",
                                    "vol_rhs_fp64_kernel<8>"};
     if (!h) return "";
+    static const char *mixed[] = {"", "vol_rhs_mixed_kernel<2>", "vol_rhs_mixed_kernel<3>",
+                                  "vol_rhs_mixed_kernel<4>", "vol_rhs_mixed_kernel<5>",
+                                  "vol_rhs_mixed_kernel<6>", "vol_rhs_mixed_kernel<7>",
+                                  "vol_rhs_mixed_kernel<8>"};
     if (h->kernel == numa::Kernel::DoubleFloat) return "vol_rhs_df64_kernel";
+    if (h->kernel == numa::Kernel::Mixed) return mixed[h->N];
     return native[h->N];
 }
 
@@ -105,6 +111,24 @@ void build_params(numa_vol *h, const double *D) {
                 h->nparams.Dcr[r] = D[ctr * Nq + r];
             }
         }
+    }
+    {
+        numa::MixedParams &m = h->mparams;
+        for (int t = 0; t < 16; ++t) {
+            m.De[t] = static_cast<float>(h->nparams.De[t]);
+            m.Do[t] = static_cast<float>(h->nparams.Do[t]);
+        }
+        for (int t = 0; t < 4; ++t) {
+            m.Dc[t] = static_cast<float>(h->nparams.Dc[t]);
+            m.Dcr[t] = static_cast<float>(h->nparams.Dcr[t]);
+        }
+        for (int k = 0; k < 5; ++k) m.c[k] = static_cast<float>(c[k + 1]);
+        const long double g = h->eos.gamma;
+        m.K = static_cast<float>(std::pow((long double)h->eos.p0, 1.0L - g) *
+                                 std::pow((long double)h->eos.R, g));
+        m.gm1 = static_cast<float>(g - 1.0L);
+        m.gamma = static_cast<float>(g);
+        m.grav = static_cast<float>(h->eos.grav);
     }
     if (h->N != 7) return;
     numa::DfParams &P = h->dparams;
@@ -170,6 +194,41 @@ cudaError_t create_native(numa_vol *h, const numa_geometry *geo, const double *D
     h->geo.A = slots[13];
     h->geo.D = dD;
     h->kernel = numa::Kernel::Native;
+    return cudaSuccess;
+}
+
+// Mixed layout: 12 FP32 arrays (g[0..8], Jinv, rho_ref, theta_ref).
+cudaError_t create_mixed(numa_vol *h, const numa_geometry *geo) {
+    const int64_t P = padded(h->M);
+    h->block_bytes = sizeof(float) * 12 * P;
+    cudaError_t e = cudaMalloc(&h->d_block, h->block_bytes);
+    if (e != cudaSuccess) {
+        h->d_block = nullptr;
+        return e;
+    }
+    double *tmp = nullptr;
+    e = cudaMalloc(&tmp, sizeof(double) * (P > 0 ? P : 1));
+    if (e != cudaSuccess) return e;
+    float *base = static_cast<float *>(h->d_block);
+    float *slots[12];
+    for (int s = 0; s < 12; ++s) slots[s] = base + s * P;
+    const double *src[12] = {geo->g[0], geo->g[1], geo->g[2], geo->g[3], geo->g[4], geo->g[5],
+                             geo->g[6], geo->g[7], geo->g[8], geo->Jinv, geo->rho_ref,
+                             geo->rhotheta_ref};
+    const size_t bytes = sizeof(double) * h->M;
+    for (int s = 0; s < 12 && e == cudaSuccess; ++s) {
+        if (bytes) e = cudaMemcpy(tmp, src[s], bytes, cudaMemcpyDefault);
+        if (e == cudaSuccess) e = numa::launch_to_f32(tmp, slots[s], h->M, 0);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(0);
+    }
+    cudaFree(tmp);
+    if (e != cudaSuccess) return e;
+    for (int s = 0; s < 9; ++s) h->mgeo.g[s] = slots[s];
+    h->mgeo.Jinv = slots[9];
+    h->mgeo.rho_ref = slots[10];
+    h->mgeo.theta_ref = slots[11];
+    h->kernel = numa::Kernel::Mixed;
+    h->elem = sizeof(float);
     return cudaSuccess;
 }
 
@@ -258,9 +317,7 @@ int numa_vol_create(const numa_mesh *mesh, const numa_geometry *geo, const numa_
         if (!geo->g[s]) return fail(NUMA_EINVAL, "numa_vol_create: NULL metric array");
     if (!geo->Jinv || !geo->rho_ref || !geo->rhotheta_ref)
         return fail(NUMA_EINVAL, "numa_vol_create: NULL Jinv or reference array");
-    if (prec == NUMA_MIXED)
-        return fail(NUMA_EUNSUPPORTED, "numa_vol_create: NUMA_MIXED is not implemented");
-    if (prec != NUMA_FP64 && prec != NUMA_DF64)
+    if (prec != NUMA_FP64 && prec != NUMA_DF64 && prec != NUMA_MIXED)
         return fail(NUMA_EINVAL, "numa_vol_create: unknown precision");
     if (prec == NUMA_DF64 && mesh->N != 7)
         return fail(NUMA_EUNSUPPORTED, "numa_vol_create: NUMA_DF64 is implemented for N = 7 only");
@@ -279,12 +336,23 @@ int numa_vol_create(const numa_mesh *mesh, const numa_geometry *geo, const numa_
         delete h;
         return fail_cuda(e, "numa_vol_create: cudaGetDevice");
     }
+    e = cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device);
+    if (e == cudaSuccess) e = cudaMalloc(&h->d_err, 256);
+    if (e == cudaSuccess) e = cudaMemset(h->d_err, 0, 256);
+    if (e != cudaSuccess) {
+        cudaFree(h->d_err);
+        delete h;
+        return fail_cuda(e, "numa_vol_create: status word");
+    }
     double D[(NUMA_MAX_N + 1) * (NUMA_MAX_N + 1)];
     numa::gll_diff_matrix(h->N, D);
 
     build_params(h, D);
     bool use_native = prec == NUMA_FP64;
-    if (!use_native) {
+    if (prec == NUMA_MIXED) {
+        e = create_mixed(h, geo);
+        use_native = false;
+    } else if (!use_native) {
         bool in_range = true;
         e = create_df(h, geo, &in_range);
         if (e == cudaSuccess && !in_range) use_native = true;   // geometry out of range
@@ -292,6 +360,7 @@ int numa_vol_create(const numa_mesh *mesh, const numa_geometry *geo, const numa_
     if (use_native && e == cudaSuccess) e = create_native(h, geo, D);
     if (e != cudaSuccess) {
         cudaFree(h->d_block);
+        cudaFree(h->d_err);
         delete h;
         return fail_cuda(e, "numa_vol_create: upload of geometry");
     }
@@ -303,10 +372,19 @@ int numa_vol_create(const numa_mesh *mesh, const numa_geometry *geo, const numa_
 
 namespace {
 
-cudaError_t launch(numa_vol *h, const double *q, double *rhs, cudaStream_t s) {
+// Elements [e0, e0 + count) of the handle's mesh.
+cudaError_t launch(numa_vol *h, const void *q, void *rhs, int64_t e0, int64_t count,
+                   cudaStream_t s) {
+    const numa::ElemRange r{e0, count, h->M};
+    if (h->kernel == numa::Kernel::Mixed)
+        return numa::launch_vol_rhs_mixed(h->N, r, h->mgeo, h->mparams,
+                                          static_cast<const float *>(q), static_cast<float *>(rhs),
+                                          h->d_err, h->num_sms, s);
     if (h->kernel == numa::Kernel::DoubleFloat)
-        return numa::launch_vol_rhs_df64(h->Ne, h->dgeo, h->dparams, q, rhs, s);
-    return numa::launch_vol_rhs_fp64(h->N, h->Ne, h->geo, h->nparams, q, rhs, s);
+        return numa::launch_vol_rhs_df64(r, h->dgeo, h->dparams, static_cast<const double *>(q),
+                                         static_cast<double *>(rhs), s);
+    return numa::launch_vol_rhs_fp64(h->N, r, h->geo, h->nparams,
+                                     static_cast<const double *>(q), static_cast<double *>(rhs), s);
 }
 
 }  // namespace
@@ -320,26 +398,33 @@ int numa_vol_rhs(numa_vol *h, const void *q, void *rhs, void *stream) {
     if (!q || !rhs) return fail(NUMA_EINVAL, "numa_vol_rhs: NULL q or rhs");
     if (!aligned16(q) || !aligned16(rhs))
         return fail(NUMA_EINVAL, "numa_vol_rhs: q and rhs must be 16-byte aligned");
-    const size_t bytes = sizeof(double) * numa::kFields * h->M;
+    const size_t bytes = h->elem * numa::kFields * h->M;
     if (overlap(q, rhs, bytes)) return fail(NUMA_EINVAL, "numa_vol_rhs: q and rhs overlap");
     if (!is_device_pointer(q) || !is_device_pointer(rhs))
         return fail(NUMA_EINVAL, "numa_vol_rhs: q and rhs must be device pointers");
-    cudaError_t e = launch(h, static_cast<const double *>(q), static_cast<double *>(rhs),
-                           static_cast<cudaStream_t>(stream));
+    cudaError_t e = launch(h, q, rhs, 0, h->Ne, static_cast<cudaStream_t>(stream));
     if (e != cudaSuccess) return fail_cuda(e, "numa_vol_rhs: launch");
     return NUMA_OK;
 }
 
-int numa_vol_rhs_host(numa_vol *h, const double *q, double *rhs) {
+int numa_vol_rhs_host(numa_vol *h, const void *q, void *rhs) {
     g_last_error.clear();
     if (!h) return fail(NUMA_EINVAL, "numa_vol_rhs_host: NULL handle");
     if (h->Ne == 0) return NUMA_OK;
     if (!q || !rhs) return fail(NUMA_EINVAL, "numa_vol_rhs_host: NULL q or rhs");
-    const size_t bytes = sizeof(double) * numa::kFields * h->M;
+    const size_t bytes = h->elem * numa::kFields * h->M;
     if (overlap(q, rhs, bytes)) return fail(NUMA_EINVAL, "numa_vol_rhs_host: q and rhs overlap");
     cudaError_t e = cudaSuccess;
-    if (!h->host_stream) e = cudaStreamCreateWithFlags(&h->host_stream, cudaStreamNonBlocking);
-    if (e != cudaSuccess) return fail_cuda(e, "numa_vol_rhs_host: stream");
+    if (!h->host_stream) {
+        e = cudaStreamCreateWithFlags(&h->host_stream, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->h2d_stream, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->d2h_stream, cudaStreamNonBlocking);
+        for (int c = 0; c < numa_vol::kChunks && e == cudaSuccess; ++c) {
+            e = cudaEventCreateWithFlags(&h->ev_in[c], cudaEventDisableTiming);
+            if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_out[c], cudaEventDisableTiming);
+        }
+        if (e != cudaSuccess) return fail_cuda(e, "numa_vol_rhs_host: streams");
+    }
     if (!h->d_stage) {
         e = cudaMalloc(&h->d_stage, 2 * bytes);
         if (e != cudaSuccess) {
@@ -347,14 +432,48 @@ int numa_vol_rhs_host(numa_vol *h, const double *q, double *rhs) {
             return fail_cuda(e, "numa_vol_rhs_host: staging allocation");
         }
     }
-    double *dq = h->d_stage;
-    double *dr = h->d_stage + numa::kFields * h->M;
-    e = cudaMemcpyAsync(dq, q, bytes, cudaMemcpyHostToDevice, h->host_stream);
-    if (e == cudaSuccess)
-        e = launch(h, dq, dr, h->host_stream);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(rhs, dr, bytes, cudaMemcpyDeviceToHost, h->host_stream);
+    // Chunks of elements flow through three streams: copy-in of chunk c + 1,
+    // compute of chunk c and copy-out of chunk c - 1 overlap.
+    char *dq = static_cast<char *>(h->d_stage);
+    char *dr = dq + bytes;
+    const char *hq = static_cast<const char *>(q);
+    char *hr = static_cast<char *>(rhs);
+    const int64_t n3 = (int64_t)h->Nq * h->Nq * h->Nq;
+    const int chunks = (int)std::min<int64_t>(numa_vol::kChunks, h->Ne);
+    const size_t plane = h->elem * h->M;
+    for (int c = 0; c < chunks && e == cudaSuccess; ++c) {
+        const int64_t e0 = h->Ne * c / chunks, e1 = h->Ne * (c + 1) / chunks;
+        const size_t off = h->elem * e0 * n3, len = h->elem * (e1 - e0) * n3;
+        for (int b = 0; b < numa::kFields && e == cudaSuccess; ++b)
+            e = cudaMemcpyAsync(dq + b * plane + off, hq + b * plane + off, len,
+                                cudaMemcpyHostToDevice, h->h2d_stream);
+        if (e == cudaSuccess) e = cudaEventRecord(h->ev_in[c], h->h2d_stream);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(h->host_stream, h->ev_in[c], 0);
+        if (e == cudaSuccess) e = launch(h, dq, dr, e0, e1 - e0, h->host_stream);
+        if (e == cudaSuccess) e = cudaEventRecord(h->ev_out[c], h->host_stream);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(h->d2h_stream, h->ev_out[c], 0);
+        for (int b = 0; b < numa::kFields && e == cudaSuccess; ++b)
+            e = cudaMemcpyAsync(hr + b * plane + off, dr + b * plane + off, len,
+                                cudaMemcpyDeviceToHost, h->d2h_stream);
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->d2h_stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->host_stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->h2d_stream);
     if (e != cudaSuccess) return fail_cuda(e, "numa_vol_rhs_host");
+    return numa_vol_status(h, h->host_stream);
+}
+
+int numa_vol_status(numa_vol *h, void *stream) {
+    if (!h) return fail(NUMA_EINVAL, "numa_vol_status: NULL handle");
+    int flag = 0;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    cudaError_t e = cudaMemcpyAsync(&flag, h->d_err, sizeof(int), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e == cudaSuccess && flag) e = cudaMemsetAsync(h->d_err, 0, sizeof(int), s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return fail_cuda(e, "numa_vol_status");
+    if (flag) return fail(NUMA_ETIMEOUT, "numa_vol_rhs: a bounded wait on staged copies timed out; "
+                                         "the rhs of the affected elements is incomplete");
     return NUMA_OK;
 }
 
@@ -365,8 +484,15 @@ void numa_vol_destroy(numa_vol *h) {
     if (cur != h->device) cudaSetDevice(h->device);
     cudaDeviceSynchronize();
     if (h->host_stream) cudaStreamDestroy(h->host_stream);
+    if (h->h2d_stream) cudaStreamDestroy(h->h2d_stream);
+    if (h->d2h_stream) cudaStreamDestroy(h->d2h_stream);
+    for (int c = 0; c < numa_vol::kChunks; ++c) {
+        if (h->ev_in[c]) cudaEventDestroy(h->ev_in[c]);
+        if (h->ev_out[c]) cudaEventDestroy(h->ev_out[c]);
+    }
     cudaFree(h->d_stage);
     cudaFree(h->d_block);
+    cudaFree(h->d_err);
     if (cur != h->device) cudaSetDevice(cur);
     delete h;
 }

@@ -155,11 +155,11 @@ __device__ void element_fp64(const DfGeometry &geo, const DfParams &P, const dou
 
 __global__ void __launch_bounds__(N3, 2)
 vol_rhs_df64_kernel(DfGeometry geo, DfParams P, const double *__restrict__ q,
-                    double *__restrict__ rhs, int64_t M) {
+                    double *__restrict__ rhs, int64_t M, int64_t e0) {
     extern __shared__ float2 sbuf[];  // [direction*5 + field][slot], 15 * 512 float2
     const int l = threadIdx.x;
     const int i = l & 7, j = (l >> 3) & 7, k = l >> 6;
-    const int64_t e = blockIdx.x;
+    const int64_t e = e0 + blockIdx.x;
     const int64_t node = e * N3 + l;
 
     // ---- phase 1: state, p', fluxes -----------------------------------
@@ -330,14 +330,14 @@ cudaError_t launch_to_df(const double *src, float2 *dst, int64_t M, double thres
     return cudaGetLastError();
 }
 
-cudaError_t launch_vol_rhs_df64(int64_t Ne, const DfGeometry &geo, const DfParams &P,
+cudaError_t launch_vol_rhs_df64(ElemRange r, const DfGeometry &geo, const DfParams &P,
                                 const double *q, double *rhs, cudaStream_t s) {
-    if (Ne == 0) return cudaSuccess;
+    if (r.count <= 0) return cudaSuccess;
     const size_t smem = sizeof(float2) * kFields * 3 * N3;
     cudaError_t e = cudaFuncSetAttribute(vol_rhs_df64_kernel,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    vol_rhs_df64_kernel<<<(unsigned)Ne, N3, smem, s>>>(geo, P, q, rhs, Ne * N3);
+    vol_rhs_df64_kernel<<<(unsigned)r.count, N3, smem, s>>>(geo, P, q, rhs, r.M, r.e0);
     return cudaGetLastError();
 }
 

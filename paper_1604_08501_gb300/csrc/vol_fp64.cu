@@ -25,27 +25,12 @@
 // sweeps by line (in place), combination by point.
 #include <cuda_runtime.h>
 
+#include "element_sweep.cuh"
 #include "numa_internal.h"
 
 namespace numa {
 
 namespace {
-
-// Shared-memory slot of position n on line `line` (lines of Nq points).  For
-// Nq = 8 an XOR swizzle keeps the 8-byte accesses of all three phases free of
-// bank conflicts; other orders use the plain layout.
-template <int NQ>
-__device__ __forceinline__ int slot(int line, int n) {
-    if constexpr (NQ == 8) return line * 8 + (n ^ ((line & 6) | ((line >> 3) & 1)));
-    else return line * NQ + n;
-}
-
-template <int NQ>
-__device__ __forceinline__ int dir_slot(int d, int i, int j, int k) {
-    if (d == 0) return slot<NQ>(NQ * k + j, i);
-    if (d == 1) return slot<NQ>(NQ * k + i, j);
-    return slot<NQ>(NQ * j + i, k);
-}
 
 // p0 (R Theta / p0)^gamma, the equation of state of Sec. 2.  Not inlined:
 // the rhs kernel calls it only where the series does not apply, and keeping
@@ -81,17 +66,14 @@ constexpr int min_ctas() {
 template <int NQ>
 __global__ void __launch_bounds__(NQ * NQ * NQ, min_ctas<NQ>())
 vol_rhs_fp64_kernel(DeviceGeometry geo, NativeParams P, const double *__restrict__ q,
-                    double *__restrict__ rhs, int64_t M) {
+                    double *__restrict__ rhs, int64_t M, int64_t e0) {
     constexpr int N3 = NQ * NQ * NQ;
     constexpr int NL = NQ * NQ;               // lines per (direction, field)
-    constexpr int HALF = NQ / 2;
-    constexpr bool ODD = (NQ & 1) != 0;
-    constexpr int C = NQ / 2;                 // centre index for odd Nq
     extern __shared__ double sF[];            // [direction*5 + field][slot]
 
     const int l = threadIdx.x;
     const int i = l % NQ, j = (l / NQ) % NQ, k = l / (NQ * NQ);
-    const int64_t node = (int64_t)blockIdx.x * N3 + l;
+    const int64_t node = (e0 + blockIdx.x) * N3 + l;
 
     // ---- phase 1: p', fluxes ----------------------------------------
     const double rho = q[node];
@@ -105,7 +87,7 @@ vol_rhs_fp64_kernel(DeviceGeometry geo, NativeParams P, const double *__restrict
                      g3 = geo.g[3 * d + 2][node];
         const double v = fma(g3, U[2], fma(g2, U[1], g1 * U[0]));
         const double u = v * rinv;
-        const int s = dir_slot<NQ>(d, i, j, k);
+        const int s = dir_slot<NQ, double>(d, i, j, k);
         double *F = sF + d * kFields * N3 + s;
         F[0 * N3] = v;
         F[1 * N3] = fma(U[0], u, g1 * pp);
@@ -116,37 +98,8 @@ vol_rhs_fp64_kernel(DeviceGeometry geo, NativeParams P, const double *__restrict
     __syncthreads();
 
     // ---- phase 2: even-odd sweeps, one line per task, in place --------
-    for (int item = l; item < 3 * kFields * NL; item += N3) {
-        double *buf = sF + (item / NL) * N3;
-        const int line = item % NL;
-        double F[NQ];
-#pragma unroll
-        for (int n = 0; n < NQ; ++n) F[n] = buf[slot<NQ>(line, n)];
-        double E[HALF > 0 ? HALF : 1], O[HALF > 0 ? HALF : 1];
-#pragma unroll
-        for (int m = 0; m < HALF; ++m) {
-            E[m] = F[m] + F[NQ - 1 - m];
-            O[m] = F[m] - F[NQ - 1 - m];
-        }
-        double Sc = 0.0;
-#pragma unroll
-        for (int r = 0; r < HALF; ++r) {
-            double a = ODD ? P.Dc[r] * F[C] : 0.0, b = 0.0;
-#pragma unroll
-            for (int m = 0; m < HALF; ++m) {
-                a = fma(P.De[r * HALF + m], E[m], a);
-                b = fma(P.Do[r * HALF + m], O[m], b);
-            }
-            buf[slot<NQ>(line, r)] = b + a;
-            buf[slot<NQ>(line, NQ - 1 - r)] = b - a;
-        }
-        if (ODD) {
-            // centre row: D[c][N-m] = -D[c][m] and D[c][c] = 0, so S_c = sum_m D[c][m] O_m
-#pragma unroll
-            for (int m = 0; m < HALF; ++m) Sc = fma(P.Dcr[m], O[m], Sc);
-            buf[slot<NQ>(line, C)] = Sc;
-        }
-    }
+    for (int item = l; item < 3 * kFields * NL; item += N3)
+        sweep_line<NQ>(sF + (item / NL) * N3, item % NL, P);
     __syncthreads();
 
     // ---- phase 3: combine, scale, gravity, store ----------------------
@@ -154,9 +107,9 @@ vol_rhs_fp64_kernel(DeviceGeometry geo, NativeParams P, const double *__restrict
     const double drho = rho - geo.rho_ref[node];
 #pragma unroll
     for (int b = 0; b < kFields; ++b) {
-        const double R = sF[(0 * kFields + b) * N3 + dir_slot<NQ>(0, i, j, k)] +
-                         sF[(1 * kFields + b) * N3 + dir_slot<NQ>(1, i, j, k)] +
-                         sF[(2 * kFields + b) * N3 + dir_slot<NQ>(2, i, j, k)];
+        const double R = sF[(0 * kFields + b) * N3 + dir_slot<NQ, double>(0, i, j, k)] +
+                         sF[(1 * kFields + b) * N3 + dir_slot<NQ, double>(1, i, j, k)] +
+                         sF[(2 * kFields + b) * N3 + dir_slot<NQ, double>(2, i, j, k)];
         double v = -Jinv * R;
         if (b == 3) v = fma(-drho, P.eos.grav, v);
         rhs[b * M + node] = v;
@@ -164,7 +117,7 @@ vol_rhs_fp64_kernel(DeviceGeometry geo, NativeParams P, const double *__restrict
 }
 
 template <int NQ>
-cudaError_t launch_nq(int64_t Ne, const DeviceGeometry &geo, const NativeParams &P,
+cudaError_t launch_nq(ElemRange r, const DeviceGeometry &geo, const NativeParams &P,
                       const double *q, double *rhs, cudaStream_t s) {
     constexpr int N3 = NQ * NQ * NQ;
     const size_t smem = sizeof(double) * kFields * 3 * N3;
@@ -173,7 +126,7 @@ cudaError_t launch_nq(int64_t Ne, const DeviceGeometry &geo, const NativeParams 
     cudaError_t e = cudaFuncSetAttribute(vol_rhs_fp64_kernel<NQ>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    vol_rhs_fp64_kernel<NQ><<<(unsigned)Ne, N3, smem, s>>>(geo, P, q, rhs, Ne * N3);
+    vol_rhs_fp64_kernel<NQ><<<(unsigned)r.count, N3, smem, s>>>(geo, P, q, rhs, r.M, r.e0);
     return cudaGetLastError();
 }
 
@@ -197,18 +150,18 @@ cudaError_t launch_reference_eos(const double *theta_ref, double *w, double *A, 
     return cudaGetLastError();
 }
 
-cudaError_t launch_vol_rhs_fp64(int N, int64_t Ne, const DeviceGeometry &geo,
+cudaError_t launch_vol_rhs_fp64(int N, ElemRange r, const DeviceGeometry &geo,
                                 const NativeParams &P, const double *q, double *rhs,
                                 cudaStream_t s) {
-    if (Ne == 0) return cudaSuccess;
+    if (r.count <= 0) return cudaSuccess;
     switch (N) {
-        case 1: return launch_nq<2>(Ne, geo, P, q, rhs, s);
-        case 2: return launch_nq<3>(Ne, geo, P, q, rhs, s);
-        case 3: return launch_nq<4>(Ne, geo, P, q, rhs, s);
-        case 4: return launch_nq<5>(Ne, geo, P, q, rhs, s);
-        case 5: return launch_nq<6>(Ne, geo, P, q, rhs, s);
-        case 6: return launch_nq<7>(Ne, geo, P, q, rhs, s);
-        case 7: return launch_nq<8>(Ne, geo, P, q, rhs, s);
+        case 1: return launch_nq<2>(r, geo, P, q, rhs, s);
+        case 2: return launch_nq<3>(r, geo, P, q, rhs, s);
+        case 3: return launch_nq<4>(r, geo, P, q, rhs, s);
+        case 4: return launch_nq<5>(r, geo, P, q, rhs, s);
+        case 5: return launch_nq<6>(r, geo, P, q, rhs, s);
+        case 6: return launch_nq<7>(r, geo, P, q, rhs, s);
+        case 7: return launch_nq<8>(r, geo, P, q, rhs, s);
         default: return cudaErrorInvalidValue;
     }
 }

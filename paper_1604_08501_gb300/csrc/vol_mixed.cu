@@ -1,0 +1,295 @@
+// Mixed-precision element volume term (NUMA_MIXED), orders N = 1..7.
+//
+// The operation of Sec. 2, Eq. (2) (sign and flux form of the paper's r/s
+// subroutines, Sec. 3) on FP32 data:
+//   state   (rho', U1, U2, U3, Theta'), the perturbations rho' = rho - rho_ref and
+//           Theta' = Theta - Theta_ref, so no significant bits go to the large
+//           hydrostatic part;
+//   geometry and reference state in FP32 (rounded once at create time);
+//   fluxes, sweeps and rhs in FP32.
+// p' = p(Theta) - p(Theta_ref) = p_ref ((1 + x)^gamma - 1), x = Theta'/Theta_ref,
+// is evaluated from Theta' directly (binomial series for |x| <= 1/64,
+// expm1(gamma log1p(x)) beyond), so it has no cancellation and FP32 suffices:
+// relative error ~1e-7.  p_ref/Theta_ref = K Theta_ref^(gamma - 1) with
+// K = p0^(1 - gamma) R^gamma is recomputed per point instead of being stored,
+// which keeps the traffic at the algorithmic 88 bytes per point
+// (5 + 9 + 1 + 2 arrays read, 5 written, 4 bytes each).  The kernel is bound by
+// HBM bandwidth, and the extra arithmetic is free.
+//
+// Structure as in vol_fp64.cu: fluxes by point into shared memory, even-odd D
+// sweeps by line in place, combination by point.  Two kernels:
+//  * vol_rhs_mixed_kernel<Nq>: one CTA of Nq^3 threads per element, direct loads.
+//  * vol_rhs_mixed_bulk_kernel (Nq = 8): persistent CTAs, 2 per SM.  The element
+//    slab (17 arrays x 2 KB, contiguous per array and element) is staged in
+//    shared memory by bulk asynchronous copies (cp.async.bulk) completing on an
+//    mbarrier.  Each CTA prefetches its next element while it computes the
+//    current one, so the loads stay in flight during the arithmetic.  Waits are
+//    bounded: on a timeout the kernel sets bit 0 of *err, drains its copies
+//    (again bounded) and returns.
+#include <cuda_runtime.h>
+
+#include "bulk_copy.cuh"
+#include "element_sweep.cuh"
+#include "numa_internal.h"
+
+namespace numa {
+
+namespace {
+
+__device__ __forceinline__ float pressure_perturbation_f32(float thp, float th0,
+                                                           const MixedParams &P) {
+    if (th0 > 0.0f) {
+        const float w = 1.0f / th0;
+        const float A = P.K * exp2f(P.gm1 * log2f(th0));      // p(Theta_ref) / Theta_ref
+        const float x = thp * w;
+        if (fabsf(x) <= 0.015625f) {
+            float g = P.c[4];
+#pragma unroll
+            for (int k = 3; k >= 0; --k) g = fmaf(g, x, P.c[k]);   // sum_k c_{k+1} x^k
+            return (A * thp) * g;
+        }
+        return (A * th0) * expm1f(P.gamma * log1pf(x));
+    }
+    // Theta_ref = 0 (the paper's full-pressure form): p' = p(Theta').
+    return P.K * powf(thp, P.gamma);
+}
+
+template <int NQ>
+constexpr int mixed_min_ctas() {
+    constexpr int n = 1536 / (NQ * NQ * NQ);
+    return n < 1 ? 1 : (n > 32 ? 32 : n);
+}
+
+template <int NQ>
+__global__ void __launch_bounds__(NQ * NQ * NQ, mixed_min_ctas<NQ>())
+vol_rhs_mixed_kernel(MixedGeometry geo, MixedParams P, const float *__restrict__ q,
+                     float *__restrict__ rhs, int64_t M, int64_t e0) {
+    constexpr int N3 = NQ * NQ * NQ;
+    constexpr int NL = NQ * NQ;
+    extern __shared__ float sFm[];            // [direction*5 + field][slot]
+
+    const int l = threadIdx.x;
+    const int i = l % NQ, j = (l / NQ) % NQ, k = l / (NQ * NQ);
+    const int64_t node = (e0 + blockIdx.x) * N3 + l;
+
+    // ---- phase 1: p', fluxes ----------------------------------------
+    const float rp = q[node];
+    const float U[3] = {q[M + node], q[2 * M + node], q[3 * M + node]};
+    const float thp = q[4 * M + node];
+    const float th0 = geo.theta_ref[node];
+    const float rho = geo.rho_ref[node] + rp;
+    const float Th = th0 + thp;
+    const float pp = pressure_perturbation_f32(thp, th0, P);
+    const float rinv = 1.0f / rho;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        const float g1 = geo.g[3 * d][node], g2 = geo.g[3 * d + 1][node],
+                    g3 = geo.g[3 * d + 2][node];
+        const float v = fmaf(g3, U[2], fmaf(g2, U[1], g1 * U[0]));
+        const float u = v * rinv;
+        float *F = sFm + d * kFields * N3 + dir_slot<NQ, float>(d, i, j, k);
+        F[0 * N3] = v;
+        F[1 * N3] = fmaf(U[0], u, g1 * pp);
+        F[2 * N3] = fmaf(U[1], u, g2 * pp);
+        F[3 * N3] = fmaf(U[2], u, g3 * pp);
+        F[4 * N3] = Th * u;
+    }
+    __syncthreads();
+
+    // ---- phase 2: even-odd sweeps, one line per task, in place --------
+    for (int item = l; item < 3 * kFields * NL; item += N3)
+        sweep_line<NQ>(sFm + (item / NL) * N3, item % NL, P);
+    __syncthreads();
+
+    // ---- phase 3: combine, scale, gravity, store ----------------------
+    const float Jinv = geo.Jinv[node];
+#pragma unroll
+    for (int b = 0; b < kFields; ++b) {
+        const float R = sFm[(0 * kFields + b) * N3 + dir_slot<NQ, float>(0, i, j, k)] +
+                        sFm[(1 * kFields + b) * N3 + dir_slot<NQ, float>(1, i, j, k)] +
+                        sFm[(2 * kFields + b) * N3 + dir_slot<NQ, float>(2, i, j, k)];
+        float v = -Jinv * R;
+        if (b == 3) v = fmaf(-rp, P.grav, v);
+        rhs[b * M + node] = v;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Nq = 8, persistent, bulk-copy staged.
+// ---------------------------------------------------------------------------
+constexpr int kSlabArrays = 17;                       // 5 state + 9 metric + Jinv + 2 reference
+constexpr int kPts = 512;
+constexpr uint32_t kSlabBytes = kPts * sizeof(float);  // one array of one element
+constexpr size_t kBulkSmem = sizeof(float) * (2 * kSlabArrays + 3 * kFields) * kPts;
+
+__device__ __forceinline__ void issue_slab(int64_t e, int64_t M, const float *q,
+                                           const MixedGeometry &geo, float *st, uint64_t *bar) {
+    mbar_arrive_expect_tx(bar, kSlabArrays * kSlabBytes);
+    const int64_t off = e * kPts;
+#pragma unroll
+    for (int a = 0; a < kFields; ++a) bulk_g2s(st + a * kPts, q + a * M + off, kSlabBytes, bar);
+#pragma unroll
+    for (int a = 0; a < 9; ++a) bulk_g2s(st + (kFields + a) * kPts, geo.g[a] + off, kSlabBytes, bar);
+    bulk_g2s(st + 14 * kPts, geo.Jinv + off, kSlabBytes, bar);
+    bulk_g2s(st + 15 * kPts, geo.rho_ref + off, kSlabBytes, bar);
+    bulk_g2s(st + 16 * kPts, geo.theta_ref + off, kSlabBytes, bar);
+}
+
+__global__ void __launch_bounds__(kPts, 2)
+vol_rhs_mixed_bulk_kernel(MixedGeometry geo, MixedParams P, const float *__restrict__ q,
+                          float *__restrict__ rhs, int64_t M, int64_t e0, int64_t e_end,
+                          int *err) {
+    constexpr int NQ = 8;
+    extern __shared__ __align__(128) float smem_f[];
+    __shared__ __align__(8) uint64_t bar[2];
+    float *const stage0 = smem_f;
+    float *const stage1 = smem_f + kSlabArrays * kPts;
+    float *sF = smem_f + 2 * kSlabArrays * kPts;
+
+    const int l = threadIdx.x;
+    const int i = l & 7, j = (l >> 3) & 7, k = l >> 6;
+    if (l == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+
+    uint32_t parity0 = 0u, parity1 = 0u;
+    bool pending0 = false, pending1 = false;   // meaningful in thread 0 only
+    int64_t e = e0 + blockIdx.x;
+    if (l == 0 && e < e_end) {
+        issue_slab(e, M, q, geo, stage0, &bar[0]);
+        pending0 = true;
+    }
+    int buf = 0;
+    bool failed = false;
+    for (; e < e_end; e += gridDim.x) {
+        const int64_t en = e + gridDim.x;
+        if (l == 0 && en < e_end) {
+            // The other stage was last read before the closing barrier of the
+            // previous iteration; order those reads before the async writes.
+            fence_proxy_async();
+            issue_slab(en, M, q, geo, buf ? stage0 : stage1, buf ? &bar[0] : &bar[1]);
+            if (buf) pending0 = true;
+            else pending1 = true;
+        }
+        const bool ok = bulk_wait(buf ? &bar[1] : &bar[0], buf ? parity1 : parity0);
+        if (__syncthreads_or(!ok)) {
+            failed = true;
+            break;
+        }
+        if (buf) {
+            parity1 ^= 1u;
+            pending1 = false;
+        } else {
+            parity0 ^= 1u;
+            pending0 = false;
+        }
+        const float *st = buf ? stage1 : stage0;
+
+        // ---- phase 1: p', fluxes ------------------------------------
+        const float rp = st[0 * kPts + l];
+        const float U[3] = {st[1 * kPts + l], st[2 * kPts + l], st[3 * kPts + l]};
+        const float thp = st[4 * kPts + l];
+        const float th0 = st[16 * kPts + l];
+        const float rho = st[15 * kPts + l] + rp;
+        const float Th = th0 + thp;
+        const float pp = pressure_perturbation_f32(thp, th0, P);
+        const float rinv = 1.0f / rho;
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            const float g1 = st[(kFields + 3 * d) * kPts + l];
+            const float g2 = st[(kFields + 3 * d + 1) * kPts + l];
+            const float g3 = st[(kFields + 3 * d + 2) * kPts + l];
+            const float v = fmaf(g3, U[2], fmaf(g2, U[1], g1 * U[0]));
+            const float u = v * rinv;
+            float *F = sF + d * kFields * kPts + dir_slot<NQ, float>(d, i, j, k);
+            F[0 * kPts] = v;
+            F[1 * kPts] = fmaf(U[0], u, g1 * pp);
+            F[2 * kPts] = fmaf(U[1], u, g2 * pp);
+            F[3 * kPts] = fmaf(U[2], u, g3 * pp);
+            F[4 * kPts] = Th * u;
+        }
+        const float Jinv = st[14 * kPts + l];
+        __syncthreads();
+
+        // ---- phase 2: even-odd sweeps ---------------------------------
+        for (int item = l; item < 3 * kFields * 64; item += kPts)
+            sweep_line<NQ>(sF + (item >> 6) * kPts, item & 63, P);
+        __syncthreads();
+
+        // ---- phase 3: combine, scale, gravity, store ------------------
+        const int64_t node = e * kPts + l;
+#pragma unroll
+        for (int b = 0; b < kFields; ++b) {
+            const float R = sF[(0 * kFields + b) * kPts + dir_slot<NQ, float>(0, i, j, k)] +
+                            sF[(1 * kFields + b) * kPts + dir_slot<NQ, float>(1, i, j, k)] +
+                            sF[(2 * kFields + b) * kPts + dir_slot<NQ, float>(2, i, j, k)];
+            float v = -Jinv * R;
+            if (b == 3) v = fmaf(-rp, P.grav, v);
+            rhs[b * M + node] = v;
+        }
+        // No barrier here: this element's stage was last read in phase 1 (before
+        // the barrier after it), and the barrier after the next wait orders this
+        // phase 3's reads of sF before the next phase 1 writes it.
+        buf ^= 1;
+    }
+    if (failed && l == 0) {
+        atomicOr(err, 1);
+        // Drain the copies still in flight into this CTA's shared memory.
+        if (pending0) bulk_wait(&bar[0], parity0);
+        if (pending1) bulk_wait(&bar[1], parity1);
+    }
+}
+
+template <int NQ>
+cudaError_t launch_nq(ElemRange r, const MixedGeometry &geo, const MixedParams &P, const float *q,
+                      float *rhs, cudaStream_t s) {
+    constexpr int N3 = NQ * NQ * NQ;
+    const size_t smem = sizeof(float) * kFields * 3 * N3;
+    vol_rhs_mixed_kernel<NQ><<<(unsigned)r.count, N3, smem, s>>>(geo, P, q, rhs, r.M, r.e0);
+    return cudaGetLastError();
+}
+
+__global__ void to_f32_kernel(const double *__restrict__ src, float *__restrict__ dst, int64_t M) {
+    for (int64_t m = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; m < M;
+         m += (int64_t)gridDim.x * blockDim.x)
+        dst[m] = __double2float_rn(src[m]);
+}
+
+}  // namespace
+
+cudaError_t launch_to_f32(const double *src, float *dst, int64_t M, cudaStream_t s) {
+    if (M == 0) return cudaSuccess;
+    to_f32_kernel<<<1216, 256, 0, s>>>(src, dst, M);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_vol_rhs_mixed(int N, ElemRange r, const MixedGeometry &geo,
+                                 const MixedParams &P, const float *q, float *rhs, int *err,
+                                 int num_sms, cudaStream_t s) {
+    if (r.count <= 0) return cudaSuccess;
+    if (N == 7) {
+        cudaError_t e = cudaFuncSetAttribute(vol_rhs_mixed_bulk_kernel,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)kBulkSmem);
+        if (e != cudaSuccess) return e;
+        const int64_t ctas = r.count < 2 * (int64_t)num_sms ? r.count : 2 * (int64_t)num_sms;
+        vol_rhs_mixed_bulk_kernel<<<(unsigned)ctas, kPts, kBulkSmem, s>>>(
+            geo, P, q, rhs, r.M, r.e0, r.e0 + r.count, err);
+        return cudaGetLastError();
+    }
+    switch (N) {
+        case 1: return launch_nq<2>(r, geo, P, q, rhs, s);
+        case 2: return launch_nq<3>(r, geo, P, q, rhs, s);
+        case 3: return launch_nq<4>(r, geo, P, q, rhs, s);
+        case 4: return launch_nq<5>(r, geo, P, q, rhs, s);
+        case 5: return launch_nq<6>(r, geo, P, q, rhs, s);
+        case 6: return launch_nq<7>(r, geo, P, q, rhs, s);
+        case 7: return launch_nq<8>(r, geo, P, q, rhs, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace numa

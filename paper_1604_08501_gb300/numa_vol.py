@@ -53,7 +53,8 @@ class VolumeTerm:
     """One mesh on the current CUDA device (numa_vol_create ... numa_vol_destroy).
 
     precision: "fp64" (every operation on the FP64 pipe), "df64" (double-float
-    arithmetic on the FP32 pipes, N = 7) or "mixed"."""
+    arithmetic on the FP32 pipes, N = 7) or "mixed" (FP32 perturbation state,
+    see workload.perturbation_state)."""
 
     def __init__(self, N: int, num_elements: int, g, Jinv, rho_ref, rhotheta_ref,
                  p0: float, R: float, cp: float, grav: float, precision: str = "fp64"):
@@ -63,6 +64,7 @@ class VolumeTerm:
         self.Nq = self.N + 1
         self.M = self.Ne * self.Nq ** 3
         self.precision = precision
+        self.dtype_name = "float32" if precision == "mixed" else "float64"
         keep: list = []
         geo = _lib.numa_geometry()
         g = list(g)
@@ -97,19 +99,25 @@ class VolumeTerm:
         """The kernel numa_vol_rhs launches for this handle."""
         return _lib.load().numa_vol_kernel_name(self.handle).decode()
 
+    def _torch_dtype(self):
+        import torch
+        return torch.float32 if self.dtype_name == "float32" else torch.float64
+
     def rhs(self, q, out=None, stream=None):
         """Enqueue rhs = volume term of q on ``stream`` (default: torch's current
-        stream).  q and out are (5, M) float64 CUDA tensors."""
+        stream).  q and out are (5, M) CUDA tensors: float64 for "fp64" and
+        "df64", float32 perturbation state (rho', U1, U2, U3, Theta') for "mixed"."""
         import torch
-        if not (isinstance(q, torch.Tensor) and q.is_cuda and q.dtype == torch.float64):
-            raise TypeError("q must be a float64 CUDA tensor")
+        dt = self._torch_dtype()
+        if not (isinstance(q, torch.Tensor) and q.is_cuda and q.dtype == dt):
+            raise TypeError(f"q must be a {dt} CUDA tensor")
         if q.numel() != NFIELDS * self.M or not q.is_contiguous():
             raise ValueError(f"q must be contiguous with {NFIELDS} x {self.M} entries")
         if out is None:
-            out = torch.empty((NFIELDS, self.M), dtype=torch.float64, device=q.device)
-        elif not (out.is_cuda and out.dtype == torch.float64 and out.is_contiguous()
+            out = torch.empty((NFIELDS, self.M), dtype=dt, device=q.device)
+        elif not (out.is_cuda and out.dtype == dt and out.is_contiguous()
                   and out.numel() == NFIELDS * self.M):
-            raise ValueError("out must be a contiguous float64 CUDA tensor like q")
+            raise ValueError("out must be a contiguous CUDA tensor like q")
         if stream is None:
             stream = torch.cuda.current_stream(q.device)
         s = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
@@ -120,26 +128,35 @@ class VolumeTerm:
     def rhs_host(self, q, out=None):
         """Volume term of a host state through numa_vol_rhs_host (host-to-device
         copy, kernel, device-to-host copy; synchronous).  Accepts numpy arrays or
-        CPU torch tensors (pinned memory copies fastest) and returns ``out``."""
+        CPU torch tensors of the handle's state type (pinned memory copies
+        fastest) and returns ``out``."""
         import torch
         if isinstance(q, torch.Tensor):
-            if q.is_cuda or q.dtype != torch.float64 or not q.is_contiguous():
-                raise TypeError("q must be a contiguous float64 CPU tensor")
+            if q.is_cuda or q.dtype != self._torch_dtype() or not q.is_contiguous():
+                raise TypeError("q must be a contiguous CPU tensor of the handle's type")
             qp = q.data_ptr()
             if out is None:
-                out = torch.empty((NFIELDS, self.M), dtype=torch.float64,
-                                  pin_memory=q.is_pinned())
+                out = torch.empty((NFIELDS, self.M), dtype=q.dtype, pin_memory=q.is_pinned())
             op = out.data_ptr()
         else:
-            q = np.ascontiguousarray(q, dtype=np.float64)
+            q = np.ascontiguousarray(q, dtype=self.dtype_name)
             qp = q.ctypes.data
             if out is None:
-                out = np.empty((NFIELDS, self.M))
+                out = np.empty((NFIELDS, self.M), dtype=self.dtype_name)
             op = out.ctypes.data if isinstance(out, np.ndarray) else out.data_ptr()
         if int(np.prod(q.shape)) != NFIELDS * self.M:
             raise ValueError(f"q must have {NFIELDS} x {self.M} entries")
         check(_lib.load().numa_vol_rhs_host(self.handle, C.c_void_p(qp), C.c_void_p(op)))
         return out
+
+    def status(self, stream=None) -> None:
+        """numa_vol_status: raise NumaError(NUMA_ETIMEOUT) if a kernel enqueued on
+        this handle gave up a bounded wait (reads and clears the status word)."""
+        import torch
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        s = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+        check(_lib.load().numa_vol_status(self.handle, C.c_void_p(s)))
 
     def close(self) -> None:
         if getattr(self, "_h", None) is not None and self._h.value:

@@ -216,6 +216,16 @@ def perturbed_state(mesh: Mesh, rho_ref, rhotheta_ref, seed: int,
     return q
 
 
+def perturbation_state(q: np.ndarray, rho_ref: np.ndarray, rhotheta_ref: np.ndarray) -> np.ndarray:
+    """The FP32 state a mixed-precision handle takes: (rho - rho_ref, U1, U2, U3,
+    Theta - Theta_ref), differences formed in FP64 and then rounded once."""
+    out = np.empty(q.shape, dtype=np.float32)
+    out[0] = q[0] - rho_ref
+    out[1:4] = q[1:4]
+    out[4] = q[4] - rhotheta_ref
+    return out
+
+
 @dataclass
 class Workload:
     """Everything one evaluation of the volume term needs."""
@@ -239,6 +249,10 @@ class Workload:
     @property
     def M(self):
         return self.mesh.M
+
+    def q_mixed(self) -> np.ndarray:
+        """The state in the FP32 perturbation form of the mixed-precision mode."""
+        return perturbation_state(self.q, self.rho_ref, self.rhotheta_ref)
 
     def problem(self) -> dict:
         """Geometry and constants in the dict form the oracle and the binding take."""

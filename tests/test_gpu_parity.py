@@ -174,7 +174,7 @@ def test_invalid_pointers_are_rejected_and_context_survives():
         assert_parity(res.cpu().numpy(), oracle.vol_rhs_o2(prob, w.q))
     with pytest.raises(NumaError):
         VolumeTerm(3, 1, [np.ones(64)] * 9, np.ones(64), np.ones(64), np.ones(64),
-                   p0=1e5, R=287.0, cp=1004.0, grav=9.8, precision="mixed").close()
+                   p0=1e5, R=287.0, cp=1004.0, grav=9.8, precision="df64").close()
 
 
 def test_handles_of_different_orders_interleave():
