@@ -20,6 +20,8 @@ vol_rhs_o2(prob, q)     fluxes once per node, then the D contractions.
 vol_rhs_points(prob, q, ids)  Eq. (2) at selected nodes only.
 vol_rhs_abs(prob, q)    running error bound |Jinv| sum |D| |F| per point.
 condition_numbers(prob, q)  per field max(bound) / max|rhs|.
+lsrk(prob, q, dt, n)    n steps of the 5-stage 4th-order 2N-storage Runge-Kutta
+                        scheme (Carpenter-Kennedy 1994) on dq/dt = volume term.
 
 ``prob`` is a dict with keys N, Ne, g (9 x M), Jinv, rho_ref, rhotheta_ref
 (each M = Ne*(N+1)^3 doubles, [e][k][j][i] order) and constants p0, R, cp,
@@ -66,6 +68,10 @@ def _configure(lib):
     lib.oracle_vol_rhs_points.argtypes = [C.POINTER(_Problem), _DP, C.c_int64,
                                           C.POINTER(C.c_int64), _DP]
     lib.oracle_vol_rhs_abs.argtypes = [C.POINTER(_Problem), _DP, _DP]
+    lib.oracle_lsrk_coefficients.argtypes = [_DP, _DP, _DP]
+    lib.oracle_lsrk.argtypes = [C.POINTER(_Problem), _DP, C.c_double, C.c_int, C.c_int]
+    lib.oracle_lsrk_scalar.argtypes = [C.c_double, C.c_double, C.c_double, C.c_int]
+    lib.oracle_lsrk_scalar.restype = C.c_double
     lib.oracle_max_threads.restype = C.c_int
     return lib
 
@@ -181,6 +187,26 @@ def vol_rhs_abs(prob: dict, q) -> np.ndarray:
     return out
 
 
+def lsrk_coefficients():
+    """(A, B, C) of the five-stage fourth-order 2N-storage Runge-Kutta scheme."""
+    A, B, Cc = np.zeros(5), np.zeros(5), np.zeros(5)
+    _load().oracle_lsrk_coefficients(_ptr(A), _ptr(B), _ptr(Cc))
+    return A, B, Cc
+
+
+def lsrk(prob: dict, q, dt: float, nsteps: int, nthreads: int = 0) -> np.ndarray:
+    """q advanced by nsteps low-storage RK steps of dq/dt = volume term (a copy)."""
+    b = _Bound(prob)
+    out = np.array(b.state(q), dtype=np.float64, copy=True)
+    if _load().oracle_lsrk(C.byref(b.s), _ptr(out), float(dt), int(nsteps), int(nthreads)) != 0:
+        raise RuntimeError("oracle LSRK failed")
+    return out
+
+
+def lsrk_scalar(lam: float, y0: float, dt: float, nsteps: int) -> float:
+    return _load().oracle_lsrk_scalar(float(lam), float(y0), float(dt), int(nsteps))
+
+
 def condition_numbers(prob: dict, q, rhs=None) -> np.ndarray:
     """Per field: max of the running error bound over max |rhs|."""
     ab = vol_rhs_abs(prob, q)
@@ -201,4 +227,5 @@ def vol_rhs_points(prob: dict, q, node_ids) -> np.ndarray:
 
 
 __all__ = ["gll_nodes", "diff_matrix", "pressure", "vol_rhs_o1", "vol_rhs_o2",
-           "vol_rhs_points", "vol_rhs_abs", "condition_numbers", "max_threads", "build_oracle"]
+           "vol_rhs_points", "vol_rhs_abs", "condition_numbers", "lsrk", "lsrk_coefficients",
+           "lsrk_scalar", "max_threads", "build_oracle"]

@@ -8,6 +8,7 @@ import subprocess
 import pytest
 
 import oracle
+import test_oracle_lsrk as lsrk_pins
 import test_oracle_pins as pins
 
 SRC = os.path.join(os.path.dirname(oracle.__file__), "numa_oracle.c")
@@ -42,6 +43,10 @@ MUTATIONS = [
     ("D diagonal sign", "if (m != n) v += 1.0L /", "if (m != n) v -= 1.0L /", None),
     ("GLL Newton step sign", "x -= dx;", "x += dx;", None),
     ("pointwise evaluator drops Jinv", "double v = -P->Jinv[node] * s[b];", "double v = -s[b];", None),
+    ("LSRK A coefficient digit", "-2404267990393.0 / 2016746695238.0", "-2404267990393.0 / 2016746695239.0", None),
+    ("LSRK B coefficient sign", "    5161836677717.0 / 13612068292357.0", "    -5161836677717.0 / 13612068292357.0", None),
+    ("LSRK stage update order", "q[m] = q[m] + LSRK_B[s] * dq[m];", "q[m] = q[m] + LSRK_A[s] * dq[m];", None),
+    ("LSRK register not carried", "dq[m] = LSRK_A[s] * dq[m] + dt * rhs[m];", "dq[m] = dt * rhs[m];", None),
 ]
 
 PIN_CHECKS = [
@@ -56,6 +61,10 @@ PIN_CHECKS = [
     lambda: [pins.test_forms_agree_on_warped_mesh(N, 2) for N in (2, 4)],
     lambda: pins.test_element_independence(),
     lambda: pins.test_axis_permutation_symmetry(2),
+    lambda: lsrk_pins.test_coefficients_satisfy_fourth_order_conditions(),
+    lambda: lsrk_pins.test_scalar_convergence_is_fourth_order(),
+    lambda: lsrk_pins.test_lsrk_one_step_matches_explicit_stages(),
+    lambda: lsrk_pins.test_lsrk_converges_at_fourth_order_on_the_volume_term(2, 2.0),
 ]
 
 
