@@ -397,6 +397,80 @@ def run_gpu(args):
     return 0
 
 
+def run_batched(args):
+    """The batched workload: 64 independent instances (N from {3,4,5,7},
+    512..32768 elements) advanced by 10 low-storage RK steps at dt = 0.01 s in one
+    graph-captured persistent launch.  Metric: volume-term evaluations per
+    second, in GDOF/s (points x 5 stages x steps / time)."""
+    import torch
+    rank, local, world = dist_setup("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    from paper_1604_08501_gb300 import build as lib_build
+    from paper_1604_08501_gb300 import workload as wl
+    from paper_1604_08501_gb300.numa_vol import Batch, VolumeTerm
+    lib_build.build()
+    plan = wl.batch_plan(count=args.instances)
+    works = [wl.make_workload(N, n, seed=seed) for N, n, seed in plan]
+    nsteps, dt = 10, 0.01
+    out = {}
+    for prec in args.precisions:
+        if prec not in ("fp64", "mixed"):
+            continue
+        vts, states, points = [], [], 0
+        for w in works:
+            vts.append(VolumeTerm.from_problem(w.problem(), precision=prec))
+            q0 = w.q_mixed() if prec == "mixed" else w.q
+            states.append(torch.from_numpy(q0).to(dev))
+            points += w.M
+        b = Batch(prec)
+        for vt, q in zip(vts, states):
+            b.add(vt, q)
+        b.autotune()
+        stream = torch.cuda.current_stream(dev)
+        for _ in range(args.warmup):
+            b.advance(nsteps, dt, stream)
+        torch.cuda.synchronize(dev)
+        sampler = ClockSampler(gpu_id_for(local)) if rank == 0 else None
+        if sampler:
+            sampler.start()
+        t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        barrier(dev)
+        t0.record(stream)
+        for _ in range(args.steps):
+            b.advance(nsteps, dt, stream)
+        t1.record(stream)
+        torch.cuda.synchronize(dev)
+        barrier(dev)
+        clocks = sampler.stop() if sampler else None
+        ms = t0.elapsed_time(t1) / args.steps
+        evals = points * 5 * nsteps
+        value, tmax = aggregate(evals * args.steps, ms * 1e-3 * args.steps, dev)
+        out[prec] = {"value": value / 1e9, "ms_per_launch": tmax * 1e3 / args.steps,
+                     "points": points, "instances": len(plan),
+                     "tiles": {str(nq): b.tile(nq) for nq in (4, 5, 6, 8)}, "clocks": clocks}
+        b.close()
+        for vt in vts:
+            vt.close()
+        del states
+        torch.cuda.empty_cache()
+    if rank == 0:
+        head = args.precisions[0]
+        line = {"metric": "batched volume-RHS GDOF/s (points x RK stages / s)",
+                "value": out[head]["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": out[head]["ms_per_launch"],
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": {"fp64": "f64", "mixed": "f32 (perturbation state)"}[head],
+                "data": "synthetic",
+                "config": {"workload": f"{len(plan)} instances, N in {{3,4,5,7}}, 512..32768 elements "
+                                       f"(log-uniform, cubes), 10 LSRK(5,4) steps at dt = 0.01 s "
+                                       f"per launch", "points": out[head]["points"]},
+                "gpu_launches": args.steps, "clocks": out[head]["clocks"], "precision": head,
+                "variants": {k: v for k, v in out.items() if k != head}}
+        print(json.dumps(line))
+    return 0
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
@@ -409,14 +483,23 @@ def main(argv=None):
                     help="skip the host-buffer end-to-end leg (for profiling runs)")
     ap.add_argument("--n", type=int, default=32,
                     help="elements per axis; 32 is the timed workload, smaller is for ncu")
-    ap.add_argument("--precision", default="fp64,df64,mixed",
-                    help="comma-separated precision modes; the first is the headline value")
+    ap.add_argument("--precision", default=None,
+                    help="comma-separated precision modes; the first is the headline value "
+                         "(default fp64,df64,mixed; batched: fp64,mixed)")
+    ap.add_argument("--workload", choices=["single", "batched"], default="single",
+                    help="single: one evaluation of the 32^3-element N=7 mesh per step (the "
+                         "benchmark); batched: the 64-instance LSRK batch")
+    ap.add_argument("--instances", type=int, default=64, help="batched: number of instances")
     args = ap.parse_args(argv)
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
+    if args.precision is None:
+        args.precision = "fp64,mixed" if args.workload == "batched" else "fp64,df64,mixed"
     args.precisions = [p for p in args.precision.split(",") if p]
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "batched":
+        return run_batched(args)
     return run_gpu(args)
 
 

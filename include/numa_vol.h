@@ -192,6 +192,67 @@ const char *numa_vol_last_error(void);
  */
 int numa_vol_diff_matrix(int N, double *D_out);
 
+/* ------------------------------------------------------------------------- */
+/* Batched time integration                                                  */
+/* ------------------------------------------------------------------------- */
+
+/*
+ * A batch advances many instances (handles of any order and size) of
+ * dq/dt = v(q), with v the volume term above, by the five-stage fourth-order
+ * low-storage Runge-Kutta scheme of Carpenter and Kennedy (NASA TM-109112,
+ * 1994).  Per stage s = 0..4: dq <- A_s dq + dt v(q), q <- q + B_s dq, with
+ * dq = 0 at the start of each call.  The paper (Sec. 2) frames the volume term
+ * as the rate function of such an explicit solver.
+ *
+ * The volume term couples only the points of one element, so elements advance
+ * independently: one persistent kernel takes tiles of elements of every
+ * instance through all stages with q and dq on chip.  Each element's result
+ * is the same whichever other instances share the launch (bitwise), because
+ * its arithmetic does not depend on them.  The kernel, and the reset of its
+ * work counter, are captured once in a CUDA graph per (nsteps, dt) and
+ * replayed.
+ */
+typedef struct numa_batch numa_batch;
+
+/* Create an empty batch on the current device.  prec: NUMA_FP64 (native FP64
+ * handles, FP64 state) or NUMA_MIXED (mixed handles, FP32 perturbation state).
+ * Errors: NUMA_EINVAL, NUMA_EUNSUPPORTED (other precisions), NUMA_ENOMEM,
+ * NUMA_ECUDA. */
+int numa_batch_create(numa_precision prec, numa_batch **out);
+
+/* Add an instance: handle h (created with the batch's precision on the same
+ * device; the batch neither copies nor frees it, and it must outlive its use
+ * in the batch) and its state q, a device pointer to 5 planes of M values of
+ * the handle's state type, 16-byte aligned, that numa_batch_advance updates in
+ * place.  *index (optional) receives the instance's position.
+ * Errors: NUMA_EINVAL. */
+int numa_batch_add(numa_batch *b, const numa_vol *h, void *q, int *index);
+
+/* Remove every instance (the handles and states are untouched). */
+int numa_batch_clear(numa_batch *b);
+
+/* Number of instances. */
+int numa_batch_size(const numa_batch *b);
+
+/* Advance every instance by nsteps steps of size dt, as one graph launch on
+ * `stream` (asynchronous).  The first call after the batch changed uploads
+ * the work list (synchronous) and captures the graph.  Errors: NUMA_EINVAL,
+ * NUMA_ENOMEM, NUMA_ECUDA. */
+int numa_batch_advance(numa_batch *b, int nsteps, double dt, void *stream);
+
+/* Choose the elements per work item for each order present by timing one
+ * step on copies of the current states (synchronous; states unchanged). */
+int numa_batch_autotune(numa_batch *b, void *stream);
+
+/* Elements per work item the batch uses for order Nq (2..8). */
+int numa_batch_tile(const numa_batch *b, int nq);
+
+/* Message for the last batch error on the calling thread. */
+const char *numa_batch_last_error(void);
+
+/* Release a batch (synchronises the device first).  NULL is a no-op. */
+void numa_batch_destroy(numa_batch *b);
+
 #ifdef __cplusplus
 }
 #endif

@@ -70,6 +70,19 @@ def load() -> C.CDLL:
     lib.numa_vol_kernel_name.restype = C.c_char_p
     lib.numa_vol_diff_matrix.argtypes = [C.c_int, _DP]
     lib.numa_vol_diff_matrix.restype = C.c_int
+    lib.numa_batch_create.argtypes = [C.c_int, C.POINTER(C.c_void_p)]
+    lib.numa_batch_add.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(C.c_int)]
+    lib.numa_batch_clear.argtypes = [C.c_void_p]
+    lib.numa_batch_size.argtypes = [C.c_void_p]
+    lib.numa_batch_advance.argtypes = [C.c_void_p, C.c_int, C.c_double, C.c_void_p]
+    lib.numa_batch_autotune.argtypes = [C.c_void_p, C.c_void_p]
+    lib.numa_batch_tile.argtypes = [C.c_void_p, C.c_int]
+    lib.numa_batch_last_error.restype = C.c_char_p
+    lib.numa_batch_destroy.argtypes = [C.c_void_p]
+    lib.numa_batch_destroy.restype = None
+    for name in ("numa_batch_create", "numa_batch_add", "numa_batch_clear", "numa_batch_size",
+                 "numa_batch_advance", "numa_batch_autotune", "numa_batch_tile"):
+        getattr(lib, name).restype = C.c_int
     _lib = lib
     return lib
 
@@ -77,4 +90,10 @@ def load() -> C.CDLL:
 def check(code: int) -> None:
     if code != NUMA_OK:
         msg = load().numa_vol_last_error().decode(errors="replace")
+        raise NumaError(code, msg)
+
+
+def check_batch(code: int) -> None:
+    if code != NUMA_OK:
+        msg = load().numa_batch_last_error().decode(errors="replace")
         raise NumaError(code, msg)

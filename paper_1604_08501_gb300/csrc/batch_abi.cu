@@ -1,0 +1,315 @@
+// C ABI of batched time integration: many volume-term instances (handles of
+// mixed order and size) advanced together by the low-storage Runge-Kutta
+// scheme in one persistent, graph-captured launch.  See include/numa_vol.h.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "numa_internal.h"
+#include "numa_vol.h"
+
+namespace {
+
+// The five-stage fourth-order 2N-storage coefficients of Carpenter and
+// Kennedy (NASA TM-109112, 1994).
+const numa::LsrkCoef kLsrk = {
+    {0.0, -567301805773.0 / 1357537059087.0, -2404267990393.0 / 2016746695238.0,
+     -3550918686646.0 / 2091501179385.0, -1275806237668.0 / 842570457699.0},
+    {1432997174477.0 / 9575080441755.0, 5161836677717.0 / 13612068292357.0,
+     1720146321549.0 / 2090206949498.0, 3134564353537.0 / 4481467310338.0,
+     2277821191437.0 / 14882151754819.0}};
+
+thread_local std::string g_batch_error;
+
+int bfail(int code, const std::string &msg) {
+    g_batch_error = msg;
+    return code;
+}
+
+int bfail_cuda(cudaError_t e, const char *where) {
+    int code = (e == cudaErrorMemoryAllocation) ? NUMA_ENOMEM : NUMA_ECUDA;
+    return bfail(code, std::string(where) + ": " + cudaGetErrorName(e) + " (" +
+                           cudaGetErrorString(e) + ")");
+}
+
+}  // namespace
+
+struct numa_batch {
+    numa_precision prec = NUMA_FP64;
+    int device = 0;
+    int num_sms = 0;
+    std::vector<numa::BatchInstance> inst;
+    int tile_mult[9] = {4, 4, 4, 4, 4, 4, 4, 4, 4};   // elements per item / elements per pass, by Nq
+    // device scratch: instance table, work items, claim counter
+    numa::BatchInstance *d_inst = nullptr;
+    size_t inst_cap = 0;
+    numa::BatchItem *d_items = nullptr;
+    size_t items_cap = 0;
+    int num_items = 0;
+    int *d_counter = nullptr;
+    bool dirty = true;
+    // captured launch: counter reset + persistent kernel
+    cudaStream_t cap_stream = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    int g_nsteps = -1;
+    double g_dt = 0.0;
+    cudaEvent_t launched = nullptr;   // recorded after each launch: the tables are in use until then
+};
+
+namespace numa {
+
+// Build the work list for `inst` with the given tiles; items of one instance
+// are contiguous and instances keep their order.
+std::vector<BatchItem> build_items(const std::vector<BatchInstance> &inst, const int *tile_mult) {
+    std::vector<BatchItem> items;
+    for (size_t k = 0; k < inst.size(); ++k) {
+        const int nq = inst[k].nq;
+        const int64_t ne = inst[k].M / ((int64_t)nq * nq * nq);
+        const int64_t tile = (int64_t)elements_per_pass(nq) * std::max(1, tile_mult[nq]);
+        for (int64_t e0 = 0; e0 < ne; e0 += tile)
+            items.push_back(BatchItem{(int)k, nq, e0, std::min(tile, ne - e0)});
+    }
+    return items;
+}
+
+}  // namespace numa
+
+namespace {
+
+cudaError_t upload(numa_batch *b, const std::vector<numa::BatchInstance> &inst,
+                   const std::vector<numa::BatchItem> &items, cudaStream_t s) {
+    // A previous launch may still read the tables on the caller's stream.
+    cudaError_t e = cudaEventSynchronize(b->launched);
+    if (e != cudaSuccess) return e;
+    if (inst.size() > b->inst_cap) {
+        cudaFree(b->d_inst);
+        b->d_inst = nullptr;
+        b->inst_cap = std::max<size_t>(inst.size(), 2 * b->inst_cap);
+        e = cudaMalloc(&b->d_inst, sizeof(numa::BatchInstance) * b->inst_cap);
+        if (e != cudaSuccess) {
+            b->inst_cap = 0;
+            return e;
+        }
+    }
+    if (items.size() > b->items_cap) {
+        cudaFree(b->d_items);
+        b->d_items = nullptr;
+        b->items_cap = std::max<size_t>(items.size(), 2 * b->items_cap);
+        e = cudaMalloc(&b->d_items, sizeof(numa::BatchItem) * b->items_cap);
+        if (e != cudaSuccess) {
+            b->items_cap = 0;
+            return e;
+        }
+    }
+    if (!inst.empty())
+        e = cudaMemcpyAsync(b->d_inst, inst.data(), sizeof(numa::BatchInstance) * inst.size(),
+                            cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess && !items.empty())
+        e = cudaMemcpyAsync(b->d_items, items.data(), sizeof(numa::BatchItem) * items.size(),
+                            cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);   // pageable sources
+    b->num_items = (int)items.size();
+    return e;
+}
+
+void drop_graph(numa_batch *b) {
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    b->exec = nullptr;
+    b->graph = nullptr;
+    b->g_nsteps = -1;
+}
+
+int grid_of(const numa_batch *b) { return b->num_sms; }   // one 512-thread CTA per SM
+
+}  // namespace
+
+extern "C" {
+
+const char *numa_batch_last_error(void) { return g_batch_error.c_str(); }
+
+int numa_batch_create(numa_precision prec, numa_batch **out) {
+    g_batch_error.clear();
+    if (!out) return bfail(NUMA_EINVAL, "numa_batch_create: out is NULL");
+    *out = nullptr;
+    if (prec != NUMA_FP64 && prec != NUMA_MIXED)
+        return bfail(NUMA_EUNSUPPORTED, "numa_batch_create: batches are NUMA_FP64 or NUMA_MIXED");
+    numa_batch *b = new (std::nothrow) numa_batch();
+    if (!b) return bfail(NUMA_ENOMEM, "numa_batch_create: host allocation failed");
+    b->prec = prec;
+    cudaError_t e = cudaGetDevice(&b->device);
+    if (e == cudaSuccess)
+        e = cudaDeviceGetAttribute(&b->num_sms, cudaDevAttrMultiProcessorCount, b->device);
+    if (e == cudaSuccess) e = numa::prepare_batch_lsrk();
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_counter, 256);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->launched, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventRecord(b->launched, b->cap_stream);
+    if (e != cudaSuccess) {
+        cudaFree(b->d_counter);
+        delete b;
+        return bfail_cuda(e, "numa_batch_create");
+    }
+    *out = b;
+    return NUMA_OK;
+}
+
+int numa_batch_add(numa_batch *b, const numa_vol *h, void *q, int *index) {
+    g_batch_error.clear();
+    if (!b || !h || !q) return bfail(NUMA_EINVAL, "numa_batch_add: NULL argument");
+    if ((reinterpret_cast<uintptr_t>(q) & 15u) != 0)
+        return bfail(NUMA_EINVAL, "numa_batch_add: q must be 16-byte aligned");
+    const bool mixed = b->prec == NUMA_MIXED;
+    if (mixed ? h->kernel != numa::Kernel::Mixed : h->kernel != numa::Kernel::Native)
+        return bfail(NUMA_EINVAL, "numa_batch_add: handle precision differs from the batch's "
+                                  "(NUMA_FP64 batches take NUMA_FP64 handles)");
+    if (h->device != b->device)
+        return bfail(NUMA_EINVAL, "numa_batch_add: handle lives on another device");
+    numa::BatchInstance I{};
+    I.N = h->N;
+    I.nq = h->Nq;
+    I.M = h->M;
+    I.q = q;
+    I.geo = h->geo;
+    I.np = h->nparams;
+    I.mgeo = h->mgeo;
+    I.mp = h->mparams;
+    b->inst.push_back(I);
+    b->dirty = true;
+    if (index) *index = (int)b->inst.size() - 1;
+    return NUMA_OK;
+}
+
+int numa_batch_clear(numa_batch *b) {
+    if (!b) return bfail(NUMA_EINVAL, "numa_batch_clear: NULL batch");
+    b->inst.clear();
+    b->dirty = true;
+    return NUMA_OK;
+}
+
+int numa_batch_size(const numa_batch *b) { return b ? (int)b->inst.size() : 0; }
+
+int numa_batch_advance(numa_batch *b, int nsteps, double dt, void *stream) {
+    g_batch_error.clear();
+    if (!b) return bfail(NUMA_EINVAL, "numa_batch_advance: NULL batch");
+    if (nsteps < 0) return bfail(NUMA_EINVAL, "numa_batch_advance: nsteps < 0");
+    if (nsteps == 0 || b->inst.empty()) return NUMA_OK;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    cudaError_t e = cudaSuccess;
+    if (b->dirty) {
+        drop_graph(b);
+        e = upload(b, b->inst, numa::build_items(b->inst, b->tile_mult), b->cap_stream);
+        if (e != cudaSuccess) return bfail_cuda(e, "numa_batch_advance: upload of the work list");
+        b->dirty = false;
+    }
+    if (!b->exec || b->g_nsteps != nsteps || b->g_dt != dt) {
+        drop_graph(b);
+        e = cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess) e = cudaMemsetAsync(b->d_counter, 0, sizeof(int), b->cap_stream);
+        if (e == cudaSuccess)
+            e = numa::launch_batch_lsrk(b->prec == NUMA_MIXED, b->d_inst, b->d_items, b->num_items,
+                                        b->d_counter, kLsrk, nsteps, dt, grid_of(b), b->cap_stream);
+        cudaGraph_t g = nullptr;
+        const cudaError_t e2 = cudaStreamEndCapture(b->cap_stream, &g);
+        if (e == cudaSuccess) e = e2;
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&b->exec, g, 0);
+        if (e != cudaSuccess) {
+            if (g) cudaGraphDestroy(g);
+            b->exec = nullptr;
+            return bfail_cuda(e, "numa_batch_advance: graph capture");
+        }
+        b->graph = g;
+        b->g_nsteps = nsteps;
+        b->g_dt = dt;
+    }
+    e = cudaGraphLaunch(b->exec, s);
+    if (e == cudaSuccess) e = cudaEventRecord(b->launched, s);
+    if (e != cudaSuccess) return bfail_cuda(e, "numa_batch_advance: graph launch");
+    return NUMA_OK;
+}
+
+int numa_batch_autotune(numa_batch *b, void *stream) {
+    g_batch_error.clear();
+    if (!b) return bfail(NUMA_EINVAL, "numa_batch_autotune: NULL batch");
+    if (b->inst.empty()) return NUMA_OK;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const size_t elem = b->prec == NUMA_MIXED ? sizeof(float) : sizeof(double);
+    const int cands[] = {1, 2, 4, 8, 16, 32};
+    cudaEvent_t t0 = nullptr, t1 = nullptr;
+    cudaError_t e = cudaEventCreate(&t0);
+    if (e == cudaSuccess) e = cudaEventCreate(&t1);
+    for (int nq = 2; nq <= 8 && e == cudaSuccess; ++nq) {
+        // the instances of this order, on copies of their states
+        std::vector<numa::BatchInstance> sub;
+        std::vector<void *> copies;
+        for (const auto &I : b->inst) {
+            if (I.nq != nq) continue;
+            void *c = nullptr;
+            e = cudaMalloc(&c, elem * numa::kFields * I.M);
+            if (e != cudaSuccess) break;
+            copies.push_back(c);
+            e = cudaMemcpyAsync(c, I.q, elem * numa::kFields * I.M, cudaMemcpyDeviceToDevice, s);
+            numa::BatchInstance J = I;
+            J.q = c;
+            sub.push_back(J);
+        }
+        float best = 1e30f;
+        int best_m = b->tile_mult[nq];
+        for (int m : cands) {
+            if (e != cudaSuccess || sub.empty()) break;
+            int mult[9];
+            std::fill(mult, mult + 9, m);
+            e = upload(b, sub, numa::build_items(sub, mult), s);
+            float ms = 1e30f;
+            for (int rep = 0; rep < 2 && e == cudaSuccess; ++rep) {
+                e = cudaMemsetAsync(b->d_counter, 0, sizeof(int), s);
+                if (e == cudaSuccess) e = cudaEventRecord(t0, s);
+                if (e == cudaSuccess)
+                    e = numa::launch_batch_lsrk(b->prec == NUMA_MIXED, b->d_inst, b->d_items,
+                                                b->num_items, b->d_counter, kLsrk, 1, 1e-6,
+                                                grid_of(b), s);
+                if (e == cudaSuccess) e = cudaEventRecord(t1, s);
+                if (e == cudaSuccess) e = cudaEventRecord(b->launched, s);
+                if (e == cudaSuccess) e = cudaEventSynchronize(t1);
+                float t = 0.f;
+                if (e == cudaSuccess) e = cudaEventElapsedTime(&t, t0, t1);
+                ms = std::min(ms, t);
+            }
+            if (e == cudaSuccess && ms < best) {
+                best = ms;
+                best_m = m;
+            }
+        }
+        for (void *c : copies) cudaFree(c);
+        if (e == cudaSuccess) b->tile_mult[nq] = best_m;
+    }
+    if (t0) cudaEventDestroy(t0);
+    if (t1) cudaEventDestroy(t1);
+    b->dirty = true;   // the work list is rebuilt with the chosen tiles
+    if (e != cudaSuccess) return bfail_cuda(e, "numa_batch_autotune");
+    return NUMA_OK;
+}
+
+int numa_batch_tile(const numa_batch *b, int nq) {
+    if (!b || nq < 2 || nq > 8) return 0;
+    return numa::elements_per_pass(nq) * b->tile_mult[nq];
+}
+
+void numa_batch_destroy(numa_batch *b) {
+    if (!b) return;
+    cudaDeviceSynchronize();
+    drop_graph(b);
+    if (b->launched) cudaEventDestroy(b->launched);
+    if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
+    cudaFree(b->d_inst);
+    cudaFree(b->d_items);
+    cudaFree(b->d_counter);
+    delete b;
+}
+
+}  // extern "C"

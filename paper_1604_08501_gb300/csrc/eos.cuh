@@ -1,0 +1,62 @@
+// Pressure perturbation p' = p(Theta) - p(Theta_ref) for the native FP64 and
+// the mixed-precision kernels (equation of state of Sec. 2:
+// p = p0 (R Theta / p0)^gamma, gamma = cp / (cp - R)).
+//
+// Both evaluate p' = p_ref ((1 + x)^gamma - 1) with x = Theta'/Theta_ref,
+// written A Theta' g(x) with A = p_ref / Theta_ref and
+// g(x) = sum_k binom(gamma, k) x^(k-1).  That is the same quantity as the
+// difference of two pressures, without its cancellation.  The series is used
+// for |x| <= 1/64; elsewhere (and where Theta_ref = 0) the definition is
+// evaluated.
+#pragma once
+
+#include "numa_internal.h"
+
+namespace numa {
+
+// p0 (R Theta / p0)^gamma, the equation of state of Sec. 2.  Not inlined:
+// the rhs kernel calls it only where the series does not apply, and keeping
+// pow out of line keeps its registers out of the kernel's budget.
+static __device__ __noinline__ double eos_pressure(double Th, const EosConstants &c) {
+    return __dmul_rn(c.p0, pow(__ddiv_rn(__dmul_rn(c.R, Th), c.p0), c.gamma));
+}
+
+// p' from the binomial series where it converges fast, pow elsewhere.
+static __device__ __forceinline__ double pressure_perturbation(double Th, double th0, double w, double A,
+                                                        const NativeParams &P) {
+    const double thp = Th - th0;              // Theta'
+    const double x = thp * w;                 // Theta' / Theta_ref
+    if (fabs(x) <= 0.015625) {
+        double g = P.c[8];
+#pragma unroll
+        for (int k = 7; k >= 0; --k) g = fma(g, x, P.c[k]);   // sum_k c_{k+1} x^k
+        return (A * thp) * g;
+    }
+    // Outside the series range (or Theta_ref = 0, where w and A are not finite
+    // and x is inf or NaN): the definition, two evaluations of the equation of state.
+    return eos_pressure(Th, P.eos) - eos_pressure(th0, P.eos);
+}
+
+// FP32 form from the perturbation Theta' itself (mixed precision): series
+// for |x| <= 1/64, expm1(gamma log1p(x)) beyond, both free of cancellation.
+// A = K Theta_ref^(gamma - 1) with K = p0^(1 - gamma) R^gamma is recomputed
+// here instead of being read from memory.
+static __device__ __forceinline__ float pressure_perturbation_f32(float thp, float th0,
+                                                           const MixedParams &P) {
+    if (th0 > 0.0f) {
+        const float w = 1.0f / th0;
+        const float A = P.K * exp2f(P.gm1 * log2f(th0));      // p(Theta_ref) / Theta_ref
+        const float x = thp * w;
+        if (fabsf(x) <= 0.015625f) {
+            float g = P.c[4];
+#pragma unroll
+            for (int k = 3; k >= 0; --k) g = fmaf(g, x, P.c[k]);   // sum_k c_{k+1} x^k
+            return (A * thp) * g;
+        }
+        return (A * th0) * expm1f(P.gamma * log1pf(x));
+    }
+    // Theta_ref = 0 (the paper's full-pressure form): p' = p(Theta').
+    return P.K * powf(thp, P.gamma);
+}
+
+}  // namespace numa

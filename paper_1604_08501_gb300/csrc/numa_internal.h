@@ -121,6 +121,43 @@ struct DfParams {
 
 enum class Kernel { Native, DoubleFloat, Mixed };
 
+// Device-side description of one instance of a batch: its order, size, state
+// and the geometry/parameters of its handle (FP64 or mixed, per the batch).
+struct BatchInstance {
+    int N, nq;
+    int64_t M;
+    void *q;
+    DeviceGeometry geo;
+    NativeParams np;
+    MixedGeometry mgeo;
+    MixedParams mp;
+};
+
+// One work item: elements [e0, e0 + count) of an instance.
+struct BatchItem {
+    int instance;
+    int nq;
+    int64_t e0;
+    int64_t count;
+};
+
+// Coefficients of the five-stage fourth-order 2N-storage Runge-Kutta scheme.
+struct LsrkCoef {
+    double A[5], B[5];
+};
+
+// Launch of the persistent batched integrator (batch_lsrk.cu): items are
+// claimed through *counter (reset to 0 by the caller before the launch).
+// prepare_batch_lsrk() sets the kernels' shared-memory opt-in on the current
+// device; call it before the first launch (and outside stream capture).
+cudaError_t prepare_batch_lsrk();
+cudaError_t launch_batch_lsrk(bool mixed, const BatchInstance *inst, const BatchItem *items,
+                              int num_items, int *counter, const LsrkCoef &co, int nsteps,
+                              double dt, int grid, cudaStream_t s);
+
+// Elements one CTA pass holds for order Nq (512 threads, one per point).
+inline int elements_per_pass(int nq) { return 512 / (nq * nq * nq); }
+
 }  // namespace numa
 
 struct numa_vol {

@@ -26,34 +26,12 @@
 #include <cuda_runtime.h>
 
 #include "element_sweep.cuh"
+#include "eos.cuh"
 #include "numa_internal.h"
 
 namespace numa {
 
 namespace {
-
-// p0 (R Theta / p0)^gamma, the equation of state of Sec. 2.  Not inlined:
-// the rhs kernel calls it only where the series does not apply, and keeping
-// pow out of line keeps its registers out of the kernel's budget.
-__device__ __noinline__ double eos_pressure(double Th, const EosConstants &c) {
-    return __dmul_rn(c.p0, pow(__ddiv_rn(__dmul_rn(c.R, Th), c.p0), c.gamma));
-}
-
-// p' from the binomial series where it converges fast, pow elsewhere.
-__device__ __forceinline__ double pressure_perturbation(double Th, double th0, double w, double A,
-                                                        const NativeParams &P) {
-    const double thp = Th - th0;              // Theta'
-    const double x = thp * w;                 // Theta' / Theta_ref
-    if (fabs(x) <= 0.015625) {
-        double g = P.c[8];
-#pragma unroll
-        for (int k = 7; k >= 0; --k) g = fma(g, x, P.c[k]);   // sum_k c_{k+1} x^k
-        return (A * thp) * g;
-    }
-    // Outside the series range (or Theta_ref = 0, where w and A are not finite
-    // and x is inf or NaN): the definition, two evaluations of the equation of state.
-    return eos_pressure(Th, P.eos) - eos_pressure(th0, P.eos);
-}
 
 // Resident CTAs per SM the register budget is sized for: 1024 threads per SM,
 // at most 32 CTAs.

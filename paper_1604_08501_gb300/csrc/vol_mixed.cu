@@ -30,29 +30,12 @@
 
 #include "bulk_copy.cuh"
 #include "element_sweep.cuh"
+#include "eos.cuh"
 #include "numa_internal.h"
 
 namespace numa {
 
 namespace {
-
-__device__ __forceinline__ float pressure_perturbation_f32(float thp, float th0,
-                                                           const MixedParams &P) {
-    if (th0 > 0.0f) {
-        const float w = 1.0f / th0;
-        const float A = P.K * exp2f(P.gm1 * log2f(th0));      // p(Theta_ref) / Theta_ref
-        const float x = thp * w;
-        if (fabsf(x) <= 0.015625f) {
-            float g = P.c[4];
-#pragma unroll
-            for (int k = 3; k >= 0; --k) g = fmaf(g, x, P.c[k]);   // sum_k c_{k+1} x^k
-            return (A * thp) * g;
-        }
-        return (A * th0) * expm1f(P.gamma * log1pf(x));
-    }
-    // Theta_ref = 0 (the paper's full-pressure form): p' = p(Theta').
-    return P.K * powf(thp, P.gamma);
-}
 
 template <int NQ>
 constexpr int mixed_min_ctas() {

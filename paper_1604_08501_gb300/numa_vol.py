@@ -16,7 +16,7 @@ import ctypes as C
 import numpy as np
 
 from . import _lib
-from ._lib import NUMA_DF64, NUMA_FP64, NUMA_MIXED, NumaError, check
+from ._lib import NUMA_DF64, NUMA_FP64, NUMA_MIXED, NumaError, check, check_batch
 
 NFIELDS = 5
 
@@ -176,4 +176,75 @@ class VolumeTerm:
             pass
 
 
-__all__ = ["VolumeTerm", "diff_matrix", "NumaError"]
+class Batch:
+    """Batched low-storage Runge-Kutta integration of many VolumeTerm instances
+    (numa_batch_*).  States are CUDA tensors the batch updates in place."""
+
+    def __init__(self, precision: str = "fp64"):
+        self.precision = precision
+        h = C.c_void_p()
+        prec = {"fp64": NUMA_FP64, "mixed": NUMA_MIXED}[precision]
+        check_batch(_lib.load().numa_batch_create(prec, C.byref(h)))
+        self._h = h
+        self._keep = []          # (VolumeTerm, state) pairs the device table points to
+
+    @property
+    def handle(self) -> int:
+        if self._h is None or not self._h.value:
+            raise RuntimeError("Batch is closed")
+        return self._h.value
+
+    def add(self, vt: "VolumeTerm", q) -> int:
+        import torch
+        if not (isinstance(q, torch.Tensor) and q.is_cuda and q.is_contiguous()
+                and q.dtype == vt._torch_dtype() and q.numel() == NFIELDS * vt.M):
+            raise TypeError("q must be the instance's contiguous CUDA state tensor")
+        idx = C.c_int()
+        check_batch(_lib.load().numa_batch_add(self.handle, C.c_void_p(vt.handle),
+                                               C.c_void_p(q.data_ptr()), C.byref(idx)))
+        self._keep.append((vt, q))
+        return idx.value
+
+    def clear(self) -> None:
+        check_batch(_lib.load().numa_batch_clear(self.handle))
+        self._keep = []
+
+    def __len__(self) -> int:
+        return _lib.load().numa_batch_size(self.handle)
+
+    def _stream(self, stream):
+        import torch
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        return stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+
+    def advance(self, nsteps: int, dt: float, stream=None) -> None:
+        check_batch(_lib.load().numa_batch_advance(self.handle, int(nsteps), float(dt),
+                                                   C.c_void_p(self._stream(stream))))
+
+    def autotune(self, stream=None) -> None:
+        check_batch(_lib.load().numa_batch_autotune(self.handle, C.c_void_p(self._stream(stream))))
+
+    def tile(self, nq: int) -> int:
+        return _lib.load().numa_batch_tile(self.handle, int(nq))
+
+    def close(self) -> None:
+        if getattr(self, "_h", None) is not None and self._h.value:
+            _lib.load().numa_batch_destroy(self._h)
+        self._h = None
+        self._keep = []
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+__all__ = ["VolumeTerm", "Batch", "diff_matrix", "NumaError"]

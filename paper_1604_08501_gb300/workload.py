@@ -276,6 +276,19 @@ def make_workload(N: int, n, seed: int, L: float = 10_000.0, warp: float = 0.05,
                     meta={"L": L, "warp": warp, "T": T, "eps": eps, "vmax": vmax, "n": n})
 
 
+def batch_plan(count: int = 64, seed: int = 99, orders=(3, 4, 5, 7),
+               ne_range=(512, 32768)):
+    """Orders and sizes of a batch of independent instances: N uniform from
+    `orders`, element count log-uniform in `ne_range`, rounded to a cube
+    n^3 with n = round(Ne^(1/3)).  Instance i uses state seed 100 + i.
+    Returns a list of (N, n, seed)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    Ns = rng.choice(np.asarray(orders), size=count)
+    ne = np.exp(rng.uniform(np.log(ne_range[0]), np.log(ne_range[1]), size=count))
+    ns = np.rint(np.cbrt(ne)).astype(int)
+    return [(int(N), int(n), 100 + i) for i, (N, n) in enumerate(zip(Ns, ns))]
+
+
 # The two single-GPU workloads: the small parity case and the timed case.
 PARITY_SMALL = dict(N=4, n=8, seed=0, name="N=4 (Nq=5), 8^3=512 elements, warped 10 km box")
 BENCH_FULL = dict(N=7, n=32, seed=1,
