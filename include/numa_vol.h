@@ -54,6 +54,7 @@ extern "C" {
 #define NUMA_ECUDA (-3)         /* a CUDA call or kernel launch failed                    */
 #define NUMA_EUNSUPPORTED (-4)  /* valid request this build does not implement            */
 #define NUMA_ETIMEOUT (-5)      /* a kernel's bounded wait on its own staged copies ran out */
+#define NUMA_ELIMIT (-6)        /* a count exceeds a fixed maximum of the call              */
 
 #define NUMA_MAX_N 7            /* orders N = 1 .. 7 (Nq = 2 .. 8)                        */
 
@@ -252,6 +253,43 @@ const char *numa_batch_last_error(void);
 
 /* Release a batch (synchronises the device first).  NULL is a no-op. */
 void numa_batch_destroy(numa_batch *b);
+
+/*
+ * Advance instances like numa_batch_advance, without allocating any memory.
+ * The paper has no counterpart.  It is for callers that cannot call
+ * cudaMalloc once running.  An example is a serving process that has committed
+ * all of its HBM budget to resident ensemble states; another is an
+ * application whose allocator forbids growth after start-up.
+ *
+ * handles[k] (NUMA_FP64 or NUMA_MIXED handles, all of one kind, on the current
+ * device) and states[k] (its state: a device pointer, 16-byte aligned, updated
+ * in place), for k < count, with 1 <= count <= NUMA_NOALLOC_MAX_INSTANCES.
+ * Each call advances every instance by nsteps steps of size dt, with the same
+ * scheme, tiles (4 passes per work item) and per-element arithmetic as a
+ * numa_batch of those handles without autotuning.
+ *
+ * Scratch: the work counter and the instance table live in one fixed __device__
+ * array of the library (about 57 KB, held by every GPU that loads the library
+ * until the process exits).  The first call on a device does a one-time
+ * set-up there: it looks up the array's device address and sets the kernel's
+ * shared-memory limit.  Make that first call before any stream capture.
+ * Every call overwrites the same array, so calls whose kernels may overlap on
+ * the GPU (other streams, other host threads) race.  Serialise them on one
+ * stream.
+ *
+ * The call builds the table on its own stack, copies it into the array,
+ * zeroes the counter and launches, all on `stream` (asynchronous; the table
+ * copy from the stack is staged before the call returns).  It calls no
+ * allocator: no cudaMalloc or cudaFree, no host heap, and it records no error
+ * message.
+ * Returns NUMA_OK; NUMA_ELIMIT if count > NUMA_NOALLOC_MAX_INSTANCES (or the
+ * total work exceeds 2^31 - 1 items); NUMA_EINVAL for a NULL or misaligned
+ * pointer, count < 1, nsteps < 0, handles of mixed kinds or of another device,
+ * or a double-float handle; NUMA_ECUDA if a CUDA call fails.
+ */
+#define NUMA_NOALLOC_MAX_INSTANCES 64
+int numa_batch_advance_noalloc(const numa_vol *const *handles, void *const *states, int count,
+                               int nsteps, double dt, void *stream);
 
 #ifdef __cplusplus
 }

@@ -10,13 +10,14 @@ import os
 
 from .build import LIB
 
-NUMA_OK, NUMA_EINVAL, NUMA_ENOMEM, NUMA_ECUDA, NUMA_EUNSUPPORTED, NUMA_ETIMEOUT = 0, -1, -2, -3, -4, -5
+NUMA_OK, NUMA_EINVAL, NUMA_ENOMEM, NUMA_ECUDA, NUMA_EUNSUPPORTED, NUMA_ETIMEOUT, NUMA_ELIMIT = 0, -1, -2, -3, -4, -5, -6
+NUMA_NOALLOC_MAX_INSTANCES = 64
 NUMA_MAX_N = 7
 NUMA_FP64, NUMA_MIXED, NUMA_DF64 = 0, 1, 2
 
 _ERRNAMES = {NUMA_EINVAL: "NUMA_EINVAL", NUMA_ENOMEM: "NUMA_ENOMEM",
              NUMA_ECUDA: "NUMA_ECUDA", NUMA_EUNSUPPORTED: "NUMA_EUNSUPPORTED",
-             NUMA_ETIMEOUT: "NUMA_ETIMEOUT"}
+             NUMA_ETIMEOUT: "NUMA_ETIMEOUT", NUMA_ELIMIT: "NUMA_ELIMIT"}
 
 _DP = C.POINTER(C.c_double)
 
@@ -80,6 +81,9 @@ def load() -> C.CDLL:
     lib.numa_batch_last_error.restype = C.c_char_p
     lib.numa_batch_destroy.argtypes = [C.c_void_p]
     lib.numa_batch_destroy.restype = None
+    lib.numa_batch_advance_noalloc.argtypes = [C.POINTER(C.c_void_p), C.POINTER(C.c_void_p), C.c_int,
+                                               C.c_int, C.c_double, C.c_void_p]
+    lib.numa_batch_advance_noalloc.restype = C.c_int
     for name in ("numa_batch_create", "numa_batch_add", "numa_batch_clear", "numa_batch_size",
                  "numa_batch_advance", "numa_batch_autotune", "numa_batch_tile"):
         getattr(lib, name).restype = C.c_int
