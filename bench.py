@@ -471,6 +471,124 @@ def run_batched(args):
     return 0
 
 
+def run_serving(args):
+    """The serving workload: a Poisson stream of ensemble-member requests (mean
+    args.rate per second), each an instance drawn from a pool of meshes sized as
+    in the batched workload (N in {3,4,5,7}, 512..32768 elements), advancing
+    k in {1, 5, 20} LSRK steps at dt = 0.01 s on device-resident state.  The
+    engine admits by a 120 GB HBM budget with up to 256 members resident and
+    advances all resident members one step per round (continuous batching).
+    Latency of a request: from its scheduled arrival to the moment its final
+    state is in host memory.  Throughput: point x stage evaluations of all
+    requests over the span from the first arrival to the last completion."""
+    import torch
+    rank, local, world = dist_setup("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    from paper_1604_08501_gb300 import build as lib_build
+    from paper_1604_08501_gb300 import workload as wl
+    from paper_1604_08501_gb300.numa_vol import Engine, VolumeTerm
+    lib_build.build()
+    plan = wl.batch_plan(count=args.pool)
+    works = [wl.make_workload(N, n, seed=seed) for N, n, seed in plan]
+    rng = np.random.Generator(np.random.PCG64(2024 + rank))
+    total = args.requests
+    gaps = rng.exponential(1.0 / args.rate, size=total)
+    pick = rng.integers(0, len(works), size=total)
+    ks = rng.choice(np.array([1, 5, 20]), size=total)
+    dt = 0.01
+    out = {}
+    for prec in args.precisions:
+        if prec not in ("fp64", "mixed"):
+            continue
+        vts = [VolumeTerm.from_problem(w.problem(), precision=prec) for w in works]
+        q0s = []
+        for w in works:
+            a = w.q_mixed() if prec == "mixed" else w.q
+            t = torch.empty(a.shape, dtype=torch.float32 if prec == "mixed" else torch.float64,
+                            pin_memory=True)
+            t.numpy()[...] = a
+            q0s.append(t)
+        free = [[] for _ in works]          # pinned output buffers, reused per mesh
+
+        def take(j):
+            return free[j].pop() if free[j] else torch.empty_like(q0s[j]).pin_memory()
+
+        with Engine(prec, budget_bytes=args.budget_gb << 30, max_members=256) as eng:
+            # warm-up: a few requests through the same path, not timed
+            for j in range(min(args.warmup, len(works))):
+                o = take(j)
+                eng.submit(vts[j], q0s[j], o, 1, dt)
+                eng.run_until_idle()
+                free[j].append(o)
+            base = eng.stats()
+            sampler = ClockSampler(gpu_id_for(local)) if rank == 0 else None
+            if sampler:
+                sampler.start()
+            barrier(dev)
+            t0 = time.monotonic()
+            arrive = t0 + np.cumsum(gaps)
+            ids, bufs, nxt, done = {}, {}, 0, 0
+            while done < total:
+                now = time.monotonic()
+                while nxt < total and arrive[nxt] <= now:
+                    j = int(pick[nxt])
+                    o = take(j)
+                    rid = eng.submit(vts[j], q0s[j], o, int(ks[nxt]), dt)
+                    ids[rid], bufs[rid] = nxt, (j, o)
+                    nxt += 1
+                st = eng.stats()
+                if st["queued"] == 0 and st["resident"] == 0:
+                    if nxt >= total:
+                        raise RuntimeError("engine idle with requests unaccounted for")
+                    time.sleep(max(0.0, min(arrive[nxt] - time.monotonic(), 0.01)))
+                    continue
+                for rid in eng.progress():
+                    j, o = bufs.pop(rid)
+                    free[j].append(o)
+                    done += 1
+            lat, last = np.empty(total), 0.0
+            for rid, i in ids.items():
+                inf = eng.query(rid)
+                lat[i] = inf["done_s"] - arrive[i]
+                last = max(last, inf["done_s"])
+            barrier(dev)
+            clocks = sampler.stop() if sampler else None
+            st = eng.stats()
+            stages = st["point_stages"] - base["point_stages"]
+            span = last - t0
+            value, tmax = aggregate(int(stages), span, dev)
+            offered = float(np.mean([works[int(j)].M for j in pick]) * 5 * np.mean(ks) * args.rate)
+            out[prec] = {"value": value / 1e9, "span_s": tmax,
+                         "latency_ms": {"p50": float(np.percentile(lat, 50) * 1e3),
+                                        "p99": float(np.percentile(lat, 99) * 1e3),
+                                        "max": float(lat.max() * 1e3)},
+                         "offered_gdofs": offered / 1e9, "rounds": st["rounds"] - base["rounds"],
+                         "requests": total, "clocks": clocks}
+        for vt in vts:
+            vt.close()
+        del q0s, free
+        torch.cuda.empty_cache()
+    if rank == 0:
+        head = args.precisions[0]
+        line = {"metric": "serving GDOF/s (points x RK stages / s) with p50/p99 request latency",
+                "value": out[head]["value"], "unit": UNIT, "n_gpus": world, "steps": total,
+                "warmup": args.warmup, "ms_per_step": out[head]["span_s"] * 1e3 / total,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": {"fp64": "f64", "mixed": "f32 (perturbation state)"}[head],
+                "data": "synthetic",
+                "config": {"workload": f"Poisson arrivals at {args.rate:g} req/s, {total} requests, "
+                                       f"each one of {len(plan)} instances (N in {{3,4,5,7}}, "
+                                       f"512..32768 elements) advancing k in {{1,5,20}} LSRK(5,4) "
+                                       f"steps at dt = 0.01 s; budget {args.budget_gb} GB, "
+                                       f"<= 256 members resident"},
+                "latency_ms": out[head]["latency_ms"], "offered_gdofs": out[head]["offered_gdofs"],
+                "gpu_launches": out[head]["rounds"], "clocks": out[head]["clocks"],
+                "precision": head, "variants": {k: v for k, v in out.items() if k != head}}
+        print(json.dumps(line))
+    return 0
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
@@ -486,20 +604,27 @@ def main(argv=None):
     ap.add_argument("--precision", default=None,
                     help="comma-separated precision modes; the first is the headline value "
                          "(default fp64,df64,mixed; batched: fp64,mixed)")
-    ap.add_argument("--workload", choices=["single", "batched"], default="single",
+    ap.add_argument("--workload", choices=["single", "batched", "serving"], default="single",
                     help="single: one evaluation of the 32^3-element N=7 mesh per step (the "
-                         "benchmark); batched: the 64-instance LSRK batch")
+                         "benchmark); batched: the 64-instance LSRK batch; serving: a Poisson "
+                         "request stream through the continuous-batching engine")
     ap.add_argument("--instances", type=int, default=64, help="batched: number of instances")
+    ap.add_argument("--rate", type=float, default=200.0, help="serving: mean arrivals per second")
+    ap.add_argument("--requests", type=int, default=600, help="serving: requests per precision")
+    ap.add_argument("--pool", type=int, default=16, help="serving: distinct instances drawn from")
+    ap.add_argument("--budget-gb", type=int, default=120, help="serving: HBM budget of the states")
     args = ap.parse_args(argv)
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     if args.precision is None:
-        args.precision = "fp64,mixed" if args.workload == "batched" else "fp64,df64,mixed"
+        args.precision = ("fp64,df64,mixed" if args.workload == "single" else "fp64,mixed")
     args.precisions = [p for p in args.precision.split(",") if p]
     if args.impl == "reference":
         return run_reference(args)
     if args.workload == "batched":
         return run_batched(args)
+    if args.workload == "serving":
+        return run_serving(args)
     return run_gpu(args)
 
 

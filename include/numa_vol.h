@@ -254,6 +254,79 @@ const char *numa_batch_last_error(void);
 /* Release a batch (synchronises the device first).  NULL is a no-op. */
 void numa_batch_destroy(numa_batch *b);
 
+/* ------------------------------------------------------------------------- */
+/* Serving engine: continuous batching of ensemble-member requests           */
+/* ------------------------------------------------------------------------- */
+
+/*
+ * An engine serves requests, each an ensemble member to be advanced: a mesh
+ * (a numa_vol handle the caller created and keeps alive), an initial state in
+ * host memory, a number of low-storage RK steps and a step size.  The engine
+ * reserves its HBM budget once, as an arena for members' states, and admits
+ * requests in arrival order while a member slot is free and the arena has room.
+ * Each numa_engine_progress call is one round: admit, advance every resident
+ * member by one step in one persistent launch (one per distinct dt), return
+ * the finished members' states to their host buffers.  Requests submitted
+ * while others run join at the next round.  A member's result is bitwise the
+ * same whichever members share its rounds.  Engines are not thread-safe.
+ */
+typedef struct numa_engine numa_engine;
+
+#define NUMA_REQ_QUEUED 0
+#define NUMA_REQ_RUNNING 1
+#define NUMA_REQ_DONE 2
+#define NUMA_REQ_CANCELLED 3
+
+typedef struct {
+    int64_t id;
+    int status;                        /* NUMA_REQ_*                                    */
+    double submit_s, admit_s, done_s;  /* steady-clock seconds (0 where not reached)    */
+} numa_request_info;
+
+typedef struct {
+    int queued, resident;
+    size_t bytes_used, bytes_budget;   /* arena bytes held by members / reserved         */
+    int64_t completed, rounds;
+    double point_stages;               /* sum over launches of points x 5 RK stages      */
+} numa_engine_counters;
+
+/* Create an engine on the current device: prec NUMA_FP64 or NUMA_MIXED,
+ * budget_bytes of device memory reserved now for members' states, at most
+ * max_members resident.  Errors: NUMA_EINVAL, NUMA_EUNSUPPORTED, NUMA_ENOMEM
+ * (the budget cannot be reserved), NUMA_ECUDA. */
+int numa_engine_create(numa_precision prec, size_t budget_bytes, int max_members,
+                       numa_engine **out);
+
+/* Queue a request.  mesh: a handle of the engine's precision on its device.
+ * q0_host: the initial state (5 planes of M values of the handle's state type)
+ * and q_out_host: where the final state goes; both host memory, read and
+ * written during later progress calls, kept alive until the request is done or
+ * cancelled.  nsteps >= 1, dt > 0.  *id receives the request id.
+ * Errors: NUMA_EINVAL (malformed request; the engine is unchanged),
+ * NUMA_ELIMIT (the state exceeds the whole budget: it can never be admitted). */
+int numa_engine_submit(numa_engine *e, const numa_vol *mesh, const void *q0_host,
+                       void *q_out_host, int nsteps, double dt, int64_t *id);
+
+/* Cancel a queued request now, or a running one at the start of the next
+ * round (its state is discarded).  Errors: NUMA_EINVAL (unknown or finished). */
+int numa_engine_cancel(numa_engine *e, int64_t id);
+
+/* One round (synchronous).  Up to max_done ids of requests finished in this
+ * round go to done_ids, their count to *num_done.  Errors: NUMA_ECUDA. */
+int numa_engine_progress(numa_engine *e, int64_t *done_ids, int max_done, int *num_done);
+
+/* Status and timestamps of a request. */
+int numa_engine_query(const numa_engine *e, int64_t id, numa_request_info *out);
+
+/* Counters of the engine. */
+int numa_engine_stats(const numa_engine *e, numa_engine_counters *out);
+
+/* Message for the last engine error on the calling thread. */
+const char *numa_engine_last_error(void);
+
+/* Release an engine and its reserved memory (queued requests are dropped). */
+void numa_engine_destroy(numa_engine *e);
+
 /*
  * Advance instances like numa_batch_advance, without allocating any memory.
  * The paper has no counterpart.  It is for callers that cannot call

@@ -35,6 +35,20 @@ class numa_geometry(C.Structure):
                 ("rhotheta_ref", C.c_void_p)]
 
 
+class numa_request_info(C.Structure):
+    _fields_ = [("id", C.c_int64), ("status", C.c_int), ("submit_s", C.c_double),
+                ("admit_s", C.c_double), ("done_s", C.c_double)]
+
+
+class numa_engine_counters(C.Structure):
+    _fields_ = [("queued", C.c_int), ("resident", C.c_int), ("bytes_used", C.c_size_t),
+                ("bytes_budget", C.c_size_t), ("completed", C.c_int64), ("rounds", C.c_int64),
+                ("point_stages", C.c_double)]
+
+
+NUMA_REQ_QUEUED, NUMA_REQ_RUNNING, NUMA_REQ_DONE, NUMA_REQ_CANCELLED = 0, 1, 2, 3
+
+
 class NumaError(RuntimeError):
     def __init__(self, code: int, msg: str):
         super().__init__(f"{_ERRNAMES.get(code, code)}: {msg}")
@@ -81,6 +95,20 @@ def load() -> C.CDLL:
     lib.numa_batch_last_error.restype = C.c_char_p
     lib.numa_batch_destroy.argtypes = [C.c_void_p]
     lib.numa_batch_destroy.restype = None
+    lib.numa_engine_create.argtypes = [C.c_int, C.c_size_t, C.c_int, C.POINTER(C.c_void_p)]
+    lib.numa_engine_submit.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int,
+                                       C.c_double, C.POINTER(C.c_int64)]
+    lib.numa_engine_cancel.argtypes = [C.c_void_p, C.c_int64]
+    lib.numa_engine_progress.argtypes = [C.c_void_p, C.POINTER(C.c_int64), C.c_int,
+                                         C.POINTER(C.c_int)]
+    lib.numa_engine_query.argtypes = [C.c_void_p, C.c_int64, C.POINTER(numa_request_info)]
+    lib.numa_engine_stats.argtypes = [C.c_void_p, C.POINTER(numa_engine_counters)]
+    lib.numa_engine_last_error.restype = C.c_char_p
+    lib.numa_engine_destroy.argtypes = [C.c_void_p]
+    lib.numa_engine_destroy.restype = None
+    for name in ("numa_engine_create", "numa_engine_submit", "numa_engine_cancel",
+                 "numa_engine_progress", "numa_engine_query", "numa_engine_stats"):
+        getattr(lib, name).restype = C.c_int
     lib.numa_batch_advance_noalloc.argtypes = [C.POINTER(C.c_void_p), C.POINTER(C.c_void_p), C.c_int,
                                                C.c_int, C.c_double, C.c_void_p]
     lib.numa_batch_advance_noalloc.restype = C.c_int
@@ -94,6 +122,12 @@ def load() -> C.CDLL:
 def check(code: int) -> None:
     if code != NUMA_OK:
         msg = load().numa_vol_last_error().decode(errors="replace")
+        raise NumaError(code, msg)
+
+
+def check_engine(code: int) -> None:
+    if code != NUMA_OK:
+        msg = load().numa_engine_last_error().decode(errors="replace")
         raise NumaError(code, msg)
 
 

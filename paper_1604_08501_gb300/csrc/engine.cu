@@ -1,0 +1,383 @@
+// Serving engine: continuous batching of ensemble-member requests over the
+// batched low-storage Runge-Kutta integrator.  See include/numa_vol.h.
+//
+// A request names a resident mesh (a numa_vol handle the caller created), an
+// initial state and a number of RK steps.  The engine keeps members' states
+// in an arena it reserves once (the HBM budget), so admission never calls
+// cudaMalloc.  Each call of numa_engine_progress is one round:
+//   1. retire cancelled members;
+//   2. admit queued requests in arrival order while a member slot is free and
+//      the arena has room (first fit); the head of the queue waits if it does
+//      not fit yet, so later requests cannot starve it;
+//   3. advance every resident member by one step, all in one persistent launch
+//      (members of different dt in one launch each);
+//   4. copy finished members' states to their host buffers and free them.
+// Requests that arrive during a round join at the next round while the others
+// are still resident.  That is the continuous batching.  Elements evolve
+// independently in the volume term, so a member's result is bitwise the same
+// whichever members share its rounds.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "numa_internal.h"
+#include "numa_vol.h"
+
+namespace {
+
+thread_local std::string g_engine_error;
+
+int efail(int code, const std::string &msg) {
+    g_engine_error = msg;
+    return code;
+}
+
+int efail_cuda(cudaError_t e, const char *where) {
+    int code = (e == cudaErrorMemoryAllocation) ? NUMA_ENOMEM : NUMA_ECUDA;
+    return efail(code, std::string(where) + ": " + cudaGetErrorName(e) + " (" +
+                           cudaGetErrorString(e) + ")");
+}
+
+const numa::LsrkCoef kCoef = {
+    {0.0, -567301805773.0 / 1357537059087.0, -2404267990393.0 / 2016746695238.0,
+     -3550918686646.0 / 2091501179385.0, -1275806237668.0 / 842570457699.0},
+    {1432997174477.0 / 9575080441755.0, 5161836677717.0 / 13612068292357.0,
+     1720146321549.0 / 2090206949498.0, 3134564353537.0 / 4481467310338.0,
+     2277821191437.0 / 14882151754819.0}};
+
+constexpr size_t kAlign = 256;
+
+// First-fit allocator over the arena, with coalescing of free neighbours.
+struct Arena {
+    char *base = nullptr;
+    size_t size = 0;
+    std::map<size_t, size_t> free_blocks;   // offset -> length
+    size_t used = 0;
+
+    void reset(char *b, size_t n) {
+        base = b;
+        size = n;
+        free_blocks.clear();
+        if (n) free_blocks[0] = n;
+        used = 0;
+    }
+    // Returns an offset, or SIZE_MAX when no free block is large enough.
+    size_t alloc(size_t n) {
+        n = (n + kAlign - 1) / kAlign * kAlign;
+        for (auto it = free_blocks.begin(); it != free_blocks.end(); ++it) {
+            if (it->second < n) continue;
+            const size_t off = it->first, len = it->second;
+            free_blocks.erase(it);
+            if (len > n) free_blocks[off + n] = len - n;
+            used += n;
+            return off;
+        }
+        return SIZE_MAX;
+    }
+    void release(size_t off, size_t n) {
+        n = (n + kAlign - 1) / kAlign * kAlign;
+        used -= n;
+        auto it = free_blocks.emplace(off, n).first;
+        auto next = std::next(it);
+        if (next != free_blocks.end() && it->first + it->second == next->first) {
+            it->second += next->second;
+            free_blocks.erase(next);
+        }
+        if (it != free_blocks.begin()) {
+            auto prev = std::prev(it);
+            if (prev->first + prev->second == it->first) {
+                prev->second += it->second;
+                free_blocks.erase(it);
+            }
+        }
+    }
+};
+
+struct Request {
+    int64_t id;
+    const numa_vol *mesh;
+    const void *q0;
+    void *q_out;
+    int nsteps, remaining;
+    double dt;
+    size_t bytes, off;
+    int status;
+};
+
+double now_s() {
+    using namespace std::chrono;
+    return duration<double>(steady_clock::now().time_since_epoch()).count();
+}
+
+}  // namespace
+
+struct numa_engine {
+    numa_precision prec = NUMA_FP64;
+    int device = 0, num_sms = 0, max_members = 0;
+    size_t elem = 8;
+    Arena arena;
+    void *d_arena = nullptr;
+    numa::BatchInstance *d_inst = nullptr;
+    numa::BatchItem *d_items = nullptr;
+    size_t items_cap = 0;
+    int *d_counter = nullptr;
+    cudaStream_t stream = nullptr;
+    int64_t next_id = 1;
+    std::deque<Request> queue;
+    std::vector<Request> resident;
+    std::map<int64_t, numa_request_info> info;
+    int64_t completed = 0, rounds = 0;
+    double point_stages = 0.0;
+    int tile_mult = 4;
+};
+
+namespace {
+
+size_t state_bytes(const numa_engine *e, const numa_vol *h) {
+    return e->elem * numa::kFields * (size_t)h->M;
+}
+
+void set_status(numa_engine *e, int64_t id, int status, bool stamp_done = false) {
+    auto &inf = e->info[id];
+    inf.status = status;
+    if (stamp_done) inf.done_s = now_s();
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *numa_engine_last_error(void) { return g_engine_error.c_str(); }
+
+int numa_engine_create(numa_precision prec, size_t budget_bytes, int max_members,
+                       numa_engine **out) {
+    g_engine_error.clear();
+    if (!out) return efail(NUMA_EINVAL, "numa_engine_create: out is NULL");
+    *out = nullptr;
+    if (prec != NUMA_FP64 && prec != NUMA_MIXED)
+        return efail(NUMA_EUNSUPPORTED, "numa_engine_create: NUMA_FP64 or NUMA_MIXED only");
+    if (max_members < 1 || budget_bytes < kAlign)
+        return efail(NUMA_EINVAL, "numa_engine_create: need max_members >= 1 and a budget");
+    numa_engine *e = new (std::nothrow) numa_engine();
+    if (!e) return efail(NUMA_ENOMEM, "numa_engine_create: host allocation failed");
+    e->prec = prec;
+    e->elem = prec == NUMA_MIXED ? sizeof(float) : sizeof(double);
+    e->max_members = max_members;
+    e->items_cap = (size_t)max_members * 8192;
+    cudaError_t err = cudaGetDevice(&e->device);
+    if (err == cudaSuccess)
+        err = cudaDeviceGetAttribute(&e->num_sms, cudaDevAttrMultiProcessorCount, e->device);
+    if (err == cudaSuccess) err = numa::prepare_batch_lsrk();
+    if (err == cudaSuccess) err = cudaMalloc(&e->d_arena, budget_bytes);
+    if (err == cudaSuccess) err = cudaMalloc(&e->d_inst, sizeof(numa::BatchInstance) * max_members);
+    if (err == cudaSuccess) err = cudaMalloc(&e->d_items, sizeof(numa::BatchItem) * e->items_cap);
+    if (err == cudaSuccess) err = cudaMalloc(&e->d_counter, 256);
+    if (err == cudaSuccess) err = cudaStreamCreateWithFlags(&e->stream, cudaStreamNonBlocking);
+    if (err != cudaSuccess) {
+        cudaFree(e->d_arena);
+        cudaFree(e->d_inst);
+        cudaFree(e->d_items);
+        cudaFree(e->d_counter);
+        delete e;
+        return efail_cuda(err, "numa_engine_create: reserving device memory");
+    }
+    e->arena.reset(static_cast<char *>(e->d_arena), budget_bytes);
+    *out = e;
+    return NUMA_OK;
+}
+
+int numa_engine_submit(numa_engine *e, const numa_vol *mesh, const void *q0_host, void *q_out_host,
+                       int nsteps, double dt, int64_t *id) {
+    g_engine_error.clear();
+    if (id) *id = 0;
+    if (!e) return efail(NUMA_EINVAL, "numa_engine_submit: NULL engine");
+    if (!mesh || !q0_host || !q_out_host)
+        return efail(NUMA_EINVAL, "numa_engine_submit: NULL mesh or buffer");
+    if (nsteps < 1 || !(dt > 0.0))
+        return efail(NUMA_EINVAL, "numa_engine_submit: need nsteps >= 1 and dt > 0");
+    const bool mixed = e->prec == NUMA_MIXED;
+    if (mixed ? mesh->kernel != numa::Kernel::Mixed : mesh->kernel != numa::Kernel::Native)
+        return efail(NUMA_EINVAL, "numa_engine_submit: mesh handle precision differs from the engine's");
+    if (mesh->device != e->device)
+        return efail(NUMA_EINVAL, "numa_engine_submit: mesh handle lives on another device");
+    const size_t bytes = state_bytes(e, mesh);
+    if (bytes > e->arena.size)
+        return efail(NUMA_ELIMIT, "numa_engine_submit: the member's state exceeds the whole HBM budget");
+    Request r{e->next_id++, mesh, q0_host, q_out_host, nsteps, nsteps, dt, bytes, SIZE_MAX,
+              NUMA_REQ_QUEUED};
+    numa_request_info inf{};
+    inf.id = r.id;
+    inf.status = NUMA_REQ_QUEUED;
+    inf.submit_s = now_s();
+    e->info[r.id] = inf;
+    e->queue.push_back(r);
+    if (id) *id = r.id;
+    return NUMA_OK;
+}
+
+int numa_engine_cancel(numa_engine *e, int64_t id) {
+    if (!e) return efail(NUMA_EINVAL, "numa_engine_cancel: NULL engine");
+    for (auto it = e->queue.begin(); it != e->queue.end(); ++it)
+        if (it->id == id) {
+            e->queue.erase(it);
+            set_status(e, id, NUMA_REQ_CANCELLED, true);
+            return NUMA_OK;
+        }
+    for (auto &r : e->resident)
+        if (r.id == id) {
+            r.status = NUMA_REQ_CANCELLED;   // retired at the start of the next round
+            return NUMA_OK;
+        }
+    return efail(NUMA_EINVAL, "numa_engine_cancel: no queued or running request with this id");
+}
+
+int numa_engine_progress(numa_engine *e, int64_t *done_ids, int max_done, int *num_done) {
+    g_engine_error.clear();
+    if (num_done) *num_done = 0;
+    if (!e) return efail(NUMA_EINVAL, "numa_engine_progress: NULL engine");
+    cudaError_t err = cudaSuccess;
+    // 1. retire cancelled members
+    for (size_t k = 0; k < e->resident.size();) {
+        Request &r = e->resident[k];
+        if (r.status == NUMA_REQ_CANCELLED) {
+            e->arena.release(r.off, r.bytes);
+            set_status(e, r.id, NUMA_REQ_CANCELLED, true);
+            e->resident.erase(e->resident.begin() + k);
+        } else {
+            ++k;
+        }
+    }
+    // 2. admit in arrival order
+    while (!e->queue.empty() && (int)e->resident.size() < e->max_members) {
+        Request r = e->queue.front();
+        const size_t off = e->arena.alloc(r.bytes);
+        if (off == SIZE_MAX) break;   // the head waits for room
+        e->queue.pop_front();
+        r.off = off;
+        r.status = NUMA_REQ_RUNNING;
+        err = cudaMemcpyAsync(e->arena.base + off, r.q0, r.bytes, cudaMemcpyHostToDevice, e->stream);
+        if (err != cudaSuccess) return efail_cuda(err, "numa_engine_progress: state upload");
+        e->info[r.id].status = NUMA_REQ_RUNNING;
+        e->info[r.id].admit_s = now_s();
+        e->resident.push_back(r);
+    }
+    if (e->resident.empty()) return NUMA_OK;
+    // 3. one step for every resident member, one launch per distinct dt
+    std::vector<double> dts;
+    for (const auto &r : e->resident)
+        if (std::find(dts.begin(), dts.end(), r.dt) == dts.end()) dts.push_back(r.dt);
+    for (double dt : dts) {
+        std::vector<numa::BatchInstance> inst;
+        for (const auto &r : e->resident) {
+            if (r.dt != dt) continue;
+            numa::BatchInstance I{};
+            I.N = r.mesh->N;
+            I.nq = r.mesh->Nq;
+            I.M = r.mesh->M;
+            I.q = e->arena.base + r.off;
+            I.geo = r.mesh->geo;
+            I.np = r.mesh->nparams;
+            I.mgeo = r.mesh->mgeo;
+            I.mp = r.mesh->mparams;
+            inst.push_back(I);
+            e->point_stages += 5.0 * (double)r.mesh->M;
+        }
+        int mult[9];
+        std::fill(mult, mult + 9, e->tile_mult);
+        std::vector<numa::BatchItem> items = numa::build_items(inst, mult);
+        if (items.size() > e->items_cap) {
+            cudaFree(e->d_items);
+            e->items_cap = items.size();
+            err = cudaMalloc(&e->d_items, sizeof(numa::BatchItem) * e->items_cap);
+            if (err != cudaSuccess) {
+                e->d_items = nullptr;
+                e->items_cap = 0;
+                return efail_cuda(err, "numa_engine_progress: work list");
+            }
+        }
+        err = cudaMemcpyAsync(e->d_inst, inst.data(), sizeof(numa::BatchInstance) * inst.size(),
+                              cudaMemcpyHostToDevice, e->stream);
+        if (err == cudaSuccess)
+            err = cudaMemcpyAsync(e->d_items, items.data(), sizeof(numa::BatchItem) * items.size(),
+                                  cudaMemcpyHostToDevice, e->stream);
+        if (err == cudaSuccess) err = cudaMemsetAsync(e->d_counter, 0, sizeof(int), e->stream);
+        if (err == cudaSuccess)
+            err = numa::launch_batch_lsrk(e->prec == NUMA_MIXED, e->d_inst, e->d_items,
+                                          (int)items.size(), e->d_counter, kCoef, 1, dt,
+                                          e->num_sms, e->stream);
+        // the host vectors are sources of in-flight copies: wait before they go
+        if (err == cudaSuccess) err = cudaStreamSynchronize(e->stream);
+        if (err != cudaSuccess) return efail_cuda(err, "numa_engine_progress: step");
+    }
+    ++e->rounds;
+    // 4. retire finished members
+    std::vector<Request> done;
+    for (size_t k = 0; k < e->resident.size();) {
+        Request &r = e->resident[k];
+        if (--r.remaining == 0) {
+            err = cudaMemcpyAsync(r.q_out, e->arena.base + r.off, r.bytes, cudaMemcpyDeviceToHost,
+                                  e->stream);
+            if (err != cudaSuccess) return efail_cuda(err, "numa_engine_progress: result copy");
+            done.push_back(r);
+            e->resident.erase(e->resident.begin() + k);
+        } else {
+            ++k;
+        }
+    }
+    if (!done.empty()) {
+        err = cudaStreamSynchronize(e->stream);
+        if (err != cudaSuccess) return efail_cuda(err, "numa_engine_progress: result copy");
+        int n = 0;
+        for (const auto &r : done) {
+            e->arena.release(r.off, r.bytes);
+            set_status(e, r.id, NUMA_REQ_DONE, true);
+            ++e->completed;
+            if (done_ids && n < max_done) done_ids[n] = r.id;
+            ++n;
+        }
+        if (num_done) *num_done = std::min(n, max_done);
+    }
+    return NUMA_OK;
+}
+
+int numa_engine_query(const numa_engine *e, int64_t id, numa_request_info *out) {
+    if (!e || !out) return efail(NUMA_EINVAL, "numa_engine_query: NULL argument");
+    auto it = e->info.find(id);
+    if (it == e->info.end()) return efail(NUMA_EINVAL, "numa_engine_query: unknown request id");
+    *out = it->second;
+    return NUMA_OK;
+}
+
+int numa_engine_stats(const numa_engine *e, numa_engine_counters *out) {
+    if (!e || !out) return efail(NUMA_EINVAL, "numa_engine_stats: NULL argument");
+    out->queued = (int)e->queue.size();
+    out->resident = (int)e->resident.size();
+    out->bytes_used = e->arena.used;
+    out->bytes_budget = e->arena.size;
+    out->completed = e->completed;
+    out->rounds = e->rounds;
+    out->point_stages = e->point_stages;
+    return NUMA_OK;
+}
+
+void numa_engine_destroy(numa_engine *e) {
+    if (!e) return;
+    if (e->stream) {
+        cudaStreamSynchronize(e->stream);
+        cudaStreamDestroy(e->stream);
+    }
+    cudaFree(e->d_arena);
+    cudaFree(e->d_inst);
+    cudaFree(e->d_items);
+    cudaFree(e->d_counter);
+    delete e;
+}
+
+}  // extern "C"

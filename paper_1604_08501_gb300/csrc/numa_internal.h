@@ -2,6 +2,8 @@
 #pragma once
 
 #include <cstdint>
+#include <vector>
+
 #include <cuda_runtime.h>
 
 #include "numa_vol.h"
@@ -157,6 +159,9 @@ cudaError_t launch_batch_lsrk(bool mixed, const BatchInstance *inst, const Batch
 
 // Elements one CTA pass holds for order Nq (512 threads, one per point).
 inline int elements_per_pass(int nq) { return 512 / (nq * nq * nq); }
+
+// Work list for instances with tile_mult[nq] passes per item (batch_abi.cu).
+std::vector<BatchItem> build_items(const std::vector<BatchInstance> &inst, const int *tile_mult);
 
 }  // namespace numa
 

@@ -16,7 +16,8 @@ import ctypes as C
 import numpy as np
 
 from . import _lib
-from ._lib import NUMA_DF64, NUMA_FP64, NUMA_MIXED, NumaError, check, check_batch
+from ._lib import (NUMA_DF64, NUMA_FP64, NUMA_MIXED, NumaError, check, check_batch,
+                   check_engine)
 
 NFIELDS = 5
 
@@ -247,4 +248,101 @@ class Batch:
             pass
 
 
-__all__ = ["VolumeTerm", "Batch", "diff_matrix", "NumaError"]
+def _host_ptr(a):
+    """Address of a host buffer (numpy array or CPU torch tensor)."""
+    if isinstance(a, np.ndarray):
+        if not a.flags.c_contiguous:
+            raise ValueError("host buffers must be contiguous")
+        return a.ctypes.data
+    import torch
+    if isinstance(a, torch.Tensor) and not a.is_cuda and a.is_contiguous():
+        return a.data_ptr()
+    raise TypeError("host buffers are numpy arrays or contiguous CPU tensors")
+
+
+class Engine:
+    """Serving engine (numa_engine_*): continuous batching of ensemble-member
+    requests.  Each request advances a copy of an initial state on a resident
+    mesh (a VolumeTerm) by nsteps low-storage RK steps; the final state lands
+    in the request's host output buffer."""
+
+    STATUS = {0: "queued", 1: "running", 2: "done", 3: "cancelled"}
+
+    def __init__(self, precision: str = "fp64", budget_bytes: int = 1 << 30,
+                 max_members: int = 256):
+        self.precision = precision
+        h = C.c_void_p()
+        prec = {"fp64": NUMA_FP64, "mixed": NUMA_MIXED}[precision]
+        check_engine(_lib.load().numa_engine_create(prec, int(budget_bytes), int(max_members),
+                                                    C.byref(h)))
+        self._h = h
+        self._bufs = {}          # request id -> (mesh, q0, out) kept alive while in flight
+
+    @property
+    def handle(self) -> int:
+        if self._h is None or not self._h.value:
+            raise RuntimeError("Engine is closed")
+        return self._h.value
+
+    def submit(self, mesh: "VolumeTerm", q0, out, nsteps: int, dt: float) -> int:
+        rid = C.c_int64()
+        check_engine(_lib.load().numa_engine_submit(
+            self.handle, C.c_void_p(mesh.handle), C.c_void_p(_host_ptr(q0)),
+            C.c_void_p(_host_ptr(out)), int(nsteps), float(dt), C.byref(rid)))
+        self._bufs[rid.value] = (mesh, q0, out)
+        return rid.value
+
+    def cancel(self, rid: int) -> None:
+        check_engine(_lib.load().numa_engine_cancel(self.handle, C.c_int64(rid)))
+
+    def progress(self, max_done: int = 4096):
+        ids = (C.c_int64 * max_done)()
+        n = C.c_int()
+        check_engine(_lib.load().numa_engine_progress(self.handle, ids, max_done, C.byref(n)))
+        done = [ids[k] for k in range(n.value)]
+        for rid in done:
+            self._bufs.pop(rid, None)
+        return done
+
+    def query(self, rid: int) -> dict:
+        info = _lib.numa_request_info()
+        check_engine(_lib.load().numa_engine_query(self.handle, C.c_int64(rid), C.byref(info)))
+        if info.status == 3:
+            self._bufs.pop(rid, None)
+        return {"id": info.id, "status": self.STATUS[info.status], "submit_s": info.submit_s,
+                "admit_s": info.admit_s, "done_s": info.done_s}
+
+    def stats(self) -> dict:
+        c = _lib.numa_engine_counters()
+        check_engine(_lib.load().numa_engine_stats(self.handle, C.byref(c)))
+        return {f: getattr(c, f) for f, _ in c._fields_}
+
+    def run_until_idle(self, max_rounds: int = 1_000_000):
+        done = []
+        for _ in range(max_rounds):
+            st = self.stats()
+            if st["queued"] == 0 and st["resident"] == 0:
+                break
+            done += self.progress()
+        return done
+
+    def close(self) -> None:
+        if getattr(self, "_h", None) is not None and self._h.value:
+            _lib.load().numa_engine_destroy(self._h)
+        self._h = None
+        self._bufs = {}
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+__all__ = ["VolumeTerm", "Batch", "Engine", "diff_matrix", "NumaError"]

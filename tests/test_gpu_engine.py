@@ -1,0 +1,163 @@
+"""GPU tests of the serving engine (numa_engine_*): continuous batching of
+ensemble-member requests.
+
+* Each request's result equals the batched integrator's on the same member,
+  bitwise.  It is within the batch tests' 3e-12 (FP64 increments) of the
+  oracle's integrator.
+* A request's result is bitwise the same alone and in a mix where other
+  requests arrive while it runs.
+* Admission by the HBM budget: a request that does not fit waits, then runs.
+* Host-side failures return status codes and leave the engine usable:
+  malformed requests, a state larger than the budget, cancellation of a queued
+  and of a running request.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1604_08501_gb300 import build
+from paper_1604_08501_gb300 import workload as wl
+from paper_1604_08501_gb300.numa_vol import Batch, Engine, NumaError, VolumeTerm
+from conftest import rel_err
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+DT = 0.01
+MESHES = [(3, (3, 2, 1), 31), (7, (2, 1, 1), 32), (5, (2, 2, 1), 33), (4, (2, 2, 2), 34)]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    build.build()
+
+
+@pytest.fixture(scope="module")
+def pool():
+    works = [wl.make_workload(N, shape, seed=seed) for N, shape, seed in MESHES]
+    vts = [VolumeTerm.from_problem(w.problem()) for w in works]
+    yield works, vts
+    for vt in vts:
+        vt.close()
+
+
+def batch_reference(vt, q0, nsteps, precision="fp64"):
+    q = torch.from_numpy(np.ascontiguousarray(q0)).cuda()
+    with Batch(precision) as b:
+        b.add(vt, q)
+        b.advance(nsteps, DT)
+    torch.cuda.synchronize()
+    return q.cpu().numpy()
+
+
+def test_results_equal_the_batch_and_the_oracle(pool):
+    works, vts = pool
+    ks = [3, 1, 5, 2]
+    outs = [np.empty_like(w.q) for w in works]
+    with Engine("fp64", budget_bytes=1 << 30) as eng:
+        ids = [eng.submit(vt, w.q, o, k, DT) for vt, w, o, k in zip(vts, works, outs, ks)]
+        done = eng.run_until_idle()
+        assert sorted(done) == sorted(ids)
+        for rid in ids:
+            assert eng.query(rid)["status"] == "done"
+    for w, vt, o, k in zip(works, vts, outs, ks):
+        assert np.array_equal(o, batch_reference(vt, w.q, k))
+        ref = oracle.lsrk(w.problem(), w.q, DT, k)
+        for f, (mx, _) in enumerate(rel_err(o - w.q, ref - w.q)):
+            assert mx <= 3e-12, (w.N, k, f, mx)
+
+
+def test_result_is_the_same_alone_and_in_the_mix(pool):
+    works, vts = pool
+    w, vt = works[1], vts[1]
+    alone = np.empty_like(w.q)
+    with Engine("fp64", budget_bytes=1 << 30) as eng:
+        eng.submit(vt, w.q, alone, 4, DT)
+        eng.run_until_idle()
+    mixed = np.empty_like(w.q)
+    others = [np.empty_like(x.q) for x in works]
+    with Engine("fp64", budget_bytes=1 << 30) as eng:
+        eng.submit(vts[0], works[0].q, others[0], 6, DT)
+        eng.progress()                                    # round 1: member 0 alone
+        rid = eng.submit(vt, w.q, mixed, 4, DT)           # arrives while 0 runs
+        eng.progress()
+        eng.submit(vts[2], works[2].q, others[2], 2, DT)  # arrives while both run
+        eng.submit(vts[3], works[3].q, others[3], 1, DT)
+        eng.progress()
+        assert eng.stats()["resident"] >= 2              # work overlaps in one launch
+        eng.run_until_idle()
+        assert eng.query(rid)["status"] == "done"
+    assert np.array_equal(alone, mixed)
+
+
+def test_admission_waits_for_budget(pool):
+    works, vts = pool
+    w = works[3]
+    need = w.q.nbytes
+    outs = [np.empty_like(w.q) for _ in range(3)]
+    with Engine("fp64", budget_bytes=need + 4096, max_members=8) as eng:
+        ids = [eng.submit(vts[3], w.q, o, 2, DT) for o in outs]
+        seen = []
+        while True:
+            st = eng.stats()
+            if st["queued"] == 0 and st["resident"] == 0:
+                break
+            eng.progress()
+            seen.append(eng.stats()["resident"])
+        assert max(seen) <= 1                             # one member fits at a time
+        for rid in ids:
+            assert eng.query(rid)["status"] == "done"
+        assert eng.stats()["bytes_used"] == 0
+    ref = batch_reference(vts[3], w.q, 2)
+    for o in outs:
+        assert np.array_equal(o, ref)
+
+
+def test_host_side_failures_return_codes_and_leave_the_engine_usable(pool):
+    works, vts = pool
+    w, vt = works[0], vts[0]
+    out = np.empty_like(w.q)
+    with Engine("fp64", budget_bytes=w.q.nbytes + 4096) as eng:
+        with pytest.raises(NumaError, match="EINVAL"):
+            eng.submit(vt, w.q, out, 0, DT)                  # malformed: no steps
+        with pytest.raises(NumaError, match="EINVAL"):
+            eng.submit(vt, w.q, out, 2, -1.0)                # malformed: dt <= 0
+        big = works[3]
+        with pytest.raises(NumaError, match="ELIMIT"):
+            eng.submit(vts[3], big.q, np.empty_like(big.q), 1, DT)   # exceeds the whole budget
+        mixed_vt = VolumeTerm.from_problem(w.problem(), precision="mixed")
+        with pytest.raises(NumaError, match="precision"):
+            eng.submit(mixed_vt, w.q_mixed(), np.empty_like(w.q_mixed()), 1, DT)
+        mixed_vt.close()
+        # cancellation: a queued request never runs, a running one is retired
+        a = eng.submit(vt, w.q, out, 5, DT)
+        b = eng.submit(vt, w.q, np.empty_like(w.q), 5, DT)   # queued behind a (budget)
+        eng.progress()
+        assert eng.query(a)["status"] == "running" and eng.query(b)["status"] == "queued"
+        eng.cancel(b)
+        eng.cancel(a)
+        assert eng.query(b)["status"] == "cancelled"
+        eng.progress()
+        assert eng.query(a)["status"] == "cancelled"
+        assert eng.stats()["bytes_used"] == 0 and eng.stats()["resident"] == 0
+        with pytest.raises(NumaError):
+            eng.cancel(a)                                    # already finished
+        # still serves
+        c = eng.submit(vt, w.q, out, 1, DT)
+        eng.run_until_idle()
+        assert eng.query(c)["status"] == "done"
+    assert np.array_equal(out, batch_reference(vt, w.q, 1))
+
+
+def test_mixed_precision_engine_matches_its_batch(pool):
+    works, _ = pool
+    w = works[2]
+    vt = VolumeTerm.from_problem(w.problem(), precision="mixed")
+    q0 = w.q_mixed()
+    out = np.empty_like(q0)
+    with Engine("mixed", budget_bytes=1 << 28) as eng:
+        eng.submit(vt, q0, out, 3, DT)
+        eng.run_until_idle()
+    assert np.array_equal(out, batch_reference(vt, q0, 3, "mixed"))
+    vt.close()
