@@ -23,6 +23,8 @@
 // from the batch's autotuner.
 #include <cuda_runtime.h>
 
+#include <mutex>
+
 #include "batch_tile.cuh"
 
 namespace numa {
@@ -36,6 +38,8 @@ batch_lsrk_kernel(const BatchInstance *__restrict__ inst, const BatchItem *__res
     extern __shared__ __align__(16) double smem_d[];
     __shared__ BatchInstance sI;
     __shared__ int s_item;
+    __shared__ tile_t<MIXED> sco[10];
+    load_stage_coefficients<MIXED>(co, sco);   // visible after the first barrier below
     for (;;) {
         if (threadIdx.x == 0) s_item = atomicAdd(counter, 1);
         __syncthreads();
@@ -51,13 +55,13 @@ batch_lsrk_kernel(const BatchInstance *__restrict__ inst, const BatchItem *__res
         }
         __syncthreads();
         switch (item.nq) {
-            case 2: run_tile<2, MIXED>(sI, item.e0, item.count, co, nsteps, dt, smem_d); break;
-            case 3: run_tile<3, MIXED>(sI, item.e0, item.count, co, nsteps, dt, smem_d); break;
-            case 4: run_tile<4, MIXED>(sI, item.e0, item.count, co, nsteps, dt, smem_d); break;
-            case 5: run_tile<5, MIXED>(sI, item.e0, item.count, co, nsteps, dt, smem_d); break;
-            case 6: run_tile<6, MIXED>(sI, item.e0, item.count, co, nsteps, dt, smem_d); break;
-            case 7: run_tile<7, MIXED>(sI, item.e0, item.count, co, nsteps, dt, smem_d); break;
-            case 8: run_tile<8, MIXED>(sI, item.e0, item.count, co, nsteps, dt, smem_d); break;
+            case 2: run_tile<2, MIXED>(sI, item.e0, item.count, sco, nsteps, dt, smem_d); break;
+            case 3: run_tile<3, MIXED>(sI, item.e0, item.count, sco, nsteps, dt, smem_d); break;
+            case 4: run_tile<4, MIXED>(sI, item.e0, item.count, sco, nsteps, dt, smem_d); break;
+            case 5: run_tile<5, MIXED>(sI, item.e0, item.count, sco, nsteps, dt, smem_d); break;
+            case 6: run_tile<6, MIXED>(sI, item.e0, item.count, sco, nsteps, dt, smem_d); break;
+            case 7: run_tile<7, MIXED>(sI, item.e0, item.count, sco, nsteps, dt, smem_d); break;
+            case 8: run_tile<8, MIXED>(sI, item.e0, item.count, sco, nsteps, dt, smem_d); break;
             default: break;
         }
         __syncthreads();   // sI and s_item are rewritten by the next claim
@@ -67,6 +71,21 @@ batch_lsrk_kernel(const BatchInstance *__restrict__ inst, const BatchItem *__res
 }  // namespace
 
 cudaError_t prepare_batch_lsrk() {
+    // once per device: the sweep tables into this unit's constant memory
+    static std::mutex mu;
+    static bool uploaded[64] = {};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    {
+        std::lock_guard<std::mutex> lock(mu);
+        if (!uploaded[dev]) {
+            e = upload_sweep_tables();
+            if (e != cudaSuccess) return e;
+            uploaded[dev] = true;
+        }
+    }
     return cudaFuncSetAttribute(batch_lsrk_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)(sizeof(double) * 3 * kFields * kThreads));
 }

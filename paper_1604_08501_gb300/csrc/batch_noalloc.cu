@@ -52,6 +52,8 @@ batch_lsrk_noalloc_kernel(unsigned char *scratch, LsrkCoef co, int nsteps, doubl
     extern __shared__ __align__(16) double smem_d[];
     __shared__ BatchInstance sI;
     __shared__ int s_item;
+    __shared__ tile_t<MIXED> sco[10];
+    load_stage_coefficients<MIXED>(co, sco);   // visible after the first barrier below
     const int num_items = tab->num_items;
     for (;;) {
         if (threadIdx.x == 0) s_item = atomicAdd(counter, 1);
@@ -73,13 +75,13 @@ batch_lsrk_noalloc_kernel(unsigned char *scratch, LsrkCoef co, int nsteps, doubl
         const int64_t e0 = (int64_t)(it - tab->first_item[k]) * tile;
         const int64_t count = ne - e0 < tile ? ne - e0 : tile;
         switch (nq) {
-            case 2: run_tile<2, MIXED>(sI, e0, count, co, nsteps, dt, smem_d); break;
-            case 3: run_tile<3, MIXED>(sI, e0, count, co, nsteps, dt, smem_d); break;
-            case 4: run_tile<4, MIXED>(sI, e0, count, co, nsteps, dt, smem_d); break;
-            case 5: run_tile<5, MIXED>(sI, e0, count, co, nsteps, dt, smem_d); break;
-            case 6: run_tile<6, MIXED>(sI, e0, count, co, nsteps, dt, smem_d); break;
-            case 7: run_tile<7, MIXED>(sI, e0, count, co, nsteps, dt, smem_d); break;
-            case 8: run_tile<8, MIXED>(sI, e0, count, co, nsteps, dt, smem_d); break;
+            case 2: run_tile<2, MIXED>(sI, e0, count, sco, nsteps, dt, smem_d); break;
+            case 3: run_tile<3, MIXED>(sI, e0, count, sco, nsteps, dt, smem_d); break;
+            case 4: run_tile<4, MIXED>(sI, e0, count, sco, nsteps, dt, smem_d); break;
+            case 5: run_tile<5, MIXED>(sI, e0, count, sco, nsteps, dt, smem_d); break;
+            case 6: run_tile<6, MIXED>(sI, e0, count, sco, nsteps, dt, smem_d); break;
+            case 7: run_tile<7, MIXED>(sI, e0, count, sco, nsteps, dt, smem_d); break;
+            case 8: run_tile<8, MIXED>(sI, e0, count, sco, nsteps, dt, smem_d); break;
             default: break;
         }
         __syncthreads();   // sI and s_item are rewritten by the next claim
@@ -96,7 +98,7 @@ const LsrkCoef kCoef = {
      2277821191437.0 / 14882151754819.0}};
 
 // One-time set-up per device, with that device current: the device address of
-// the scratch array and the kernels' shared-memory opt-in.
+// the scratch array, the sweep tables and the kernels' shared-memory opt-in.
 constexpr int kMaxDevices = 64;
 struct DeviceSetup {
     bool done;
@@ -114,6 +116,8 @@ cudaError_t setup(int dev, DeviceSetup *out) {
         cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
         if (e != cudaSuccess) return e;
         e = cudaDeviceGetAttribute(&s.num_sms, cudaDevAttrMultiProcessorCount, dev);
+        if (e != cudaSuccess) return e;
+        e = upload_sweep_tables();
         if (e != cudaSuccess) return e;
         e = cudaFuncSetAttribute(batch_lsrk_noalloc_kernel<false>,
                                  cudaFuncAttributeMaxDynamicSharedMemorySize,

@@ -3,6 +3,8 @@
 // 5 * nsteps stages (see batch_lsrk.cu for the scheme and the design).
 #pragma once
 
+#include <cuda_runtime.h>
+
 #include <type_traits>
 
 #include "element_sweep.cuh"
@@ -15,20 +17,79 @@ namespace {
 
 constexpr int kThreads = 512;
 
+// Sweep tables per Nq (index Nq; 2..8 used).  They depend only on the order:
+// every handle's D is the library's GLL D.  In constant memory, every
+// coefficient of a sweep is a constant-bank operand of its FMA, as in the
+// single-evaluation kernels, where the tables are kernel parameters.
+template <typename T>
+struct SweepTables {
+    T De[16], Do[16], Dc[4], Dcr[4];
+};
+__constant__ SweepTables<double> c_sweep64[9];
+__constant__ SweepTables<float> c_sweep32[9];
+
+// Fills this translation unit's tables on the current device (synchronous).
+inline cudaError_t upload_sweep_tables() {
+    SweepTables<double> t64[9] = {};
+    SweepTables<float> t32[9] = {};
+    for (int N = 1; N <= 7; ++N) {
+        double D[64];
+        gll_diff_matrix(N, D);
+        SweepTables<double> &a = t64[N + 1];
+        sweep_tables(N, D, a.De, a.Do, a.Dc, a.Dcr);
+        SweepTables<float> &b = t32[N + 1];
+        for (int t = 0; t < 16; ++t) {
+            b.De[t] = static_cast<float>(a.De[t]);
+            b.Do[t] = static_cast<float>(a.Do[t]);
+        }
+        for (int t = 0; t < 4; ++t) {
+            b.Dc[t] = static_cast<float>(a.Dc[t]);
+            b.Dcr[t] = static_cast<float>(a.Dcr[t]);
+        }
+    }
+    cudaError_t e = cudaMemcpyToSymbol(c_sweep64, t64, sizeof(t64));
+    if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_sweep32, t32, sizeof(t32));
+    return e;
+}
+
+// Stage coefficients of the scheme in the tile's arithmetic type: A[s] at
+// [s], B[s] at [5 + s].  The kernels keep them in shared memory.
+template <bool MIXED>
+using tile_t = typename std::conditional<MIXED, float, double>::type;
+
+template <bool MIXED>
+__device__ __forceinline__ void load_stage_coefficients(const LsrkCoef &co, tile_t<MIXED> *sco) {
+    if (threadIdx.x < 5) {
+        sco[threadIdx.x] = static_cast<tile_t<MIXED>>(co.A[threadIdx.x]);
+        sco[5 + threadIdx.x] = static_cast<tile_t<MIXED>>(co.B[threadIdx.x]);
+    }
+}
+
 template <int NQ, bool MIXED>
-__device__ void run_tile(const BatchInstance &I, int64_t e0, int64_t count, const LsrkCoef &co,
-                         int nsteps, double dt, void *smem) {
-    using T = typename std::conditional<MIXED, float, double>::type;
+__device__ void run_tile(const BatchInstance &I, int64_t e0, int64_t count,
+                         const tile_t<MIXED> *sco, int nsteps, double dt, void *smem) {
+    using T = tile_t<MIXED>;
     constexpr int N3 = NQ * NQ * NQ;
     constexpr int NL = NQ * NQ;
     constexpr int EPP = kThreads / N3;          // elements per pass
+    constexpr int BLK = EPP * N3;               // one (direction, field) block of sF
+    constexpr int TASKS = 3 * kFields * EPP * NL;   // lines per stage
     T *sF = static_cast<T *>(smem);             // [(d*5 + b)*EPP + el][slot]
     const int l = threadIdx.x;
     const int el = l / N3, p = l % N3;
     const int i = p % NQ, j = (p / NQ) % NQ, k = p / NL;
+    // this thread's flux slot of field b in direction d: f[d] + b * BLK
+    int f[3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) f[d] = d * kFields * BLK + el * N3 + dir_slot<NQ, T>(d, i, j, k);
     const int64_t M = I.M;
     T *qv = static_cast<T *>(I.q);
     const T dtt = static_cast<T>(dt);
+    T grav;
+    if constexpr (MIXED)
+        grav = I.mp.grav;
+    else
+        grav = I.np.eos.grav;
 
     for (int64_t base = e0; base < e0 + count; base += EPP) {
         const int npass = (int)((e0 + count - base) < EPP ? (e0 + count - base) : EPP);
@@ -41,6 +102,16 @@ __device__ void run_tile(const BatchInstance &I, int64_t e0, int64_t count, cons
             dq[b] = T(0);
         }
         if (!active) q[0] = MIXED ? T(0) : T(1);   // idle threads hold a harmless state
+        // per-point constants of the mixed mode, kept for all stages
+        float th0 = 0.f, rho0 = 0.f;
+        EosRef32 er{0.f, 0.f};
+        if constexpr (MIXED) {
+            if (active) {
+                th0 = __ldg(I.mgeo.theta_ref + node);
+                rho0 = __ldg(I.mgeo.rho_ref + node);
+                if (th0 > 0.f) er = eos_reference_f32(th0, I.mp);
+            }
+        }
 
         for (int step = 0; step < nsteps; ++step) {
 #pragma unroll 1
@@ -52,10 +123,9 @@ __device__ void run_tile(const BatchInstance &I, int64_t e0, int64_t count, cons
                     if constexpr (MIXED) {
 #pragma unroll
                         for (int s2 = 0; s2 < 9; ++s2) g[s2] = __ldg(I.mgeo.g[s2] + node);
-                        const T t0 = __ldg(I.mgeo.theta_ref + node);
-                        rho = __ldg(I.mgeo.rho_ref + node) + q[0];
-                        Th = t0 + q[4];
-                        pp = pressure_perturbation_f32(q[4], t0, I.mp);
+                        rho = rho0 + q[0];
+                        Th = th0 + q[4];
+                        pp = pressure_perturbation_f32(q[4], th0, er, I.mp);
                     } else {
 #pragma unroll
                         for (int s2 = 0; s2 < 9; ++s2) g[s2] = __ldg(I.geo.g[s2] + node);
@@ -64,45 +134,49 @@ __device__ void run_tile(const BatchInstance &I, int64_t e0, int64_t count, cons
                         pp = pressure_perturbation(Th, __ldg(I.geo.theta_ref + node),
                                                    __ldg(I.geo.w + node), __ldg(I.geo.A + node), I.np);
                     }
-                    const T rinv = T(1) / rho;
+                    T rinv;
+                    if constexpr (MIXED)
+                        rinv = T(1) / rho;
+                    else
+                        rinv = __drcp_rn(rho);   // the correctly rounded 1/rho, as 1.0 / rho
 #pragma unroll
                     for (int d = 0; d < 3; ++d) {
                         const T g1 = g[3 * d], g2 = g[3 * d + 1], g3 = g[3 * d + 2];
                         const T v = fma(g3, q[3], fma(g2, q[2], g1 * q[1]));
                         const T u = v * rinv;
-                        T *F = sF + (d * kFields * EPP + el) * N3 + dir_slot<NQ, T>(d, i, j, k);
-                        F[0 * EPP * N3] = v;
-                        F[1 * EPP * N3] = fma(q[1], u, g1 * pp);
-                        F[2 * EPP * N3] = fma(q[2], u, g2 * pp);
-                        F[3 * EPP * N3] = fma(q[3], u, g3 * pp);
-                        F[4 * EPP * N3] = Th * u;
+                        T *F = sF + f[d];
+                        F[0 * BLK] = v;
+                        F[1 * BLK] = fma(q[1], u, g1 * pp);
+                        F[2 * BLK] = fma(q[2], u, g2 * pp);
+                        F[3 * BLK] = fma(q[3], u, g3 * pp);
+                        F[4 * BLK] = Th * u;
                     }
                 }
                 __syncthreads();
-                // ---- phase 2: sweeps ------------------------------------
-                for (int t = l; t < 3 * kFields * npass * NL; t += kThreads) {
-                    const int bd = t / (npass * NL), rem = t % (npass * NL);
-                    if constexpr (MIXED)
-                        sweep_line<NQ>(sF + (bd * EPP + rem / NL) * N3, rem % NL, I.mp);
-                    else
-                        sweep_line<NQ>(sF + (bd * EPP + rem / NL) * N3, rem % NL, I.np);
+                // ---- phase 2: sweeps, one line per task ------------------
+#pragma unroll 1
+                for (int t = l; t < TASKS; t += kThreads) {
+                    const int bd = t / (EPP * NL), rem = t % (EPP * NL);
+                    const int e = rem / NL, line = rem % NL;
+                    if (e < npass) {
+                        if constexpr (MIXED)
+                            sweep_line<NQ>(sF + bd * BLK + e * N3, line, c_sweep32[NQ]);
+                        else
+                            sweep_line<NQ>(sF + bd * BLK + e * N3, line, c_sweep64[NQ]);
+                    }
                 }
                 __syncthreads();
                 // ---- phase 3: rhs, stage update ------------------------
                 if (active) {
-                    const T a = static_cast<T>(co.A[st]), bcoef = static_cast<T>(co.B[st]);
+                    const T a = sco[st], bcoef = sco[5 + st];
                     const T jinv = MIXED ? T(__ldg(I.mgeo.Jinv + node)) : T(__ldg(I.geo.Jinv + node));
                     // rho - rho_ref of this stage's state, taken before q is updated below
                     const T drho = MIXED ? q[0] : q[0] - T(__ldg(I.geo.rho_ref + node));
 #pragma unroll
                     for (int b = 0; b < kFields; ++b) {
-                        const T *base_b = sF + el * N3;
-                        const T R = base_b[(0 * kFields + b) * EPP * N3 + dir_slot<NQ, T>(0, i, j, k)] +
-                                    base_b[(1 * kFields + b) * EPP * N3 + dir_slot<NQ, T>(1, i, j, k)] +
-                                    base_b[(2 * kFields + b) * EPP * N3 + dir_slot<NQ, T>(2, i, j, k)];
+                        const T R = sF[f[0] + b * BLK] + sF[f[1] + b * BLK] + sF[f[2] + b * BLK];
                         T rhs = -jinv * R;
-                        if (b == 3)
-                            rhs = fma(-drho, static_cast<T>(MIXED ? I.mp.grav : I.np.eos.grav), rhs);
+                        if (b == 3) rhs = fma(-drho, grav, rhs);
                         dq[b] = fma(a, dq[b], dtt * rhs);
                         q[b] = fma(bcoef, dq[b], q[b]);
                     }

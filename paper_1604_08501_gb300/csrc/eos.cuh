@@ -5,9 +5,13 @@
 // Both evaluate p' = p_ref ((1 + x)^gamma - 1) with x = Theta'/Theta_ref,
 // written A Theta' g(x) with A = p_ref / Theta_ref and
 // g(x) = sum_k binom(gamma, k) x^(k-1).  That is the same quantity as the
-// difference of two pressures, without its cancellation.  The series is used
-// for |x| <= 1/64; elsewhere (and where Theta_ref = 0) the definition is
-// evaluated.
+// difference of two pressures, without its cancellation.  FP64 takes 9 terms
+// of the series for |x| <= 1/64 and 15 for |x| <= 1/8 (truncation below
+// 2^-55 relative for gamma near 1.4 in both); FP32 takes 5 terms for
+// |x| <= 1/64.  Elsewhere (and where Theta_ref = 0) a closed form is
+// evaluated.  The second FP64 tier matters in time integration: a state
+// advanced over many stages drifts past 1/64 at some points, and a warp with
+// one such lane would otherwise pay for two pow calls.
 #pragma once
 
 #include "numa_internal.h"
@@ -26,10 +30,17 @@ static __device__ __forceinline__ double pressure_perturbation(double Th, double
                                                         const NativeParams &P) {
     const double thp = Th - th0;              // Theta'
     const double x = thp * w;                 // Theta' / Theta_ref
-    if (fabs(x) <= 0.015625) {
+    const double ax = fabs(x);
+    if (ax <= 0.015625) {
         double g = P.c[8];
 #pragma unroll
         for (int k = 7; k >= 0; --k) g = fma(g, x, P.c[k]);   // sum_k c_{k+1} x^k
+        return (A * thp) * g;
+    }
+    if (ax <= 0.125) {
+        double g = P.c[14];
+#pragma unroll
+        for (int k = 13; k >= 0; --k) g = fma(g, x, P.c[k]);
         return (A * thp) * g;
     }
     // Outside the series range (or Theta_ref = 0, where w and A are not finite
@@ -40,22 +51,36 @@ static __device__ __forceinline__ double pressure_perturbation(double Th, double
 // FP32 form from the perturbation Theta' itself (mixed precision): series
 // for |x| <= 1/64, expm1(gamma log1p(x)) beyond, both free of cancellation.
 // A = K Theta_ref^(gamma - 1) with K = p0^(1 - gamma) R^gamma is recomputed
-// here instead of being read from memory.
-static __device__ __forceinline__ float pressure_perturbation_f32(float thp, float th0,
+// from Theta_ref instead of being read from memory.  eos_reference_f32 forms
+// the per-point factors (w = 1/Theta_ref and A), which a caller that keeps a
+// point for many evaluations computes once.
+struct EosRef32 {
+    float w, A;
+};
+
+static __device__ __forceinline__ EosRef32 eos_reference_f32(float th0, const MixedParams &P) {
+    return EosRef32{1.0f / th0, P.K * exp2f(P.gm1 * log2f(th0))};   // A = p(Theta_ref)/Theta_ref
+}
+
+static __device__ __forceinline__ float pressure_perturbation_f32(float thp, float th0, EosRef32 r,
                                                            const MixedParams &P) {
     if (th0 > 0.0f) {
-        const float w = 1.0f / th0;
-        const float A = P.K * exp2f(P.gm1 * log2f(th0));      // p(Theta_ref) / Theta_ref
-        const float x = thp * w;
+        const float x = thp * r.w;
         if (fabsf(x) <= 0.015625f) {
             float g = P.c[4];
 #pragma unroll
             for (int k = 3; k >= 0; --k) g = fmaf(g, x, P.c[k]);   // sum_k c_{k+1} x^k
-            return (A * thp) * g;
+            return (r.A * thp) * g;
         }
-        return (A * th0) * expm1f(P.gamma * log1pf(x));
+        return (r.A * th0) * expm1f(P.gamma * log1pf(x));
     }
     // Theta_ref = 0 (the paper's full-pressure form): p' = p(Theta').
+    return P.K * powf(thp, P.gamma);
+}
+
+static __device__ __forceinline__ float pressure_perturbation_f32(float thp, float th0,
+                                                           const MixedParams &P) {
+    if (th0 > 0.0f) return pressure_perturbation_f32(thp, th0, eos_reference_f32(th0, P), P);
     return P.K * powf(thp, P.gamma);
 }
 

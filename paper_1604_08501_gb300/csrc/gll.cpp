@@ -73,4 +73,22 @@ int gll_diff_matrix(int N, double *D) {
     return NUMA_OK;
 }
 
+void sweep_tables(int N, const double *D, double De[16], double Do[16], double Dc[4],
+                  double Dcr[4]) {
+    for (int t = 0; t < 16; ++t) De[t] = Do[t] = 0.0;
+    for (int t = 0; t < 4; ++t) Dc[t] = Dcr[t] = 0.0;
+    const int Nq = N + 1, half = Nq / 2, ctr = Nq / 2;
+    for (int r = 0; r < half; ++r) {
+        for (int m = 0; m < half; ++m) {
+            const long double a = D[r * Nq + m], b = D[r * Nq + (Nq - 1 - m)];
+            De[r * half + m] = static_cast<double>((a + b) / 2);
+            Do[r * half + m] = static_cast<double>((a - b) / 2);
+        }
+        if (Nq & 1) {
+            Dc[r] = D[r * Nq + ctr];
+            Dcr[r] = D[ctr * Nq + r];
+        }
+    }
+}
+
 }  // namespace numa

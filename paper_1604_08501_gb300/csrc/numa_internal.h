@@ -34,13 +34,13 @@ struct EosConstants {
 };
 
 // Parameters of the native kernel: EOS constants, c[k] = binom(gamma, k+1)
-// (k = 0..8, the coefficients of the p' series), and the even-odd pieces of D
+// (k = 0..14, the coefficients of the p' series), and the even-odd pieces of D
 // for r, m < Nq/2: De = (D[r][m] + D[r][N-m])/2, Do = (D[r][m] - D[r][N-m])/2,
 // Dc[r] = D[r][c] and Dcr[m] = D[c][m] (centre column and row, odd Nq).
 // Uniform across threads, so the kernel reads them as constant-bank operands.
 struct NativeParams {
     EosConstants eos;
-    double c[9];
+    double c[15];
     double De[16], Do[16], Dc[4], Dcr[4];
 };
 
@@ -105,6 +105,11 @@ cudaError_t launch_vol_rhs_mixed(int N, ElemRange r, const MixedGeometry &geo,
 
 // GLL points and differentiation matrix on the host (gll.cpp).
 int gll_diff_matrix(int N, double *D);
+
+// Even-odd sweep tables of the order-N GLL D (Nq = N + 1): De, Do
+// ((Nq/2)^2, row-major), Dc, Dcr (odd Nq).  Unused entries are zero.
+void sweep_tables(int N, const double *D, double De[16], double Do[16], double Dc[4],
+                  double Dcr[4]);
 
 // Double-float value: the unevaluated sum h + l of two floats.
 struct df {

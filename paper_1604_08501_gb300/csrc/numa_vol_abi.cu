@@ -87,31 +87,18 @@ numa::df split_host(long double x) {
     return numa::df{h, l};
 }
 
-// binom(gamma, k) for k = 0..9, in long double.
-void binomial_coefficients(double gamma, long double c[10]) {
+// binom(gamma, k) for k = 0..15, in long double.
+void binomial_coefficients(double gamma, long double c[16]) {
     c[0] = 1.0L;
-    for (int k = 1; k < 10; ++k) c[k] = c[k - 1] * ((long double)gamma - (k - 1)) / k;
+    for (int k = 1; k < 16; ++k) c[k] = c[k - 1] * ((long double)gamma - (k - 1)) / k;
 }
 
 void build_params(numa_vol *h, const double *D) {
-    long double c[10];
+    long double c[16];
     binomial_coefficients(h->eos.gamma, c);
     h->nparams.eos = h->eos;
-    for (int k = 0; k < 9; ++k) h->nparams.c[k] = static_cast<double>(c[k + 1]);
-    {
-        const int Nq = h->Nq, half = Nq / 2, ctr = Nq / 2;
-        for (int r = 0; r < half; ++r) {
-            for (int m = 0; m < half; ++m) {
-                const long double a = D[r * Nq + m], b = D[r * Nq + (Nq - 1 - m)];
-                h->nparams.De[r * half + m] = static_cast<double>((a + b) / 2);
-                h->nparams.Do[r * half + m] = static_cast<double>((a - b) / 2);
-            }
-            if (Nq & 1) {
-                h->nparams.Dc[r] = D[r * Nq + ctr];
-                h->nparams.Dcr[r] = D[ctr * Nq + r];
-            }
-        }
-    }
+    for (int k = 0; k < 15; ++k) h->nparams.c[k] = static_cast<double>(c[k + 1]);
+    numa::sweep_tables(h->N, D, h->nparams.De, h->nparams.Do, h->nparams.Dc, h->nparams.Dcr);
     {
         numa::MixedParams &m = h->mparams;
         for (int t = 0; t < 16; ++t) {

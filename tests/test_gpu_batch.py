@@ -184,3 +184,24 @@ def test_batch_of_the_mixed_size_plan_on_a_sample():
         for f, (mx, _) in enumerate(rel_err(got - q0, ref - q0)):
             assert mx <= 3e-12, (w.N, w.Ne, f, mx)
         vt.close()
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 3e-12), ("mixed", 1e-5)])
+def test_batch_across_the_eos_branches(precision, tol):
+    # Theta'/Theta_ref spread over all ranges of the pressure perturbation
+    # (series of 9 and 15 terms, closed form beyond 1/8), as states reach
+    # after many steps.
+    w = wl.make_workload(5, (2, 2, 1), seed=21)
+    x = np.random.default_rng(3).choice([1e-3, 0.03, -0.07, 0.11, -0.2], size=w.M)
+    w.q[4] = w.rhotheta_ref * (1.0 + x)
+    vt = VolumeTerm.from_problem(w.problem(), precision=precision)
+    q0 = w.q_mixed() if precision == "mixed" else w.q
+    q = torch.from_numpy(np.ascontiguousarray(q0)).cuda()
+    with Batch(precision) as b:
+        b.add(vt, q)
+        b.advance(NSTEPS, DT)
+    torch.cuda.synchronize()
+    errs = increment_errors(w, q.cpu().numpy(), mixed=precision == "mixed")
+    for f, (mx, _) in enumerate(errs):
+        assert mx <= tol, (precision, wl.FIELD_NAMES[f], mx)
+    vt.close()

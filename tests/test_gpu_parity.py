@@ -63,6 +63,20 @@ def test_parity_every_order_and_odd_sizes(N, shape):
     assert_parity(gpu_rhs(prob, w.q), oracle.vol_rhs_o2(prob, w.q), label=f"N={N} {shape}")
 
 
+@pytest.mark.parametrize("N", [3, 7])
+def test_parity_across_the_eos_branches(N):
+    # Theta'/Theta_ref in each range of the kernel's pressure perturbation:
+    # |x| <= 1/64 (9-term series), 1/64 < |x| <= 1/8 (15-term series) and
+    # |x| > 1/8 (pow), with warps that mix them.
+    w = wl.make_workload(N, (3, 2, 1), seed=40 + N)
+    q = w.q.copy()
+    rng = np.random.default_rng(N)
+    x = rng.choice([1e-3, -1e-3, 0.02, -0.05, 0.1, -0.12, 0.125, 0.2, -0.3], size=w.M)
+    q[4] = w.rhotheta_ref * (1.0 + x)
+    prob = w.problem()
+    assert_parity(gpu_rhs(prob, q), oracle.vol_rhs_o2(prob, q), label=f"N={N} EOS branches")
+
+
 def test_parity_full_size_workload():
     # N = 7 (Nq = 8), 32^3 = 32768 elements (16.8M points), seed 1: the timed
     # workload, against the complete oracle and, on a sample of points, against
