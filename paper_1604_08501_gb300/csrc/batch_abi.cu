@@ -125,7 +125,7 @@ void drop_graph(numa_batch *b) {
     b->g_nsteps = -1;
 }
 
-int grid_of(const numa_batch *b) { return b->num_sms; }   // one 512-thread CTA per SM
+int grid_of(const numa_batch *b) { return b->num_sms; }   // the launcher sizes the grid from it
 
 }  // namespace
 

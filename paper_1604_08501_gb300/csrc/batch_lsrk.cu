@@ -32,7 +32,7 @@ namespace numa {
 namespace {
 
 template <bool MIXED>
-__global__ void __launch_bounds__(kThreads, 1)
+__global__ void __launch_bounds__(kThreads, tile_ctas_per_sm<MIXED>())
 batch_lsrk_kernel(const BatchInstance *__restrict__ inst, const BatchItem *__restrict__ items,
                   int num_items, int *counter, LsrkCoef co, int nsteps, double dt) {
     extern __shared__ __align__(16) double smem_d[];
@@ -86,20 +86,25 @@ cudaError_t prepare_batch_lsrk() {
             uploaded[dev] = true;
         }
     }
-    return cudaFuncSetAttribute(batch_lsrk_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)(sizeof(double) * 3 * kFields * kThreads));
+    e = cudaFuncSetAttribute(batch_lsrk_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)tile_smem_bytes<false>());
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(batch_lsrk_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)tile_smem_bytes<true>());
 }
 
 cudaError_t launch_batch_lsrk(bool mixed, const BatchInstance *inst, const BatchItem *items,
                               int num_items, int *counter, const LsrkCoef &co, int nsteps,
-                              double dt, int grid, cudaStream_t s) {
+                              double dt, int num_sms, cudaStream_t s) {
     if (num_items <= 0 || nsteps <= 0) return cudaSuccess;
     if (mixed)
-        batch_lsrk_kernel<true><<<grid, kThreads, sizeof(float) * 3 * kFields * kThreads, s>>>(
-            inst, items, num_items, counter, co, nsteps, dt);
+        batch_lsrk_kernel<true><<<num_sms * tile_ctas_per_sm<true>(), kThreads,
+                                  tile_smem_bytes<true>(), s>>>(inst, items, num_items, counter,
+                                                                co, nsteps, dt);
     else
-        batch_lsrk_kernel<false><<<grid, kThreads, sizeof(double) * 3 * kFields * kThreads, s>>>(
-            inst, items, num_items, counter, co, nsteps, dt);
+        batch_lsrk_kernel<false><<<num_sms * tile_ctas_per_sm<false>(), kThreads,
+                                   tile_smem_bytes<false>(), s>>>(inst, items, num_items, counter,
+                                                                  co, nsteps, dt);
     return cudaGetLastError();
 }
 

@@ -45,7 +45,7 @@ constexpr size_t kScratchBytes = kCounterBytes + (sizeof(NoallocTable) + 255) / 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 
 template <bool MIXED>
-__global__ void __launch_bounds__(kThreads, 1)
+__global__ void __launch_bounds__(kThreads, tile_ctas_per_sm<MIXED>())
 batch_lsrk_noalloc_kernel(unsigned char *scratch, LsrkCoef co, int nsteps, double dt) {
     int *counter = reinterpret_cast<int *>(scratch);
     const NoallocTable *tab = reinterpret_cast<const NoallocTable *>(scratch + kCounterBytes);
@@ -121,7 +121,11 @@ cudaError_t setup(int dev, DeviceSetup *out) {
         if (e != cudaSuccess) return e;
         e = cudaFuncSetAttribute(batch_lsrk_noalloc_kernel<false>,
                                  cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)(sizeof(double) * 3 * kFields * kThreads));
+                                 (int)tile_smem_bytes<false>());
+        if (e != cudaSuccess) return e;
+        e = cudaFuncSetAttribute(batch_lsrk_noalloc_kernel<true>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)tile_smem_bytes<true>());
         if (e != cudaSuccess) return e;
         s.scratch = static_cast<unsigned char *>(p);
         s.done = true;
@@ -180,12 +184,11 @@ extern "C" int numa_batch_advance_noalloc(const numa_vol *const *handles, void *
         cudaMemsetAsync(ds.scratch, 0, sizeof(int), s) != cudaSuccess)
         return NUMA_ECUDA;
     if (mixed)
-        batch_lsrk_noalloc_kernel<true><<<ds.num_sms, kThreads,
-                                          sizeof(float) * 3 * kFields * kThreads, s>>>(
-            ds.scratch, kCoef, nsteps, dt);
+        batch_lsrk_noalloc_kernel<true><<<ds.num_sms * tile_ctas_per_sm<true>(), kThreads,
+                                          tile_smem_bytes<true>(), s>>>(ds.scratch, kCoef, nsteps, dt);
     else
-        batch_lsrk_noalloc_kernel<false><<<ds.num_sms, kThreads,
-                                           sizeof(double) * 3 * kFields * kThreads, s>>>(
-            ds.scratch, kCoef, nsteps, dt);
+        batch_lsrk_noalloc_kernel<false><<<ds.num_sms * tile_ctas_per_sm<false>(), kThreads,
+                                           tile_smem_bytes<false>(), s>>>(ds.scratch, kCoef, nsteps,
+                                                                          dt);
     return cudaGetLastError() == cudaSuccess ? NUMA_OK : NUMA_ECUDA;
 }

@@ -17,6 +17,21 @@ namespace {
 
 constexpr int kThreads = 512;
 
+// Shared memory of one CTA and CTAs per SM.  FP64: the fluxes (15 values per
+// thread); q and dq stay in registers and one CTA holds an SM (the FP64 pipe
+// binds).  Mixed: the fluxes, q and dq (10 values) and the point's geometry
+// (g and Jinv, 10 values) in shared memory, so that the kernel fits 64
+// registers and two CTAs share an SM, twice the warps to hide latency.
+constexpr int kMixedSmemWords = (3 * 5 + 2 * 5 + 10) * kThreads;
+template <bool MIXED>
+constexpr size_t tile_smem_bytes() {
+    return MIXED ? sizeof(float) * kMixedSmemWords : sizeof(double) * 3 * 5 * kThreads;
+}
+template <bool MIXED>
+constexpr int tile_ctas_per_sm() {
+    return MIXED ? 2 : 1;
+}
+
 // Sweep tables per Nq (index Nq; 2..8 used).  They depend only on the order:
 // every handle's D is the library's GLL D.  In constant memory, every
 // coefficient of a sweep is a constant-bank operand of its FMA, as in the
@@ -59,9 +74,12 @@ using tile_t = typename std::conditional<MIXED, float, double>::type;
 
 template <bool MIXED>
 __device__ __forceinline__ void load_stage_coefficients(const LsrkCoef &co, tile_t<MIXED> *sco) {
-    if (threadIdx.x < 5) {
-        sco[threadIdx.x] = static_cast<tile_t<MIXED>>(co.A[threadIdx.x]);
-        sco[5 + threadIdx.x] = static_cast<tile_t<MIXED>>(co.B[threadIdx.x]);
+    if (threadIdx.x == 0) {   // constant indices: the parameter is read in place
+#pragma unroll
+        for (int s = 0; s < 5; ++s) {
+            sco[s] = static_cast<tile_t<MIXED>>(co.A[s]);
+            sco[5 + s] = static_cast<tile_t<MIXED>>(co.B[s]);
+        }
     }
 }
 
@@ -95,14 +113,25 @@ __device__ void run_tile(const BatchInstance &I, int64_t e0, int64_t count,
         const int npass = (int)((e0 + count - base) < EPP ? (e0 + count - base) : EPP);
         const bool active = el < npass;
         const int64_t node = (base + (active ? el : 0)) * N3 + p;
-        T q[kFields], dq[kFields];
+        // q and the scheme's dq of this thread's point (registers in FP64,
+        // shared memory in the mixed mode), and the mixed mode's per-point
+        // constants, kept for all stages
+        T qr[kFields], dqr[kFields];
+        T *sQ = sF + 3 * kFields * kThreads + l;   // [b * kThreads], mixed only
+        T *sD = sQ + kFields * kThreads;
+        T *sG = sD + kFields * kThreads;           // g (9), Jinv
+        auto Q = [&](int b) -> T & {
+            if constexpr (MIXED) return sQ[b * kThreads]; else return qr[b];
+        };
+        auto DQ = [&](int b) -> T & {
+            if constexpr (MIXED) return sD[b * kThreads]; else return dqr[b];
+        };
 #pragma unroll
         for (int b = 0; b < kFields; ++b) {
-            q[b] = active ? qv[b * M + node] : T(0);
-            dq[b] = T(0);
+            Q(b) = active ? qv[b * M + node] : T(0);
+            DQ(b) = T(0);
         }
-        if (!active) q[0] = MIXED ? T(0) : T(1);   // idle threads hold a harmless state
-        // per-point constants of the mixed mode, kept for all stages
+        if (!active) Q(0) = MIXED ? T(0) : T(1);   // idle threads hold a harmless state
         float th0 = 0.f, rho0 = 0.f;
         EosRef32 er{0.f, 0.f};
         if constexpr (MIXED) {
@@ -110,6 +139,9 @@ __device__ void run_tile(const BatchInstance &I, int64_t e0, int64_t count,
                 th0 = __ldg(I.mgeo.theta_ref + node);
                 rho0 = __ldg(I.mgeo.rho_ref + node);
                 if (th0 > 0.f) er = eos_reference_f32(th0, I.mp);
+#pragma unroll
+                for (int s2 = 0; s2 < 9; ++s2) sG[s2 * kThreads] = __ldg(I.mgeo.g[s2] + node);
+                sG[9 * kThreads] = __ldg(I.mgeo.Jinv + node);
             }
         }
 
@@ -119,10 +151,13 @@ __device__ void run_tile(const BatchInstance &I, int64_t e0, int64_t count,
                 __syncthreads();   // previous phase-3 reads of sF are done
                 // ---- phase 1: p', fluxes ------------------------------
                 if (active) {
+                    T q[kFields];
+#pragma unroll
+                    for (int b = 0; b < kFields; ++b) q[b] = Q(b);
                     T rho, Th, pp, g[9];
                     if constexpr (MIXED) {
 #pragma unroll
-                        for (int s2 = 0; s2 < 9; ++s2) g[s2] = __ldg(I.mgeo.g[s2] + node);
+                        for (int s2 = 0; s2 < 9; ++s2) g[s2] = sG[s2 * kThreads];
                         rho = rho0 + q[0];
                         Th = th0 + q[4];
                         pp = pressure_perturbation_f32(q[4], th0, er, I.mp);
@@ -169,23 +204,29 @@ __device__ void run_tile(const BatchInstance &I, int64_t e0, int64_t count,
                 // ---- phase 3: rhs, stage update ------------------------
                 if (active) {
                     const T a = sco[st], bcoef = sco[5 + st];
-                    const T jinv = MIXED ? T(__ldg(I.mgeo.Jinv + node)) : T(__ldg(I.geo.Jinv + node));
-                    // rho - rho_ref of this stage's state, taken before q is updated below
-                    const T drho = MIXED ? q[0] : q[0] - T(__ldg(I.geo.rho_ref + node));
+                    T jinv, drho;   // drho: rho - rho_ref of this stage's state, before the update
+                    if constexpr (MIXED) {
+                        jinv = sG[9 * kThreads];
+                        drho = Q(0);
+                    } else {
+                        jinv = __ldg(I.geo.Jinv + node);
+                        drho = Q(0) - __ldg(I.geo.rho_ref + node);
+                    }
 #pragma unroll
                     for (int b = 0; b < kFields; ++b) {
                         const T R = sF[f[0] + b * BLK] + sF[f[1] + b * BLK] + sF[f[2] + b * BLK];
                         T rhs = -jinv * R;
                         if (b == 3) rhs = fma(-drho, grav, rhs);
-                        dq[b] = fma(a, dq[b], dtt * rhs);
-                        q[b] = fma(bcoef, dq[b], q[b]);
+                        const T d = fma(a, DQ(b), dtt * rhs);
+                        DQ(b) = d;
+                        Q(b) = fma(bcoef, d, Q(b));
                     }
                 }
             }
         }
         if (active) {
 #pragma unroll
-            for (int b = 0; b < kFields; ++b) qv[b * M + node] = q[b];
+            for (int b = 0; b < kFields; ++b) qv[b * M + node] = Q(b);
         }
     }
 }
