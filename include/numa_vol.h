@@ -172,6 +172,19 @@ int numa_vol_rhs_host(numa_vol *h, const void *q, void *rhs);
  */
 int numa_vol_status(numa_vol *h, void *stream);
 
+/*
+ * Failure-detection self-test: makes the staged kernels' bounded wait run out.
+ * Enqueues on `stream` one CTA that waits, with the same bounded mbarrier wait
+ * the staged kernels use, on a barrier nothing completes; after limit_us
+ * microseconds (1 .. 1,000,000) of GPU time the wait gives up and sets the
+ * handle's status word, so that a following numa_vol_status on the same
+ * stream returns NUMA_ETIMEOUT.  No copy or other asynchronous work is in
+ * flight when it gives up: the context and the handle stay usable.  Returns
+ * NUMA_EINVAL for a NULL handle or a limit out of range, NUMA_ECUDA if the
+ * launch fails, NUMA_OK otherwise.
+ */
+int numa_vol_selftest_wait(numa_vol *h, uint32_t limit_us, void *stream);
+
 /* Release a handle and its device memory.  NULL is a no-op.  Synchronises
  * the device before freeing. */
 void numa_vol_destroy(numa_vol *h);

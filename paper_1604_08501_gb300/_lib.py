@@ -95,6 +95,8 @@ def load() -> C.CDLL:
     lib.numa_batch_last_error.restype = C.c_char_p
     lib.numa_batch_destroy.argtypes = [C.c_void_p]
     lib.numa_batch_destroy.restype = None
+    lib.numa_vol_selftest_wait.argtypes = [C.c_void_p, C.c_uint32, C.c_void_p]
+    lib.numa_vol_selftest_wait.restype = C.c_int
     lib.numa_engine_create.argtypes = [C.c_int, C.c_size_t, C.c_int, C.POINTER(C.c_void_p)]
     lib.numa_engine_submit.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int,
                                        C.c_double, C.POINTER(C.c_int64)]

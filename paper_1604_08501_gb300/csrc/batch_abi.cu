@@ -31,6 +31,9 @@ int bfail(int code, const std::string &msg) {
 }
 
 int bfail_cuda(cudaError_t e, const char *where) {
+    // Reset the runtime's last-error state: a non-sticky error (an allocation
+    // refused) is reported here, not again by the next unrelated launch check.
+    cudaGetLastError();
     int code = (e == cudaErrorMemoryAllocation) ? NUMA_ENOMEM : NUMA_ECUDA;
     return bfail(code, std::string(where) + ": " + cudaGetErrorName(e) + " (" +
                            cudaGetErrorString(e) + ")");

@@ -2,8 +2,8 @@
 // mbarriers for staging element slabs in shared memory, in inline PTX for
 // sm_100-class GPUs.
 //
-// Every wait is bounded: bulk_wait() gives up after a fixed number of polls
-// and returns false, so a kernel never spins forever.  Rules of the untiled
+// Every wait is bounded: bulk_wait() gives up after a time limit (and a
+// fixed number of polls) and returns false, so a kernel never spins forever.  Rules of the untiled
 // bulk copy: both addresses 16-byte aligned, size a multiple of 16 bytes.
 #pragma once
 
@@ -47,21 +47,35 @@ __device__ __forceinline__ void bulk_g2s(void *dst_smem, const void *src_gmem, u
         : "memory");
 }
 
-__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+// One poll of phase `parity` of `bar`; the thread may be suspended for up to
+// about hint_ns while the phase is incomplete.
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity, uint32_t hint_ns = 1000) {
     uint32_t done;
     asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-        " selp.u32 %0, 1, 0, p;\n}" : "=r"(done) : "r"(smem_addr(bar)), "r"(parity) : "memory");
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n"
+        " selp.u32 %0, 1, 0, p;\n}" : "=r"(done) : "r"(smem_addr(bar)), "r"(parity), "r"(hint_ns)
+        : "memory");
     return done != 0;
 }
 
-// Wait for phase `parity` of `bar` to complete; false after max_polls polls.
-// Each try_wait may suspend the thread for a hardware-chosen time, so the
-// bound is far above any legitimate wait (microseconds) and far below a hang.
+__device__ __forceinline__ uint64_t global_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Wait for phase `parity` of `bar` to complete; false once limit_ns of
+// global time have passed (or after 2^22 polls, a bound that holds even if
+// the timer stood still).  Legitimate waits take microseconds; the default
+// limit of one second is far above them and far below a hang.
 __device__ __forceinline__ bool bulk_wait(uint64_t *bar, uint32_t parity,
-                                          uint32_t max_polls = 1u << 22) {
-    for (uint32_t it = 0; it < max_polls; ++it)
+                                          uint64_t limit_ns = 1000000000ull) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const uint64_t t0 = global_ns();
+    for (uint32_t it = 0; it < (1u << 22); ++it) {
         if (mbar_try_wait(bar, parity)) return true;
+        if (global_ns() - t0 > limit_ns) return false;
+    }
     return false;
 }
 

@@ -22,6 +22,9 @@ int fail(int code, const std::string &msg) {
 }
 
 int fail_cuda(cudaError_t e, const char *where) {
+    // Reset the runtime's last-error state: a non-sticky error (an allocation
+    // refused) is reported here, not again by the next unrelated launch check.
+    cudaGetLastError();
     int code = (e == cudaErrorMemoryAllocation) ? NUMA_ENOMEM : NUMA_ECUDA;
     return fail(code, std::string(where) + ": " + cudaGetErrorName(e) + " (" +
                           cudaGetErrorString(e) + ")");

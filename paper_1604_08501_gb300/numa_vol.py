@@ -159,6 +159,15 @@ class VolumeTerm:
         s = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
         check(_lib.load().numa_vol_status(self.handle, C.c_void_p(s)))
 
+    def selftest_wait(self, limit_us: int, stream=None) -> None:
+        """numa_vol_selftest_wait: enqueue a bounded device wait that runs out
+        after limit_us; the next status() on the stream raises NUMA_ETIMEOUT."""
+        import torch
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        s = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+        check(_lib.load().numa_vol_selftest_wait(self.handle, int(limit_us), C.c_void_p(s)))
+
     def close(self) -> None:
         if getattr(self, "_h", None) is not None and self._h.value:
             _lib.load().numa_vol_destroy(self._h)

@@ -161,3 +161,19 @@ def test_mixed_precision_engine_matches_its_batch(pool):
         eng.run_until_idle()
     assert np.array_equal(out, batch_reference(vt, q0, 3, "mixed"))
     vt.close()
+
+
+def test_allocation_refusal_is_a_status_code(pool):
+    # A budget no GPU holds: the arena's reservation is refused, create
+    # returns NUMA_ENOMEM, and the device stays usable (also for torch).
+    with pytest.raises(NumaError, match="ENOMEM"):
+        Engine("fp64", budget_bytes=1 << 50)
+    x = torch.ones(1000, device="cuda") * 2
+    torch.cuda.synchronize()
+    assert float(x.sum()) == 2000.0
+    works, vts = pool
+    out = np.empty_like(works[0].q)
+    with Engine("fp64", budget_bytes=1 << 26) as eng:
+        eng.submit(vts[0], works[0].q, out, 1, DT)
+        eng.run_until_idle()
+    assert np.array_equal(out, batch_reference(vts[0], works[0].q, 1))

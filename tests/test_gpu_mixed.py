@@ -14,7 +14,7 @@ import pytest
 import oracle
 from paper_1604_08501_gb300 import build
 from paper_1604_08501_gb300 import workload as wl
-from paper_1604_08501_gb300.numa_vol import VolumeTerm
+from paper_1604_08501_gb300.numa_vol import NumaError, VolumeTerm
 from conftest import rel_err
 
 pytestmark = pytest.mark.gpu
@@ -117,3 +117,29 @@ def test_mixed_bulk_kernel_ranges_and_status():
             host = vt.rhs_host(q32)
         assert np.array_equal(host, dev.cpu().numpy())
         check(host.astype(np.float64), oracle.vol_rhs_o2(prob, w.q), f"bulk {shape}")
+
+
+def test_bounded_wait_runs_out_and_reports_a_status():
+    # The staged kernels' bounded mbarrier wait, made to run out on a barrier
+    # nothing completes (no fault): numa_vol_status reports NUMA_ETIMEOUT, the
+    # status word is cleared, and the handle still computes correct results.
+    import time
+    w = wl.make_workload(7, (2, 1, 1), seed=91)
+    prob = w.problem()
+    q32 = wl.perturbation_state(w.q, w.rho_ref, w.rhotheta_ref)
+    with VolumeTerm.from_problem(prob, precision="mixed") as vt:
+        vt.status()                                   # clean to begin with
+        t0 = time.perf_counter()
+        vt.selftest_wait(20000)                       # 20 ms limit
+        with pytest.raises(NumaError, match="ETIMEOUT"):
+            vt.status()
+        waited = time.perf_counter() - t0
+        assert 0.015 <= waited < 5.0, waited          # it waited about its limit, then gave up
+        vt.status()                                   # cleared
+        qd = torch.from_numpy(q32).cuda()
+        out = vt.rhs(qd)
+        vt.status()
+        check(out.cpu().numpy().astype(np.float64), oracle.vol_rhs_o2(prob, w.q), "after a timeout")
+    with pytest.raises(NumaError, match="EINVAL"):
+        with VolumeTerm.from_problem(prob, precision="mixed") as vt:
+            vt.selftest_wait(0)
