@@ -5,13 +5,17 @@
 // Both evaluate p' = p_ref ((1 + x)^gamma - 1) with x = Theta'/Theta_ref,
 // written A Theta' g(x) with A = p_ref / Theta_ref and
 // g(x) = sum_k binom(gamma, k) x^(k-1).  That is the same quantity as the
-// difference of two pressures, without its cancellation.  FP64 takes 9 terms
-// of the series for |x| <= 1/64 and 15 for |x| <= 1/8 (truncation below
-// 2^-55 relative for gamma near 1.4 in both); FP32 takes 5 terms for
-// |x| <= 1/64.  Elsewhere (and where Theta_ref = 0) a closed form is
-// evaluated.  The second FP64 tier matters in time integration: a state
-// advanced over many stages drifts past 1/64 at some points, and a warp with
-// one such lane would otherwise pay for two pow calls.
+// difference of two pressures, without its cancellation.
+//
+// FP64 has three forms, each accurate to a few ulps over its whole range:
+// the series to 9 terms for |x| <= 1/64 and to 15 terms for |x| <= 1/8
+// (truncation below 2^-55 relative for gamma near 1.4), and
+// p_ref expm1(gamma log1p(x)) for any x > -1.  A warp takes the widest form
+// any of its lanes needs, so that a warp never runs several of them one after
+// the other: states advanced over many stages drift past 1/64, and on fine
+// meshes past 1/8.  Where Theta_ref = 0 (w and A not finite) or x <= -1 the
+// definition, two evaluations of the equation of state, is used.
+// FP32 takes 5 terms for |x| <= 1/64 and expm1f(gamma log1pf(x)) beyond.
 #pragma once
 
 #include "numa_internal.h"
@@ -25,26 +29,29 @@ static __device__ __noinline__ double eos_pressure(double Th, const EosConstants
     return __dmul_rn(c.p0, pow(__ddiv_rn(__dmul_rn(c.R, Th), c.p0), c.gamma));
 }
 
-// p' from the binomial series where it converges fast, pow elsewhere.
+// p' of one point; the form is chosen per warp (see above).  Every active
+// lane of the warp must call it together.
 static __device__ __forceinline__ double pressure_perturbation(double Th, double th0, double w, double A,
                                                         const NativeParams &P) {
     const double thp = Th - th0;              // Theta'
     const double x = thp * w;                 // Theta' / Theta_ref
     const double ax = fabs(x);
-    if (ax <= 0.015625) {
+    const unsigned lanes = __activemask();
+    if (__all_sync(lanes, ax <= 0.015625)) {
         double g = P.c[8];
 #pragma unroll
         for (int k = 7; k >= 0; --k) g = fma(g, x, P.c[k]);   // sum_k c_{k+1} x^k
         return (A * thp) * g;
     }
-    if (ax <= 0.125) {
+    if (__all_sync(lanes, ax <= 0.125)) {
         double g = P.c[14];
 #pragma unroll
         for (int k = 13; k >= 0; --k) g = fma(g, x, P.c[k]);
         return (A * thp) * g;
     }
-    // Outside the series range (or Theta_ref = 0, where w and A are not finite
-    // and x is inf or NaN): the definition, two evaluations of the equation of state.
+    // x > -1 and finite (a NaN fails the comparison, an infinite x fails < 2^1000)
+    if (__all_sync(lanes, x > -1.0 && ax < 1e300))
+        return (A * th0) * expm1(P.eos.gamma * log1p(x));
     return eos_pressure(Th, P.eos) - eos_pressure(th0, P.eos);
 }
 

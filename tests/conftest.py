@@ -29,3 +29,21 @@ def rel_err(x, ref):
             continue
         out.append((mx / scale, np.linalg.norm(d) / np.linalg.norm(ref[b])))
     return out
+
+
+def eos_banded_theta_ratio(M: int, seed: int):
+    """Theta'/Theta_ref per point for tests of the pressure-perturbation forms,
+    by blocks of 32 consecutive points (one warp when a CTA covers whole
+    elements of 32-point multiples): blocks entirely within |x| <= 1/64, within
+    1/64 < |x| <= 1/8, within 1/8 < |x| <= 0.6, and blocks that mix all three."""
+    import numpy as np
+    rng = np.random.default_rng(seed)
+    lo = [(0.0, 1 / 64), (1 / 64, 1 / 8), (1 / 8, 0.6)]
+    x = np.empty(M)
+    for b0 in range(0, M, 32):
+        n = min(32, M - b0)
+        band = (b0 // 32) % 4
+        bands = [band] * n if band < 3 else list(rng.integers(0, 3, size=n))
+        mag = np.array([rng.uniform(*lo[k]) for k in bands])
+        x[b0:b0 + n] = mag * rng.choice([-1.0, 1.0], size=n)
+    return x

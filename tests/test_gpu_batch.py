@@ -27,7 +27,7 @@ import oracle
 from paper_1604_08501_gb300 import build
 from paper_1604_08501_gb300 import workload as wl
 from paper_1604_08501_gb300.numa_vol import Batch, NumaError, VolumeTerm
-from conftest import rel_err
+from conftest import eos_banded_theta_ratio, rel_err
 
 pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
@@ -189,11 +189,10 @@ def test_batch_of_the_mixed_size_plan_on_a_sample():
 @pytest.mark.parametrize("precision,tol", [("fp64", 3e-12), ("mixed", 1e-5)])
 def test_batch_across_the_eos_branches(precision, tol):
     # Theta'/Theta_ref spread over all ranges of the pressure perturbation
-    # (series of 9 and 15 terms, closed form beyond 1/8), as states reach
-    # after many steps.
-    w = wl.make_workload(5, (2, 2, 1), seed=21)
-    x = np.random.default_rng(3).choice([1e-3, 0.03, -0.07, 0.11, -0.2], size=w.M)
-    w.q[4] = w.rhotheta_ref * (1.0 + x)
+    # (series of 9 and 15 terms, expm1/log1p beyond 1/8), by warp and mixed
+    # within warps, as states reach after many steps on fine meshes.
+    w = wl.make_workload(7, (3, 2, 1), seed=21)
+    w.q[4] = w.rhotheta_ref * (1.0 + eos_banded_theta_ratio(w.M, seed=3))
     vt = VolumeTerm.from_problem(w.problem(), precision=precision)
     q0 = w.q_mixed() if precision == "mixed" else w.q
     q = torch.from_numpy(np.ascontiguousarray(q0)).cuda()

@@ -15,7 +15,7 @@ import oracle
 from paper_1604_08501_gb300 import _lib, build
 from paper_1604_08501_gb300 import workload as wl
 from paper_1604_08501_gb300.numa_vol import VolumeTerm, NumaError
-from conftest import rel_err
+from conftest import eos_banded_theta_ratio, rel_err
 
 pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
@@ -65,14 +65,12 @@ def test_parity_every_order_and_odd_sizes(N, shape):
 
 @pytest.mark.parametrize("N", [3, 7])
 def test_parity_across_the_eos_branches(N):
-    # Theta'/Theta_ref in each range of the kernel's pressure perturbation:
-    # |x| <= 1/64 (9-term series), 1/64 < |x| <= 1/8 (15-term series) and
-    # |x| > 1/8 (pow), with warps that mix them.
+    # Theta'/Theta_ref in each range of the kernel's pressure perturbation,
+    # with warps wholly inside one range (9-term series, 15-term series,
+    # expm1/log1p) and warps that mix them (the widest form for all lanes).
     w = wl.make_workload(N, (3, 2, 1), seed=40 + N)
     q = w.q.copy()
-    rng = np.random.default_rng(N)
-    x = rng.choice([1e-3, -1e-3, 0.02, -0.05, 0.1, -0.12, 0.125, 0.2, -0.3], size=w.M)
-    q[4] = w.rhotheta_ref * (1.0 + x)
+    q[4] = w.rhotheta_ref * (1.0 + eos_banded_theta_ratio(w.M, seed=N))
     prob = w.problem()
     assert_parity(gpu_rhs(prob, q), oracle.vol_rhs_o2(prob, q), label=f"N={N} EOS branches")
 
