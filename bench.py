@@ -77,17 +77,25 @@ def measured_peaks():
         return FALLBACK_HBM_GBS, "fallback 6.8 TB/s (MEASURED_PEAKS.json absent)"
 
 
-def load_traffic(kernel: str):
-    """dram bytes per launch of ``kernel`` from the committed ncu summary, if the
-    kernel source has not changed since the counters were taken."""
+def sources_sha(paths) -> str:
+    """sha256 (16 hex digits) over the named source files, in order."""
     import hashlib
+    h = hashlib.sha256()
+    for rel in paths:
+        with open(os.path.join(ROOT, rel), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def load_traffic(kernel: str):
+    """DRAM bytes per full-size launch of ``kernel`` from the committed ncu
+    summary, if none of the kernel's source files has changed since the
+    counters were taken; None otherwise."""
     p = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         with open(p) as f:
             d = json.load(f)[kernel]
-        src = os.path.join(ROOT, d["source"])
-        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
-        if sha != d["source_sha"]:
+        if sources_sha(d["sources"]) != d["sources_sha"]:
             return None
         return float(d["dram_bytes_per_launch"])
     except Exception:

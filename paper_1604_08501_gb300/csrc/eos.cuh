@@ -15,7 +15,8 @@
 // the other: states advanced over many stages drift past 1/64, and on fine
 // meshes past 1/8.  Where Theta_ref = 0 (w and A not finite) or x <= -1 the
 // definition, two evaluations of the equation of state, is used.
-// FP32 takes 5 terms for |x| <= 1/64 and expm1f(gamma log1pf(x)) beyond.
+// FP32 likewise: 5 terms for |x| <= 1/64, 16 terms for |x| <= 1/2 (truncation
+// below 2^-26), expm1f(gamma log1pf(x)) beyond, chosen per warp.
 #pragma once
 
 #include "numa_internal.h"
@@ -55,8 +56,9 @@ static __device__ __forceinline__ double pressure_perturbation(double Th, double
     return eos_pressure(Th, P.eos) - eos_pressure(th0, P.eos);
 }
 
-// FP32 form from the perturbation Theta' itself (mixed precision): series
-// for |x| <= 1/64, expm1(gamma log1p(x)) beyond, both free of cancellation.
+// FP32 form from the perturbation Theta' itself (mixed precision): the series
+// (5 or 16 terms) or expm1f(gamma log1pf(x)), chosen per warp as in FP64, all
+// free of cancellation.
 // A = K Theta_ref^(gamma - 1) with K = p0^(1 - gamma) R^gamma is recomputed
 // from Theta_ref instead of being read from memory.  eos_reference_f32 forms
 // the per-point factors (w = 1/Theta_ref and A), which a caller that keeps a
@@ -71,17 +73,27 @@ static __device__ __forceinline__ EosRef32 eos_reference_f32(float th0, const Mi
 
 static __device__ __forceinline__ float pressure_perturbation_f32(float thp, float th0, EosRef32 r,
                                                            const MixedParams &P) {
-    if (th0 > 0.0f) {
+    const unsigned lanes = __activemask();
+    if (__all_sync(lanes, th0 > 0.0f)) {
         const float x = thp * r.w;
-        if (fabsf(x) <= 0.015625f) {
+        const float ax = fabsf(x);
+        if (__all_sync(lanes, ax <= 0.015625f)) {
             float g = P.c[4];
 #pragma unroll
             for (int k = 3; k >= 0; --k) g = fmaf(g, x, P.c[k]);   // sum_k c_{k+1} x^k
             return (r.A * thp) * g;
         }
-        return (r.A * th0) * expm1f(P.gamma * log1pf(x));
+        if (__all_sync(lanes, ax <= 0.5f)) {
+            float g = P.c[15];
+#pragma unroll
+            for (int k = 14; k >= 0; --k) g = fmaf(g, x, P.c[k]);
+            return (r.A * thp) * g;
+        }
+        if (__all_sync(lanes, x > -1.0f)) return (r.A * th0) * expm1f(P.gamma * log1pf(x));
     }
-    // Theta_ref = 0 (the paper's full-pressure form): p' = p(Theta').
+    // Theta_ref = 0 (the paper's full-pressure form): p' = p(Theta'); and,
+    // per lane, whatever the warp's common forms do not cover.
+    if (th0 > 0.0f) return (r.A * th0) * expm1f(P.gamma * log1pf(thp * r.w));
     return P.K * powf(thp, P.gamma);
 }
 

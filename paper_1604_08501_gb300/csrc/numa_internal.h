@@ -65,11 +65,11 @@ struct MixedGeometry {
 };
 
 // Parameters of the mixed-precision kernel: even-odd pieces of D (as in
-// NativeParams), c[k] = binom(gamma, k+1) for k = 0..4, K = p0^(1-gamma) R^gamma
+// NativeParams), c[k] = binom(gamma, k+1) for k = 0..15, K = p0^(1-gamma) R^gamma
 // (so p(Theta) = K Theta^gamma), gamma - 1, gamma and gravity.
 struct MixedParams {
     float De[16], Do[16], Dc[4], Dcr[4];
-    float c[5];
+    float c[16];
     float K, gm1, gamma, grav;
 };
 

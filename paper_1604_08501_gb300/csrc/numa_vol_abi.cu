@@ -65,7 +65,7 @@ const char *numa_vol_kernel_name(const numa_vol *h) {
     static const char *mixed[] = {"", "vol_rhs_mixed_kernel<2>", "vol_rhs_mixed_kernel<3>",
                                   "vol_rhs_mixed_kernel<4>", "vol_rhs_mixed_kernel<5>",
                                   "vol_rhs_mixed_kernel<6>", "vol_rhs_mixed_kernel<7>",
-                                  "vol_rhs_mixed_kernel<8>"};
+                                  "vol_rhs_mixed_bulk_kernel"};   // N = 7: the persistent staged kernel
     if (h->kernel == numa::Kernel::DoubleFloat) return "vol_rhs_df64_kernel";
     if (h->kernel == numa::Kernel::Mixed) return mixed[h->N];
     return native[h->N];
@@ -90,14 +90,14 @@ numa::df split_host(long double x) {
     return numa::df{h, l};
 }
 
-// binom(gamma, k) for k = 0..15, in long double.
-void binomial_coefficients(double gamma, long double c[16]) {
+// binom(gamma, k) for k = 0..16, in long double.
+void binomial_coefficients(double gamma, long double c[17]) {
     c[0] = 1.0L;
-    for (int k = 1; k < 16; ++k) c[k] = c[k - 1] * ((long double)gamma - (k - 1)) / k;
+    for (int k = 1; k < 17; ++k) c[k] = c[k - 1] * ((long double)gamma - (k - 1)) / k;
 }
 
 void build_params(numa_vol *h, const double *D) {
-    long double c[16];
+    long double c[17];
     binomial_coefficients(h->eos.gamma, c);
     h->nparams.eos = h->eos;
     for (int k = 0; k < 15; ++k) h->nparams.c[k] = static_cast<double>(c[k + 1]);
@@ -112,7 +112,7 @@ void build_params(numa_vol *h, const double *D) {
             m.Dc[t] = static_cast<float>(h->nparams.Dc[t]);
             m.Dcr[t] = static_cast<float>(h->nparams.Dcr[t]);
         }
-        for (int k = 0; k < 5; ++k) m.c[k] = static_cast<float>(c[k + 1]);
+        for (int k = 0; k < 16; ++k) m.c[k] = static_cast<float>(c[k + 1]);
         const long double g = h->eos.gamma;
         m.K = static_cast<float>(std::pow((long double)h->eos.p0, 1.0L - g) *
                                  std::pow((long double)h->eos.R, g));

@@ -15,7 +15,7 @@ import oracle
 from paper_1604_08501_gb300 import build
 from paper_1604_08501_gb300 import workload as wl
 from paper_1604_08501_gb300.numa_vol import NumaError, VolumeTerm
-from conftest import rel_err
+from conftest import eos_banded_theta_ratio, rel_err
 
 pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
@@ -31,7 +31,7 @@ def _cuda():
 
 def run_mixed(prob, q32):
     with VolumeTerm.from_problem(prob, precision="mixed") as vt:
-        assert vt.kernel_name.startswith("vol_rhs_mixed_kernel")
+        assert vt.kernel_name.startswith("vol_rhs_mixed")
         out = vt.rhs(torch.from_numpy(np.ascontiguousarray(q32)).cuda())
         torch.cuda.synchronize()
         return out.cpu().numpy().astype(np.float64)
@@ -143,3 +143,15 @@ def test_bounded_wait_runs_out_and_reports_a_status():
     with pytest.raises(NumaError, match="EINVAL"):
         with VolumeTerm.from_problem(prob, precision="mixed") as vt:
             vt.selftest_wait(0)
+
+
+@pytest.mark.parametrize("N", [3, 7])
+def test_mixed_across_the_eos_forms(N):
+    # Theta'/Theta_ref by warp in each range of the FP32 pressure perturbation
+    # (5-term series, 16-term series, expm1f/log1pf) and mixed within warps.
+    w = wl.make_workload(N, (3, 2, 1), seed=60 + N)
+    q = w.q.copy()
+    q[4] = w.rhotheta_ref * (1.0 + eos_banded_theta_ratio(w.M, seed=N))
+    prob = w.problem()
+    q32 = wl.perturbation_state(q, w.rho_ref, w.rhotheta_ref)
+    check(run_mixed(prob, q32), oracle.vol_rhs_o2(prob, q), f"N={N} EOS forms")
