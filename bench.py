@@ -493,6 +493,70 @@ def run_batched(args):
     return 0
 
 
+# The paper's Nq study: 3,538,944 points at Nq = 4, 8, 12 and 16 (Sec. 5).
+NQ_STUDY = {3: (48, 48, 24), 7: (24, 24, 12), 11: (16, 16, 8), 15: (12, 12, 6)}
+
+
+def run_nq_sweep(args):
+    """One evaluation per step of the 3,538,944-point mesh at each order of the
+    paper's Nq study, NUMA_FP64 (every order) and NUMA_MIXED (N <= 7).  Inputs
+    exceed L2 (0.68 GB FP64).  Metric: GDOF/s per order; `value` is Nq = 8."""
+    import torch
+    rank, local, world = dist_setup("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    from paper_1604_08501_gb300 import build as lib_build
+    from paper_1604_08501_gb300 import workload as wl
+    from paper_1604_08501_gb300.numa_vol import VolumeTerm
+    lib_build.build()
+    stream = torch.cuda.current_stream(dev)
+    per = {}
+    launches = 0
+    for N, shape in NQ_STUDY.items():
+        w = wl.make_workload(N, shape, seed=1)
+        row = {"elements": w.Ne, "points": w.M}
+        for prec in args.precisions:
+            if prec == "df64" or (prec == "mixed" and N > 7):
+                continue
+            vt = VolumeTerm.from_problem(w.problem(), precision=prec)
+            q = torch.from_numpy(w.q_mixed() if prec == "mixed" else w.q).to(dev)
+            out = torch.empty_like(q)
+            for _ in range(args.warmup):
+                vt.rhs(q, out, stream=stream)
+            torch.cuda.synchronize(dev)
+            ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                  for _ in range(args.steps)]
+            barrier(dev)
+            for t0, t1 in ev:
+                t0.record(stream)
+                vt.rhs(q, out, stream=stream)
+                t1.record(stream)
+            torch.cuda.synchronize(dev)
+            ms = statistics.median(t0.elapsed_time(t1) for t0, t1 in ev)
+            value, tmax = aggregate(w.M * args.steps, ms * 1e-3 * args.steps, dev)
+            row[prec] = {"gdofs": value / 1e9, "ms": tmax * 1e3 / args.steps,
+                         "kernel": vt.kernel_name}
+            launches += args.steps
+            vt.close()
+            del q, out
+        per[str(N + 1)] = row
+        torch.cuda.empty_cache()
+    if rank == 0:
+        head = args.precisions[0]
+        line = {"metric": "volume-RHS GDOF/s across orders, 3,538,944 points (Nq study)",
+                "value": per["8"][head]["gdofs"], "unit": UNIT, "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": per["8"][head]["ms"],
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": {"fp64": "f64", "mixed": "f32 (perturbation state)"}[head],
+                "data": "synthetic",
+                "config": {"workload": "warped 10 km box, 3,538,944 points at Nq = 4, 8, 12, 16 "
+                                       "(48x48x24, 24x24x12, 16x16x8, 12x12x6 elements), seed 1",
+                           "l2": "inputs larger than L2 (0.68 GB FP64 per step), no flush"},
+                "per_nq": per, "gpu_launches": launches, "precision": head}
+        print(json.dumps(line))
+    return 0
+
+
 def run_serving(args):
     """The serving workload: a Poisson stream of ensemble-member requests (mean
     args.rate per second), each an instance drawn from a pool of meshes sized as
@@ -626,10 +690,12 @@ def main(argv=None):
     ap.add_argument("--precision", default=None,
                     help="comma-separated precision modes; the first is the headline value "
                          "(default fp64,df64,mixed; batched: fp64,mixed)")
-    ap.add_argument("--workload", choices=["single", "batched", "serving"], default="single",
+    ap.add_argument("--workload", choices=["single", "batched", "serving", "nq-sweep"],
+                    default="single",
                     help="single: one evaluation of the 32^3-element N=7 mesh per step (the "
                          "benchmark); batched: the 64-instance LSRK batch; serving: a Poisson "
-                         "request stream through the continuous-batching engine")
+                         "request stream through the continuous-batching engine; nq-sweep: "
+                         "the paper's Nq study at 3,538,944 points")
     ap.add_argument("--instances", type=int, default=64, help="batched: number of instances")
     ap.add_argument("--rate", type=float, default=200.0, help="serving: mean arrivals per second")
     ap.add_argument("--requests", type=int, default=600, help="serving: requests per precision")
@@ -647,6 +713,8 @@ def main(argv=None):
         return run_batched(args)
     if args.workload == "serving":
         return run_serving(args)
+    if args.workload == "nq-sweep":
+        return run_nq_sweep(args)
     return run_gpu(args)
 
 

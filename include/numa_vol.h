@@ -56,7 +56,9 @@ extern "C" {
 #define NUMA_ETIMEOUT (-5)      /* a kernel's bounded wait on its own staged copies ran out */
 #define NUMA_ELIMIT (-6)        /* a count exceeds a fixed maximum of the call              */
 
-#define NUMA_MAX_N 7            /* orders N = 1 .. 7 (Nq = 2 .. 8)                        */
+#define NUMA_MAX_N 7            /* orders N = 1 .. 7 (Nq = 2 .. 8): every mode, the batch
+                                   and the engine                                          */
+#define NUMA_MAX_N_FP64 15      /* NUMA_FP64 evaluations also take N = 8 .. 15 (Nq up to 16) */
 
 /* Physical constants: EOS reference pressure p0, gas constant R, specific heat
  * at constant pressure cp (gamma = cp / (cp - R), Sec. 2), gravity grav. */
@@ -104,10 +106,14 @@ typedef struct numa_vol numa_vol;
  * 1/Theta_ref and p(Theta_ref)/Theta_ref.  p' is exactly zero wherever
  * Theta == Theta_ref.  Synchronous.
  *
- * mesh->N in [1, NUMA_MAX_N]; mesh->num_elements >= 0; every pointer of geo
- * non-null; c->cp > c->R > 0 and c->p0 > 0.  On success *out receives the
- * handle (release with numa_vol_destroy).  Errors: NUMA_EINVAL,
- * NUMA_ENOMEM, NUMA_ECUDA, NUMA_EUNSUPPORTED (NUMA_DF64 with N != 7).
+ * mesh->N in [1, NUMA_MAX_N_FP64] for NUMA_FP64 and in [1, NUMA_MAX_N] for
+ * the other modes; mesh->num_elements >= 0; every pointer of geo non-null;
+ * c->cp > c->R > 0 and c->p0 > 0.  On success *out receives the handle
+ * (release with numa_vol_destroy).  Errors: NUMA_EINVAL, NUMA_ENOMEM,
+ * NUMA_ECUDA, NUMA_EUNSUPPORTED (NUMA_DF64 with N != 7; NUMA_MIXED with
+ * N > 7).  Handles of N > 7 evaluate one element per CTA of (N+1)^2 threads,
+ * one pass per field (vol_rhs_fp64_high_kernel); the batch and the engine
+ * take handles of N <= 7 only.
  *
  * NUMA_MIXED takes the state as FP32 perturbations from the reference state:
  * plane 0 holds rho - rho_ref, plane 4 holds Theta - Theta_ref, and planes 1-3
@@ -117,9 +123,10 @@ typedef struct numa_vol numa_vol;
  * of the full state: about 1e-7 times the sweep condition number, normwise.
  *
  * NUMA_FP64 and NUMA_DF64 compute the same operation.  Both evaluate
- * p(Theta) - p(Theta_ref) as p_ref ((1 + x)^gamma - 1) by its binomial series
- * in x = (Theta - Theta_ref)/Theta_ref where |x| <= 1/64, and by pow
- * elsewhere.  The error of NUMA_FP64 against an exact evaluation is a few
+ * p(Theta) - p(Theta_ref) as p_ref ((1 + x)^gamma - 1) in x =
+ * (Theta - Theta_ref)/Theta_ref: NUMA_FP64 by its binomial series (|x| <= 1/8)
+ * or expm1(gamma log1p(x)), the form chosen per warp of 32 points;
+ * NUMA_DF64 by the series where |x| <= 1/64 and by pow elsewhere.  The error of NUMA_FP64 against an exact evaluation is a few
  * units of 2^-53 times the condition number of the D sweeps (the ratio of
  * sum |Jinv D F| to |rhs|).  The factor for NUMA_DF64 is about 2^-48, so
  * NUMA_DF64 suits states with well-conditioned sweeps, such as the benchmark's
@@ -202,7 +209,7 @@ const char *numa_vol_last_error(void);
 /*
  * Host-only: write the (N+1) x (N+1) GLL differentiation matrix the kernels
  * apply, row-major, D[i*(N+1) + n] = l_n'(xi_i) (the paper's D(i,n)), into
- * D_out.  Needs no GPU.  Errors: NUMA_EINVAL.
+ * D_out, for N in [1, NUMA_MAX_N_FP64].  Needs no GPU.  Errors: NUMA_EINVAL.
  */
 int numa_vol_diff_matrix(int N, double *D_out);
 
@@ -239,7 +246,7 @@ int numa_batch_create(numa_precision prec, numa_batch **out);
  * in the batch) and its state q, a device pointer to 5 planes of M values of
  * the handle's state type, 16-byte aligned, that numa_batch_advance updates in
  * place.  *index (optional) receives the instance's position.
- * Errors: NUMA_EINVAL. */
+ * Errors: NUMA_EINVAL; NUMA_EUNSUPPORTED for a handle of order N > NUMA_MAX_N. */
 int numa_batch_add(numa_batch *b, const numa_vol *h, void *q, int *index);
 
 /* Remove every instance (the handles and states are untouched). */
@@ -316,7 +323,8 @@ int numa_engine_create(numa_precision prec, size_t budget_bytes, int max_members
  * written during later progress calls, kept alive until the request is done or
  * cancelled.  nsteps >= 1, dt > 0.  *id receives the request id.
  * Errors: NUMA_EINVAL (malformed request; the engine is unchanged),
- * NUMA_ELIMIT (the state exceeds the whole budget: it can never be admitted). */
+ * NUMA_ELIMIT (the state exceeds the whole budget: it can never be admitted),
+ * NUMA_EUNSUPPORTED (a mesh of order N > NUMA_MAX_N). */
 int numa_engine_submit(numa_engine *e, const numa_vol *mesh, const void *q0_host,
                        void *q_out_host, int nsteps, double dt, int64_t *id);
 
@@ -371,7 +379,8 @@ void numa_engine_destroy(numa_engine *e);
  * Returns NUMA_OK; NUMA_ELIMIT if count > NUMA_NOALLOC_MAX_INSTANCES (or the
  * total work exceeds 2^31 - 1 items); NUMA_EINVAL for a NULL or misaligned
  * pointer, count < 1, nsteps < 0, handles of mixed kinds or of another device,
- * or a double-float handle; NUMA_ECUDA if a CUDA call fails.
+ * or a double-float handle; NUMA_EUNSUPPORTED for a handle of order
+ * N > NUMA_MAX_N; NUMA_ECUDA if a CUDA call fails.
  */
 #define NUMA_NOALLOC_MAX_INSTANCES 64
 int numa_batch_advance_noalloc(const numa_vol *const *handles, void *const *states, int count,

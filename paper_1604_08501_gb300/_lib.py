@@ -13,6 +13,7 @@ from .build import LIB
 NUMA_OK, NUMA_EINVAL, NUMA_ENOMEM, NUMA_ECUDA, NUMA_EUNSUPPORTED, NUMA_ETIMEOUT, NUMA_ELIMIT = 0, -1, -2, -3, -4, -5, -6
 NUMA_NOALLOC_MAX_INSTANCES = 64
 NUMA_MAX_N = 7
+NUMA_MAX_N_FP64 = 15
 NUMA_FP64, NUMA_MIXED, NUMA_DF64 = 0, 1, 2
 
 _ERRNAMES = {NUMA_EINVAL: "NUMA_EINVAL", NUMA_ENOMEM: "NUMA_ENOMEM",

@@ -168,6 +168,8 @@ int numa_batch_add(numa_batch *b, const numa_vol *h, void *q, int *index) {
     if ((reinterpret_cast<uintptr_t>(q) & 15u) != 0)
         return bfail(NUMA_EINVAL, "numa_batch_add: q must be 16-byte aligned");
     const bool mixed = b->prec == NUMA_MIXED;
+    if (h->N > NUMA_MAX_N)
+        return bfail(NUMA_EUNSUPPORTED, "numa_batch_add: the batch takes orders N <= 7");
     if (mixed ? h->kernel != numa::Kernel::Mixed : h->kernel != numa::Kernel::Native)
         return bfail(NUMA_EINVAL, "numa_batch_add: handle precision differs from the batch's "
                                   "(NUMA_FP64 batches take NUMA_FP64 handles)");

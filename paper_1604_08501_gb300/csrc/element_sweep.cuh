@@ -3,7 +3,10 @@
 //
 // Fluxes of one element are kept per (direction, field) in line-major order:
 // direction r has lines (k, j) with position i, s has lines (k, i) with
-// position j, t has lines (j, i) with position k.  For Nq = 8 an XOR swizzle
+// position j, t has lines (j, i) with position k.  For Nq > 8 every line has
+// 16 slots and slot(line, n) = 16 line + (n ^ (line & 15)): 16 consecutive
+// lines, or 16 consecutive points of a line, cover all banks with 8-byte
+// values (one half-warp wavefront).  For Nq = 8 an XOR swizzle
 // slot(line, n) = 8 line + (n ^ h(line)) keeps the accesses free of bank
 // conflicts when points write, lines read and write, and points read back:
 //   8-byte values: h(line) = (line & 6) | ((line >> 3) & 1)
@@ -25,7 +28,9 @@ namespace numa {
 
 template <int NQ, typename T>
 __device__ __forceinline__ int slot(int line, int n) {
-    if constexpr (NQ == 8 && sizeof(T) == 8)
+    if constexpr (NQ > 8)   // lines padded to 16 slots, XOR swizzle over 16
+        return line * 16 + (n ^ (line & 15));
+    else if constexpr (NQ == 8 && sizeof(T) == 8)
         return line * 8 + (n ^ ((line & 6) | ((line >> 3) & 1)));
     else if constexpr (NQ == 8 && sizeof(T) == 4)
         return line * 8 + (n ^ ((((line >> 2) & 1) << 2) | (((line >> 4) & 1) << 1) | ((line >> 3) & 1)));

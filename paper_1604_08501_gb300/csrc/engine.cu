@@ -206,6 +206,8 @@ int numa_engine_submit(numa_engine *e, const numa_vol *mesh, const void *q0_host
     if (nsteps < 1 || !(dt > 0.0))
         return efail(NUMA_EINVAL, "numa_engine_submit: need nsteps >= 1 and dt > 0");
     const bool mixed = e->prec == NUMA_MIXED;
+    if (mesh->N > NUMA_MAX_N)
+        return efail(NUMA_EUNSUPPORTED, "numa_engine_submit: the engine takes orders N <= 7");
     if (mixed ? mesh->kernel != numa::Kernel::Mixed : mesh->kernel != numa::Kernel::Native)
         return efail(NUMA_EINVAL, "numa_engine_submit: mesh handle precision differs from the engine's");
     if (mesh->device != e->device)

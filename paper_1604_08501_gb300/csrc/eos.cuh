@@ -32,8 +32,10 @@ static __device__ __noinline__ double eos_pressure(double Th, const EosConstants
 
 // p' of one point; the form is chosen per warp (see above).  Every active
 // lane of the warp must call it together.
+// Params: NativeParams or HighParams (the series coefficients c and eos).
+template <typename Params>
 static __device__ __forceinline__ double pressure_perturbation(double Th, double th0, double w, double A,
-                                                        const NativeParams &P) {
+                                                        const Params &P) {
     const double thp = Th - th0;              // Theta'
     const double x = thp * w;                 // Theta' / Theta_ref
     const double ax = fabs(x);

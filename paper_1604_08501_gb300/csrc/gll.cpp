@@ -39,9 +39,9 @@ void legendre(int N, long double x, long double *P, long double *dP) {
 }  // namespace
 
 int gll_diff_matrix(int N, double *D) {
-    if (N < 1 || N > NUMA_MAX_N || !D) return NUMA_EINVAL;
+    if (N < 1 || N > NUMA_MAX_N_FP64 || !D) return NUMA_EINVAL;
     const int Nq = N + 1;
-    long double x[NUMA_MAX_N + 1], PN[NUMA_MAX_N + 1];
+    long double x[NUMA_MAX_N_FP64 + 1], PN[NUMA_MAX_N_FP64 + 1];
     const long double pi = 3.141592653589793238462643383279502884L;
     x[0] = -1.0L;
     x[N] = 1.0L;

@@ -44,6 +44,14 @@ struct NativeParams {
     double De[16], Do[16], Dc[4], Dcr[4];
 };
 
+// Parameters of the native kernel for orders N = 8..15 (Nq = 9..16): the same
+// quantities as NativeParams with even-odd tables up to (Nq/2)^2 = 64 entries.
+struct HighParams {
+    EosConstants eos;
+    double c[15];
+    double De[64], Do[64], Dc[8], Dcr[8];
+};
+
 // Per-point arrays of the double-float path (N = 7): float2 (h, l) pairs, and
 // the reference state in FP64, so that rho - rho_ref and Theta - Theta_ref are
 // exact FP64 differences before they are split.
@@ -80,6 +88,11 @@ struct DfParams;  // defined below
 // reference_eos: w = 1/Theta_ref, A = p(Theta_ref)/Theta_ref per point.
 cudaError_t launch_reference_eos(const double *theta_ref, double *w, double *A, int64_t M,
                                  EosConstants c, cudaStream_t s);
+// Native FP64 for N = 8..15 (vol_fp64_high.cu): one CTA of Nq^2 threads per
+// element, one pass per field.
+cudaError_t launch_vol_rhs_fp64_high(int N, ElemRange r, const DeviceGeometry &geo,
+                                     const HighParams &P, const double *q, double *rhs,
+                                     cudaStream_t s);
 cudaError_t launch_vol_rhs_fp64(int N, ElemRange r, const DeviceGeometry &geo,
                                 const NativeParams &P, const double *q, double *rhs,
                                 cudaStream_t s);
@@ -126,7 +139,9 @@ struct DfParams {
     double D[64];      // D for the native fallback
 };
 
-enum class Kernel { Native, DoubleFloat, Mixed };
+// Native: vol_rhs_fp64_kernel (N <= 7); NativeHigh: vol_rhs_fp64_high_kernel
+// (N = 8..15); DoubleFloat and Mixed: the other precision modes (N <= 7).
+enum class Kernel { Native, NativeHigh, DoubleFloat, Mixed };
 
 // Device-side description of one instance of a batch: its order, size, state
 // and the geometry/parameters of its handle (FP64 or mixed, per the batch).
@@ -188,6 +203,7 @@ struct numa_vol {
     numa::DfGeometry dgeo{};        // double-float path
     numa::DfParams dparams{};
     numa::NativeParams nparams{};
+    numa::HighParams hparams{};   // N >= 8
     numa::MixedGeometry mgeo{};     // mixed-precision path
     numa::MixedParams mparams{};
     size_t elem = sizeof(double);   // bytes per state/rhs value (4 for NUMA_MIXED)

@@ -60,7 +60,11 @@ const char *numa_vol_kernel_name(const numa_vol *h) {
     static const char *native[] = {"", "vol_rhs_fp64_kernel<2>", "vol_rhs_fp64_kernel<3>",
                                    "vol_rhs_fp64_kernel<4>", "vol_rhs_fp64_kernel<5>",
                                    "vol_rhs_fp64_kernel<6>", "vol_rhs_fp64_kernel<7>",
-                                   "vol_rhs_fp64_kernel<8>"};
+                                   "vol_rhs_fp64_kernel<8>", "vol_rhs_fp64_high_kernel<9>",
+                                   "vol_rhs_fp64_high_kernel<10>", "vol_rhs_fp64_high_kernel<11>",
+                                   "vol_rhs_fp64_high_kernel<12>", "vol_rhs_fp64_high_kernel<13>",
+                                   "vol_rhs_fp64_high_kernel<14>", "vol_rhs_fp64_high_kernel<15>",
+                                   "vol_rhs_fp64_high_kernel<16>"};
     if (!h) return "";
     static const char *mixed[] = {"", "vol_rhs_mixed_kernel<2>", "vol_rhs_mixed_kernel<3>",
                                   "vol_rhs_mixed_kernel<4>", "vol_rhs_mixed_kernel<5>",
@@ -74,8 +78,8 @@ const char *numa_vol_kernel_name(const numa_vol *h) {
 int numa_vol_diff_matrix(int N, double *D_out) {
     g_last_error.clear();
     if (!D_out) return fail(NUMA_EINVAL, "numa_vol_diff_matrix: D_out is NULL");
-    if (N < 1 || N > NUMA_MAX_N)
-        return fail(NUMA_EINVAL, "numa_vol_diff_matrix: N must be in [1, 7]");
+    if (N < 1 || N > NUMA_MAX_N_FP64)
+        return fail(NUMA_EINVAL, "numa_vol_diff_matrix: N must be in [1, 15]");
     return numa::gll_diff_matrix(N, D_out);
 }
 
@@ -101,6 +105,12 @@ void build_params(numa_vol *h, const double *D) {
     binomial_coefficients(h->eos.gamma, c);
     h->nparams.eos = h->eos;
     for (int k = 0; k < 15; ++k) h->nparams.c[k] = static_cast<double>(c[k + 1]);
+    if (h->N >= 8) {   // the high-order kernel's parameters; no other mode runs N >= 8
+        h->hparams.eos = h->eos;
+        for (int k = 0; k < 15; ++k) h->hparams.c[k] = h->nparams.c[k];
+        numa::sweep_tables(h->N, D, h->hparams.De, h->hparams.Do, h->hparams.Dc, h->hparams.Dcr);
+        return;
+    }
     numa::sweep_tables(h->N, D, h->nparams.De, h->nparams.Do, h->nparams.Dc, h->nparams.Dcr);
     {
         numa::MixedParams &m = h->mparams;
@@ -183,7 +193,7 @@ cudaError_t create_native(numa_vol *h, const numa_geometry *geo, const double *D
     h->geo.w = slots[12];
     h->geo.A = slots[13];
     h->geo.D = dD;
-    h->kernel = numa::Kernel::Native;
+    h->kernel = h->N > NUMA_MAX_N ? numa::Kernel::NativeHigh : numa::Kernel::Native;
     return cudaSuccess;
 }
 
@@ -295,8 +305,10 @@ int numa_vol_create(const numa_mesh *mesh, const numa_geometry *geo, const numa_
     if (!out) return fail(NUMA_EINVAL, "numa_vol_create: out is NULL");
     *out = nullptr;
     if (!mesh || !geo || !c) return fail(NUMA_EINVAL, "numa_vol_create: NULL argument");
-    if (mesh->N < 1 || mesh->N > NUMA_MAX_N)
-        return fail(NUMA_EINVAL, "numa_vol_create: N must be in [1, 7]");
+    if (mesh->N < 1 || mesh->N > NUMA_MAX_N_FP64)
+        return fail(NUMA_EINVAL, "numa_vol_create: N must be in [1, 15]");
+    if (mesh->N > NUMA_MAX_N && prec != NUMA_FP64)
+        return fail(NUMA_EUNSUPPORTED, "numa_vol_create: orders N > 7 are implemented in NUMA_FP64 only");
     if (mesh->num_elements < 0)
         return fail(NUMA_EINVAL, "numa_vol_create: num_elements must be >= 0");
     if (mesh->num_elements > (int64_t)INT32_MAX)
@@ -334,7 +346,7 @@ int numa_vol_create(const numa_mesh *mesh, const numa_geometry *geo, const numa_
         delete h;
         return fail_cuda(e, "numa_vol_create: status word");
     }
-    double D[(NUMA_MAX_N + 1) * (NUMA_MAX_N + 1)];
+    double D[(NUMA_MAX_N_FP64 + 1) * (NUMA_MAX_N_FP64 + 1)];
     numa::gll_diff_matrix(h->N, D);
 
     build_params(h, D);
@@ -373,6 +385,10 @@ cudaError_t launch(numa_vol *h, const void *q, void *rhs, int64_t e0, int64_t co
     if (h->kernel == numa::Kernel::DoubleFloat)
         return numa::launch_vol_rhs_df64(r, h->dgeo, h->dparams, static_cast<const double *>(q),
                                          static_cast<double *>(rhs), s);
+    if (h->kernel == numa::Kernel::NativeHigh)
+        return numa::launch_vol_rhs_fp64_high(h->N, r, h->geo, h->hparams,
+                                              static_cast<const double *>(q),
+                                              static_cast<double *>(rhs), s);
     return numa::launch_vol_rhs_fp64(h->N, r, h->geo, h->nparams,
                                      static_cast<const double *>(q), static_cast<double *>(rhs), s);
 }

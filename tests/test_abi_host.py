@@ -49,7 +49,7 @@ def test_library_exports_every_declared_symbol(lib):
         assert hasattr(lib, name), name
 
 
-@pytest.mark.parametrize("N", range(1, 8))
+@pytest.mark.parametrize("N", range(1, 16))
 def test_library_diff_matrix_matches_oracle(N):
     D_lib = diff_matrix(N)
     D_or = oracle.diff_matrix(N)
@@ -59,10 +59,10 @@ def test_library_diff_matrix_matches_oracle(N):
 
 
 def test_diff_matrix_rejects_bad_order(lib):
-    D = np.zeros(64)
+    D = np.zeros(256)
     p = D.ctypes.data_as(C.POINTER(C.c_double))
     assert lib.numa_vol_diff_matrix(0, p) == _lib.NUMA_EINVAL
-    assert lib.numa_vol_diff_matrix(8, p) == _lib.NUMA_EINVAL
+    assert lib.numa_vol_diff_matrix(16, p) == _lib.NUMA_EINVAL
     assert b"N must be" in lib.numa_vol_last_error()
     assert lib.numa_vol_diff_matrix(3, None) == _lib.NUMA_EINVAL
 
@@ -81,10 +81,16 @@ def test_create_rejects_invalid_arguments_without_a_gpu(lib):
     geo, keep = _geometry(8)
     consts = _lib.numa_constants(1e5, 287.0, 1004.0, 9.8)
     h = C.c_void_p()
-    for N, Ne in ((0, 1), (8, 1), (-1, 1), (1, -1)):
+    for N, Ne in ((0, 1), (16, 1), (-1, 1), (1, -1)):
         mesh = _lib.numa_mesh(Ne, N)
         assert lib.numa_vol_create(C.byref(mesh), C.byref(geo), C.byref(consts), 0,
                                    C.byref(h)) == _lib.NUMA_EINVAL
+        assert h.value is None
+    # orders above 7 exist in NUMA_FP64 only (checked before any device work)
+    for prec in (_lib.NUMA_MIXED, _lib.NUMA_DF64):
+        mesh = _lib.numa_mesh(1, 8)
+        assert lib.numa_vol_create(C.byref(mesh), C.byref(geo), C.byref(consts), prec,
+                                   C.byref(h)) == _lib.NUMA_EUNSUPPORTED
         assert h.value is None
     mesh = _lib.numa_mesh(1, 1)
     bad = _lib.numa_constants(1e5, 287.0, 200.0, 9.8)         # cp < R
