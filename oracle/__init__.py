@@ -24,8 +24,9 @@ lsrk(prob, q, dt, n)    n steps of the 5-stage 4th-order 2N-storage Runge-Kutta
                         scheme (Carpenter-Kennedy 1994) on dq/dt = volume term.
 
 ``prob`` is a dict with keys N, Ne, g (9 x M), Jinv, rho_ref, rhotheta_ref
-(each M = Ne*(N+1)^3 doubles, [e][k][j][i] order) and constants p0, R, cp,
-grav.  ``q`` is a (5, M) float64 array (rho, U1, U2, U3, Theta).
+(each M = Ne*(N+1)^3 doubles, [e][k][j][i] order), constants p0, R, cp,
+grav, and optionally ntracers (0..3, default 0).  ``q`` is a (5 + ntracers, M)
+float64 array (rho, U1, U2, U3, Theta, Q1..).
 """
 from __future__ import annotations
 
@@ -52,6 +53,7 @@ class _Problem(C.Structure):
         ("R", C.c_double),
         ("cp", C.c_double),
         ("grav", C.c_double),
+        ("ntracers", C.c_int),
     ]
 
 
@@ -131,6 +133,7 @@ class _Bound:
     def __init__(self, prob: dict):
         N = int(prob["N"])
         self.N, self.Ne = N, int(prob["Ne"])
+        self.nf = 5 + int(prob.get("ntracers", 0))
         self.M = self.Ne * (N + 1) ** 3
         self.D = np.ascontiguousarray(prob["D"] if "D" in prob else diff_matrix(N),
                                     dtype=np.float64)
@@ -150,19 +153,20 @@ class _Bound:
         s.Jinv, s.rho_ref, s.rhotheta_ref = _ptr(self.Jinv), _ptr(self.rho_ref), _ptr(self.rt_ref)
         s.p0, s.R, s.cp, s.grav = (float(prob["p0"]), float(prob["R"]),
                                    float(prob["cp"]), float(prob["grav"]))
+        s.ntracers = self.nf - 5
         self.s = s
 
     def state(self, q) -> np.ndarray:
-        q = np.ascontiguousarray(q, dtype=np.float64).reshape(5, -1)
+        q = np.ascontiguousarray(q, dtype=np.float64).reshape(self.nf, -1)
         if q.shape[1] != self.M:
-            raise ValueError("q must be (5, Ne*(N+1)^3)")
+            raise ValueError("q must be (5 + ntracers, Ne*(N+1)^3)")
         return q
 
 
 def vol_rhs_o1(prob: dict, q) -> np.ndarray:
     b = _Bound(prob)
     q = b.state(q)
-    out = np.empty((5, b.M))
+    out = np.empty((b.nf, b.M))
     if _load().oracle_vol_rhs_o1(C.byref(b.s), _ptr(q), _ptr(out)) != 0:
         raise RuntimeError("oracle O1 rejected its arguments")
     return out
@@ -171,7 +175,7 @@ def vol_rhs_o1(prob: dict, q) -> np.ndarray:
 def vol_rhs_o2(prob: dict, q, nthreads: int = 0) -> np.ndarray:
     b = _Bound(prob)
     q = b.state(q)
-    out = np.empty((5, b.M))
+    out = np.empty((b.nf, b.M))
     if _load().oracle_vol_rhs_o2(C.byref(b.s), _ptr(q), _ptr(out), int(nthreads)) != 0:
         raise RuntimeError("oracle O2 failed")
     return out
@@ -181,7 +185,7 @@ def vol_rhs_abs(prob: dict, q) -> np.ndarray:
     """Running error bound: |Jinv| sum_d sum_n |D| |F| (+ |gravity term|) per point."""
     b = _Bound(prob)
     q = b.state(q)
-    out = np.empty((5, b.M))
+    out = np.empty((b.nf, b.M))
     if _load().oracle_vol_rhs_abs(C.byref(b.s), _ptr(q), _ptr(out)) != 0:
         raise RuntimeError("oracle error bound rejected its arguments")
     return out
@@ -210,15 +214,15 @@ def lsrk_scalar(lam: float, y0: float, dt: float, nsteps: int) -> float:
 def condition_numbers(prob: dict, q, rhs=None) -> np.ndarray:
     """Per field: max of the running error bound over max |rhs|."""
     ab = vol_rhs_abs(prob, q)
-    rhs = vol_rhs_o2(prob, q) if rhs is None else np.asarray(rhs).reshape(5, -1)
-    return np.array([ab[f].max() / max(np.abs(rhs[f]).max(), 1e-300) for f in range(5)])
+    rhs = vol_rhs_o2(prob, q) if rhs is None else np.asarray(rhs).reshape(ab.shape[0], -1)
+    return np.array([ab[f].max() / max(np.abs(rhs[f]).max(), 1e-300) for f in range(ab.shape[0])])
 
 
 def vol_rhs_points(prob: dict, q, node_ids) -> np.ndarray:
     b = _Bound(prob)
     q = b.state(q)
     ids = np.ascontiguousarray(node_ids, dtype=np.int64)
-    out = np.empty((5, ids.size))
+    out = np.empty((b.nf, ids.size))
     rc = _load().oracle_vol_rhs_points(C.byref(b.s), _ptr(q), ids.size,
                                        ids.ctypes.data_as(C.POINTER(C.c_int64)), _ptr(out))
     if rc != 0:

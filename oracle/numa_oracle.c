@@ -49,7 +49,7 @@
 #include <omp.h>
 #endif
 
-#define ORACLE_NFIELDS 5
+#define ORACLE_MAXFIELDS 8   /* rho, U1, U2, U3, Theta and up to three tracers */
 #define ORACLE_MAXNQ 16
 
 typedef struct {
@@ -61,7 +61,10 @@ typedef struct {
     const double *rho_ref;     /* reference density per node                    */
     const double *rhotheta_ref;/* reference Theta = rho*theta per node          */
     double p0, R, cp, grav;    /* EOS constants and gravitational acceleration  */
+    int ntracers;              /* passive tracers Q1..Q3 after Theta (0..3)     */
 } oracle_problem;
+
+#define NF(P) (5 + (P)->ntracers)   /* fields of the state */
 
 /* ------------------------------------------------------------------------- */
 /* GLL nodes and the differentiation matrix (inputs of Eq. (2): "D is the    */
@@ -155,7 +158,7 @@ double oracle_pressure(double Theta, double p0, double R, double cp)
 /* State and contravariant flux of direction d at one node (Eq. (1) flux
  * column f_a contracted with g_{a,d}, as in refFluxR / refFluxS). */
 static void node_flux(const oracle_problem *P, const double *q, int64_t M,
-                      int64_t m, int d, double F[ORACLE_NFIELDS])
+                      int64_t m, int d, double F[ORACLE_MAXFIELDS])
 {
     double rho = q[0 * M + m];
     double U1 = q[1 * M + m], U2 = q[2 * M + m], U3 = q[3 * M + m];
@@ -169,12 +172,14 @@ static void node_flux(const oracle_problem *P, const double *q, int64_t M,
     F[2] = U2 * u + g2 * pp;
     F[3] = U3 * u + g3 * pp;
     F[4] = Th * u;
+    /* tracers are advected like Theta: flux Q u, no pressure term (Sec. 2) */
+    for (int t = 0; t < P->ntracers; ++t) F[5 + t] = q[(5 + t) * M + m] * u;
 }
 
 static int check_problem(const oracle_problem *P)
 {
     if (!P || P->N < 1 || P->N >= ORACLE_MAXNQ || P->Ne < 0 || !P->D || !P->Jinv ||
-        !P->rho_ref || !P->rhotheta_ref)
+        !P->rho_ref || !P->rhotheta_ref || P->ntracers < 0 || P->ntracers > 3)
         return -1;
     for (int s = 0; s < 9; ++s)
         if (!P->g[s]) return -1;
@@ -204,10 +209,10 @@ static void o1_direction(const oracle_problem *P, const double *q, double *rhs, 
                         if (d == 0) { m = ((e * Nq + k) * Nq + j) * Nq + n; iota = i; }
                         else if (d == 1) { m = ((e * Nq + k) * Nq + n) * Nq + i; iota = j; }
                         else { m = ((e * Nq + n) * Nq + j) * Nq + i; iota = k; }
-                        double F[ORACLE_NFIELDS];
+                        double F[ORACLE_MAXFIELDS];
                         node_flux(P, q, M, m, d, F);
                         double JiD = P->Jinv[node] * P->D[iota * Nq + n];
-                        for (int b = 0; b < ORACLE_NFIELDS; ++b)
+                        for (int b = 0; b < NF(P); ++b)
                             rhs[b * M + node] = rhs[b * M + node] - JiD * F[b];
                     }
 }
@@ -217,7 +222,7 @@ int oracle_vol_rhs_o1(const oracle_problem *P, const double *q, double *rhs)
     if (check_problem(P) || !q || !rhs) return -1;
     const int Nq = P->N + 1;
     const int64_t M = P->Ne * Nq * Nq * Nq;
-    memset(rhs, 0, sizeof(double) * ORACLE_NFIELDS * (size_t)M);
+    memset(rhs, 0, sizeof(double) * NF(P) * (size_t)M);
     for (int d = 0; d < 3; ++d) o1_direction(P, q, rhs, d);
     for (int64_t m = 0; m < M; ++m)
         rhs[3 * M + m] = rhs[3 * M + m] - (q[0 * M + m] - P->rho_ref[m]) * P->grav;
@@ -243,7 +248,7 @@ int oracle_vol_rhs_o2(const oracle_problem *P, const double *q, double *rhs, int
 #endif
     {
         /* F[d][b][node-in-element] */
-        double *F = (double *)malloc(sizeof(double) * 3 * ORACLE_NFIELDS * (size_t)n3);
+        double *F = (double *)malloc(sizeof(double) * 3 * NF(P) * (size_t)n3);
         if (!F) {
             err = 1;
         } else {
@@ -253,19 +258,19 @@ int oracle_vol_rhs_o2(const oracle_problem *P, const double *q, double *rhs, int
             for (int64_t e = 0; e < P->Ne; ++e) {
                 for (int l = 0; l < n3; ++l)
                     for (int d = 0; d < 3; ++d) {
-                        double Fn[ORACLE_NFIELDS];
+                        double Fn[ORACLE_MAXFIELDS];
                         node_flux(P, q, M, e * n3 + l, d, Fn);
-                        for (int b = 0; b < ORACLE_NFIELDS; ++b)
-                            F[(d * ORACLE_NFIELDS + b) * n3 + l] = Fn[b];
+                        for (int b = 0; b < NF(P); ++b)
+                            F[(d * NF(P) + b) * n3 + l] = Fn[b];
                     }
                 for (int k = 0; k < Nq; ++k)
                     for (int j = 0; j < Nq; ++j)
                         for (int i = 0; i < Nq; ++i) {
                             int64_t node = e * n3 + (k * Nq + j) * Nq + i;
-                            for (int b = 0; b < ORACLE_NFIELDS; ++b) {
-                                const double *Fr = F + (0 * ORACLE_NFIELDS + b) * n3;
-                                const double *Fs = F + (1 * ORACLE_NFIELDS + b) * n3;
-                                const double *Ft = F + (2 * ORACLE_NFIELDS + b) * n3;
+                            for (int b = 0; b < NF(P); ++b) {
+                                const double *Fr = F + (0 * NF(P) + b) * n3;
+                                const double *Fs = F + (1 * NF(P) + b) * n3;
+                                const double *Ft = F + (2 * NF(P) + b) * n3;
                                 double s = 0.0;
                                 for (int n = 0; n < Nq; ++n)
                                     s += P->D[i * Nq + n] * Fr[(k * Nq + j) * Nq + n];
@@ -305,7 +310,7 @@ int oracle_vol_rhs_points(const oracle_problem *P, const double *q, int64_t npts
         int64_t e = node / n3;
         int64_t l = node % n3;
         int i = (int)(l % Nq), j = (int)((l / Nq) % Nq), k = (int)(l / (Nq * Nq));
-        double s[ORACLE_NFIELDS] = {0, 0, 0, 0, 0};
+        double s[ORACLE_MAXFIELDS] = {0};
         for (int d = 0; d < 3; ++d) {
             int iota = d == 0 ? i : (d == 1 ? j : k);
             for (int n = 0; n < Nq; ++n) {
@@ -313,13 +318,13 @@ int oracle_vol_rhs_points(const oracle_problem *P, const double *q, int64_t npts
                 if (d == 0) m = ((e * Nq + k) * Nq + j) * Nq + n;
                 else if (d == 1) m = ((e * Nq + k) * Nq + n) * Nq + i;
                 else m = ((e * Nq + n) * Nq + j) * Nq + i;
-                double F[ORACLE_NFIELDS];
+                double F[ORACLE_MAXFIELDS];
                 node_flux(P, q, M, m, d, F);
-                for (int b = 0; b < ORACLE_NFIELDS; ++b)
+                for (int b = 0; b < NF(P); ++b)
                     s[b] += P->D[iota * Nq + n] * F[b];
             }
         }
-        for (int b = 0; b < ORACLE_NFIELDS; ++b) {
+        for (int b = 0; b < NF(P); ++b) {
             double v = -P->Jinv[node] * s[b];
             if (b == 3) v = v - (q[0 * M + node] - P->rho_ref[node]) * P->grav;
             out[b * npts + p] = v;
@@ -348,7 +353,7 @@ int oracle_vol_rhs_abs(const oracle_problem *P, const double *q, double *out)
     for (int64_t node = 0; node < M; ++node) {
         int64_t e = node / n3, l = node % n3;
         int i = (int)(l % Nq), j = (int)((l / Nq) % Nq), k = (int)(l / (Nq * Nq));
-        double s[ORACLE_NFIELDS] = {0, 0, 0, 0, 0};
+        double s[ORACLE_MAXFIELDS] = {0};
         for (int d = 0; d < 3; ++d) {
             int iota = d == 0 ? i : (d == 1 ? j : k);
             for (int n = 0; n < Nq; ++n) {
@@ -356,13 +361,13 @@ int oracle_vol_rhs_abs(const oracle_problem *P, const double *q, double *out)
                 if (d == 0) m = ((e * Nq + k) * Nq + j) * Nq + n;
                 else if (d == 1) m = ((e * Nq + k) * Nq + n) * Nq + i;
                 else m = ((e * Nq + n) * Nq + j) * Nq + i;
-                double F[ORACLE_NFIELDS];
+                double F[ORACLE_MAXFIELDS];
                 node_flux(P, q, M, m, d, F);
-                for (int b = 0; b < ORACLE_NFIELDS; ++b)
+                for (int b = 0; b < NF(P); ++b)
                     s[b] += fabs(P->D[iota * Nq + n]) * fabs(F[b]);
             }
         }
-        for (int b = 0; b < ORACLE_NFIELDS; ++b) {
+        for (int b = 0; b < NF(P); ++b) {
             double v = fabs(P->Jinv[node]) * s[b];
             if (b == 3) v = v + fabs((q[0 * M + node] - P->rho_ref[node]) * P->grav);
             out[b * M + node] = v;
@@ -417,7 +422,7 @@ int oracle_lsrk(const oracle_problem *P, double *q, double dt, int nsteps, int n
 {
     if (check_problem(P) || !q || nsteps < 0) return -1;
     const int Nq = P->N + 1;
-    const size_t n = (size_t)ORACLE_NFIELDS * (size_t)(P->Ne * Nq * Nq * Nq);
+    const size_t n = (size_t)NF(P) * (size_t)(P->Ne * Nq * Nq * Nq);
     double *dq = (double *)calloc(n ? n : 1, sizeof(double));
     double *rhs = (double *)malloc(sizeof(double) * (n ? n : 1));
     if (!dq || !rhs) {

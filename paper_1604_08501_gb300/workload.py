@@ -44,7 +44,7 @@ from dataclasses import dataclass, field
 import numpy as np
 
 NFIELDS = 5
-FIELD_NAMES = ("rho", "U1", "U2", "U3", "Theta")
+FIELD_NAMES = ("rho", "U1", "U2", "U3", "Theta", "Q1", "Q2", "Q3")
 
 
 @dataclass(frozen=True)
@@ -257,23 +257,39 @@ class Workload:
     def problem(self) -> dict:
         """Geometry and constants in the dict form the oracle and the binding take."""
         d = {"N": self.mesh.N, "Ne": self.mesh.Ne, "g": self.mesh.g, "Jinv": self.mesh.Jinv,
-             "rho_ref": self.rho_ref, "rhotheta_ref": self.rhotheta_ref}
+             "rho_ref": self.rho_ref, "rhotheta_ref": self.rhotheta_ref,
+             "ntracers": self.q.shape[0] - NFIELDS}
         d.update(self.consts.as_dict())
         return d
 
 
+def tracer_state(mesh: Mesh, rho: np.ndarray, seed: int, count: int) -> np.ndarray:
+    """Passive tracers Q_t = rho r_t, mixing ratios r_t = 0.01 (1 + 0.5 B_t)
+    with B_t a sum of seeded Gaussian bumps as for the state, drawn from their
+    own generator (seed, 1) so that the five base fields do not change."""
+    rng = np.random.Generator(np.random.PCG64([seed, 1]))
+    Q = np.empty((count, mesh.M))
+    for t in range(count):
+        Q[t] = rho * 0.01 * (1.0 + 0.5 * _eval_bumps(mesh.x, _bumps(rng, mesh.L)))
+    return Q
+
+
 def make_workload(N: int, n, seed: int, L: float = 10_000.0, warp: float = 0.05,
                   consts: Constants = DRY_AIR, T: float = 300.0, eps: float = 1e-3,
-                  vmax: float = 10.0, name: str = "") -> Workload:
-    """Warped box of order N with the seeded perturbed hydrostatic state.
+                  vmax: float = 10.0, name: str = "", tracers: int = 0) -> Workload:
+    """Warped box of order N with the seeded perturbed hydrostatic state and
+    ``tracers`` (0..3) passive tracers after Theta.
     ``n`` is the number of elements per axis, or a tuple (nx, ny, nz)."""
     shape = (n, n, n) if np.isscalar(n) else tuple(int(v) for v in n)
     mesh = warped_box(N, shape, L=L, warp=warp)
     rho_ref, rt_ref = hydrostatic_reference(mesh.x[2], consts, T)
     q = perturbed_state(mesh, rho_ref, rt_ref, seed, eps=eps, vmax=vmax)
+    if tracers:
+        q = np.concatenate([q, tracer_state(mesh, q[0], seed, tracers)])
     return Workload(mesh=mesh, consts=consts, rho_ref=rho_ref, rhotheta_ref=rt_ref,
                     q=q, seed=seed, name=name,
-                    meta={"L": L, "warp": warp, "T": T, "eps": eps, "vmax": vmax, "n": n})
+                    meta={"L": L, "warp": warp, "T": T, "eps": eps, "vmax": vmax, "n": n,
+                          "tracers": tracers})
 
 
 def batch_plan(count: int = 64, seed: int = 99, orders=(3, 4, 5, 7),

@@ -319,3 +319,47 @@ def test_workload_statistics():
     # Same seed, same inputs; another seed, other inputs.
     assert np.array_equal(wl.make_workload(4, 3, seed=0).q, w.q)
     assert not np.array_equal(wl.make_workload(4, 3, seed=1).q, w.q)
+
+
+# --------------------------------------------------------------------------
+# Passive tracers (the paper's 8-field form: Q1..Q3 after Theta, Sec. 2)
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("N", [2, 4])
+def test_tracers_leave_the_five_fields_unchanged(N):
+    # Tracers are passive: adding them changes no bit of the other fields.
+    w5 = wl.make_workload(N, 2, seed=31)
+    w8 = wl.make_workload(N, 2, seed=31, tracers=3)
+    r5 = oracle.vol_rhs_o2(w5.problem(), w5.q)
+    r8 = oracle.vol_rhs_o2(w8.problem(), w8.q)
+    assert r8.shape == (8, w8.M)
+    assert np.array_equal(r8[:5], r5)
+
+
+def test_tracer_copies_of_theta_and_of_a_mixing_ratio_times_rho():
+    # A tracer equal to Theta is advected exactly like Theta: identical flux,
+    # identical rhs bits.  A tracer c * rho (constant mixing ratio) has rhs
+    # c * rhs_rho, the mass equation scaled (to rounding).
+    w = wl.make_workload(3, (3, 2, 1), seed=32, tracers=3)
+    q = w.q.copy()
+    q[5] = q[4]
+    q[6] = 0.25 * q[0]
+    q[7] = 0.0
+    prob = w.problem()
+    for rhs in (oracle.vol_rhs_o2(prob, q), oracle.vol_rhs_o1(prob, q)):
+        assert np.array_equal(rhs[5], rhs[4])
+        np.testing.assert_allclose(rhs[6], 0.25 * rhs[0], rtol=0,
+                                   atol=1e-14 * np.max(np.abs(rhs[0])))
+        assert not np.any(rhs[7])
+
+
+def test_tracer_forms_agree_and_pointwise():
+    w = wl.make_workload(4, 2, seed=33, tracers=2)
+    prob = w.problem()
+    o1, o2 = oracle.vol_rhs_o1(prob, w.q), oracle.vol_rhs_o2(prob, w.q)
+    assert o1.shape == (7, w.M)
+    for f in range(7):
+        assert np.max(np.abs(o1[f] - o2[f])) < 1e-14 * np.max(np.abs(o2[f])), f
+    ids = np.random.default_rng(3).choice(w.M, size=60, replace=False)
+    pts = oracle.vol_rhs_points(prob, w.q, ids)
+    assert np.max(np.abs(pts - o2[:, ids])) <= 1e-14 * np.max(np.abs(o2))
