@@ -19,6 +19,7 @@ a bounded sample of the same workload); only rank 0 runs it.
 from __future__ import annotations
 
 import argparse
+import dataclasses
 import json
 import os
 import statistics
@@ -499,7 +500,8 @@ NQ_STUDY = {3: (48, 48, 24), 7: (24, 24, 12), 11: (16, 16, 8), 15: (12, 12, 6)}
 
 def run_nq_sweep(args):
     """One evaluation per step of the 3,538,944-point mesh at each order of the
-    paper's Nq study, NUMA_FP64 (every order) and NUMA_MIXED (N <= 7).  Inputs
+    paper's Nq study: NUMA_FP64 (every order), NUMA_MIXED (N <= 7), and NUMA_FP64
+    with three passive tracers (fp64_8fields: the paper's 8-field form).  Inputs
     exceed L2 (0.68 GB FP64).  Metric: GDOF/s per order; `value` is Nq = 8."""
     import torch
     rank, local, world = dist_setup("nccl")
@@ -513,13 +515,18 @@ def run_nq_sweep(args):
     per = {}
     launches = 0
     for N, shape in NQ_STUDY.items():
-        w = wl.make_workload(N, shape, seed=1)
+        w = wl.make_workload(N, shape, seed=1, tracers=3)
+        w5 = dataclasses.replace(w, q=w.q[:5])
         row = {"elements": w.Ne, "points": w.M}
-        for prec in args.precisions:
+        for prec in list(args.precisions) + ["fp64_8fields"]:
             if prec == "df64" or (prec == "mixed" and N > 7):
                 continue
-            vt = VolumeTerm.from_problem(w.problem(), precision=prec)
-            q = torch.from_numpy(w.q_mixed() if prec == "mixed" else w.q).to(dev)
+            # fp64_8fields: the paper's 8-field form (three passive tracers)
+            ww = w if prec == "fp64_8fields" else w5
+            vt = VolumeTerm.from_problem(ww.problem(),
+                                         precision="fp64" if prec == "fp64_8fields" else prec)
+            q = torch.from_numpy(np.ascontiguousarray(
+                ww.q_mixed() if prec == "mixed" else ww.q)).to(dev)
             out = torch.empty_like(q)
             for _ in range(args.warmup):
                 vt.rhs(q, out, stream=stream)

@@ -29,7 +29,8 @@
  * Layout (all per-point arrays): element-major, then k, j, i with i fastest,
  * i.e. index ((e*Nq + k)*Nq + j)*Nq + i with Nq = N + 1.  M = Ne * Nq^3.
  * State and rhs: five planes of M values each, contiguous, in the order
- * (rho, U1, U2, U3, Theta); plane b starts at element offset b*M.
+ * (rho, U1, U2, U3, Theta), then one plane per tracer (NUMA_FP64 meshes with
+ * num_tracers > 0); plane b starts at element offset b*M.
  *
  * Errors: every int-returning call returns NUMA_OK (0) or a negative code;
  * numa_vol_last_error() then returns a message for the calling thread.  No
@@ -66,10 +67,16 @@ typedef struct {
     double p0, R, cp, grav;
 } numa_constants;
 
-/* Mesh size: num_elements hexahedra of order N (Nq = N + 1 points per axis). */
+/* Mesh size: num_elements hexahedra of order N (Nq = N + 1 points per axis),
+ * and num_tracers passive tracers (0 .. NUMA_MAX_TRACERS, NUMA_FP64 only): the
+ * state and rhs then hold 5 + num_tracers planes, the tracers Q1.. after
+ * Theta, each advected like Theta (flux Q u_d, no source; the paper's 8-field
+ * form, Sec. 2).  Zero-initialise the struct so that num_tracers defaults to 0. */
+#define NUMA_MAX_TRACERS 3
 typedef struct {
     int64_t num_elements;
     int N;
+    int num_tracers;
 } numa_mesh;
 
 /* Per-point geometry and reference state, FP64, M values each, in the layout
@@ -111,7 +118,7 @@ typedef struct numa_vol numa_vol;
  * c->cp > c->R > 0 and c->p0 > 0.  On success *out receives the handle
  * (release with numa_vol_destroy).  Errors: NUMA_EINVAL, NUMA_ENOMEM,
  * NUMA_ECUDA, NUMA_EUNSUPPORTED (NUMA_DF64 with N != 7; NUMA_MIXED with
- * N > 7).  Handles of N > 7 evaluate one element per CTA of (N+1)^2 threads,
+ * N > 7; tracers with a mode other than NUMA_FP64).  Handles of N > 7 evaluate one element per CTA of (N+1)^2 threads,
  * one pass per field (vol_rhs_fp64_high_kernel); the batch and the engine
  * take handles of N <= 7 only.
  *
@@ -143,9 +150,10 @@ int numa_vol_create(const numa_mesh *mesh, const numa_geometry *geo,
 /*
  * Enqueue one evaluation of the volume term on a CUDA stream.
  *
- * q:   device pointer, 5 planes of M values (read only): doubles for NUMA_FP64
- *      and NUMA_DF64, floats (perturbation form) for NUMA_MIXED.
- * rhs: device pointer, 5 planes of M values of the same type (overwritten; the
+ * q:   device pointer, 5 (+ num_tracers) planes of M values (read only):
+ *      doubles for NUMA_FP64 and NUMA_DF64, floats (perturbation form) for
+ *      NUMA_MIXED.
+ * rhs: device pointer, as many planes of the same type (overwritten; the
  *      paper's kernel accumulates into rhsq, this call stores the volume term).
  * Both must be 16-byte aligned and must not overlap.  stream is a
  * cudaStream_t (NULL = the legacy default stream).  The call returns once
@@ -161,8 +169,9 @@ int numa_vol_rhs(numa_vol *h, const void *q, void *rhs, void *stream);
  * up to 8 chunks of elements on three internal streams, so the copy-in of one
  * chunk, the kernel on the previous one and the copy-out of the one before
  * overlap.  Device staging buffers
- * (2 x 5 x M doubles) are allocated on the first call and owned by the
- * handle.  q and rhs are host pointers to 5 planes of M values of the
+ * (2 x (5 + num_tracers) x M values) are allocated on the first call and
+ * owned by the handle.  q and rhs are host pointers to 5 (+ num_tracers)
+ * planes of M values of the
  * handle's state type (pinned memory gives full copy bandwidth).  Errors:
  * NUMA_EINVAL, NUMA_ENOMEM, NUMA_ECUDA.
  */
@@ -246,7 +255,8 @@ int numa_batch_create(numa_precision prec, numa_batch **out);
  * in the batch) and its state q, a device pointer to 5 planes of M values of
  * the handle's state type, 16-byte aligned, that numa_batch_advance updates in
  * place.  *index (optional) receives the instance's position.
- * Errors: NUMA_EINVAL; NUMA_EUNSUPPORTED for a handle of order N > NUMA_MAX_N. */
+ * Errors: NUMA_EINVAL; NUMA_EUNSUPPORTED for a handle of order N > NUMA_MAX_N
+ * or with tracers. */
 int numa_batch_add(numa_batch *b, const numa_vol *h, void *q, int *index);
 
 /* Remove every instance (the handles and states are untouched). */
@@ -324,7 +334,7 @@ int numa_engine_create(numa_precision prec, size_t budget_bytes, int max_members
  * cancelled.  nsteps >= 1, dt > 0.  *id receives the request id.
  * Errors: NUMA_EINVAL (malformed request; the engine is unchanged),
  * NUMA_ELIMIT (the state exceeds the whole budget: it can never be admitted),
- * NUMA_EUNSUPPORTED (a mesh of order N > NUMA_MAX_N). */
+ * NUMA_EUNSUPPORTED (a mesh of order N > NUMA_MAX_N or with tracers). */
 int numa_engine_submit(numa_engine *e, const numa_vol *mesh, const void *q0_host,
                        void *q_out_host, int nsteps, double dt, int64_t *id);
 
@@ -380,7 +390,7 @@ void numa_engine_destroy(numa_engine *e);
  * total work exceeds 2^31 - 1 items); NUMA_EINVAL for a NULL or misaligned
  * pointer, count < 1, nsteps < 0, handles of mixed kinds or of another device,
  * or a double-float handle; NUMA_EUNSUPPORTED for a handle of order
- * N > NUMA_MAX_N; NUMA_ECUDA if a CUDA call fails.
+ * N > NUMA_MAX_N or with tracers; NUMA_ECUDA if a CUDA call fails.
  */
 #define NUMA_NOALLOC_MAX_INSTANCES 64
 int numa_batch_advance_noalloc(const numa_vol *const *handles, void *const *states, int count,

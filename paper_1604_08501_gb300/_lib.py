@@ -28,7 +28,7 @@ class numa_constants(C.Structure):
 
 
 class numa_mesh(C.Structure):
-    _fields_ = [("num_elements", C.c_int64), ("N", C.c_int)]
+    _fields_ = [("num_elements", C.c_int64), ("N", C.c_int), ("num_tracers", C.c_int)]
 
 
 class numa_geometry(C.Structure):

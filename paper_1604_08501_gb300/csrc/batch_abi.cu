@@ -170,6 +170,8 @@ int numa_batch_add(numa_batch *b, const numa_vol *h, void *q, int *index) {
     const bool mixed = b->prec == NUMA_MIXED;
     if (h->N > NUMA_MAX_N)
         return bfail(NUMA_EUNSUPPORTED, "numa_batch_add: the batch takes orders N <= 7");
+    if (h->nf != numa::kFields)
+        return bfail(NUMA_EUNSUPPORTED, "numa_batch_add: the batch takes meshes without tracers");
     if (mixed ? h->kernel != numa::Kernel::Mixed : h->kernel != numa::Kernel::Native)
         return bfail(NUMA_EINVAL, "numa_batch_add: handle precision differs from the batch's "
                                   "(NUMA_FP64 batches take NUMA_FP64 handles)");

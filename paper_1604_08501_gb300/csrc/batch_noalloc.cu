@@ -154,7 +154,7 @@ extern "C" int numa_batch_advance_noalloc(const numa_vol *const *handles, void *
         if (!h || !states[k] || (reinterpret_cast<uintptr_t>(states[k]) & 15u) != 0 ||
             h->device != dev)
             return NUMA_EINVAL;
-        if (h->N > NUMA_MAX_N) return NUMA_EUNSUPPORTED;
+        if (h->N > NUMA_MAX_N || h->nf != kFields) return NUMA_EUNSUPPORTED;
         if (mixed ? h->kernel != Kernel::Mixed : h->kernel != Kernel::Native) return NUMA_EINVAL;
         BatchInstance &I = tab.inst[k];
         I = BatchInstance{};

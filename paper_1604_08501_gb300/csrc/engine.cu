@@ -208,6 +208,8 @@ int numa_engine_submit(numa_engine *e, const numa_vol *mesh, const void *q0_host
     const bool mixed = e->prec == NUMA_MIXED;
     if (mesh->N > NUMA_MAX_N)
         return efail(NUMA_EUNSUPPORTED, "numa_engine_submit: the engine takes orders N <= 7");
+    if (mesh->nf != numa::kFields)
+        return efail(NUMA_EUNSUPPORTED, "numa_engine_submit: the engine takes meshes without tracers");
     if (mixed ? mesh->kernel != numa::Kernel::Mixed : mesh->kernel != numa::Kernel::Native)
         return efail(NUMA_EINVAL, "numa_engine_submit: mesh handle precision differs from the engine's");
     if (mesh->device != e->device)

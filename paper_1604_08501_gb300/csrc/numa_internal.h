@@ -10,7 +10,8 @@
 
 namespace numa {
 
-constexpr int kFields = 5;
+constexpr int kFields = 5;      // rho, U1, U2, U3, Theta
+constexpr int kMaxFields = 8;   // with three passive tracers
 
 // Elements [e0, e0 + count) of a mesh whose per-point planes hold M values.
 struct ElemRange {
@@ -90,10 +91,11 @@ cudaError_t launch_reference_eos(const double *theta_ref, double *w, double *A, 
                                  EosConstants c, cudaStream_t s);
 // Native FP64 for N = 8..15 (vol_fp64_high.cu): one CTA of Nq^2 threads per
 // element, one pass per field.
-cudaError_t launch_vol_rhs_fp64_high(int N, ElemRange r, const DeviceGeometry &geo,
+// nf: 5 fields, or 5 + tracers (nf <= 8).
+cudaError_t launch_vol_rhs_fp64_high(int N, int nf, ElemRange r, const DeviceGeometry &geo,
                                      const HighParams &P, const double *q, double *rhs,
                                      cudaStream_t s);
-cudaError_t launch_vol_rhs_fp64(int N, ElemRange r, const DeviceGeometry &geo,
+cudaError_t launch_vol_rhs_fp64(int N, int nf, ElemRange r, const DeviceGeometry &geo,
                                 const NativeParams &P, const double *q, double *rhs,
                                 cudaStream_t s);
 
@@ -189,6 +191,7 @@ std::vector<BatchItem> build_items(const std::vector<BatchInstance> &inst, const
 struct numa_vol {
     int N = 0;
     int Nq = 0;
+    int nf = 5;   // fields of the state: 5 + tracers
     int64_t Ne = 0;
     int64_t M = 0;
     int device = 0;

@@ -309,6 +309,10 @@ int numa_vol_create(const numa_mesh *mesh, const numa_geometry *geo, const numa_
         return fail(NUMA_EINVAL, "numa_vol_create: N must be in [1, 15]");
     if (mesh->N > NUMA_MAX_N && prec != NUMA_FP64)
         return fail(NUMA_EUNSUPPORTED, "numa_vol_create: orders N > 7 are implemented in NUMA_FP64 only");
+    if (mesh->num_tracers < 0 || mesh->num_tracers > NUMA_MAX_TRACERS)
+        return fail(NUMA_EINVAL, "numa_vol_create: num_tracers must be in [0, 3]");
+    if (mesh->num_tracers > 0 && prec != NUMA_FP64)
+        return fail(NUMA_EUNSUPPORTED, "numa_vol_create: tracers are implemented in NUMA_FP64 only");
     if (mesh->num_elements < 0)
         return fail(NUMA_EINVAL, "numa_vol_create: num_elements must be >= 0");
     if (mesh->num_elements > (int64_t)INT32_MAX)
@@ -328,6 +332,7 @@ int numa_vol_create(const numa_mesh *mesh, const numa_geometry *geo, const numa_
     if (!h) return fail(NUMA_ENOMEM, "numa_vol_create: host allocation failed");
     h->N = mesh->N;
     h->Nq = mesh->N + 1;
+    h->nf = numa::kFields + mesh->num_tracers;
     h->Ne = mesh->num_elements;
     h->M = h->Ne * h->Nq * h->Nq * h->Nq;
     h->prec = prec;
@@ -386,10 +391,10 @@ cudaError_t launch(numa_vol *h, const void *q, void *rhs, int64_t e0, int64_t co
         return numa::launch_vol_rhs_df64(r, h->dgeo, h->dparams, static_cast<const double *>(q),
                                          static_cast<double *>(rhs), s);
     if (h->kernel == numa::Kernel::NativeHigh)
-        return numa::launch_vol_rhs_fp64_high(h->N, r, h->geo, h->hparams,
+        return numa::launch_vol_rhs_fp64_high(h->N, h->nf, r, h->geo, h->hparams,
                                               static_cast<const double *>(q),
                                               static_cast<double *>(rhs), s);
-    return numa::launch_vol_rhs_fp64(h->N, r, h->geo, h->nparams,
+    return numa::launch_vol_rhs_fp64(h->N, h->nf, r, h->geo, h->nparams,
                                      static_cast<const double *>(q), static_cast<double *>(rhs), s);
 }
 
@@ -404,7 +409,7 @@ int numa_vol_rhs(numa_vol *h, const void *q, void *rhs, void *stream) {
     if (!q || !rhs) return fail(NUMA_EINVAL, "numa_vol_rhs: NULL q or rhs");
     if (!aligned16(q) || !aligned16(rhs))
         return fail(NUMA_EINVAL, "numa_vol_rhs: q and rhs must be 16-byte aligned");
-    const size_t bytes = h->elem * numa::kFields * h->M;
+    const size_t bytes = h->elem * h->nf * h->M;
     if (overlap(q, rhs, bytes)) return fail(NUMA_EINVAL, "numa_vol_rhs: q and rhs overlap");
     if (!is_device_pointer(q) || !is_device_pointer(rhs))
         return fail(NUMA_EINVAL, "numa_vol_rhs: q and rhs must be device pointers");
@@ -418,7 +423,7 @@ int numa_vol_rhs_host(numa_vol *h, const void *q, void *rhs) {
     if (!h) return fail(NUMA_EINVAL, "numa_vol_rhs_host: NULL handle");
     if (h->Ne == 0) return NUMA_OK;
     if (!q || !rhs) return fail(NUMA_EINVAL, "numa_vol_rhs_host: NULL q or rhs");
-    const size_t bytes = h->elem * numa::kFields * h->M;
+    const size_t bytes = h->elem * h->nf * h->M;
     if (overlap(q, rhs, bytes)) return fail(NUMA_EINVAL, "numa_vol_rhs_host: q and rhs overlap");
     cudaError_t e = cudaSuccess;
     if (!h->host_stream) {
@@ -450,7 +455,7 @@ int numa_vol_rhs_host(numa_vol *h, const void *q, void *rhs) {
     for (int c = 0; c < chunks && e == cudaSuccess; ++c) {
         const int64_t e0 = h->Ne * c / chunks, e1 = h->Ne * (c + 1) / chunks;
         const size_t off = h->elem * e0 * n3, len = h->elem * (e1 - e0) * n3;
-        for (int b = 0; b < numa::kFields && e == cudaSuccess; ++b)
+        for (int b = 0; b < h->nf && e == cudaSuccess; ++b)
             e = cudaMemcpyAsync(dq + b * plane + off, hq + b * plane + off, len,
                                 cudaMemcpyHostToDevice, h->h2d_stream);
         if (e == cudaSuccess) e = cudaEventRecord(h->ev_in[c], h->h2d_stream);
@@ -458,7 +463,7 @@ int numa_vol_rhs_host(numa_vol *h, const void *q, void *rhs) {
         if (e == cudaSuccess) e = launch(h, dq, dr, e0, e1 - e0, h->host_stream);
         if (e == cudaSuccess) e = cudaEventRecord(h->ev_out[c], h->host_stream);
         if (e == cudaSuccess) e = cudaStreamWaitEvent(h->d2h_stream, h->ev_out[c], 0);
-        for (int b = 0; b < numa::kFields && e == cudaSuccess; ++b)
+        for (int b = 0; b < h->nf && e == cudaSuccess; ++b)
             e = cudaMemcpyAsync(hr + b * plane + off, dr + b * plane + off, len,
                                 cudaMemcpyDeviceToHost, h->d2h_stream);
     }

@@ -41,13 +41,16 @@ constexpr int min_ctas() {
     return n < 1 ? 1 : (n > 32 ? 32 : n);
 }
 
-template <int NQ>
+// TRACERS: nf = 5 + tracers fields (up to 8) at run time; the tracers follow
+// Theta with flux Q u_d and no source.  Without tracers nf is 5.
+template <int NQ, bool TRACERS>
 __global__ void __launch_bounds__(NQ * NQ * NQ, min_ctas<NQ>())
 vol_rhs_fp64_kernel(DeviceGeometry geo, NativeParams P, const double *__restrict__ q,
-                    double *__restrict__ rhs, int64_t M, int64_t e0) {
+                    double *__restrict__ rhs, int64_t M, int64_t e0, int nf_run) {
     constexpr int N3 = NQ * NQ * NQ;
     constexpr int NL = NQ * NQ;               // lines per (direction, field)
-    extern __shared__ double sF[];            // [direction*5 + field][slot]
+    const int nf = TRACERS ? nf_run : kFields;
+    extern __shared__ double sF[];            // [direction*nf + field][slot]
 
     const int l = threadIdx.x;
     const int i = l % NQ, j = (l / NQ) % NQ, k = l / (NQ * NQ);
@@ -59,6 +62,12 @@ vol_rhs_fp64_kernel(DeviceGeometry geo, NativeParams P, const double *__restrict
     const double Th = q[4 * M + node];
     const double pp = pressure_perturbation(Th, geo.theta_ref[node], geo.w[node], geo.A[node], P);
     const double rinv = __drcp_rn(rho);
+    double Q[kMaxFields - kFields];
+    if constexpr (TRACERS) {
+#pragma unroll
+        for (int t = 0; t < kMaxFields - kFields; ++t)
+            Q[t] = kFields + t < nf ? q[(kFields + t) * M + node] : 0.0;
+    }
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
         const double g1 = geo.g[3 * d][node], g2 = geo.g[3 * d + 1][node],
@@ -66,17 +75,22 @@ vol_rhs_fp64_kernel(DeviceGeometry geo, NativeParams P, const double *__restrict
         const double v = fma(g3, U[2], fma(g2, U[1], g1 * U[0]));
         const double u = v * rinv;
         const int s = dir_slot<NQ, double>(d, i, j, k);
-        double *F = sF + d * kFields * N3 + s;
+        double *F = sF + d * nf * N3 + s;
         F[0 * N3] = v;
         F[1 * N3] = fma(U[0], u, g1 * pp);
         F[2 * N3] = fma(U[1], u, g2 * pp);
         F[3 * N3] = fma(U[2], u, g3 * pp);
         F[4 * N3] = Th * u;
+        if constexpr (TRACERS) {
+#pragma unroll
+            for (int t = 0; t < kMaxFields - kFields; ++t)
+                if (kFields + t < nf) F[(kFields + t) * N3] = Q[t] * u;
+        }
     }
     __syncthreads();
 
     // ---- phase 2: even-odd sweeps, one line per task, in place --------
-    for (int item = l; item < 3 * kFields * NL; item += N3)
+    for (int item = l; item < 3 * nf * NL; item += N3)
         sweep_line<NQ>(sF + (item / NL) * N3, item % NL, P);
     __syncthreads();
 
@@ -84,28 +98,37 @@ vol_rhs_fp64_kernel(DeviceGeometry geo, NativeParams P, const double *__restrict
     const double Jinv = geo.Jinv[node];
     const double drho = rho - geo.rho_ref[node];
 #pragma unroll
-    for (int b = 0; b < kFields; ++b) {
-        const double R = sF[(0 * kFields + b) * N3 + dir_slot<NQ, double>(0, i, j, k)] +
-                         sF[(1 * kFields + b) * N3 + dir_slot<NQ, double>(1, i, j, k)] +
-                         sF[(2 * kFields + b) * N3 + dir_slot<NQ, double>(2, i, j, k)];
+    for (int b = 0; b < (TRACERS ? kMaxFields : kFields); ++b) {
+        if (TRACERS && b >= nf) break;
+        const double R = sF[(0 * nf + b) * N3 + dir_slot<NQ, double>(0, i, j, k)] +
+                         sF[(1 * nf + b) * N3 + dir_slot<NQ, double>(1, i, j, k)] +
+                         sF[(2 * nf + b) * N3 + dir_slot<NQ, double>(2, i, j, k)];
         double v = -Jinv * R;
         if (b == 3) v = fma(-drho, P.eos.grav, v);
         rhs[b * M + node] = v;
     }
 }
 
-template <int NQ>
-cudaError_t launch_nq(ElemRange r, const DeviceGeometry &geo, const NativeParams &P,
-                      const double *q, double *rhs, cudaStream_t s) {
+template <int NQ, bool TRACERS>
+cudaError_t launch_kernel(ElemRange r, int nf, const DeviceGeometry &geo, const NativeParams &P,
+                          const double *q, double *rhs, cudaStream_t s) {
     constexpr int N3 = NQ * NQ * NQ;
-    const size_t smem = sizeof(double) * kFields * 3 * N3;
+    const size_t smem = sizeof(double) * nf * 3 * N3;
     // The opt-in above 48 KB is per device; setting it on every launch keeps
     // multi-device processes correct and costs about a microsecond.
-    cudaError_t e = cudaFuncSetAttribute(vol_rhs_fp64_kernel<NQ>,
+    cudaError_t e = cudaFuncSetAttribute(vol_rhs_fp64_kernel<NQ, TRACERS>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    vol_rhs_fp64_kernel<NQ><<<(unsigned)r.count, N3, smem, s>>>(geo, P, q, rhs, r.M, r.e0);
+    vol_rhs_fp64_kernel<NQ, TRACERS><<<(unsigned)r.count, N3, smem, s>>>(geo, P, q, rhs, r.M, r.e0,
+                                                                         nf);
     return cudaGetLastError();
+}
+
+template <int NQ>
+cudaError_t launch_nq(ElemRange r, int nf, const DeviceGeometry &geo, const NativeParams &P,
+                      const double *q, double *rhs, cudaStream_t s) {
+    if (nf == kFields) return launch_kernel<NQ, false>(r, nf, geo, P, q, rhs, s);
+    return launch_kernel<NQ, true>(r, nf, geo, P, q, rhs, s);
 }
 
 // w = 1/Theta_ref and A = p(Theta_ref)/Theta_ref, in place of a copy of Theta_ref.
@@ -128,18 +151,19 @@ cudaError_t launch_reference_eos(const double *theta_ref, double *w, double *A, 
     return cudaGetLastError();
 }
 
-cudaError_t launch_vol_rhs_fp64(int N, ElemRange r, const DeviceGeometry &geo,
+cudaError_t launch_vol_rhs_fp64(int N, int nf, ElemRange r, const DeviceGeometry &geo,
                                 const NativeParams &P, const double *q, double *rhs,
                                 cudaStream_t s) {
     if (r.count <= 0) return cudaSuccess;
+    if (nf < kFields || nf > kMaxFields) return cudaErrorInvalidValue;
     switch (N) {
-        case 1: return launch_nq<2>(r, geo, P, q, rhs, s);
-        case 2: return launch_nq<3>(r, geo, P, q, rhs, s);
-        case 3: return launch_nq<4>(r, geo, P, q, rhs, s);
-        case 4: return launch_nq<5>(r, geo, P, q, rhs, s);
-        case 5: return launch_nq<6>(r, geo, P, q, rhs, s);
-        case 6: return launch_nq<7>(r, geo, P, q, rhs, s);
-        case 7: return launch_nq<8>(r, geo, P, q, rhs, s);
+        case 1: return launch_nq<2>(r, nf, geo, P, q, rhs, s);
+        case 2: return launch_nq<3>(r, nf, geo, P, q, rhs, s);
+        case 3: return launch_nq<4>(r, nf, geo, P, q, rhs, s);
+        case 4: return launch_nq<5>(r, nf, geo, P, q, rhs, s);
+        case 5: return launch_nq<6>(r, nf, geo, P, q, rhs, s);
+        case 6: return launch_nq<7>(r, nf, geo, P, q, rhs, s);
+        case 7: return launch_nq<8>(r, nf, geo, P, q, rhs, s);
         default: return cudaErrorInvalidValue;
     }
 }

@@ -50,7 +50,7 @@ constexpr int high_min_ctas() {
 template <int NQ>
 __global__ void __launch_bounds__(3 * NQ * NQ, high_min_ctas<NQ>())
 vol_rhs_fp64_high_kernel(DeviceGeometry geo, HighParams P, const double *__restrict__ q,
-                         double *__restrict__ rhs, int64_t M, int64_t e0) {
+                         double *__restrict__ rhs, int64_t M, int64_t e0, int nf) {
     constexpr int NL = NQ * NQ;      // columns; lines per direction
     constexpr int N3 = NQ * NL;
     constexpr int FB = NL * 16;      // one direction's flux block (padded lines)
@@ -88,7 +88,7 @@ vol_rhs_fp64_high_kernel(DeviceGeometry geo, HighParams P, const double *__restr
     }
 
 #pragma unroll 1
-    for (int b = 0; b < kFields; ++b) {
+    for (int b = 0; b < nf; ++b) {   // 5 fields, then the tracers
         if (b > 0) {
             __syncthreads();   // the previous field's combination has read sF
 #pragma unroll 2
@@ -100,7 +100,8 @@ vol_rhs_fp64_high_kernel(DeviceGeometry geo, HighParams P, const double *__restr
 #pragma unroll
                     for (int d = 0; d < 3; ++d) {
                         const double u = sU[d * N3 + k * NL + c];
-                        // F_d[U_a] = U_a u_d + g_{ad} p';  F_d[Theta] = Theta u_d
+                        // F_d[U_a] = U_a u_d + g_{ad} p';  F_d[Theta] = Theta u_d,
+                        // and likewise Q u_d for a tracer
                         const double F =
                             b < 4 ? fma(qb, u, geo.g[3 * d + (b - 1)][node] * sP[k * NL + c]) : qb * u;
                         sF[d * FB + dir_slot<NQ, double>(d, i, j, k)] = F;
@@ -130,32 +131,33 @@ vol_rhs_fp64_high_kernel(DeviceGeometry geo, HighParams P, const double *__restr
 }
 
 template <int NQ>
-cudaError_t launch_high(ElemRange r, const DeviceGeometry &geo, const HighParams &P,
+cudaError_t launch_high(ElemRange r, int nf, const DeviceGeometry &geo, const HighParams &P,
                         const double *q, double *rhs, cudaStream_t s) {
     constexpr size_t smem = high_smem_bytes<NQ>();
     cudaError_t e = cudaFuncSetAttribute(vol_rhs_fp64_high_kernel<NQ>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     vol_rhs_fp64_high_kernel<NQ><<<(unsigned)r.count, high_threads<NQ>(), smem, s>>>(geo, P, q, rhs,
-                                                                                  r.M, r.e0);
+                                                                                  r.M, r.e0, nf);
     return cudaGetLastError();
 }
 
 }  // namespace
 
-cudaError_t launch_vol_rhs_fp64_high(int N, ElemRange r, const DeviceGeometry &geo,
+cudaError_t launch_vol_rhs_fp64_high(int N, int nf, ElemRange r, const DeviceGeometry &geo,
                                      const HighParams &P, const double *q, double *rhs,
                                      cudaStream_t s) {
     if (r.count <= 0) return cudaSuccess;
+    if (nf < kFields || nf > kMaxFields) return cudaErrorInvalidValue;
     switch (N) {
-        case 8: return launch_high<9>(r, geo, P, q, rhs, s);
-        case 9: return launch_high<10>(r, geo, P, q, rhs, s);
-        case 10: return launch_high<11>(r, geo, P, q, rhs, s);
-        case 11: return launch_high<12>(r, geo, P, q, rhs, s);
-        case 12: return launch_high<13>(r, geo, P, q, rhs, s);
-        case 13: return launch_high<14>(r, geo, P, q, rhs, s);
-        case 14: return launch_high<15>(r, geo, P, q, rhs, s);
-        case 15: return launch_high<16>(r, geo, P, q, rhs, s);
+        case 8: return launch_high<9>(r, nf, geo, P, q, rhs, s);
+        case 9: return launch_high<10>(r, nf, geo, P, q, rhs, s);
+        case 10: return launch_high<11>(r, nf, geo, P, q, rhs, s);
+        case 11: return launch_high<12>(r, nf, geo, P, q, rhs, s);
+        case 12: return launch_high<13>(r, nf, geo, P, q, rhs, s);
+        case 13: return launch_high<14>(r, nf, geo, P, q, rhs, s);
+        case 14: return launch_high<15>(r, nf, geo, P, q, rhs, s);
+        case 15: return launch_high<16>(r, nf, geo, P, q, rhs, s);
         default: return cudaErrorInvalidValue;
     }
 }

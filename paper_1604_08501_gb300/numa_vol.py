@@ -58,9 +58,11 @@ class VolumeTerm:
     see workload.perturbation_state)."""
 
     def __init__(self, N: int, num_elements: int, g, Jinv, rho_ref, rhotheta_ref,
-                 p0: float, R: float, cp: float, grav: float, precision: str = "fp64"):
+                 p0: float, R: float, cp: float, grav: float, precision: str = "fp64",
+                 tracers: int = 0):
         lib = _lib.load()
         self.N = int(N)
+        self.nf = NFIELDS + int(tracers)
         self.Ne = int(num_elements)
         self.Nq = self.N + 1
         self.M = self.Ne * self.Nq ** 3
@@ -76,7 +78,7 @@ class VolumeTerm:
         geo.Jinv = _host_or_device_ptr(Jinv, self.M, keep)
         geo.rho_ref = _host_or_device_ptr(rho_ref, self.M, keep)
         geo.rhotheta_ref = _host_or_device_ptr(rhotheta_ref, self.M, keep)
-        mesh = _lib.numa_mesh(self.Ne, self.N)
+        mesh = _lib.numa_mesh(self.Ne, self.N, int(tracers))
         consts = _lib.numa_constants(float(p0), float(R), float(cp), float(grav))
         prec = {"fp64": NUMA_FP64, "df64": NUMA_DF64, "mixed": NUMA_MIXED}[precision]
         h = C.c_void_p()
@@ -87,7 +89,7 @@ class VolumeTerm:
     def from_problem(cls, prob: dict, precision: str = "fp64") -> "VolumeTerm":
         return cls(prob["N"], prob["Ne"], prob["g"], prob["Jinv"], prob["rho_ref"],
                    prob["rhotheta_ref"], prob["p0"], prob["R"], prob["cp"], prob["grav"],
-                   precision=precision)
+                   precision=precision, tracers=prob.get("ntracers", 0))
 
     @property
     def handle(self) -> int:
@@ -106,18 +108,18 @@ class VolumeTerm:
 
     def rhs(self, q, out=None, stream=None):
         """Enqueue rhs = volume term of q on ``stream`` (default: torch's current
-        stream).  q and out are (5, M) CUDA tensors: float64 for "fp64" and
+        stream).  q and out are (5 + tracers, M) CUDA tensors: float64 for "fp64" and
         "df64", float32 perturbation state (rho', U1, U2, U3, Theta') for "mixed"."""
         import torch
         dt = self._torch_dtype()
         if not (isinstance(q, torch.Tensor) and q.is_cuda and q.dtype == dt):
             raise TypeError(f"q must be a {dt} CUDA tensor")
-        if q.numel() != NFIELDS * self.M or not q.is_contiguous():
-            raise ValueError(f"q must be contiguous with {NFIELDS} x {self.M} entries")
+        if q.numel() != self.nf * self.M or not q.is_contiguous():
+            raise ValueError(f"q must be contiguous with {self.nf} x {self.M} entries")
         if out is None:
-            out = torch.empty((NFIELDS, self.M), dtype=dt, device=q.device)
+            out = torch.empty((self.nf, self.M), dtype=dt, device=q.device)
         elif not (out.is_cuda and out.dtype == dt and out.is_contiguous()
-                  and out.numel() == NFIELDS * self.M):
+                  and out.numel() == self.nf * self.M):
             raise ValueError("out must be a contiguous CUDA tensor like q")
         if stream is None:
             stream = torch.cuda.current_stream(q.device)
@@ -137,16 +139,16 @@ class VolumeTerm:
                 raise TypeError("q must be a contiguous CPU tensor of the handle's type")
             qp = q.data_ptr()
             if out is None:
-                out = torch.empty((NFIELDS, self.M), dtype=q.dtype, pin_memory=q.is_pinned())
+                out = torch.empty((self.nf, self.M), dtype=q.dtype, pin_memory=q.is_pinned())
             op = out.data_ptr()
         else:
             q = np.ascontiguousarray(q, dtype=self.dtype_name)
             qp = q.ctypes.data
             if out is None:
-                out = np.empty((NFIELDS, self.M), dtype=self.dtype_name)
+                out = np.empty((self.nf, self.M), dtype=self.dtype_name)
             op = out.ctypes.data if isinstance(out, np.ndarray) else out.data_ptr()
-        if int(np.prod(q.shape)) != NFIELDS * self.M:
-            raise ValueError(f"q must have {NFIELDS} x {self.M} entries")
+        if int(np.prod(q.shape)) != self.nf * self.M:
+            raise ValueError(f"q must have {self.nf} x {self.M} entries")
         check(_lib.load().numa_vol_rhs_host(self.handle, C.c_void_p(qp), C.c_void_p(op)))
         return out
 
@@ -207,7 +209,7 @@ class Batch:
     def add(self, vt: "VolumeTerm", q) -> int:
         import torch
         if not (isinstance(q, torch.Tensor) and q.is_cuda and q.is_contiguous()
-                and q.dtype == vt._torch_dtype() and q.numel() == NFIELDS * vt.M):
+                and q.dtype == vt._torch_dtype() and q.numel() == vt.nf * vt.M):
             raise TypeError("q must be the instance's contiguous CUDA state tensor")
         idx = C.c_int()
         check_batch(_lib.load().numa_batch_add(self.handle, C.c_void_p(vt.handle),

@@ -1,0 +1,84 @@
+"""GPU parity of the 8-field form (passive tracers Q1..Q3 after Theta, the
+paper's benchmark form, Sec. 2) in NUMA_FP64, through the C ABI.
+
+Bar: per-field normwise max relative error <= 1e-12 against the oracle's O2
+form, as for the five base fields.  Properties that hold at any size: tracers
+leave the five base fields bit for bit as without them, and a tracer equal to
+Theta has Theta's rhs bit for bit (same flux, same arithmetic).
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1604_08501_gb300 import build
+from paper_1604_08501_gb300 import workload as wl
+from paper_1604_08501_gb300.numa_vol import Batch, Engine, NumaError, VolumeTerm
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+TOL = 1e-12
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    build.build()
+
+
+def gpu_rhs(prob, q):
+    with VolumeTerm.from_problem(prob) as vt:
+        out = vt.rhs(torch.from_numpy(np.ascontiguousarray(q)).cuda())
+        torch.cuda.synchronize()
+        return out.cpu().numpy()
+
+
+@pytest.mark.parametrize("N,T", [(1, 3), (3, 1), (4, 2), (7, 3), (9, 2), (11, 3)])
+def test_tracer_parity(N, T):
+    w = wl.make_workload(N, (3, 2, 1), seed=400 + N, tracers=T)
+    prob = w.problem()
+    out = gpu_rhs(prob, w.q)
+    assert out.shape == (5 + T, w.M)
+    ref = oracle.vol_rhs_o2(prob, w.q)
+    for f in range(5 + T):
+        mx = np.max(np.abs(out[f] - ref[f])) / np.max(np.abs(ref[f]))
+        assert mx <= TOL, (N, T, wl.FIELD_NAMES[f], mx)
+
+
+@pytest.mark.parametrize("N", [7, 11])
+def test_tracers_are_passive_and_theta_copies_match(N):
+    w8 = wl.make_workload(N, (2, 2, 1), seed=410 + N, tracers=3)
+    w5 = wl.make_workload(N, (2, 2, 1), seed=410 + N)
+    q = w8.q.copy()
+    q[6] = q[4]                                   # Q2 = Theta
+    r8 = gpu_rhs(w8.problem(), q)
+    r5 = gpu_rhs(w5.problem(), w5.q)
+    assert np.array_equal(r8[:5], r5)
+    assert np.array_equal(r8[6], r8[4])
+
+
+def test_tracer_host_path_full_paper_form():
+    # The paper's benchmark element: Nq = 8 with 8 fields, on the host path.
+    w = wl.make_workload(7, (4, 3, 2), seed=420, tracers=3)
+    prob = w.problem()
+    with VolumeTerm.from_problem(prob) as vt:
+        dev = vt.rhs(torch.from_numpy(w.q).cuda()).cpu().numpy()
+        assert np.array_equal(vt.rhs_host(w.q), dev)
+    ref = oracle.vol_rhs_o2(prob, w.q)
+    for f in range(8):
+        assert np.max(np.abs(dev[f] - ref[f])) <= TOL * np.max(np.abs(ref[f])), f
+
+
+def test_tracer_handles_are_rejected_where_unsupported():
+    w = wl.make_workload(3, (2, 1, 1), seed=430, tracers=2)
+    prob = w.problem()
+    with VolumeTerm.from_problem(prob) as vt:
+        q = torch.from_numpy(w.q).cuda()
+        with Batch("fp64") as b:
+            with pytest.raises(NumaError, match="EUNSUPPORTED"):
+                b.add(vt, q)
+        with Engine("fp64", budget_bytes=1 << 24) as eng:
+            with pytest.raises(NumaError, match="EUNSUPPORTED"):
+                eng.submit(vt, w.q, np.empty_like(w.q), 1, 0.01)
+    with pytest.raises(NumaError, match="EUNSUPPORTED"):
+        VolumeTerm.from_problem(prob, precision="mixed")
