@@ -171,7 +171,7 @@ __device__ void run_tile(const BatchInstance &I, int64_t e0, int64_t count,
                     }
                     T rinv;
                     if constexpr (MIXED)
-                        rinv = T(1) / rho;
+                        rinv = __frcp_rn(rho);   // the correctly rounded 1/rho, as 1.0f / rho
                     else
                         rinv = __drcp_rn(rho);   // the correctly rounded 1/rho, as 1.0 / rho
 #pragma unroll

@@ -70,7 +70,7 @@ struct EosRef32 {
 };
 
 static __device__ __forceinline__ EosRef32 eos_reference_f32(float th0, const MixedParams &P) {
-    return EosRef32{1.0f / th0, P.K * exp2f(P.gm1 * log2f(th0))};   // A = p(Theta_ref)/Theta_ref
+    return EosRef32{__frcp_rn(th0), P.K * exp2f(P.gm1 * log2f(th0))};   // A = p(Theta_ref)/Theta_ref
 }
 
 static __device__ __forceinline__ float pressure_perturbation_f32(float thp, float th0, EosRef32 r,

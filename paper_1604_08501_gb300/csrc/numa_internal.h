@@ -212,7 +212,10 @@ struct numa_vol {
     size_t elem = sizeof(double);   // bytes per state/rhs value (4 for NUMA_MIXED)
     void *d_stage = nullptr;        // host entry point: q and rhs staging, 2 * 5 * M values
     // host entry point: copy-in, compute and copy-out streams, per-chunk events
-    cudaStream_t host_stream = nullptr, h2d_stream = nullptr, d2h_stream = nullptr;
-    static constexpr int kChunks = 8;
+    // host path: two compute streams (alternate chunks, so one chunk's tail
+    // overlaps the next chunk's start), copy-in and copy-out streams
+    cudaStream_t host_stream = nullptr, host_stream2 = nullptr, h2d_stream = nullptr,
+                 d2h_stream = nullptr;
+    static constexpr int kChunks = 32;   // chunks of the host path: short pipeline fill and drain
     cudaEvent_t ev_in[kChunks] = {}, ev_out[kChunks] = {};
 };

@@ -428,6 +428,7 @@ int numa_vol_rhs_host(numa_vol *h, const void *q, void *rhs) {
     cudaError_t e = cudaSuccess;
     if (!h->host_stream) {
         e = cudaStreamCreateWithFlags(&h->host_stream, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->host_stream2, cudaStreamNonBlocking);
         if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->h2d_stream, cudaStreamNonBlocking);
         if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->d2h_stream, cudaStreamNonBlocking);
         for (int c = 0; c < numa_vol::kChunks && e == cudaSuccess; ++c) {
@@ -443,8 +444,9 @@ int numa_vol_rhs_host(numa_vol *h, const void *q, void *rhs) {
             return fail_cuda(e, "numa_vol_rhs_host: staging allocation");
         }
     }
-    // Chunks of elements flow through three streams: copy-in of chunk c + 1,
-    // compute of chunk c and copy-out of chunk c - 1 overlap.
+    // Chunks of elements flow through four streams: copy-in of chunk c + 1,
+    // compute of chunk c (two compute streams in turn, so that consecutive
+    // chunks' kernels overlap at their ends) and copy-out of chunk c - 1.
     char *dq = static_cast<char *>(h->d_stage);
     char *dr = dq + bytes;
     const char *hq = static_cast<const char *>(q);
@@ -452,23 +454,26 @@ int numa_vol_rhs_host(numa_vol *h, const void *q, void *rhs) {
     const int64_t n3 = (int64_t)h->Nq * h->Nq * h->Nq;
     const int chunks = (int)std::min<int64_t>(numa_vol::kChunks, h->Ne);
     const size_t plane = h->elem * h->M;
+    // One 2D copy per chunk and direction moves the chunk's slice of every
+    // field plane (pitch = the plane stride).
     for (int c = 0; c < chunks && e == cudaSuccess; ++c) {
         const int64_t e0 = h->Ne * c / chunks, e1 = h->Ne * (c + 1) / chunks;
         const size_t off = h->elem * e0 * n3, len = h->elem * (e1 - e0) * n3;
-        for (int b = 0; b < h->nf && e == cudaSuccess; ++b)
-            e = cudaMemcpyAsync(dq + b * plane + off, hq + b * plane + off, len,
-                                cudaMemcpyHostToDevice, h->h2d_stream);
+        e = cudaMemcpy2DAsync(dq + off, plane, hq + off, plane, len, (size_t)h->nf,
+                              cudaMemcpyHostToDevice, h->h2d_stream);
         if (e == cudaSuccess) e = cudaEventRecord(h->ev_in[c], h->h2d_stream);
-        if (e == cudaSuccess) e = cudaStreamWaitEvent(h->host_stream, h->ev_in[c], 0);
-        if (e == cudaSuccess) e = launch(h, dq, dr, e0, e1 - e0, h->host_stream);
-        if (e == cudaSuccess) e = cudaEventRecord(h->ev_out[c], h->host_stream);
+        cudaStream_t cs = (c & 1) ? h->host_stream2 : h->host_stream;
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, h->ev_in[c], 0);
+        if (e == cudaSuccess) e = launch(h, dq, dr, e0, e1 - e0, cs);
+        if (e == cudaSuccess) e = cudaEventRecord(h->ev_out[c], cs);
         if (e == cudaSuccess) e = cudaStreamWaitEvent(h->d2h_stream, h->ev_out[c], 0);
-        for (int b = 0; b < h->nf && e == cudaSuccess; ++b)
-            e = cudaMemcpyAsync(hr + b * plane + off, dr + b * plane + off, len,
-                                cudaMemcpyDeviceToHost, h->d2h_stream);
+        if (e == cudaSuccess)
+            e = cudaMemcpy2DAsync(hr + off, plane, dr + off, plane, len, (size_t)h->nf,
+                                  cudaMemcpyDeviceToHost, h->d2h_stream);
     }
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->d2h_stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->host_stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->host_stream2);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->h2d_stream);
     if (e != cudaSuccess) return fail_cuda(e, "numa_vol_rhs_host");
     return numa_vol_status(h, h->host_stream);
@@ -495,6 +500,7 @@ void numa_vol_destroy(numa_vol *h) {
     if (cur != h->device) cudaSetDevice(h->device);
     cudaDeviceSynchronize();
     if (h->host_stream) cudaStreamDestroy(h->host_stream);
+    if (h->host_stream2) cudaStreamDestroy(h->host_stream2);
     if (h->h2d_stream) cudaStreamDestroy(h->h2d_stream);
     if (h->d2h_stream) cudaStreamDestroy(h->d2h_stream);
     for (int c = 0; c < numa_vol::kChunks; ++c) {

@@ -22,8 +22,9 @@
 //  * vol_rhs_mixed_bulk_kernel (Nq = 8): persistent CTAs, 2 per SM.  The element
 //    slab (17 arrays x 2 KB, contiguous per array and element) is staged in
 //    shared memory by bulk asynchronous copies (cp.async.bulk) completing on an
-//    mbarrier.  Each CTA prefetches its next element while it computes the
-//    current one, so the loads stay in flight during the arithmetic.  Waits are
+//    mbarrier.  Two stages: once phase 1 has read an element's slab, its stage
+//    is refilled with the element two ahead, so up to two elements' copies
+//    stay in flight during the arithmetic.  Waits are
 //    bounded: on a timeout the kernel sets bit 0 of *err, drains its copies
 //    (again bounded) and returns.
 #include <cuda_runtime.h>
@@ -63,7 +64,7 @@ vol_rhs_mixed_kernel(MixedGeometry geo, MixedParams P, const float *__restrict__
     const float rho = geo.rho_ref[node] + rp;
     const float Th = th0 + thp;
     const float pp = pressure_perturbation_f32(thp, th0, P);
-    const float rinv = 1.0f / rho;
+    const float rinv = __frcp_rn(rho);   // correctly rounded, as 1.0f / rho
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
         const float g1 = geo.g[3 * d][node], g2 = geo.g[3 * d + 1][node],
@@ -140,23 +141,21 @@ vol_rhs_mixed_bulk_kernel(MixedGeometry geo, MixedParams P, const float *__restr
 
     uint32_t parity0 = 0u, parity1 = 0u;
     bool pending0 = false, pending1 = false;   // meaningful in thread 0 only
+    const int64_t G = gridDim.x;
     int64_t e = e0 + blockIdx.x;
+    // Two elements in flight from the start: this CTA's first into stage 0,
+    // its second into stage 1.
     if (l == 0 && e < e_end) {
         issue_slab(e, M, q, geo, stage0, &bar[0]);
         pending0 = true;
     }
+    if (l == 0 && e + G < e_end) {
+        issue_slab(e + G, M, q, geo, stage1, &bar[1]);
+        pending1 = true;
+    }
     int buf = 0;
     bool failed = false;
-    for (; e < e_end; e += gridDim.x) {
-        const int64_t en = e + gridDim.x;
-        if (l == 0 && en < e_end) {
-            // The other stage was last read before the closing barrier of the
-            // previous iteration; order those reads before the async writes.
-            fence_proxy_async();
-            issue_slab(en, M, q, geo, buf ? stage0 : stage1, buf ? &bar[0] : &bar[1]);
-            if (buf) pending0 = true;
-            else pending1 = true;
-        }
+    for (; e < e_end; e += G) {
         const bool ok = bulk_wait(buf ? &bar[1] : &bar[0], buf ? parity1 : parity0);
         if (__syncthreads_or(!ok)) {
             failed = true;
@@ -179,7 +178,7 @@ vol_rhs_mixed_bulk_kernel(MixedGeometry geo, MixedParams P, const float *__restr
         const float rho = st[15 * kPts + l] + rp;
         const float Th = th0 + thp;
         const float pp = pressure_perturbation_f32(thp, th0, P);
-        const float rinv = 1.0f / rho;
+        const float rinv = __frcp_rn(rho);   // correctly rounded, as 1.0f / rho
 #pragma unroll
         for (int d = 0; d < 3; ++d) {
             const float g1 = st[(kFields + 3 * d) * kPts + l];
@@ -196,6 +195,15 @@ vol_rhs_mixed_bulk_kernel(MixedGeometry geo, MixedParams P, const float *__restr
         }
         const float Jinv = st[14 * kPts + l];
         __syncthreads();
+        // This stage is dead now (phase 1 read all of it, and phase 3 uses
+        // registers): refill it with the element two ahead, so that during the
+        // sweeps and stores two elements' copies are in flight.
+        if (l == 0 && e + 2 * G < e_end) {
+            fence_proxy_async();   // order the generic reads above before the async writes
+            issue_slab(e + 2 * G, M, q, geo, buf ? stage1 : stage0, buf ? &bar[1] : &bar[0]);
+            if (buf) pending1 = true;
+            else pending0 = true;
+        }
 
         // ---- phase 2: even-odd sweeps ---------------------------------
         for (int item = l; item < 3 * kFields * 64; item += kPts)
@@ -213,9 +221,8 @@ vol_rhs_mixed_bulk_kernel(MixedGeometry geo, MixedParams P, const float *__restr
             if (b == 3) v = fmaf(-rp, P.grav, v);
             rhs[b * M + node] = v;
         }
-        // No barrier here: this element's stage was last read in phase 1 (before
-        // the barrier after it), and the barrier after the next wait orders this
-        // phase 3's reads of sF before the next phase 1 writes it.
+        // No barrier here: the barrier after the next wait orders this phase 3's
+        // reads of sF before the next phase 1 writes it.
         buf ^= 1;
     }
     if (failed && l == 0) {
