@@ -500,9 +500,10 @@ NQ_STUDY = {3: (48, 48, 24), 7: (24, 24, 12), 11: (16, 16, 8), 15: (12, 12, 6)}
 
 def run_nq_sweep(args):
     """One evaluation per step of the 3,538,944-point mesh at each order of the
-    paper's Nq study: NUMA_FP64 (every order), NUMA_MIXED (N <= 7), and NUMA_FP64
-    with three passive tracers (fp64_8fields: the paper's 8-field form).  Inputs
-    exceed L2 (0.68 GB FP64).  Metric: GDOF/s per order; `value` is Nq = 8."""
+    paper's Nq study, NUMA_FP64 and NUMA_MIXED, with five fields and with three
+    passive tracers (*_8fields: the paper's 8-field form; mixed_8fields is also
+    its FP32 precision).  Inputs exceed L2 (0.68 GB FP64).  Metric: GDOF/s per
+    order; `value` is Nq = 8."""
     import torch
     rank, local, world = dist_setup("nccl")
     torch.cuda.set_device(local)
@@ -518,15 +519,16 @@ def run_nq_sweep(args):
         w = wl.make_workload(N, shape, seed=1, tracers=3)
         w5 = dataclasses.replace(w, q=w.q[:5])
         row = {"elements": w.Ne, "points": w.M}
-        for prec in list(args.precisions) + ["fp64_8fields"]:
-            if prec == "df64" or (prec == "mixed" and N > 7):
+        for prec in list(args.precisions) + ["fp64_8fields", "mixed_8fields"]:
+            if prec == "df64":
                 continue
-            # fp64_8fields: the paper's 8-field form (three passive tracers)
-            ww = w if prec == "fp64_8fields" else w5
-            vt = VolumeTerm.from_problem(ww.problem(),
-                                         precision="fp64" if prec == "fp64_8fields" else prec)
+            # *_8fields: the paper's 8-field form (three passive tracers);
+            # mixed_8fields is also the paper's precision (FP32)
+            ww = w if prec.endswith("_8fields") else w5
+            mode = prec.split("_")[0]
+            vt = VolumeTerm.from_problem(ww.problem(), precision=mode)
             q = torch.from_numpy(np.ascontiguousarray(
-                ww.q_mixed() if prec == "mixed" else ww.q)).to(dev)
+                ww.q_mixed() if mode == "mixed" else ww.q)).to(dev)
             out = torch.empty_like(q)
             for _ in range(args.warmup):
                 vt.rhs(q, out, stream=stream)

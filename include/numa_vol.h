@@ -59,7 +59,8 @@ extern "C" {
 
 #define NUMA_MAX_N 7            /* orders N = 1 .. 7 (Nq = 2 .. 8): every mode, the batch
                                    and the engine                                          */
-#define NUMA_MAX_N_FP64 15      /* NUMA_FP64 evaluations also take N = 8 .. 15 (Nq up to 16) */
+#define NUMA_MAX_N_FP64 15      /* NUMA_FP64 and NUMA_MIXED evaluations also take N = 8 .. 15
+                                   (Nq up to 16)                                           */
 
 /* Physical constants: EOS reference pressure p0, gas constant R, specific heat
  * at constant pressure cp (gamma = cp / (cp - R), Sec. 2), gravity grav. */
@@ -68,7 +69,8 @@ typedef struct {
 } numa_constants;
 
 /* Mesh size: num_elements hexahedra of order N (Nq = N + 1 points per axis),
- * and num_tracers passive tracers (0 .. NUMA_MAX_TRACERS, NUMA_FP64 only): the
+ * and num_tracers passive tracers (0 .. NUMA_MAX_TRACERS; NUMA_FP64 and
+ * NUMA_MIXED, where tracers are FP32 values as they are): the
  * state and rhs then hold 5 + num_tracers planes, the tracers Q1.. after
  * Theta, each advected like Theta (flux Q u_d, no source; the paper's 8-field
  * form, Sec. 2).  Zero-initialise the struct so that num_tracers defaults to 0. */
@@ -113,14 +115,14 @@ typedef struct numa_vol numa_vol;
  * 1/Theta_ref and p(Theta_ref)/Theta_ref.  p' is exactly zero wherever
  * Theta == Theta_ref.  Synchronous.
  *
- * mesh->N in [1, NUMA_MAX_N_FP64] for NUMA_FP64 and in [1, NUMA_MAX_N] for
- * the other modes; mesh->num_elements >= 0; every pointer of geo non-null;
+ * mesh->N in [1, NUMA_MAX_N_FP64] for NUMA_FP64 and NUMA_MIXED, and 7 for
+ * NUMA_DF64; mesh->num_elements >= 0; every pointer of geo non-null;
  * c->cp > c->R > 0 and c->p0 > 0.  On success *out receives the handle
  * (release with numa_vol_destroy).  Errors: NUMA_EINVAL, NUMA_ENOMEM,
- * NUMA_ECUDA, NUMA_EUNSUPPORTED (NUMA_DF64 with N != 7; NUMA_MIXED with
- * N > 7; tracers with a mode other than NUMA_FP64).  Handles of N > 7 evaluate one element per CTA of (N+1)^2 threads,
- * one pass per field (vol_rhs_fp64_high_kernel); the batch and the engine
- * take handles of N <= 7 only.
+ * NUMA_ECUDA, NUMA_EUNSUPPORTED (NUMA_DF64 with N != 7 or with tracers).
+ * Handles of N > 7 evaluate one element per CTA of 3 (N+1)^2 threads, one
+ * pass per field (vol_rhs_high_kernel); the batch and the engine take handles
+ * of N <= 7 only.
  *
  * NUMA_MIXED takes the state as FP32 perturbations from the reference state:
  * plane 0 holds rho - rho_ref, plane 4 holds Theta - Theta_ref, and planes 1-3

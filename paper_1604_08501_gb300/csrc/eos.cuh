@@ -69,12 +69,15 @@ struct EosRef32 {
     float w, A;
 };
 
-static __device__ __forceinline__ EosRef32 eos_reference_f32(float th0, const MixedParams &P) {
+template <typename Params>
+static __device__ __forceinline__ EosRef32 eos_reference_f32(float th0, const Params &P) {
     return EosRef32{__frcp_rn(th0), P.K * exp2f(P.gm1 * log2f(th0))};   // A = p(Theta_ref)/Theta_ref
 }
 
+// Params: MixedParams or HighParams32 (c, K, gm1, gamma).
+template <typename Params>
 static __device__ __forceinline__ float pressure_perturbation_f32(float thp, float th0, EosRef32 r,
-                                                           const MixedParams &P) {
+                                                           const Params &P) {
     const unsigned lanes = __activemask();
     if (__all_sync(lanes, th0 > 0.0f)) {
         const float x = thp * r.w;
@@ -99,8 +102,9 @@ static __device__ __forceinline__ float pressure_perturbation_f32(float thp, flo
     return P.K * powf(thp, P.gamma);
 }
 
+template <typename Params>
 static __device__ __forceinline__ float pressure_perturbation_f32(float thp, float th0,
-                                                           const MixedParams &P) {
+                                                           const Params &P) {
     if (th0 > 0.0f) return pressure_perturbation_f32(thp, th0, eos_reference_f32(th0, P), P);
     return P.K * powf(thp, P.gamma);
 }

@@ -53,6 +53,14 @@ struct HighParams {
     double De[64], Do[64], Dc[8], Dcr[8];
 };
 
+// The same for the mixed-precision mode at N = 8..15: FP32 tables and the FP32
+// EOS constants of MixedParams (c[k] = binom(gamma, k+1)).
+struct HighParams32 {
+    float De[64], Do[64], Dc[8], Dcr[8];
+    float c[16];
+    float K, gm1, gamma, grav;
+};
+
 // Per-point arrays of the double-float path (N = 7): float2 (h, l) pairs, and
 // the reference state in FP64, so that rho - rho_ref and Theta - Theta_ref are
 // exact FP64 differences before they are split.
@@ -95,6 +103,10 @@ cudaError_t launch_reference_eos(const double *theta_ref, double *w, double *A, 
 cudaError_t launch_vol_rhs_fp64_high(int N, int nf, ElemRange r, const DeviceGeometry &geo,
                                      const HighParams &P, const double *q, double *rhs,
                                      cudaStream_t s);
+// Mixed precision for N = 8..15 (vol_fp64_high.cu, FP32 instantiation).
+cudaError_t launch_vol_rhs_mixed_high(int N, int nf, ElemRange r, const MixedGeometry &geo,
+                                      const HighParams32 &P, const float *q, float *rhs,
+                                      cudaStream_t s);
 cudaError_t launch_vol_rhs_fp64(int N, int nf, ElemRange r, const DeviceGeometry &geo,
                                 const NativeParams &P, const double *q, double *rhs,
                                 cudaStream_t s);
@@ -114,7 +126,7 @@ cudaError_t launch_vol_rhs_df64(ElemRange r, const DfGeometry &geo, const DfPara
 cudaError_t launch_to_f32(const double *src, float *dst, int64_t M, cudaStream_t s);
 // N = 7 launches the persistent bulk-copy kernel (2 CTAs per SM); it sets
 // bit 0 of *err if a bounded wait on its copies times out.
-cudaError_t launch_vol_rhs_mixed(int N, ElemRange r, const MixedGeometry &geo,
+cudaError_t launch_vol_rhs_mixed(int N, int nf, ElemRange r, const MixedGeometry &geo,
                                  const MixedParams &P, const float *q, float *rhs, int *err,
                                  int num_sms, cudaStream_t s);
 
@@ -142,8 +154,8 @@ struct DfParams {
 };
 
 // Native: vol_rhs_fp64_kernel (N <= 7); NativeHigh: vol_rhs_fp64_high_kernel
-// (N = 8..15); DoubleFloat and Mixed: the other precision modes (N <= 7).
-enum class Kernel { Native, NativeHigh, DoubleFloat, Mixed };
+// (N = 8..15); DoubleFloat (N = 7); Mixed (N <= 7) and MixedHigh (N = 8..15).
+enum class Kernel { Native, NativeHigh, DoubleFloat, Mixed, MixedHigh };
 
 // Device-side description of one instance of a batch: its order, size, state
 // and the geometry/parameters of its handle (FP64 or mixed, per the batch).
@@ -206,7 +218,8 @@ struct numa_vol {
     numa::DfGeometry dgeo{};        // double-float path
     numa::DfParams dparams{};
     numa::NativeParams nparams{};
-    numa::HighParams hparams{};   // N >= 8
+    numa::HighParams hparams{};      // NUMA_FP64, N >= 8
+    numa::HighParams32 hmparams{};   // NUMA_MIXED, N >= 8
     numa::MixedGeometry mgeo{};     // mixed-precision path
     numa::MixedParams mparams{};
     size_t elem = sizeof(double);   // bytes per state/rhs value (4 for NUMA_MIXED)

@@ -60,18 +60,26 @@ const char *numa_vol_kernel_name(const numa_vol *h) {
     static const char *native[] = {"", "vol_rhs_fp64_kernel<2>", "vol_rhs_fp64_kernel<3>",
                                    "vol_rhs_fp64_kernel<4>", "vol_rhs_fp64_kernel<5>",
                                    "vol_rhs_fp64_kernel<6>", "vol_rhs_fp64_kernel<7>",
-                                   "vol_rhs_fp64_kernel<8>", "vol_rhs_fp64_high_kernel<9>",
-                                   "vol_rhs_fp64_high_kernel<10>", "vol_rhs_fp64_high_kernel<11>",
-                                   "vol_rhs_fp64_high_kernel<12>", "vol_rhs_fp64_high_kernel<13>",
-                                   "vol_rhs_fp64_high_kernel<14>", "vol_rhs_fp64_high_kernel<15>",
-                                   "vol_rhs_fp64_high_kernel<16>"};
+                                   "vol_rhs_fp64_kernel<8>", "vol_rhs_high_kernel<9, double>",
+                                   "vol_rhs_high_kernel<10, double>", "vol_rhs_high_kernel<11, double>",
+                                   "vol_rhs_high_kernel<12, double>", "vol_rhs_high_kernel<13, double>",
+                                   "vol_rhs_high_kernel<14, double>", "vol_rhs_high_kernel<15, double>",
+                                   "vol_rhs_high_kernel<16, double>"};
     if (!h) return "";
     static const char *mixed[] = {"", "vol_rhs_mixed_kernel<2>", "vol_rhs_mixed_kernel<3>",
                                   "vol_rhs_mixed_kernel<4>", "vol_rhs_mixed_kernel<5>",
                                   "vol_rhs_mixed_kernel<6>", "vol_rhs_mixed_kernel<7>",
                                   "vol_rhs_mixed_bulk_kernel"};   // N = 7: the persistent staged kernel
     if (h->kernel == numa::Kernel::DoubleFloat) return "vol_rhs_df64_kernel";
-    if (h->kernel == numa::Kernel::Mixed) return mixed[h->N];
+    if (h->kernel == numa::Kernel::Mixed)
+        return h->N == 7 && h->nf > numa::kFields ? "vol_rhs_mixed_kernel<8>" : mixed[h->N];
+    if (h->kernel == numa::Kernel::MixedHigh) {
+        static const char *mixed_high[] = {"vol_rhs_high_kernel<9, float>", "vol_rhs_high_kernel<10, float>",
+                                           "vol_rhs_high_kernel<11, float>", "vol_rhs_high_kernel<12, float>",
+                                           "vol_rhs_high_kernel<13, float>", "vol_rhs_high_kernel<14, float>",
+                                           "vol_rhs_high_kernel<15, float>", "vol_rhs_high_kernel<16, float>"};
+        return mixed_high[h->N - 8];
+    }
     return native[h->N];
 }
 
@@ -105,10 +113,27 @@ void build_params(numa_vol *h, const double *D) {
     binomial_coefficients(h->eos.gamma, c);
     h->nparams.eos = h->eos;
     for (int k = 0; k < 15; ++k) h->nparams.c[k] = static_cast<double>(c[k + 1]);
-    if (h->N >= 8) {   // the high-order kernel's parameters; no other mode runs N >= 8
+    const long double g = h->eos.gamma;
+    const float K = static_cast<float>(std::pow((long double)h->eos.p0, 1.0L - g) *
+                                       std::pow((long double)h->eos.R, g));
+    if (h->N >= 8) {   // the high-order kernels' parameters (FP64 and mixed)
         h->hparams.eos = h->eos;
         for (int k = 0; k < 15; ++k) h->hparams.c[k] = h->nparams.c[k];
         numa::sweep_tables(h->N, D, h->hparams.De, h->hparams.Do, h->hparams.Dc, h->hparams.Dcr);
+        numa::HighParams32 &m = h->hmparams;
+        for (int t = 0; t < 64; ++t) {
+            m.De[t] = static_cast<float>(h->hparams.De[t]);
+            m.Do[t] = static_cast<float>(h->hparams.Do[t]);
+        }
+        for (int t = 0; t < 8; ++t) {
+            m.Dc[t] = static_cast<float>(h->hparams.Dc[t]);
+            m.Dcr[t] = static_cast<float>(h->hparams.Dcr[t]);
+        }
+        for (int k = 0; k < 16; ++k) m.c[k] = static_cast<float>(c[k + 1]);
+        m.K = K;
+        m.gm1 = static_cast<float>(g - 1.0L);
+        m.gamma = static_cast<float>(g);
+        m.grav = static_cast<float>(h->eos.grav);
         return;
     }
     numa::sweep_tables(h->N, D, h->nparams.De, h->nparams.Do, h->nparams.Dc, h->nparams.Dcr);
@@ -123,9 +148,7 @@ void build_params(numa_vol *h, const double *D) {
             m.Dcr[t] = static_cast<float>(h->nparams.Dcr[t]);
         }
         for (int k = 0; k < 16; ++k) m.c[k] = static_cast<float>(c[k + 1]);
-        const long double g = h->eos.gamma;
-        m.K = static_cast<float>(std::pow((long double)h->eos.p0, 1.0L - g) *
-                                 std::pow((long double)h->eos.R, g));
+        m.K = K;
         m.gm1 = static_cast<float>(g - 1.0L);
         m.gamma = static_cast<float>(g);
         m.grav = static_cast<float>(h->eos.grav);
@@ -227,7 +250,7 @@ cudaError_t create_mixed(numa_vol *h, const numa_geometry *geo) {
     h->mgeo.Jinv = slots[9];
     h->mgeo.rho_ref = slots[10];
     h->mgeo.theta_ref = slots[11];
-    h->kernel = numa::Kernel::Mixed;
+    h->kernel = h->N > NUMA_MAX_N ? numa::Kernel::MixedHigh : numa::Kernel::Mixed;
     h->elem = sizeof(float);
     return cudaSuccess;
 }
@@ -307,12 +330,12 @@ int numa_vol_create(const numa_mesh *mesh, const numa_geometry *geo, const numa_
     if (!mesh || !geo || !c) return fail(NUMA_EINVAL, "numa_vol_create: NULL argument");
     if (mesh->N < 1 || mesh->N > NUMA_MAX_N_FP64)
         return fail(NUMA_EINVAL, "numa_vol_create: N must be in [1, 15]");
-    if (mesh->N > NUMA_MAX_N && prec != NUMA_FP64)
-        return fail(NUMA_EUNSUPPORTED, "numa_vol_create: orders N > 7 are implemented in NUMA_FP64 only");
+    if (mesh->N > NUMA_MAX_N && prec == NUMA_DF64)
+        return fail(NUMA_EUNSUPPORTED, "numa_vol_create: NUMA_DF64 is implemented for N = 7 only");
     if (mesh->num_tracers < 0 || mesh->num_tracers > NUMA_MAX_TRACERS)
         return fail(NUMA_EINVAL, "numa_vol_create: num_tracers must be in [0, 3]");
-    if (mesh->num_tracers > 0 && prec != NUMA_FP64)
-        return fail(NUMA_EUNSUPPORTED, "numa_vol_create: tracers are implemented in NUMA_FP64 only");
+    if (mesh->num_tracers > 0 && prec == NUMA_DF64)
+        return fail(NUMA_EUNSUPPORTED, "numa_vol_create: NUMA_DF64 takes no tracers");
     if (mesh->num_elements < 0)
         return fail(NUMA_EINVAL, "numa_vol_create: num_elements must be >= 0");
     if (mesh->num_elements > (int64_t)INT32_MAX)
@@ -383,8 +406,12 @@ namespace {
 cudaError_t launch(numa_vol *h, const void *q, void *rhs, int64_t e0, int64_t count,
                    cudaStream_t s) {
     const numa::ElemRange r{e0, count, h->M};
+    if (h->kernel == numa::Kernel::MixedHigh)
+        return numa::launch_vol_rhs_mixed_high(h->N, h->nf, r, h->mgeo, h->hmparams,
+                                               static_cast<const float *>(q),
+                                               static_cast<float *>(rhs), s);
     if (h->kernel == numa::Kernel::Mixed)
-        return numa::launch_vol_rhs_mixed(h->N, r, h->mgeo, h->mparams,
+        return numa::launch_vol_rhs_mixed(h->N, h->nf, r, h->mgeo, h->mparams,
                                           static_cast<const float *>(q), static_cast<float *>(rhs),
                                           h->d_err, h->num_sms, s);
     if (h->kernel == numa::Kernel::DoubleFloat)

@@ -44,13 +44,16 @@ constexpr int mixed_min_ctas() {
     return n < 1 ? 1 : (n > 32 ? 32 : n);
 }
 
-template <int NQ>
+// TRACERS: nf = 5 + tracers fields at run time (tracers Q in FP32 as they are,
+// flux Q u_d, no source).  Without tracers nf is 5.
+template <int NQ, bool TRACERS>
 __global__ void __launch_bounds__(NQ * NQ * NQ, mixed_min_ctas<NQ>())
 vol_rhs_mixed_kernel(MixedGeometry geo, MixedParams P, const float *__restrict__ q,
-                     float *__restrict__ rhs, int64_t M, int64_t e0) {
+                     float *__restrict__ rhs, int64_t M, int64_t e0, int nf_run) {
     constexpr int N3 = NQ * NQ * NQ;
     constexpr int NL = NQ * NQ;
-    extern __shared__ float sFm[];            // [direction*5 + field][slot]
+    const int nf = TRACERS ? nf_run : kFields;
+    extern __shared__ float sFm[];            // [direction*nf + field][slot]
 
     const int l = threadIdx.x;
     const int i = l % NQ, j = (l / NQ) % NQ, k = l / (NQ * NQ);
@@ -65,33 +68,45 @@ vol_rhs_mixed_kernel(MixedGeometry geo, MixedParams P, const float *__restrict__
     const float Th = th0 + thp;
     const float pp = pressure_perturbation_f32(thp, th0, P);
     const float rinv = __frcp_rn(rho);   // correctly rounded, as 1.0f / rho
+    float Q[kMaxFields - kFields];
+    if constexpr (TRACERS) {
+#pragma unroll
+        for (int t = 0; t < kMaxFields - kFields; ++t)
+            Q[t] = kFields + t < nf ? q[(kFields + t) * M + node] : 0.f;
+    }
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
         const float g1 = geo.g[3 * d][node], g2 = geo.g[3 * d + 1][node],
                     g3 = geo.g[3 * d + 2][node];
         const float v = fmaf(g3, U[2], fmaf(g2, U[1], g1 * U[0]));
         const float u = v * rinv;
-        float *F = sFm + d * kFields * N3 + dir_slot<NQ, float>(d, i, j, k);
+        float *F = sFm + d * nf * N3 + dir_slot<NQ, float>(d, i, j, k);
         F[0 * N3] = v;
         F[1 * N3] = fmaf(U[0], u, g1 * pp);
         F[2 * N3] = fmaf(U[1], u, g2 * pp);
         F[3 * N3] = fmaf(U[2], u, g3 * pp);
         F[4 * N3] = Th * u;
+        if constexpr (TRACERS) {
+#pragma unroll
+            for (int t = 0; t < kMaxFields - kFields; ++t)
+                if (kFields + t < nf) F[(kFields + t) * N3] = Q[t] * u;
+        }
     }
     __syncthreads();
 
     // ---- phase 2: even-odd sweeps, one line per task, in place --------
-    for (int item = l; item < 3 * kFields * NL; item += N3)
+    for (int item = l; item < 3 * nf * NL; item += N3)
         sweep_line<NQ>(sFm + (item / NL) * N3, item % NL, P);
     __syncthreads();
 
     // ---- phase 3: combine, scale, gravity, store ----------------------
     const float Jinv = geo.Jinv[node];
 #pragma unroll
-    for (int b = 0; b < kFields; ++b) {
-        const float R = sFm[(0 * kFields + b) * N3 + dir_slot<NQ, float>(0, i, j, k)] +
-                        sFm[(1 * kFields + b) * N3 + dir_slot<NQ, float>(1, i, j, k)] +
-                        sFm[(2 * kFields + b) * N3 + dir_slot<NQ, float>(2, i, j, k)];
+    for (int b = 0; b < (TRACERS ? kMaxFields : kFields); ++b) {
+        if (TRACERS && b >= nf) break;
+        const float R = sFm[(0 * nf + b) * N3 + dir_slot<NQ, float>(0, i, j, k)] +
+                        sFm[(1 * nf + b) * N3 + dir_slot<NQ, float>(1, i, j, k)] +
+                        sFm[(2 * nf + b) * N3 + dir_slot<NQ, float>(2, i, j, k)];
         float v = -Jinv * R;
         if (b == 3) v = fmaf(-rp, P.grav, v);
         rhs[b * M + node] = v;
@@ -233,13 +248,26 @@ vol_rhs_mixed_bulk_kernel(MixedGeometry geo, MixedParams P, const float *__restr
     }
 }
 
-template <int NQ>
-cudaError_t launch_nq(ElemRange r, const MixedGeometry &geo, const MixedParams &P, const float *q,
-                      float *rhs, cudaStream_t s) {
+template <int NQ, bool TRACERS>
+cudaError_t launch_kernel(ElemRange r, int nf, const MixedGeometry &geo, const MixedParams &P,
+                          const float *q, float *rhs, cudaStream_t s) {
     constexpr int N3 = NQ * NQ * NQ;
-    const size_t smem = sizeof(float) * kFields * 3 * N3;
-    vol_rhs_mixed_kernel<NQ><<<(unsigned)r.count, N3, smem, s>>>(geo, P, q, rhs, r.M, r.e0);
+    const size_t smem = sizeof(float) * nf * 3 * N3;
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(vol_rhs_mixed_kernel<NQ, TRACERS>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    vol_rhs_mixed_kernel<NQ, TRACERS><<<(unsigned)r.count, N3, smem, s>>>(geo, P, q, rhs, r.M, r.e0,
+                                                                          nf);
     return cudaGetLastError();
+}
+
+template <int NQ>
+cudaError_t launch_nq(ElemRange r, int nf, const MixedGeometry &geo, const MixedParams &P,
+                      const float *q, float *rhs, cudaStream_t s) {
+    if (nf == kFields) return launch_kernel<NQ, false>(r, nf, geo, P, q, rhs, s);
+    return launch_kernel<NQ, true>(r, nf, geo, P, q, rhs, s);
 }
 
 __global__ void to_f32_kernel(const double *__restrict__ src, float *__restrict__ dst, int64_t M) {
@@ -256,11 +284,12 @@ cudaError_t launch_to_f32(const double *src, float *dst, int64_t M, cudaStream_t
     return cudaGetLastError();
 }
 
-cudaError_t launch_vol_rhs_mixed(int N, ElemRange r, const MixedGeometry &geo,
+cudaError_t launch_vol_rhs_mixed(int N, int nf, ElemRange r, const MixedGeometry &geo,
                                  const MixedParams &P, const float *q, float *rhs, int *err,
                                  int num_sms, cudaStream_t s) {
     if (r.count <= 0) return cudaSuccess;
-    if (N == 7) {
+    if (nf < kFields || nf > kMaxFields) return cudaErrorInvalidValue;
+    if (N == 7 && nf == kFields) {   // the staged kernel holds the five fields' slabs
         cudaError_t e = cudaFuncSetAttribute(vol_rhs_mixed_bulk_kernel,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)kBulkSmem);
@@ -271,13 +300,13 @@ cudaError_t launch_vol_rhs_mixed(int N, ElemRange r, const MixedGeometry &geo,
         return cudaGetLastError();
     }
     switch (N) {
-        case 1: return launch_nq<2>(r, geo, P, q, rhs, s);
-        case 2: return launch_nq<3>(r, geo, P, q, rhs, s);
-        case 3: return launch_nq<4>(r, geo, P, q, rhs, s);
-        case 4: return launch_nq<5>(r, geo, P, q, rhs, s);
-        case 5: return launch_nq<6>(r, geo, P, q, rhs, s);
-        case 6: return launch_nq<7>(r, geo, P, q, rhs, s);
-        case 7: return launch_nq<8>(r, geo, P, q, rhs, s);
+        case 1: return launch_nq<2>(r, nf, geo, P, q, rhs, s);
+        case 2: return launch_nq<3>(r, nf, geo, P, q, rhs, s);
+        case 3: return launch_nq<4>(r, nf, geo, P, q, rhs, s);
+        case 4: return launch_nq<5>(r, nf, geo, P, q, rhs, s);
+        case 5: return launch_nq<6>(r, nf, geo, P, q, rhs, s);
+        case 6: return launch_nq<7>(r, nf, geo, P, q, rhs, s);
+        case 7: return launch_nq<8>(r, nf, geo, P, q, rhs, s);
         default: return cudaErrorInvalidValue;
     }
 }

@@ -218,11 +218,13 @@ def perturbed_state(mesh: Mesh, rho_ref, rhotheta_ref, seed: int,
 
 def perturbation_state(q: np.ndarray, rho_ref: np.ndarray, rhotheta_ref: np.ndarray) -> np.ndarray:
     """The FP32 state a mixed-precision handle takes: (rho - rho_ref, U1, U2, U3,
-    Theta - Theta_ref), differences formed in FP64 and then rounded once."""
+    Theta - Theta_ref, tracers...), differences formed in FP64 and then rounded
+    once."""
     out = np.empty(q.shape, dtype=np.float32)
     out[0] = q[0] - rho_ref
     out[1:4] = q[1:4]
     out[4] = q[4] - rhotheta_ref
+    out[5:] = q[5:]          # tracers, if any, as they are
     return out
 
 

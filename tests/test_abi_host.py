@@ -86,16 +86,15 @@ def test_create_rejects_invalid_arguments_without_a_gpu(lib):
         assert lib.numa_vol_create(C.byref(mesh), C.byref(geo), C.byref(consts), 0,
                                    C.byref(h)) == _lib.NUMA_EINVAL
         assert h.value is None
-    # tracers: 0..3, NUMA_FP64 only (checked before any device work)
+    # tracers: 0..3, not in NUMA_DF64 (checked before any device work)
     for T, prec, code in ((4, 0, _lib.NUMA_EINVAL), (-1, 0, _lib.NUMA_EINVAL),
-                          (1, _lib.NUMA_MIXED, _lib.NUMA_EUNSUPPORTED),
                           (3, _lib.NUMA_DF64, _lib.NUMA_EUNSUPPORTED)):
         mesh = _lib.numa_mesh(1, 7 if prec == _lib.NUMA_DF64 else 1, T)
         assert lib.numa_vol_create(C.byref(mesh), C.byref(geo), C.byref(consts), prec,
                                    C.byref(h)) == code
         assert h.value is None
-    # orders above 7 exist in NUMA_FP64 only (checked before any device work)
-    for prec in (_lib.NUMA_MIXED, _lib.NUMA_DF64):
+    # orders above 7 do not exist in NUMA_DF64 (checked before any device work)
+    for prec in (_lib.NUMA_DF64,):
         mesh = _lib.numa_mesh(1, 8)
         assert lib.numa_vol_create(C.byref(mesh), C.byref(geo), C.byref(consts), prec,
                                    C.byref(h)) == _lib.NUMA_EUNSUPPORTED

@@ -19,6 +19,7 @@ torch = pytest.importorskip("torch")
 
 TOL = 1e-12
 # The paper's Nq study: 3,538,944 points at every order.
+# Mixed precision at N = 8..15: the 1e-5 bar of the mixed mode.
 STUDY = {3: (48, 48, 24), 7: (24, 24, 12), 11: (16, 16, 8), 15: (12, 12, 6)}
 
 
@@ -30,7 +31,7 @@ def _cuda():
 
 def gpu_rhs(prob, q):
     with VolumeTerm.from_problem(prob) as vt:
-        assert vt.kernel_name == f"vol_rhs_fp64_high_kernel<{prob['N'] + 1}>"
+        assert vt.kernel_name == f"vol_rhs_high_kernel<{prob['N'] + 1}, double>"
         out = vt.rhs(torch.from_numpy(np.ascontiguousarray(q)).cuda())
         torch.cuda.synchronize()
         return out.cpu().numpy()
@@ -95,4 +96,32 @@ def test_host_entry_point_and_rejections_at_high_order():
             with pytest.raises(NumaError, match="EUNSUPPORTED"):
                 eng.submit(vt, w.q, np.empty_like(w.q), 1, 0.01)
     with pytest.raises(NumaError, match="EUNSUPPORTED"):
-        VolumeTerm.from_problem(prob, precision="mixed")
+        VolumeTerm.from_problem(prob, precision="df64")
+
+
+@pytest.mark.parametrize("N,T", [(8, 0), (11, 0), (13, 2), (15, 0), (15, 3)])
+def test_mixed_precision_high_orders(N, T):
+    # The FP32 instantiation of the high-order kernel: perturbation state,
+    # FP32 sweeps, p' from Theta'; every field within 1e-5 of the FP64 oracle.
+    w = wl.make_workload(N, (2, 1, 1), seed=500 + N, tracers=T)
+    prob = w.problem()
+    with VolumeTerm.from_problem(prob, precision="mixed") as vt:
+        assert vt.kernel_name == f"vol_rhs_high_kernel<{N + 1}, float>"
+        out = vt.rhs(torch.from_numpy(w.q_mixed()).cuda()).cpu().numpy().astype(np.float64)
+    ref = oracle.vol_rhs_o2(prob, w.q)
+    for f in range(5 + T):
+        mx = np.max(np.abs(out[f] - ref[f])) / np.max(np.abs(ref[f]))
+        assert mx <= 1e-5, (N, T, wl.FIELD_NAMES[f], mx)
+
+
+def test_mixed_high_order_across_the_eos_forms():
+    w = wl.make_workload(11, (2, 1, 1), seed=611)
+    q = w.q.copy()
+    q[4] = w.rhotheta_ref * (1.0 + eos_banded_theta_ratio(w.M, seed=11))
+    prob = w.problem()
+    with VolumeTerm.from_problem(prob, precision="mixed") as vt:
+        q32 = wl.perturbation_state(q, w.rho_ref, w.rhotheta_ref)
+        out = vt.rhs(torch.from_numpy(q32).cuda()).cpu().numpy().astype(np.float64)
+    ref = oracle.vol_rhs_o2(prob, q)
+    for f in range(5):
+        assert np.max(np.abs(out[f] - ref[f])) <= 1e-5 * np.max(np.abs(ref[f])), f

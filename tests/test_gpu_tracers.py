@@ -80,5 +80,26 @@ def test_tracer_handles_are_rejected_where_unsupported():
         with Engine("fp64", budget_bytes=1 << 24) as eng:
             with pytest.raises(NumaError, match="EUNSUPPORTED"):
                 eng.submit(vt, w.q, np.empty_like(w.q), 1, 0.01)
-    with pytest.raises(NumaError, match="EUNSUPPORTED"):
-        VolumeTerm.from_problem(prob, precision="mixed")
+    with pytest.raises(NumaError, match="EUNSUPPORTED"):   # double-float takes no tracers
+        VolumeTerm.from_problem(wl.make_workload(7, (1, 1, 1), seed=431, tracers=1).problem(),
+                                precision="df64")
+    with VolumeTerm.from_problem(prob, precision="mixed") as vm:   # mixed takes tracers,
+        with Batch("mixed") as b:                                   # the mixed batch does not
+            with pytest.raises(NumaError, match="EUNSUPPORTED"):
+                b.add(vm, torch.from_numpy(w.q_mixed()).cuda())
+
+
+@pytest.mark.parametrize("N,T", [(2, 3), (4, 1), (7, 3)])
+def test_mixed_precision_tracers(N, T):
+    # FP32 8-field form (the paper's benchmark precision and field count):
+    # every field within the mixed mode's 1e-5 bar of the FP64 oracle.
+    w = wl.make_workload(N, (3, 2, 1), seed=440 + N, tracers=T)
+    prob = w.problem()
+    with VolumeTerm.from_problem(prob, precision="mixed") as vt:
+        if N == 7:
+            assert vt.kernel_name == "vol_rhs_mixed_kernel<8>"
+        out = vt.rhs(torch.from_numpy(w.q_mixed()).cuda()).cpu().numpy().astype(np.float64)
+    ref = oracle.vol_rhs_o2(prob, w.q)
+    for f in range(5 + T):
+        mx = np.max(np.abs(out[f] - ref[f])) / np.max(np.abs(ref[f]))
+        assert mx <= 1e-5, (N, T, wl.FIELD_NAMES[f], mx)
