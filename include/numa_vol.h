@@ -351,6 +351,17 @@ int numa_engine_progress(numa_engine *e, int64_t *done_ids, int max_done, int *n
 /* Status and timestamps of a request. */
 int numa_engine_query(const numa_engine *e, int64_t id, numa_request_info *out);
 
+/* Checkpoint of a queued or running request: copies its state after its last
+ * completed step (the initial state if not yet admitted) into state_host
+ * (host memory of the mesh's state size) and stores the number of steps done
+ * in *steps_done (optional).  A step of the scheme depends on the state alone,
+ * so submitting that state with the remaining steps, to this or another
+ * engine, resumes the request: the final state is bit for bit the one the
+ * uninterrupted request produces.  Synchronous; call between progress calls.
+ * Errors: NUMA_EINVAL (NULL argument; no queued or running request with this
+ * id), NUMA_ECUDA. */
+int numa_engine_checkpoint(numa_engine *e, int64_t id, void *state_host, int *steps_done);
+
 /* Counters of the engine. */
 int numa_engine_stats(const numa_engine *e, numa_engine_counters *out);
 

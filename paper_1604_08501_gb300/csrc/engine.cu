@@ -16,6 +16,11 @@
 // are still resident.  That is the continuous batching.  Elements evolve
 // independently in the volume term, so a member's result is bitwise the same
 // whichever members share its rounds.
+//
+// Checkpoint and resume: a step of the 2N-storage scheme starts from the state
+// alone (its register restarts at zero), so the state after a member's last
+// completed step and the number of steps done are a complete checkpoint;
+// submitting the state with the remaining steps resumes it, bit for bit.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -352,6 +357,29 @@ int numa_engine_progress(numa_engine *e, int64_t *done_ids, int max_done, int *n
         if (num_done) *num_done = std::min(n, max_done);
     }
     return NUMA_OK;
+}
+
+int numa_engine_checkpoint(numa_engine *e, int64_t id, void *state_host, int *steps_done) {
+    g_engine_error.clear();
+    if (steps_done) *steps_done = 0;
+    if (!e || !state_host) return efail(NUMA_EINVAL, "numa_engine_checkpoint: NULL argument");
+    for (const auto &r : e->queue)
+        if (r.id == id) {   // not admitted yet: its state is the initial state
+            std::memcpy(state_host, r.q0, r.bytes);
+            return NUMA_OK;
+        }
+    for (const auto &r : e->resident)
+        if (r.id == id && r.status == NUMA_REQ_RUNNING) {
+            // progress() ends every round with the stream idle, so the arena
+            // holds the state after the member's last completed step
+            const cudaError_t err = cudaMemcpyAsync(state_host, e->arena.base + r.off, r.bytes,
+                                                    cudaMemcpyDeviceToHost, e->stream);
+            const cudaError_t err2 = err == cudaSuccess ? cudaStreamSynchronize(e->stream) : err;
+            if (err2 != cudaSuccess) return efail_cuda(err2, "numa_engine_checkpoint");
+            if (steps_done) *steps_done = r.nsteps - r.remaining;
+            return NUMA_OK;
+        }
+    return efail(NUMA_EINVAL, "numa_engine_checkpoint: no queued or running request with this id");
 }
 
 int numa_engine_query(const numa_engine *e, int64_t id, numa_request_info *out) {

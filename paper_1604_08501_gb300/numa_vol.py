@@ -323,6 +323,17 @@ class Engine:
         return {"id": info.id, "status": self.STATUS[info.status], "submit_s": info.submit_s,
                 "admit_s": info.admit_s, "done_s": info.done_s}
 
+    def checkpoint(self, rid: int, out=None):
+        """numa_engine_checkpoint: (state after the request's last completed
+        step, steps done).  Submit the state with the remaining steps to resume."""
+        mesh, q0, _ = self._bufs[rid]
+        if out is None:
+            out = np.empty_like(np.asarray(q0))
+        done = C.c_int()
+        check_engine(_lib.load().numa_engine_checkpoint(self.handle, C.c_int64(rid),
+                                                        C.c_void_p(_host_ptr(out)), C.byref(done)))
+        return out, done.value
+
     def stats(self) -> dict:
         c = _lib.numa_engine_counters()
         check_engine(_lib.load().numa_engine_stats(self.handle, C.byref(c)))

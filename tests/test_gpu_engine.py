@@ -177,3 +177,30 @@ def test_allocation_refusal_is_a_status_code(pool):
         eng.submit(vts[0], works[0].q, out, 1, DT)
         eng.run_until_idle()
     assert np.array_equal(out, batch_reference(vts[0], works[0].q, 1))
+
+
+def test_checkpoint_and_resume_is_bitwise(pool):
+    # A request checkpointed after some rounds and resumed (remaining steps) in a
+    # fresh engine ends in the same bits as the uninterrupted request.
+    works, vts = pool
+    w, vt = works[2], vts[2]
+    full = np.empty_like(w.q)
+    with Engine("fp64", budget_bytes=1 << 28) as eng:
+        eng.submit(vt, w.q, full, 6, DT)
+        eng.run_until_idle()
+    part = np.empty_like(w.q)
+    with Engine("fp64", budget_bytes=1 << 28) as eng:
+        queued = eng.submit(vt, w.q, np.empty_like(w.q), 2, DT)
+        snap0, d0 = eng.checkpoint(queued)                  # not admitted: the initial state
+        assert d0 == 0 and np.array_equal(snap0, w.q)
+        rid = eng.submit(vt, w.q, np.empty_like(w.q), 6, DT)
+        eng.progress()
+        eng.progress()
+        snap, done = eng.checkpoint(rid)
+        assert done == 2 and not np.array_equal(snap, w.q)
+        eng.cancel(rid)
+        eng.run_until_idle()
+    with Engine("fp64", budget_bytes=1 << 28) as eng:
+        eng.submit(vt, snap, part, 6 - done, DT)
+        eng.run_until_idle()
+    assert np.array_equal(part, full)
