@@ -66,6 +66,9 @@ vol_rhs_high_kernel(typename HighTypes<T>::Geo geo, typename HighTypes<T>::Param
     constexpr int N3 = NQ * NL;
     constexpr int FB = NL * 16;      // one direction's flux block (padded lines)
     constexpr int KS = (NQ + 2) / 3; // k-planes per slab
+    // k-loop unrolling: full in FP32 (registers to spare, more loads in
+    // flight), two planes in FP64 (register budget)
+    constexpr int KU = MIXED ? KS : 2;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T *sU = reinterpret_cast<T *>(smem_raw);   // u_d of every point: [d][k][j][i]
     T *sP = sU + 3 * N3;                       // p' of every point: [k][j][i]
@@ -78,7 +81,7 @@ vol_rhs_high_kernel(typename HighTypes<T>::Geo geo, typename HighTypes<T>::Param
     const int64_t node0 = (e0 + blockIdx.x) * N3 + c;  // point (i, j, 0); + k NL
 
     // ---- pass 0: u_d, p', and the density fluxes F_d[rho] = g_d . U ------
-#pragma unroll 2
+#pragma unroll(KU)
     for (int kk = 0; kk < KS; ++kk) {
         const int k = kb + kk;
         if (k < NQ) {
@@ -108,7 +111,7 @@ vol_rhs_high_kernel(typename HighTypes<T>::Geo geo, typename HighTypes<T>::Param
     for (int b = 0; b < nf; ++b) {   // 5 fields, then the tracers
         if (b > 0) {
             __syncthreads();   // the previous field's combination has read sF
-#pragma unroll 2
+#pragma unroll(KU)
             for (int kk = 0; kk < KS; ++kk) {
                 const int k = kb + kk;
                 if (k < NQ) {
@@ -132,7 +135,7 @@ vol_rhs_high_kernel(typename HighTypes<T>::Geo geo, typename HighTypes<T>::Param
         sweep_line<NQ>(sF + slab * FB, c, P);
         __syncthreads();
         // ---- rhs_b of the slab: -Jinv (S_r + S_s + S_t), gravity on U3 ------
-#pragma unroll 2
+#pragma unroll(KU)
         for (int kk = 0; kk < KS; ++kk) {
             const int k = kb + kk;
             if (k < NQ) {
