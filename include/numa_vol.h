@@ -53,7 +53,7 @@ extern "C" {
 #define NUMA_EINVAL (-1)        /* null pointer, N out of range, bad size or misalignment */
 #define NUMA_ENOMEM (-2)        /* device allocation failed                               */
 #define NUMA_ECUDA (-3)         /* a CUDA call or kernel launch failed                    */
-#define NUMA_EUNSUPPORTED (-4)  /* valid request this build does not implement            */
+#define NUMA_EUNSUPPORTED (-4)  /* a valid request the library does not implement            */
 #define NUMA_ETIMEOUT (-5)      /* a kernel's bounded wait on its own staged copies ran out */
 #define NUMA_ELIMIT (-6)        /* a count exceeds a fixed maximum of the call              */
 

@@ -79,7 +79,7 @@ def test_result_is_the_same_alone_and_in_the_mix(pool):
     others = [np.empty_like(x.q) for x in works]
     with Engine("fp64", budget_bytes=1 << 30) as eng:
         eng.submit(vts[0], works[0].q, others[0], 6, DT)
-        eng.progress()                                    # round 1: member 0 alone
+        eng.progress()                                    # first engine round: member 0 alone
         rid = eng.submit(vt, w.q, mixed, 4, DT)           # arrives while 0 runs
         eng.progress()
         eng.submit(vts[2], works[2].q, others[2], 2, DT)  # arrives while both run
