@@ -348,7 +348,9 @@ int numa_engine_cancel(numa_engine *e, int64_t id);
  * round go to done_ids, their count to *num_done.  Errors: NUMA_ECUDA. */
 int numa_engine_progress(numa_engine *e, int64_t *done_ids, int max_done, int *num_done);
 
-/* Status and timestamps of a request. */
+/* Status and timestamps of a request.  The engine keeps the records of its
+ * 2^20 most recently finished (done or cancelled) requests; an older finished
+ * id, like an unknown one, returns NUMA_EINVAL. */
 int numa_engine_query(const numa_engine *e, int64_t id, numa_request_info *out);
 
 /* Checkpoint of a queued or running request: copies its state after its last

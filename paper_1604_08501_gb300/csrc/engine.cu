@@ -141,6 +141,8 @@ struct numa_engine {
     std::deque<Request> queue;
     std::vector<Request> resident;
     std::map<int64_t, numa_request_info> info;
+    std::deque<int64_t> finished;          // ids of done or cancelled requests, oldest first
+    size_t keep_finished = size_t(1) << 20;  // records of finished requests kept for query
     int64_t completed = 0, rounds = 0;
     double point_stages = 0.0;
     int tile_mult = 4;
@@ -156,6 +158,15 @@ void set_status(numa_engine *e, int64_t id, int status, bool stamp_done = false)
     auto &inf = e->info[id];
     inf.status = status;
     if (stamp_done) inf.done_s = now_s();
+    if (status == NUMA_REQ_DONE || status == NUMA_REQ_CANCELLED) {
+        // a long-running engine keeps the records of its most recent finished
+        // requests only
+        e->finished.push_back(id);
+        while (e->finished.size() > e->keep_finished) {
+            e->info.erase(e->finished.front());
+            e->finished.pop_front();
+        }
+    }
 }
 
 }  // namespace
