@@ -135,8 +135,9 @@ typedef struct numa_vol numa_vol;
  * p(Theta) - p(Theta_ref) as p_ref ((1 + x)^gamma - 1) in x =
  * (Theta - Theta_ref)/Theta_ref: NUMA_FP64 by its binomial series (|x| <= 1/8)
  * or expm1(gamma log1p(x)), the form chosen per warp of 32 points;
- * NUMA_DF64 by the series where |x| <= 1/64 and by pow elsewhere.  The error of NUMA_FP64 against an exact evaluation is a few
- * units of 2^-53 times the condition number of the D sweeps (the ratio of
+ * NUMA_DF64 by the series where |x| <= 1/64 and by pow elsewhere.  The error
+ * of NUMA_FP64 against an exact evaluation is a few units of 2^-53 times the
+ * condition number of the D sweeps (the ratio of
  * sum |Jinv D F| to |rhs|).  The factor for NUMA_DF64 is about 2^-48, so
  * NUMA_DF64 suits states with well-conditioned sweeps, such as the benchmark's
  * per-point random velocities.  Smooth fields with a large mean (a uniform wind)

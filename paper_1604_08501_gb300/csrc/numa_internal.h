@@ -153,8 +153,9 @@ struct DfParams {
     double D[64];      // D for the native fallback
 };
 
-// Native: vol_rhs_fp64_kernel (N <= 7); NativeHigh: vol_rhs_fp64_high_kernel
-// (N = 8..15); DoubleFloat (N = 7); Mixed (N <= 7) and MixedHigh (N = 8..15).
+// Native: vol_rhs_fp64_kernel (N <= 7); NativeHigh: vol_rhs_high_kernel<Nq, double>
+// (N = 8..15); DoubleFloat (N = 7); Mixed (N <= 7) and MixedHigh:
+// vol_rhs_high_kernel<Nq, float> (N = 8..15).
 enum class Kernel { Native, NativeHigh, DoubleFloat, Mixed, MixedHigh };
 
 // Device-side description of one instance of a batch: its order, size, state

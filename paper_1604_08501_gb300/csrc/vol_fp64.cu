@@ -1,4 +1,5 @@
-// Native FP64 element volume term on sm_103a, orders N = 1..7.
+// Native FP64 element volume term on sm_103a, orders N = 1..7 (N = 8..15:
+// vol_fp64_high.cu), with or without passive tracers.
 //
 // Computes, per element and point, the pressure perturbation from the Theta
 // equation of state, the contravariant fluxes of the five fields in the three
@@ -9,8 +10,9 @@
 // On GB300 the FP64 pipe (about 0.53 T DFMA/s) binds this kernel, so the
 // design minimises FP64 instructions per point:
 //  * p' = p(Theta) - p(Theta_ref) is evaluated as p_ref ((1+x)^gamma - 1) by
-//    its binomial series in x = (Theta - Theta_ref)/Theta_ref for |x| <= 1/64
-//    (12 FP64 operations, and no cancellation), and by pow elsewhere.
+//    its binomial series in x = (Theta - Theta_ref)/Theta_ref (12 FP64
+//    operations for |x| <= 1/64, and no cancellation); eos.cuh has the wider
+//    forms.
 //  * 1/rho is formed once; u_d = (g_d . U) * (1/rho).
 //  * The fluxes are computed once per point into shared memory (the paper's
 //    flux precompute, Sec. 3, opt. level 5).

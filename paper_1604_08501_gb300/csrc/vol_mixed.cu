@@ -1,4 +1,5 @@
-// Mixed-precision element volume term (NUMA_MIXED), orders N = 1..7.
+// Mixed-precision element volume term (NUMA_MIXED), orders N = 1..7 (N = 8..15:
+// vol_fp64_high.cu), with or without passive tracers.
 //
 // The operation of Sec. 2, Eq. (2) (sign and flux form of the paper's r/s
 // subroutines, Sec. 3) on FP32 data:
