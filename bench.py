@@ -79,12 +79,18 @@ def measured_peaks():
 
 
 def sources_sha(paths) -> str:
-    """sha256 (16 hex digits) over the named source files, in order."""
+    """sha256 (16 hex digits) over the code of the named C/CUDA source files, in
+    order: comments removed and whitespace collapsed, so that an edit to a
+    comment does not count as a change of the kernel."""
     import hashlib
+    import re
     h = hashlib.sha256()
     for rel in paths:
-        with open(os.path.join(ROOT, rel), "rb") as f:
-            h.update(f.read())
+        with open(os.path.join(ROOT, rel), encoding="utf-8") as f:
+            text = f.read()
+        text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)   # block comments
+        text = re.sub(r"//[^\n]*", " ", text)                # line comments
+        h.update(" ".join(text.split()).encode())
     return h.hexdigest()[:16]
 
 
