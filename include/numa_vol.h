@@ -162,7 +162,10 @@ int numa_vol_create(const numa_mesh *mesh, const numa_geometry *geo,
  * cudaStream_t (NULL = the legacy default stream).  The call returns once
  * the kernel is enqueued; rhs is complete when the stream reaches that
  * point.  Errors: NUMA_EINVAL (null handle/pointer, misalignment,
- * overlap), NUMA_ECUDA (launch failure).  Ne = 0 enqueues nothing.
+ * overlap), NUMA_ECUDA (launch failure).  Ne = 0 enqueues nothing.  The call
+ * may be made while `stream` is being captured into a CUDA graph (after one
+ * call outside capture on the device); a replay evaluates the captured q into
+ * the captured rhs.
  */
 int numa_vol_rhs(numa_vol *h, const void *q, void *rhs, void *stream);
 
