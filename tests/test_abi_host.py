@@ -123,3 +123,33 @@ def test_binding_fails_loudly_without_the_library(monkeypatch, tmp_path):
     monkeypatch.setattr(_lib, "LIB", str(tmp_path / "missing.so"))
     with pytest.raises(RuntimeError, match="not built"):
         _lib.load()
+
+
+def test_batch_engine_and_noalloc_reject_bad_arguments_without_a_gpu(lib):
+    # Host-side validation returns status codes before any device work.
+    vp = C.c_void_p
+    assert lib.numa_batch_create(_lib.NUMA_DF64, C.byref(vp())) == _lib.NUMA_EUNSUPPORTED
+    assert lib.numa_batch_create(_lib.NUMA_FP64, None) == _lib.NUMA_EINVAL
+    assert lib.numa_batch_add(None, None, None, None) == _lib.NUMA_EINVAL
+    assert lib.numa_batch_advance(None, 1, 0.01, None) == _lib.NUMA_EINVAL
+    assert lib.numa_batch_tile(None, 8) == 0
+    assert lib.numa_engine_create(_lib.NUMA_DF64, 1 << 20, 4, C.byref(vp())) == _lib.NUMA_EUNSUPPORTED
+    assert lib.numa_engine_create(_lib.NUMA_FP64, 1 << 20, 0, C.byref(vp())) == _lib.NUMA_EINVAL
+    assert lib.numa_engine_create(_lib.NUMA_FP64, 16, 4, C.byref(vp())) == _lib.NUMA_EINVAL
+    rid = C.c_int64()
+    assert lib.numa_engine_submit(None, None, None, None, 1, 0.01, C.byref(rid)) == _lib.NUMA_EINVAL
+    assert lib.numa_engine_cancel(None, 1) == _lib.NUMA_EINVAL
+    n = C.c_int()
+    assert lib.numa_engine_progress(None, None, 0, C.byref(n)) == _lib.NUMA_EINVAL
+    assert lib.numa_engine_query(None, 1, None) == _lib.NUMA_EINVAL
+    assert lib.numa_engine_stats(None, None) == _lib.NUMA_EINVAL
+    assert lib.numa_engine_checkpoint(None, 1, None, None) == _lib.NUMA_EINVAL
+    assert b"NULL" in lib.numa_engine_last_error()
+    lib.numa_engine_destroy(None)                        # no-op
+    # the allocation-free advance: NULL arrays, counts out of range
+    hs = (C.c_void_p * 65)()
+    ss = (C.c_void_p * 65)()
+    assert lib.numa_batch_advance_noalloc(None, None, 1, 1, 0.01, None) == _lib.NUMA_EINVAL
+    assert lib.numa_batch_advance_noalloc(hs, ss, 0, 1, 0.01, None) == _lib.NUMA_EINVAL
+    assert lib.numa_batch_advance_noalloc(hs, ss, 65, 1, 0.01, None) == _lib.NUMA_ELIMIT
+    assert lib.numa_batch_advance_noalloc(hs, ss, 1, -1, 0.01, None) == _lib.NUMA_EINVAL
