@@ -697,7 +697,8 @@ def run_serving(args):
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=300)
+    ap.add_argument("--steps", type=int, default=None,
+                    help="timed steps (default: 300 single, 5 batched, 50 nq-sweep)")
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", choices=["numa", "reference"], default="numa")
     ap.add_argument("--no-cpu-baseline", action="store_true",
@@ -725,6 +726,8 @@ def main(argv=None):
     args = ap.parse_args(argv)
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
+    if args.steps is None:   # a few minutes at most for each workload
+        args.steps = {"single": 300, "batched": 5, "nq-sweep": 50, "serving": 300}[args.workload]
     if args.precision is None:
         args.precision = ("fp64,df64,mixed" if args.workload == "single" else "fp64,mixed")
     args.precisions = [p for p in args.precision.split(",") if p]
