@@ -619,7 +619,8 @@ def run_serving(args):
         def take(j):
             return free[j].pop() if free[j] else torch.empty_like(q0s[j]).pin_memory()
 
-        with Engine(prec, budget_bytes=args.budget_gb << 30, max_members=256) as eng:
+        with Engine(prec, budget_bytes=args.budget_gb << 30, max_members=256,
+                    round_steps=args.round_steps) as eng:
             # warm-up: a few requests through the same path, not timed
             for j in range(min(args.warmup, len(works))):
                 o = take(j)
@@ -686,7 +687,8 @@ def run_serving(args):
                                        f"each one of {len(plan)} instances (N in {{3,4,5,7}}, "
                                        f"512..32768 elements) advancing k in {{1,5,20}} LSRK(5,4) "
                                        f"steps at dt = 0.01 s; budget {args.budget_gb} GB, "
-                                       f"<= 256 members resident"},
+                                       f"<= 256 members resident, rounds of up to "
+                                       f"{args.round_steps} step(s)"},
                 "latency_ms": out[head]["latency_ms"], "offered_gdofs": out[head]["offered_gdofs"],
                 "gpu_launches": out[head]["rounds"], "clocks": out[head]["clocks"],
                 "precision": head, "variants": {k: v for k, v in out.items() if k != head}}
@@ -721,6 +723,8 @@ def main(argv=None):
     ap.add_argument("--requests", type=int, default=600, help="serving: requests per precision")
     ap.add_argument("--pool", type=int, default=16, help="serving: distinct instances drawn from")
     ap.add_argument("--budget-gb", type=int, default=120, help="serving: HBM budget of the states")
+    ap.add_argument("--round-steps", type=int, default=4,
+                    help="serving: steps per engine round at most (never past a completion)")
     ap.add_argument("--orders", default="",
                     help="nq-sweep: comma-separated orders N to run (default 3,7,11,15)")
     args = ap.parse_args(argv)

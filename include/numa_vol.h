@@ -357,6 +357,14 @@ int numa_engine_progress(numa_engine *e, int64_t *done_ids, int max_done, int *n
  * id, like an unknown one, returns NUMA_EINVAL. */
 int numa_engine_query(const numa_engine *e, int64_t id, numa_request_info *out);
 
+/* Steps per round (default 1).  A round then advances every resident member
+ * by s = min(max_steps, the smallest remaining step count of the residents)
+ * steps in one launch, with each member's state kept on chip across them: no
+ * member finishes later than with single steps, and results are bit for bit
+ * the same, but requests arriving during a round wait up to s steps for
+ * admission.  Errors: NUMA_EINVAL (NULL engine, max_steps < 1). */
+int numa_engine_set_round_steps(numa_engine *e, int max_steps);
+
 /* Checkpoint of a queued or running request: copies its state after its last
  * completed step (the initial state if not yet admitted) into state_host
  * (host memory of the mesh's state size) and stores the number of steps done

@@ -9,8 +9,9 @@
 //   2. admit queued requests in arrival order while a member slot is free and
 //      the arena has room (first fit); the head of the queue waits if it does
 //      not fit yet, so later requests cannot starve it;
-//   3. advance every resident member by one step, all in one persistent launch
-//      (members of different dt in one launch each);
+//   3. advance every resident member by s steps, all in one persistent launch
+//      (members of different dt in one launch each): s = 1 by default, or up
+//      to a set limit but never past the next member's completion;
 //   4. copy finished members' states to their host buffers and free them.
 // Requests that arrive during a round join at the next round while the others
 // are still resident.  That is the continuous batching.  Elements evolve
@@ -146,6 +147,7 @@ struct numa_engine {
     int64_t completed = 0, rounds = 0;
     double point_stages = 0.0;
     int tile_mult = 4;
+    int max_round_steps = 1;   // steps per round: up to this, and never past a completion
 };
 
 namespace {
@@ -292,7 +294,11 @@ int numa_engine_progress(numa_engine *e, int64_t *done_ids, int max_done, int *n
         e->resident.push_back(r);
     }
     if (e->resident.empty()) return NUMA_OK;
-    // 3. one step for every resident member, one launch per distinct dt
+    // 3. s steps for every resident member, one launch per distinct dt: s is
+    //    the smallest remaining step count, at most max_round_steps, so every
+    //    member that finishes does so in the round it would with single steps
+    int steps = e->max_round_steps;
+    for (const auto &r : e->resident) steps = std::min(steps, r.remaining);
     std::vector<double> dts;
     for (const auto &r : e->resident)
         if (std::find(dts.begin(), dts.end(), r.dt) == dts.end()) dts.push_back(r.dt);
@@ -310,7 +316,7 @@ int numa_engine_progress(numa_engine *e, int64_t *done_ids, int max_done, int *n
             I.mgeo = r.mesh->mgeo;
             I.mp = r.mesh->mparams;
             inst.push_back(I);
-            e->point_stages += 5.0 * (double)r.mesh->M;
+            e->point_stages += 5.0 * steps * (double)r.mesh->M;
         }
         int mult[9];
         std::fill(mult, mult + 9, e->tile_mult);
@@ -333,7 +339,7 @@ int numa_engine_progress(numa_engine *e, int64_t *done_ids, int max_done, int *n
         if (err == cudaSuccess) err = cudaMemsetAsync(e->d_counter, 0, sizeof(int), e->stream);
         if (err == cudaSuccess)
             err = numa::launch_batch_lsrk(e->prec == NUMA_MIXED, e->d_inst, e->d_items,
-                                          (int)items.size(), e->d_counter, kCoef, 1, dt,
+                                          (int)items.size(), e->d_counter, kCoef, steps, dt,
                                           e->num_sms, e->stream);
         // the host vectors are sources of in-flight copies: wait before they go
         if (err == cudaSuccess) err = cudaStreamSynchronize(e->stream);
@@ -344,7 +350,8 @@ int numa_engine_progress(numa_engine *e, int64_t *done_ids, int max_done, int *n
     std::vector<Request> done;
     for (size_t k = 0; k < e->resident.size();) {
         Request &r = e->resident[k];
-        if (--r.remaining == 0) {
+        r.remaining -= steps;
+        if (r.remaining == 0) {
             err = cudaMemcpyAsync(r.q_out, e->arena.base + r.off, r.bytes, cudaMemcpyDeviceToHost,
                                   e->stream);
             if (err != cudaSuccess) return efail_cuda(err, "numa_engine_progress: result copy");
@@ -367,6 +374,12 @@ int numa_engine_progress(numa_engine *e, int64_t *done_ids, int max_done, int *n
         }
         if (num_done) *num_done = std::min(n, max_done);
     }
+    return NUMA_OK;
+}
+
+int numa_engine_set_round_steps(numa_engine *e, int max_steps) {
+    if (!e || max_steps < 1) return efail(NUMA_EINVAL, "numa_engine_set_round_steps: need max_steps >= 1");
+    e->max_round_steps = max_steps;
     return NUMA_OK;
 }
 

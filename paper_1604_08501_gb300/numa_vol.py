@@ -280,7 +280,7 @@ class Engine:
     STATUS = {0: "queued", 1: "running", 2: "done", 3: "cancelled"}
 
     def __init__(self, precision: str = "fp64", budget_bytes: int = 1 << 30,
-                 max_members: int = 256):
+                 max_members: int = 256, round_steps: int = 1):
         self.precision = precision
         h = C.c_void_p()
         prec = {"fp64": NUMA_FP64, "mixed": NUMA_MIXED}[precision]
@@ -288,6 +288,8 @@ class Engine:
                                                     C.byref(h)))
         self._h = h
         self._bufs = {}          # request id -> (mesh, q0, out) kept alive while in flight
+        if round_steps != 1:
+            check_engine(_lib.load().numa_engine_set_round_steps(self.handle, int(round_steps)))
 
     @property
     def handle(self) -> int:

@@ -204,3 +204,26 @@ def test_checkpoint_and_resume_is_bitwise(pool):
         eng.submit(vt, snap, part, 6 - done, DT)
         eng.run_until_idle()
     assert np.array_equal(part, full)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_multi_step_rounds_give_the_same_bits(pool, precision):
+    # Rounds of up to 4 steps (never past a completion) against single-step
+    # rounds: the same final states bit for bit, in fewer rounds.
+    works, _ = pool
+    vts = [VolumeTerm.from_problem(w.problem(), precision=precision) for w in works]
+    q0s = [w.q_mixed() if precision == "mixed" else w.q for w in works]
+    ks = [7, 3, 5, 1]
+    results = {}
+    for rs in (1, 4):
+        outs = [np.empty_like(q) for q in q0s]
+        with Engine(precision, budget_bytes=1 << 28, round_steps=rs) as eng:
+            for vt, q, o, k in zip(vts, q0s, outs, ks):
+                eng.submit(vt, q, o, k, DT)
+            eng.run_until_idle()
+            results[rs] = (outs, eng.stats()["rounds"])
+    for a, b in zip(results[1][0], results[4][0]):
+        assert np.array_equal(a, b)
+    assert results[4][1] < results[1][1]
+    for vt in vts:
+        vt.close()
