@@ -29,8 +29,9 @@
  * Layout (all per-point arrays): element-major, then k, j, i with i fastest,
  * i.e. index ((e*Nq + k)*Nq + j)*Nq + i with Nq = N + 1.  M = Ne * Nq^3.
  * State and rhs: five planes of M values each, contiguous, in the order
- * (rho, U1, U2, U3, Theta), then one plane per tracer (NUMA_FP64 meshes with
- * num_tracers > 0); plane b starts at element offset b*M.
+ * (rho, U1, U2, U3, Theta), then one plane per tracer (meshes with
+ * num_tracers > 0; the tracers follow Theta: flux Q u_d, no source, the
+ * paper's 8-field form of Eq. (1)); plane b starts at element offset b*M.
  *
  * Errors: every int-returning call returns NUMA_OK (0) or a negative code;
  * numa_vol_last_error() then returns a message for the calling thread.  No
@@ -53,14 +54,14 @@ extern "C" {
 #define NUMA_EINVAL (-1)        /* null pointer, N out of range, bad size or misalignment */
 #define NUMA_ENOMEM (-2)        /* device allocation failed                               */
 #define NUMA_ECUDA (-3)         /* a CUDA call or kernel launch failed                    */
-#define NUMA_EUNSUPPORTED (-4)  /* a valid request the library does not implement            */
+#define NUMA_EUNSUPPORTED (-4)  /* a valid request the library does not implement          */
 #define NUMA_ETIMEOUT (-5)      /* a kernel's bounded wait on its own staged copies ran out */
-#define NUMA_ELIMIT (-6)        /* a count exceeds a fixed maximum of the call              */
+#define NUMA_ELIMIT (-6)        /* a count exceeds a fixed maximum of the call            */
 
 #define NUMA_MAX_N 7            /* orders N = 1 .. 7 (Nq = 2 .. 8): every mode, the batch
-                                   and the engine                                          */
-#define NUMA_MAX_N_FP64 15      /* NUMA_FP64 and NUMA_MIXED evaluations also take N = 8 .. 15
-                                   (Nq up to 16)                                           */
+                                   and the engine                                         */
+#define NUMA_MAX_N_FP64 15      /* NUMA_FP64 and NUMA_MIXED evaluations also take
+                                   N = 8 .. 15 (Nq up to 16)                              */
 
 /* Physical constants: EOS reference pressure p0, gas constant R, specific heat
  * at constant pressure cp (gamma = cp / (cp - R), Sec. 2), gravity grav. */
@@ -122,11 +123,12 @@ typedef struct numa_vol numa_vol;
  * NUMA_ECUDA, NUMA_EUNSUPPORTED (NUMA_DF64 with N != 7 or with tracers).
  * Handles of N > 7 evaluate one element per CTA of 3 (N+1)^2 threads, one
  * pass per field (vol_rhs_high_kernel); the batch and the engine take handles
- * of N <= 7 only.
+ * of N <= 7 without tracers only.
  *
  * NUMA_MIXED takes the state as FP32 perturbations from the reference state:
- * plane 0 holds rho - rho_ref, plane 4 holds Theta - Theta_ref, and planes 1-3
- * hold U1..U3.  It writes the (same) rhs in FP32.  The geometry is rounded to
+ * plane 0 holds rho - rho_ref, plane 4 holds Theta - Theta_ref, planes 1-3
+ * hold U1..U3, and tracer planes (if any) hold the tracers as they are.  It
+ * writes the (same) rhs in FP32.  The geometry is rounded to
  * FP32 once.  p' is evaluated from Theta - Theta_ref without cancellation
  * (series in x, or expm1(gamma log1p(x))).  Error against the FP64 volume term
  * of the full state: about 1e-7 times the sweep condition number, normwise.
@@ -301,8 +303,9 @@ void numa_batch_destroy(numa_batch *b);
  * reserves its HBM budget once, as an arena for members' states, and admits
  * requests in arrival order while a member slot is free and the arena has room.
  * Each numa_engine_progress call is one round: admit, advance every resident
- * member by one step in one persistent launch (one per distinct dt), return
- * the finished members' states to their host buffers.  Requests submitted
+ * member by one step (or several, numa_engine_set_round_steps) in one
+ * persistent launch (one per distinct dt), return the finished members'
+ * states to their host buffers.  Requests submitted
  * while others run join at the next round.  A member's result is bitwise the
  * same whichever members share its rounds.  Engines are not thread-safe.
  */
