@@ -11,10 +11,11 @@
 //    lanes and loop over k;
 //  * a first pass forms the contravariant velocities u_d and p' of all points
 //    into shared memory (4 Nq^3 values);
-//  * then one pass per field b: its three flux arrays F_d[b] into shared
-//    memory (3 Nq^2 lines of 16 slots), the three D sweeps in place (one line
-//    per thread, even-odd split), and rhs_b of the thread's points straight
-//    to HBM.
+//  * then one pass per group of fields (one field in FP64; as many as
+//    shared memory holds in FP32): their flux arrays into shared memory
+//    (3 Nq^2 lines of 16 slots per field), the D sweeps in place (one line per
+//    thread and field, even-odd split), and the rhs of the thread's points
+//    straight to HBM.
 // Shared memory: (4 Nq^3 + 48 Nq^2) values, 224 KB at Nq = 16 in FP64 (every
 // operation FP64; bound by the FP64 pipe like the low orders) and 112 KB in
 // the mixed mode (FP32 perturbation state and arithmetic, as vol_mixed.cu).
@@ -31,23 +32,41 @@ namespace {
 // T: double (NUMA_FP64) or float (NUMA_MIXED: FP32 perturbation state
 // (rho', U, Theta', tracers), FP32 geometry, p' from Theta' without
 // cancellation).
-template <int NQ, typename T>
-constexpr size_t high_smem_bytes() {
-    return sizeof(T) * (4 * NQ * NQ * NQ + 3 * NQ * NQ * 16);
-}
 
 // Threads: three per (i, j) column, each owning a slab of KS = ceil(Nq/3)
-// k-planes in the point phases and one line in the sweep phase
+// k-planes in the point phases and one line per field in the sweep phase
 // (3 directions x Nq^2 lines = 3 Nq^2 threads).
 template <int NQ>
-constexpr int high_threads() {
+__host__ __device__ constexpr int high_threads() {
     return 3 * NQ * NQ;
+}
+
+// Fields per pass.  FP64: one (the flux arrays of one field already take
+// 98 KB at Nq = 16).  FP32: as many as fit the shared memory of the CTAs per
+// SM the thread count allows (two CTAs up to 512 threads each), so that fewer
+// passes re-read the element and fewer barriers separate them.
+template <int NQ, typename T>
+__host__ __device__ constexpr int high_group() {
+    if constexpr (sizeof(T) == 8) {
+        return 1;
+    } else {
+        constexpr size_t fixed = sizeof(T) * 4 * NQ * NQ * NQ;   // u_d and p'
+        constexpr size_t per = sizeof(T) * 3 * NQ * NQ * 16;     // one field's fluxes
+        constexpr size_t budget = (2 * high_threads<NQ>() <= 1024 ? 113 : 226) * 1024;
+        constexpr size_t g = budget > fixed ? (budget - fixed) / per : 1;
+        return g < 1 ? 1 : (g > kMaxFields ? kMaxFields : (int)g);
+    }
+}
+
+template <int NQ, typename T>
+__host__ __device__ constexpr size_t high_smem_bytes() {
+    return sizeof(T) * (4 * NQ * NQ * NQ + high_group<NQ, T>() * 3 * NQ * NQ * 16);
 }
 
 // CTAs per SM the register budget is sized for: two where two CTAs' shared
 // memory fits an SM and still leaves 64 registers per thread, else one.
 template <int NQ, typename T>
-constexpr int high_min_ctas() {
+__host__ __device__ constexpr int high_min_ctas() {
     return (2 * (high_smem_bytes<NQ, T>() + 1024) <= 228 * 1024 && 2 * high_threads<NQ>() <= 1024)
                ? 2
                : 1;
@@ -66,13 +85,14 @@ vol_rhs_high_kernel(typename HighTypes<T>::Geo geo, typename HighTypes<T>::Param
     constexpr int N3 = NQ * NL;
     constexpr int FB = NL * 16;      // one direction's flux block (padded lines)
     constexpr int KS = (NQ + 2) / 3; // k-planes per slab
+    constexpr int G = high_group<NQ, T>();
     // k-loop unrolling: full in FP32 (registers to spare, more loads in
     // flight), two planes in FP64 (register budget)
     constexpr int KU = MIXED ? KS : 2;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T *sU = reinterpret_cast<T *>(smem_raw);   // u_d of every point: [d][k][j][i]
     T *sP = sU + 3 * N3;                       // p' of every point: [k][j][i]
-    T *sF = sU + 4 * N3;                       // fluxes of one field: [d][line][slot]
+    T *sF = sU + 4 * N3;                       // fluxes of a group: [field][d][line][slot]
 
     const int t = threadIdx.x;
     const int c = t % NL, slab = t / NL;
@@ -80,76 +100,104 @@ vol_rhs_high_kernel(typename HighTypes<T>::Geo geo, typename HighTypes<T>::Param
     const int kb = slab * KS;                          // first k-plane of the slab
     const int64_t node0 = (e0 + blockIdx.x) * N3 + c;  // point (i, j, 0); + k NL
 
-    // ---- pass 0: u_d, p', and the density fluxes F_d[rho] = g_d . U ------
+    // Flux of field b in direction d at a point: F_d[rho] = g_d . U,
+    // F_d[U_a] = U_a u_d + g_{ad} p', F_d[Theta] = Theta u_d, tracers Q u_d.
+    // ---- pass 0: u_d, p', and the fluxes of the first group ---------------
 #pragma unroll(KU)
     for (int kk = 0; kk < KS; ++kk) {
         const int k = kb + kk;
         if (k < NQ) {
             const int64_t node = node0 + k * NL;
-            const T U1 = q[M + node], U2 = q[2 * M + node], U3 = q[3 * M + node];
-            T rinv;
+            const T U[3] = {q[M + node], q[2 * M + node], q[3 * M + node]};
+            T rinv, pp, Th;
             if constexpr (MIXED) {
                 const float th0 = geo.theta_ref[node];
-                sP[k * NL + c] = pressure_perturbation_f32(q[4 * M + node], th0, P);
+                pp = pressure_perturbation_f32(q[4 * M + node], th0, P);
                 rinv = __frcp_rn(geo.rho_ref[node] + q[node]);
+                Th = th0 + q[4 * M + node];
             } else {
-                sP[k * NL + c] = pressure_perturbation(q[4 * M + node], geo.theta_ref[node],
-                                                       geo.w[node], geo.A[node], P);
+                pp = pressure_perturbation(q[4 * M + node], geo.theta_ref[node], geo.w[node],
+                                           geo.A[node], P);
                 rinv = __drcp_rn(q[node]);
+                Th = q[4 * M + node];
             }
+            sP[k * NL + c] = pp;
 #pragma unroll
             for (int d = 0; d < 3; ++d) {
-                const T v = fma(geo.g[3 * d + 2][node], U3,
-                                fma(geo.g[3 * d + 1][node], U2, geo.g[3 * d][node] * U1));
-                sU[d * N3 + k * NL + c] = v * rinv;
-                sF[d * FB + dir_slot<NQ, T>(d, i, j, k)] = v;
+                const T g[3] = {geo.g[3 * d][node], geo.g[3 * d + 1][node], geo.g[3 * d + 2][node]};
+                const T v = fma(g[2], U[2], fma(g[1], U[1], g[0] * U[0]));
+                const T u = v * rinv;
+                sU[d * N3 + k * NL + c] = u;
+                const int sl = dir_slot<NQ, T>(d, i, j, k);
+#pragma unroll
+                for (int b = 0; b < G; ++b) {
+                    if (b >= nf) break;
+                    T F;
+                    if (b == 0) F = v;
+                    else if (b < 4) F = fma(U[b - 1], u, g[b - 1] * pp);
+                    else if (b == 4) F = Th * u;
+                    else F = q[b * M + node] * u;
+                    sF[(b * 3 + d) * FB + sl] = F;
+                }
             }
         }
     }
 
 #pragma unroll 1
-    for (int b = 0; b < nf; ++b) {   // 5 fields, then the tracers
-        if (b > 0) {
-            __syncthreads();   // the previous field's combination has read sF
+    for (int b0 = 0; b0 < nf; b0 += G) {   // groups of G fields: 5 fields, then the tracers
+        const int gn = nf - b0 < G ? nf - b0 : G;
+        if (b0 > 0) {
+            __syncthreads();   // the previous group's combination has read sF
 #pragma unroll(KU)
             for (int kk = 0; kk < KS; ++kk) {
                 const int k = kb + kk;
                 if (k < NQ) {
                     const int64_t node = node0 + k * NL;
-                    T qb = q[b * M + node];
-                    if (MIXED && b == 4) qb += geo.theta_ref[node];   // Theta = Theta_ref + Theta'
 #pragma unroll
-                    for (int d = 0; d < 3; ++d) {
-                        const T u = sU[d * N3 + k * NL + c];
-                        // F_d[U_a] = U_a u_d + g_{ad} p';  F_d[Theta] = Theta u_d,
-                        // and likewise Q u_d for a tracer
-                        const T F =
-                            b < 4 ? fma(qb, u, geo.g[3 * d + (b - 1)][node] * sP[k * NL + c]) : qb * u;
-                        sF[d * FB + dir_slot<NQ, T>(d, i, j, k)] = F;
+                    for (int gl = 0; gl < G; ++gl) {
+                        if (gl >= gn) break;
+                        const int b = b0 + gl;
+                        T qb = q[b * M + node];
+                        if (MIXED && b == 4) qb += geo.theta_ref[node];   // Theta = Theta_ref + Theta'
+#pragma unroll
+                        for (int d = 0; d < 3; ++d) {
+                            const T u = sU[d * N3 + k * NL + c];
+                            const T F =
+                                b < 4 ? fma(qb, u, geo.g[3 * d + (b - 1)][node] * sP[k * NL + c]) : qb * u;
+                            sF[(gl * 3 + d) * FB + dir_slot<NQ, T>(d, i, j, k)] = F;
+                        }
                     }
                 }
             }
         }
         __syncthreads();
-        // ---- sweeps: thread t sweeps line c of direction `slab` ------------
-        sweep_line<NQ>(sF + slab * FB, c, P);
+        // ---- sweeps: line c of direction `slab`, for each field of the group
+#pragma unroll 1
+        for (int gl = 0; gl < gn; ++gl) sweep_line<NQ>(sF + (gl * 3 + slab) * FB, c, P);
         __syncthreads();
-        // ---- rhs_b of the slab: -Jinv (S_r + S_s + S_t), gravity on U3 ------
+        // ---- rhs of the group's fields: -Jinv (S_r + S_s + S_t), gravity on U3
 #pragma unroll(KU)
         for (int kk = 0; kk < KS; ++kk) {
             const int k = kb + kk;
             if (k < NQ) {
                 const int64_t node = node0 + k * NL;
-                const T R = sF[dir_slot<NQ, T>(0, i, j, k)] + sF[FB + dir_slot<NQ, T>(1, i, j, k)] +
-                            sF[2 * FB + dir_slot<NQ, T>(2, i, j, k)];
-                T v = -geo.Jinv[node] * R;
-                if (b == 3) {
-                    if constexpr (MIXED)
-                        v = fma(-q[node], P.grav, v);   // rho' is the stored state
-                    else
-                        v = fma(-(q[node] - geo.rho_ref[node]), P.eos.grav, v);
+                const T jinv = geo.Jinv[node];
+                const int s0 = dir_slot<NQ, T>(0, i, j, k), s1 = dir_slot<NQ, T>(1, i, j, k),
+                          s2 = dir_slot<NQ, T>(2, i, j, k);
+#pragma unroll
+                for (int gl = 0; gl < G; ++gl) {
+                    if (gl >= gn) break;
+                    const int b = b0 + gl;
+                    const T *F = sF + gl * 3 * FB;
+                    T v = -jinv * (F[s0] + F[FB + s1] + F[2 * FB + s2]);
+                    if (b == 3) {
+                        if constexpr (MIXED)
+                            v = fma(-q[node], P.grav, v);   // rho' is the stored state
+                        else
+                            v = fma(-(q[node] - geo.rho_ref[node]), P.eos.grav, v);
+                    }
+                    rhs[b * M + node] = v;
                 }
-                rhs[b * M + node] = v;
             }
         }
     }
