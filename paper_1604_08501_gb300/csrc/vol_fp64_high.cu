@@ -162,8 +162,14 @@ vol_rhs_high_kernel(typename HighTypes<T>::Geo geo, typename HighTypes<T>::Param
 #pragma unroll
                         for (int d = 0; d < 3; ++d) {
                             const T u = sU[d * N3 + k * NL + c];
-                            const T F =
-                                b < 4 ? fma(qb, u, geo.g[3 * d + (b - 1)][node] * sP[k * NL + c]) : qb * u;
+                            T F = qb * u;
+                            if (b < 4) {
+                                // g_{b,d} by selection: a run-time index into the
+                                // parameter's pointer array would copy it to local memory
+                                const T *gp = b == 1 ? geo.g[3 * d]
+                                                     : (b == 2 ? geo.g[3 * d + 1] : geo.g[3 * d + 2]);
+                                F = fma(qb, u, gp[node] * sP[k * NL + c]);
+                            }
                             sF[(gl * 3 + d) * FB + dir_slot<NQ, T>(d, i, j, k)] = F;
                         }
                     }
