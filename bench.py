@@ -22,6 +22,7 @@ import argparse
 import dataclasses
 import json
 import os
+import platform
 import statistics
 import subprocess
 import sys
@@ -233,22 +234,54 @@ def oracle_sample(w, elements: int):
     return sub, np.ascontiguousarray(w.q[:, :m]), m
 
 
-def cpu_baseline(w, min_seconds: float = 10.0):
+def cpu_model() -> str:
+    """The host CPU's model string (x86 'model name', else the Arm implementer
+    and part numbers), for the CPU baseline's record."""
+    try:
+        fields = {}
+        for line in open("/proc/cpuinfo"):
+            k, _, v = line.partition(":")
+            fields.setdefault(k.strip(), v.strip())
+        if "model name" in fields:
+            return fields["model name"]
+        if "CPU part" in fields:
+            return f"{platform.machine()} implementer {fields.get('CPU implementer', '?')} " \
+                   f"part {fields['CPU part']}"
+    except OSError:
+        pass
+    return platform.machine()
+
+
+def time_oracle(prob, q, min_seconds: float, nthreads: int = 0):
+    """Repeated oracle O2 runs for at least min_seconds: (runs, seconds)."""
     import oracle
-    prob, q, m = oracle_sample(w, CPU_SAMPLE_ELEMENTS)
-    oracle.vol_rhs_o2(prob, q)        # warm-up (page-in)
+    oracle.vol_rhs_o2(prob, q, nthreads)        # warm-up (page-in)
     runs, t0 = 0, time.perf_counter()
     while True:
-        oracle.vol_rhs_o2(prob, q)
+        oracle.vol_rhs_o2(prob, q, nthreads)
         runs += 1
         el = time.perf_counter() - t0
         if el >= min_seconds:
-            break
+            return runs, el
+
+
+def cpu_baseline(w, min_seconds: float = 10.0, single_seconds: float = 4.0):
+    """Oracle O2 on the host: all cores (the baseline value), then one core on
+    a smaller sample of the same workload."""
+    import oracle
+    prob, q, m = oracle_sample(w, CPU_SAMPLE_ELEMENTS)
+    runs, el = time_oracle(prob, q, min_seconds)
+    prob1, q1, m1 = oracle_sample(w, CPU_SAMPLE_ELEMENTS // 16)
+    runs1, el1 = time_oracle(prob1, q1, single_seconds, nthreads=1)
     return {"value": runs * m / el / 1e9, "unit": UNIT, "cores": oracle.max_threads(),
             "kind": "oracle",
             "sample": f"first {prob['Ne']} of {w.Ne} elements ({m} points) of the timed workload, "
                       f"oracle O2 (fluxes once per point, OpenMP over elements), {runs} runs "
-                      f"in {el:.1f} s"}
+                      f"in {el:.1f} s",
+            "single_core": {"value": runs1 * m1 / el1 / 1e9, "unit": UNIT, "cores": 1,
+                            "sample": f"first {prob1['Ne']} elements ({m1} points), {runs1} "
+                                      f"runs in {el1:.1f} s"},
+            "cpu_model": cpu_model()}
 
 
 def run_reference(args):
@@ -307,8 +340,11 @@ def time_variant(vt, q, q_host, dev, K, W, rank, e2e=True):
     torch.cuda.synchronize(dev)
     barrier(dev)
     clocks = sampler.stop() if sampler else None
+    per_launch = [a.elapsed_time(b) for a, b in ev]
     res = {"region_ms": t_start.elapsed_time(t_end),
-           "kernel_ms": float(np.mean([a.elapsed_time(b) for a, b in ev])),
+           "kernel_ms": float(np.mean(per_launch)),
+           "launch_ms": {"mean": float(np.mean(per_launch)),
+                         "median": float(np.median(per_launch)), "best": float(np.min(per_launch))},
            "clocks": clocks, "e2e_s": None}
     if e2e:
         # H2D of q from pinned memory, the kernel, D2H of rhs, every step.
@@ -395,7 +431,9 @@ def run_gpu(args):
                 "dtype": dtypes.get(head_prec, head_prec), "data": "synthetic",
                 "config": workload_config(w, name), "roofline": roof, "roofline_other": other,
                 "e2e": head["e2e"], "gpu_launches": K, "clocks": head["clocks"],
-                "precision": head_prec}
+                "precision": head_prec, "launch_ms": head["launch_ms"],
+                "field_dof_rate": {"value": head["value"] * 5, "unit": "G field-DOF/s",
+                                   "fields": 5}}
         variants = {}
         for prec in args.precisions[1:]:
             r = results[prec]
@@ -403,7 +441,7 @@ def run_gpu(args):
             variants[prec] = {"value": r["value"], "unit": UNIT, "ms_per_step": r["ms_per_step"],
                               "dtype": dtypes.get(prec, prec), "roofline": vr,
                               "roofline_other": vo, "e2e": r["e2e"], "gpu_launches": K,
-                              "clocks": r["clocks"]}
+                              "clocks": r["clocks"], "launch_ms": r["launch_ms"]}
         if variants:
             line["variants"] = variants
         if world == 1 and not args.no_cpu_baseline and args.n == 32:
@@ -426,7 +464,7 @@ def run_batched(args):
     from paper_1604_08501_gb300.numa_vol import Batch, VolumeTerm
     lib_build.build()
     plan = wl.batch_plan(count=args.instances)
-    works = [wl.make_workload(N, n, seed=seed) for N, n, seed in plan]
+    works = [wl.integration_workload(N, n, seed) for N, n, seed in plan]
     nsteps, dt = 10, 0.01
     out = {}
     for prec in args.precisions:
@@ -490,8 +528,9 @@ def run_batched(args):
                 "dtype": {"fp64": "f64", "mixed": "f32 (perturbation state)"}[head],
                 "data": "synthetic",
                 "config": {"workload": f"{len(plan)} instances, N in {{3,4,5,7}}, 512..32768 elements "
-                                       f"(log-uniform, cubes), 10 LSRK(5,4) steps at dt = 0.01 s "
-                                       f"per launch from the initial states",
+                                       f"(log-uniform, cubes), smooth velocities (peak 10 m/s), "
+                                       f"10 LSRK(5,4) steps at dt = 0.01 s per launch from the "
+                                       f"initial states",
                            "points": out[head]["points"],
                            "l2": "states restored before each launch (a copy larger than L2)"},
                 "gpu_launches": args.steps, "clocks": out[head]["clocks"], "precision": head,
@@ -595,7 +634,7 @@ def run_serving(args):
     from paper_1604_08501_gb300.numa_vol import Engine, VolumeTerm
     lib_build.build()
     plan = wl.batch_plan(count=args.pool)
-    works = [wl.make_workload(N, n, seed=seed) for N, n, seed in plan]
+    works = [wl.integration_workload(N, n, seed) for N, n, seed in plan]
     rng = np.random.Generator(np.random.PCG64(2024 + rank))
     total = args.requests
     gaps = rng.exponential(1.0 / args.rate, size=total)
@@ -685,7 +724,8 @@ def run_serving(args):
                 "data": "synthetic",
                 "config": {"workload": f"Poisson arrivals at {args.rate:g} req/s, {total} requests, "
                                        f"each one of {len(plan)} instances (N in {{3,4,5,7}}, "
-                                       f"512..32768 elements) advancing k in {{1,5,20}} LSRK(5,4) "
+                                       f"512..32768 elements, smooth velocities) advancing "
+                                       f"k in {{1,5,20}} LSRK(5,4) "
                                        f"steps at dt = 0.01 s; budget {args.budget_gb} GB, "
                                        f"<= 256 members resident, rounds of up to "
                                        f"{args.round_steps} step(s)"},

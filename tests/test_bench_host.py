@@ -63,3 +63,12 @@ def test_roofline_entries_pick_the_binding_bound():
     roof, other = bench.roofline_entries("vol_rhs_df64_kernel", 1.0, w)
     assert roof["bound"] == "hbm"
     assert roof["achieved"] == pytest.approx(176 * w.M / 1e-3 / 1e9)
+
+
+def test_cpu_baseline_records_all_cores_and_one_core():
+    from paper_1604_08501_gb300 import workload as wl
+    w = wl.make_workload(2, 4, seed=1)
+    d = bench.cpu_baseline(w, min_seconds=0.05, single_seconds=0.05)
+    assert d["kind"] == "oracle" and d["value"] > 0 and d["cores"] >= 1
+    assert d["single_core"]["cores"] == 1 and d["single_core"]["value"] > 0
+    assert isinstance(d["cpu_model"], str) and d["cpu_model"]
