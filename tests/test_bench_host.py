@@ -68,7 +68,8 @@ def test_roofline_entries_pick_the_binding_bound():
 def test_cpu_baseline_records_all_cores_and_one_core():
     from paper_1604_08501_gb300 import workload as wl
     w = wl.make_workload(2, 4, seed=1)
-    d = bench.cpu_baseline(w, min_seconds=0.05, single_seconds=0.05)
+    d = bench.cpu_baseline(w, parity_w=wl.make_workload(1, 2, seed=0))
     assert d["kind"] == "oracle" and d["value"] > 0 and d["cores"] >= 1
     assert d["single_core"]["cores"] == 1 and d["single_core"]["value"] > 0
+    assert d["parity_workload"]["points"] == 8 * 8 and d["parity_workload"]["value"] > 0
     assert isinstance(d["cpu_model"], str) and d["cpu_model"]
