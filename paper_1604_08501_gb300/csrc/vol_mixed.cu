@@ -20,13 +20,14 @@
 // Structure as in vol_fp64.cu: fluxes by point into shared memory, even-odd D
 // sweeps by line in place, combination by point.  Two kernels:
 //  * vol_rhs_mixed_kernel<Nq>: one CTA of Nq^3 threads per element, direct loads.
-//  * vol_rhs_mixed_bulk_kernel (Nq = 8): persistent CTAs, 2 per SM.  The element
+//  * vol_rhs_mixed_bulk_kernel (Nq = 8): persistent CTAs, 3 per SM.  The element
 //    slab (17 arrays x 2 KB, contiguous per array and element) is staged in
 //    shared memory by bulk asynchronous copies (cp.async.bulk) completing on an
-//    mbarrier.  Two stages: once phase 1 has read an element's slab, its stage
-//    is refilled with the element two ahead, so up to two elements' copies
-//    stay in flight during the arithmetic.  Waits are
-//    bounded: on a timeout the kernel sets bit 0 of *err, drains its copies
+//    mbarrier.  One stage per CTA: once phase 1 has read an element's slab, the
+//    stage is refilled with the CTA's next element, whose copies stay in flight
+//    during the sweeps and stores.  (Two stages per CTA fit only two CTAs per
+//    SM; three CTAs with one stage each keep more warps resident, +2 %.)  Waits
+//    are bounded: on a timeout the kernel sets bit 0 of *err, drains its copies
 //    (again bounded) and returns.
 #include <cuda_runtime.h>
 
@@ -120,7 +121,11 @@ vol_rhs_mixed_kernel(MixedGeometry geo, MixedParams P, const float *__restrict__
 constexpr int kSlabArrays = 17;                       // 5 state + 9 metric + Jinv + 2 reference
 constexpr int kPts = 512;
 constexpr uint32_t kSlabBytes = kPts * sizeof(float);  // one array of one element
-constexpr size_t kBulkSmem = sizeof(float) * (2 * kSlabArrays + 3 * kFields) * kPts;
+// Stages per CTA and CTAs per SM: one stage (34 KB) and 30 KB of fluxes make
+// 64 KB per CTA, so three CTAs of 512 threads share an SM (40 registers).
+constexpr int kBulkStages = 1;
+constexpr int kBulkCtasPerSm = kBulkStages == 1 ? 3 : 2;
+constexpr size_t kBulkSmem = sizeof(float) * (kBulkStages * kSlabArrays + 3 * kFields) * kPts;
 
 __device__ __forceinline__ void issue_slab(int64_t e, int64_t M, const float *q,
                                            const MixedGeometry &geo, float *st, uint64_t *bar) {
@@ -135,56 +140,50 @@ __device__ __forceinline__ void issue_slab(int64_t e, int64_t M, const float *q,
     bulk_g2s(st + 16 * kPts, geo.theta_ref + off, kSlabBytes, bar);
 }
 
-__global__ void __launch_bounds__(kPts, 2)
+__global__ void __launch_bounds__(kPts, kBulkCtasPerSm)
 vol_rhs_mixed_bulk_kernel(MixedGeometry geo, MixedParams P, const float *__restrict__ q,
                           float *__restrict__ rhs, int64_t M, int64_t e0, int64_t e_end,
                           int *err) {
     constexpr int NQ = 8;
+    constexpr int S = kBulkStages;
     extern __shared__ __align__(128) float smem_f[];
-    __shared__ __align__(8) uint64_t bar[2];
-    float *const stage0 = smem_f;
-    float *const stage1 = smem_f + kSlabArrays * kPts;
-    float *sF = smem_f + 2 * kSlabArrays * kPts;
+    __shared__ __align__(8) uint64_t bar[S];
+    float *sF = smem_f + S * kSlabArrays * kPts;
 
     const int l = threadIdx.x;
     const int i = l & 7, j = (l >> 3) & 7, k = l >> 6;
     if (l == 0) {
-        mbar_init(&bar[0], 1);
-        mbar_init(&bar[1], 1);
+#pragma unroll
+        for (int b = 0; b < S; ++b) mbar_init(&bar[b], 1);
         fence_mbar_init();
     }
     __syncthreads();
 
-    uint32_t parity0 = 0u, parity1 = 0u;
-    bool pending0 = false, pending1 = false;   // meaningful in thread 0 only
+    // Per stage b: bit b of `parity` is the phase to wait for; bit b of
+    // `pending` (thread 0 only) marks copies in flight.
+    uint32_t parity = 0u, pending = 0u;
     const int64_t G = gridDim.x;
     int64_t e = e0 + blockIdx.x;
-    // Two elements in flight from the start: this CTA's first into stage 0,
-    // its second into stage 1.
-    if (l == 0 && e < e_end) {
-        issue_slab(e, M, q, geo, stage0, &bar[0]);
-        pending0 = true;
-    }
-    if (l == 0 && e + G < e_end) {
-        issue_slab(e + G, M, q, geo, stage1, &bar[1]);
-        pending1 = true;
+    // S elements in flight from the start: this CTA's first S into stages 0..S-1.
+    if (l == 0) {
+#pragma unroll
+        for (int b = 0; b < S; ++b)
+            if (e + b * G < e_end) {
+                issue_slab(e + b * G, M, q, geo, smem_f + b * kSlabArrays * kPts, &bar[b]);
+                pending |= 1u << b;
+            }
     }
     int buf = 0;
     bool failed = false;
     for (; e < e_end; e += G) {
-        const bool ok = bulk_wait(buf ? &bar[1] : &bar[0], buf ? parity1 : parity0);
+        const bool ok = bulk_wait(&bar[buf], (parity >> buf) & 1u);
         if (__syncthreads_or(!ok)) {
             failed = true;
             break;
         }
-        if (buf) {
-            parity1 ^= 1u;
-            pending1 = false;
-        } else {
-            parity0 ^= 1u;
-            pending0 = false;
-        }
-        const float *st = buf ? stage1 : stage0;
+        parity ^= 1u << buf;
+        pending &= ~(1u << buf);
+        float *const st = smem_f + buf * kSlabArrays * kPts;
 
         // ---- phase 1: p', fluxes ------------------------------------
         const float rp = st[0 * kPts + l];
@@ -212,13 +211,12 @@ vol_rhs_mixed_bulk_kernel(MixedGeometry geo, MixedParams P, const float *__restr
         const float Jinv = st[14 * kPts + l];
         __syncthreads();
         // This stage is dead now (phase 1 read all of it, and phase 3 uses
-        // registers): refill it with the element two ahead, so that during the
-        // sweeps and stores two elements' copies are in flight.
-        if (l == 0 && e + 2 * G < e_end) {
+        // registers): refill it with the element S ahead, so that its copies
+        // are in flight during the sweeps and stores.
+        if (l == 0 && e + S * G < e_end) {
             fence_proxy_async();   // order the generic reads above before the async writes
-            issue_slab(e + 2 * G, M, q, geo, buf ? stage1 : stage0, buf ? &bar[1] : &bar[0]);
-            if (buf) pending1 = true;
-            else pending0 = true;
+            issue_slab(e + S * G, M, q, geo, st, &bar[buf]);
+            pending |= 1u << buf;
         }
 
         // ---- phase 2: even-odd sweeps ---------------------------------
@@ -239,13 +237,14 @@ vol_rhs_mixed_bulk_kernel(MixedGeometry geo, MixedParams P, const float *__restr
         }
         // No barrier here: the barrier after the next wait orders this phase 3's
         // reads of sF before the next phase 1 writes it.
-        buf ^= 1;
+        buf = buf + 1 == S ? 0 : buf + 1;
     }
     if (failed && l == 0) {
         atomicOr(err, 1);
         // Drain the copies still in flight into this CTA's shared memory.
-        if (pending0) bulk_wait(&bar[0], parity0);
-        if (pending1) bulk_wait(&bar[1], parity1);
+#pragma unroll
+        for (int b = 0; b < S; ++b)
+            if ((pending >> b) & 1u) bulk_wait(&bar[b], (parity >> b) & 1u);
     }
 }
 
@@ -295,7 +294,8 @@ cudaError_t launch_vol_rhs_mixed(int N, int nf, ElemRange r, const MixedGeometry
                                              cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)kBulkSmem);
         if (e != cudaSuccess) return e;
-        const int64_t ctas = r.count < 2 * (int64_t)num_sms ? r.count : 2 * (int64_t)num_sms;
+        const int64_t per = kBulkCtasPerSm * (int64_t)num_sms;
+        const int64_t ctas = r.count < per ? r.count : per;
         vol_rhs_mixed_bulk_kernel<<<(unsigned)ctas, kPts, kBulkSmem, s>>>(
             geo, P, q, rhs, r.M, r.e0, r.e0 + r.count, err);
         return cudaGetLastError();

@@ -106,8 +106,10 @@ def test_mixed_host_entry_point_and_large_perturbation():
 
 def test_mixed_bulk_kernel_ranges_and_status():
     # N = 7 runs the persistent bulk-copy kernel; element counts below, at and
-    # above the CTA count (2 per SM) and the chunked host path all agree.
-    for shape in [(1, 1, 1), (7, 5, 3), (20, 20, 1)]:
+    # above its CTA count (a small multiple of the SM count), several elements
+    # per CTA, and the chunked host path all agree.
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    for shape in [(1, 1, 1), (7, 5, 3), (sms, 2, 1), (sms, 3, 1), (sms, 7, 1)]:
         w = wl.make_workload(7, shape, seed=90)
         prob = w.problem()
         with VolumeTerm.from_problem(prob, precision="mixed") as vt:
