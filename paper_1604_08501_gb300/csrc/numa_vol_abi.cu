@@ -416,7 +416,7 @@ cudaError_t launch(numa_vol *h, const void *q, void *rhs, int64_t e0, int64_t co
                                           h->d_err, h->num_sms, s);
     if (h->kernel == numa::Kernel::DoubleFloat)
         return numa::launch_vol_rhs_df64(r, h->dgeo, h->dparams, static_cast<const double *>(q),
-                                         static_cast<double *>(rhs), s);
+                                         static_cast<double *>(rhs), h->num_sms, s);
     if (h->kernel == numa::Kernel::NativeHigh)
         return numa::launch_vol_rhs_fp64_high(h->N, h->nf, r, h->geo, h->hparams,
                                               static_cast<const double *>(q),
