@@ -5,7 +5,10 @@ or the mathematics fixes, never against a retyped copy of its own formula.
   root finders, exact differentiation of polynomials of degree <= N.
 * Zero perturbation: the state equals the hydrostatic reference and U = 0,
   so the rhs is exactly zero.
-* Free stream on affine meshes: a uniform state gives zero flux divergence.
+* Free stream on affine meshes: a uniform state gives zero flux divergence;
+  on warped meshes the same holds with metrics in Kopriva's conservative
+  curl form (tests/curl_metrics.py), and fails with the analytic metrics,
+  which do not satisfy the discrete metric identities.
 * Manufactured closed forms on a non-orthogonal affine mesh: (i) a linear
   velocity field, (ii) a linear pressure perturbation with gravity.
 * The paper's nondimensional constants on one N = 1 element, derived by hand
@@ -128,6 +131,40 @@ def test_free_stream_affine(N):
     scale = mesh.Jinv.max() * np.abs(oracle.diff_matrix(N)).sum(axis=1).max() * F
     for out in all_forms(prob, q):
         assert np.max(np.abs(out)) <= 1e-13 * scale
+
+
+def test_curl_form_metrics_equal_the_analytic_ones_on_affine_meshes():
+    from curl_metrics import curl_form_metrics
+    for N in (1, 2, 4, 7):
+        mesh = wl.warped_box(N, (2, 2, 2), warp=0.0)
+        g = curl_form_metrics(mesh.x, N, mesh.Ne)
+        assert np.max(np.abs(g - mesh.g)) <= 2e-12 * np.max(np.abs(mesh.g))
+
+
+@pytest.mark.parametrize("N", [2, 3, 4, 7, 11])
+def test_free_stream_warped_with_curl_form_metrics(N):
+    # Uniform flow on the warped box: with curl-form metrics the flux
+    # divergence vanishes to rounding.  The computed metrics carry rounding of
+    # order eps s |g| (one D, s = max row sum of |D|) and the divergence
+    # applies D again, so |rhs| <= s^2 eps B with B the running bound
+    # J^-1 sum |D| |F|.  The analytic metrics break the discrete metric
+    # identities and miss that bound by orders of magnitude (up to N = 11).
+    from curl_metrics import curl_form_metrics
+    mesh = wl.warped_box(N, (2, 2, 1))
+    c = wl.Constants(p0=1.0e5, R=287.0, cp=1004.0, grav=0.0)
+    rho, vel, Th = 1.2, np.array([3.0, -2.0, 5.0]), 350.0
+    q = np.empty((5, mesh.M))
+    q[0], q[1:4], q[4] = rho, (rho * vel)[:, None], Th
+    s = np.max(np.sum(np.abs(oracle.diff_matrix(N)), axis=1))
+    prob = problem(mesh, c, 1.1, 340.0)
+    prob["g"] = curl_form_metrics(mesh.x, N, mesh.Ne)
+    B = np.max(oracle.vol_rhs_abs(prob, q), axis=1)
+    for out in all_forms(prob, q):
+        assert np.all(np.max(np.abs(out), axis=1) <= s * s * 2.0 ** -53 * B)
+    analytic = problem(mesh, c, 1.1, 340.0)
+    out = oracle.vol_rhs_o2(analytic, q)
+    Ba = np.max(oracle.vol_rhs_abs(analytic, q), axis=1)
+    assert np.max(np.abs(out)[0]) > 100 * s * s * 2.0 ** -53 * Ba[0]
 
 
 def _manufactured_linear_velocity(N):
