@@ -633,7 +633,8 @@ def run_serving(args):
     in the batched workload (N in {3,4,5,7}, 512..32768 elements), advancing
     k in {1, 5, 20} LSRK steps at dt = 0.01 s on device-resident state.  The
     engine admits by a 120 GB HBM budget with up to 256 members resident and
-    advances all resident members one step per round (continuous batching).
+    advances the resident members by up to --round-steps steps per round
+    (continuous batching), under the chosen round policy.
     Latency of a request: from its scheduled arrival to the moment its final
     state is in host memory.  Throughput: point x stage evaluations of all
     requests over the span from the first arrival to the last completion."""
@@ -665,13 +666,27 @@ def run_serving(args):
                             pin_memory=True)
             t.numpy()[...] = a
             q0s.append(t)
-        free = [[] for _ in works]          # pinned output buffers, reused per mesh
+        # Pinned output buffers, reused per mesh and allocated before the timed
+        # region (a pinned allocation takes milliseconds and would stall the
+        # serving loop): per mesh, as many as its requests arriving within any
+        # 0.25 s; any further one is allocated on demand and counted.
+        arrive_rel = np.cumsum(gaps)
+        free = []
+        for j in range(len(works)):
+            t = arrive_rel[pick == j]
+            need = int(np.max(np.searchsorted(t, t + 0.25) - np.arange(t.size))) if t.size else 0
+            free.append([torch.empty(q0s[j].shape, dtype=q0s[j].dtype, pin_memory=True)
+                         for _ in range(max(need, 1))])
+        late = [0]
 
         def take(j):
-            return free[j].pop() if free[j] else torch.empty_like(q0s[j]).pin_memory()
+            if free[j]:
+                return free[j].pop()
+            late[0] += 1
+            return torch.empty(q0s[j].shape, dtype=q0s[j].dtype, pin_memory=True)
 
         with Engine(prec, budget_bytes=args.budget_gb << 30, max_members=256,
-                    round_steps=args.round_steps) as eng:
+                    round_steps=args.round_steps, round_policy=args.round_policy) as eng:
             # warm-up: a few requests through the same path, not timed
             for j in range(min(args.warmup, len(works))):
                 o = take(j)
@@ -679,6 +694,7 @@ def run_serving(args):
                 eng.run_until_idle()
                 free[j].append(o)
             base = eng.stats()
+            late[0] = 0
             sampler = ClockSampler(gpu_id_for(local)) if rank == 0 else None
             if sampler:
                 sampler.start()
@@ -721,7 +737,8 @@ def run_serving(args):
                                         "p99": float(np.percentile(lat, 99) * 1e3),
                                         "max": float(lat.max() * 1e3)},
                          "offered_gdofs": offered / 1e9, "rounds": st["rounds"] - base["rounds"],
-                         "requests": total, "clocks": clocks}
+                         "requests": total, "late_pinned_allocations": late[0],
+                         "clocks": clocks}
         for vt in vts:
             vt.close()
         del q0s, free
@@ -740,8 +757,10 @@ def run_serving(args):
                                        f"k in {{1,5,20}} LSRK(5,4) "
                                        f"steps at dt = 0.01 s; budget {args.budget_gb} GB, "
                                        f"<= 256 members resident, rounds of up to "
-                                       f"{args.round_steps} step(s)"},
+                                       f"{args.round_steps} step(s), {args.round_policy} "
+                                       f"round policy"},
                 "latency_ms": out[head]["latency_ms"], "offered_gdofs": out[head]["offered_gdofs"],
+                "late_pinned_allocations": out[head]["late_pinned_allocations"],
                 "gpu_launches": out[head]["rounds"], "clocks": out[head]["clocks"],
                 "precision": head, "variants": {k: v for k, v in out.items() if k != head}}
         print(json.dumps(line))
@@ -777,6 +796,8 @@ def main(argv=None):
     ap.add_argument("--budget-gb", type=int, default=120, help="serving: HBM budget of the states")
     ap.add_argument("--round-steps", type=int, default=4,
                     help="serving: steps per engine round at most (never past a completion)")
+    ap.add_argument("--round-policy", choices=["lockstep", "per_member"], default="lockstep",
+                    help="serving: every member the same steps per round, or each its own")
     ap.add_argument("--orders", default="",
                     help="nq-sweep: comma-separated orders N to run (default 3,7,11,15)")
     args = ap.parse_args(argv)

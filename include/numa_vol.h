@@ -368,6 +368,21 @@ int numa_engine_query(const numa_engine *e, int64_t id, numa_request_info *out);
  * admission.  Errors: NUMA_EINVAL (NULL engine, max_steps < 1). */
 int numa_engine_set_round_steps(numa_engine *e, int max_steps);
 
+/* How a round with a step limit above 1 (numa_engine_set_round_steps) splits
+ * its steps among the residents.
+ *   NUMA_ROUND_LOCKSTEP (default): every member advances by the same s, the
+ *     smallest remaining step count up to the limit (above).
+ *   NUMA_ROUND_PER_MEMBER: each member advances by its own min(limit, its
+ *     remaining steps) in the same launch (the persistent kernel takes the
+ *     costliest work items first).  Long requests no longer advance at the
+ *     pace of the shortest one, so they finish in fewer rounds; a short
+ *     request now waits, within its round, for the longer members' steps.
+ * Results are bit for bit the same under either policy.  Errors: NUMA_EINVAL
+ * (NULL engine, unknown policy). */
+#define NUMA_ROUND_LOCKSTEP 0
+#define NUMA_ROUND_PER_MEMBER 1
+int numa_engine_set_round_policy(numa_engine *e, int policy);
+
 /* Checkpoint of a queued or running request: copies its state after its last
  * completed step (the initial state if not yet admitted) into state_host
  * (host memory of the mesh's state size) and stores the number of steps done

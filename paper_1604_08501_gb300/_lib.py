@@ -107,13 +107,15 @@ def load() -> C.CDLL:
     lib.numa_engine_query.argtypes = [C.c_void_p, C.c_int64, C.POINTER(numa_request_info)]
     lib.numa_engine_checkpoint.argtypes = [C.c_void_p, C.c_int64, C.c_void_p, C.POINTER(C.c_int)]
     lib.numa_engine_set_round_steps.argtypes = [C.c_void_p, C.c_int]
+    lib.numa_engine_set_round_policy.argtypes = [C.c_void_p, C.c_int]
     lib.numa_engine_stats.argtypes = [C.c_void_p, C.POINTER(numa_engine_counters)]
     lib.numa_engine_last_error.restype = C.c_char_p
     lib.numa_engine_destroy.argtypes = [C.c_void_p]
     lib.numa_engine_destroy.restype = None
     for name in ("numa_engine_create", "numa_engine_submit", "numa_engine_cancel",
                  "numa_engine_progress", "numa_engine_query", "numa_engine_stats",
-                 "numa_engine_checkpoint", "numa_engine_set_round_steps"):
+                 "numa_engine_checkpoint", "numa_engine_set_round_steps",
+                 "numa_engine_set_round_policy"):
         getattr(lib, name).restype = C.c_int
     lib.numa_batch_advance_noalloc.argtypes = [C.POINTER(C.c_void_p), C.POINTER(C.c_void_p), C.c_int,
                                                C.c_int, C.c_double, C.c_void_p]

@@ -54,14 +54,15 @@ batch_lsrk_kernel(const BatchInstance *__restrict__ inst, const BatchItem *__res
                 dst[w] = src[w];
         }
         __syncthreads();
+        const int ns = sI.nsteps > 0 ? sI.nsteps : nsteps;
         switch (item.nq) {
-            case 2: run_tile<2, MIXED>(sI, item.e0, item.count, sco, nsteps, dt, smem_d); break;
-            case 3: run_tile<3, MIXED>(sI, item.e0, item.count, sco, nsteps, dt, smem_d); break;
-            case 4: run_tile<4, MIXED>(sI, item.e0, item.count, sco, nsteps, dt, smem_d); break;
-            case 5: run_tile<5, MIXED>(sI, item.e0, item.count, sco, nsteps, dt, smem_d); break;
-            case 6: run_tile<6, MIXED>(sI, item.e0, item.count, sco, nsteps, dt, smem_d); break;
-            case 7: run_tile<7, MIXED>(sI, item.e0, item.count, sco, nsteps, dt, smem_d); break;
-            case 8: run_tile<8, MIXED>(sI, item.e0, item.count, sco, nsteps, dt, smem_d); break;
+            case 2: run_tile<2, MIXED>(sI, item.e0, item.count, sco, ns, dt, smem_d); break;
+            case 3: run_tile<3, MIXED>(sI, item.e0, item.count, sco, ns, dt, smem_d); break;
+            case 4: run_tile<4, MIXED>(sI, item.e0, item.count, sco, ns, dt, smem_d); break;
+            case 5: run_tile<5, MIXED>(sI, item.e0, item.count, sco, ns, dt, smem_d); break;
+            case 6: run_tile<6, MIXED>(sI, item.e0, item.count, sco, ns, dt, smem_d); break;
+            case 7: run_tile<7, MIXED>(sI, item.e0, item.count, sco, ns, dt, smem_d); break;
+            case 8: run_tile<8, MIXED>(sI, item.e0, item.count, sco, ns, dt, smem_d); break;
             default: break;
         }
         __syncthreads();   // sI and s_item are rewritten by the next claim

@@ -74,14 +74,15 @@ batch_lsrk_noalloc_kernel(unsigned char *scratch, LsrkCoef co, int nsteps, doubl
         const int64_t tile = (int64_t)(kThreads / (nq * nq * nq)) * kPassesPerItem;
         const int64_t e0 = (int64_t)(it - tab->first_item[k]) * tile;
         const int64_t count = ne - e0 < tile ? ne - e0 : tile;
+        const int ns = sI.nsteps > 0 ? sI.nsteps : nsteps;
         switch (nq) {
-            case 2: run_tile<2, MIXED>(sI, e0, count, sco, nsteps, dt, smem_d); break;
-            case 3: run_tile<3, MIXED>(sI, e0, count, sco, nsteps, dt, smem_d); break;
-            case 4: run_tile<4, MIXED>(sI, e0, count, sco, nsteps, dt, smem_d); break;
-            case 5: run_tile<5, MIXED>(sI, e0, count, sco, nsteps, dt, smem_d); break;
-            case 6: run_tile<6, MIXED>(sI, e0, count, sco, nsteps, dt, smem_d); break;
-            case 7: run_tile<7, MIXED>(sI, e0, count, sco, nsteps, dt, smem_d); break;
-            case 8: run_tile<8, MIXED>(sI, e0, count, sco, nsteps, dt, smem_d); break;
+            case 2: run_tile<2, MIXED>(sI, e0, count, sco, ns, dt, smem_d); break;
+            case 3: run_tile<3, MIXED>(sI, e0, count, sco, ns, dt, smem_d); break;
+            case 4: run_tile<4, MIXED>(sI, e0, count, sco, ns, dt, smem_d); break;
+            case 5: run_tile<5, MIXED>(sI, e0, count, sco, ns, dt, smem_d); break;
+            case 6: run_tile<6, MIXED>(sI, e0, count, sco, ns, dt, smem_d); break;
+            case 7: run_tile<7, MIXED>(sI, e0, count, sco, ns, dt, smem_d); break;
+            case 8: run_tile<8, MIXED>(sI, e0, count, sco, ns, dt, smem_d); break;
             default: break;
         }
         __syncthreads();   // sI and s_item are rewritten by the next claim

@@ -11,7 +11,8 @@
 //      not fit yet, so later requests cannot starve it;
 //   3. advance every resident member by s steps, all in one persistent launch
 //      (members of different dt in one launch each): s = 1 by default, or up
-//      to a set limit but never past the next member's completion;
+//      to a set limit but never past the next member's completion; or, under
+//      the per-member policy, each member by its own min(limit, remaining);
 //   4. copy finished members' states to their host buffers and free them.
 // Requests that arrive during a round join at the next round while the others
 // are still resident.  That is the continuous batching.  Elements evolve
@@ -148,6 +149,7 @@ struct numa_engine {
     double point_stages = 0.0;
     int tile_mult = 4;
     int max_round_steps = 1;   // steps per round: up to this, and never past a completion
+    int round_policy = NUMA_ROUND_LOCKSTEP;
 };
 
 namespace {
@@ -294,16 +296,22 @@ int numa_engine_progress(numa_engine *e, int64_t *done_ids, int max_done, int *n
         e->resident.push_back(r);
     }
     if (e->resident.empty()) return NUMA_OK;
-    // 3. s steps for every resident member, one launch per distinct dt: s is
-    //    the smallest remaining step count, at most max_round_steps, so every
-    //    member that finishes does so in the round it would with single steps
+    // 3. advance the residents, one launch per distinct dt.  Lockstep: every
+    //    member by s, the smallest remaining step count up to max_round_steps,
+    //    so every member that finishes does so in the round it would with
+    //    single steps.  Per member: each by min(max_round_steps, remaining).
     int steps = e->max_round_steps;
     for (const auto &r : e->resident) steps = std::min(steps, r.remaining);
+    const bool per_member = e->round_policy == NUMA_ROUND_PER_MEMBER;
+    auto steps_of = [&](const Request &r) {
+        return per_member ? std::min(e->max_round_steps, r.remaining) : steps;
+    };
     std::vector<double> dts;
     for (const auto &r : e->resident)
         if (std::find(dts.begin(), dts.end(), r.dt) == dts.end()) dts.push_back(r.dt);
     for (double dt : dts) {
         std::vector<numa::BatchInstance> inst;
+        int launch_steps = 1;
         for (const auto &r : e->resident) {
             if (r.dt != dt) continue;
             numa::BatchInstance I{};
@@ -315,12 +323,25 @@ int numa_engine_progress(numa_engine *e, int64_t *done_ids, int max_done, int *n
             I.np = r.mesh->nparams;
             I.mgeo = r.mesh->mgeo;
             I.mp = r.mesh->mparams;
+            I.nsteps = steps_of(r);
+            launch_steps = std::max(launch_steps, I.nsteps);
             inst.push_back(I);
-            e->point_stages += 5.0 * steps * (double)r.mesh->M;
+            e->point_stages += 5.0 * I.nsteps * (double)r.mesh->M;
         }
         int mult[9];
         std::fill(mult, mult + 9, e->tile_mult);
         std::vector<numa::BatchItem> items = numa::build_items(inst, mult);
+        if (per_member) {
+            // costliest items first (points x steps), so that the long ones
+            // do not start last and set the launch's tail
+            auto cost = [&](const numa::BatchItem &it) {
+                return (double)it.count * it.nq * it.nq * it.nq * inst[it.instance].nsteps;
+            };
+            std::stable_sort(items.begin(), items.end(),
+                             [&](const numa::BatchItem &a, const numa::BatchItem &b) {
+                                 return cost(a) > cost(b);
+                             });
+        }
         if (items.size() > e->items_cap) {
             cudaFree(e->d_items);
             e->items_cap = items.size();
@@ -339,8 +360,8 @@ int numa_engine_progress(numa_engine *e, int64_t *done_ids, int max_done, int *n
         if (err == cudaSuccess) err = cudaMemsetAsync(e->d_counter, 0, sizeof(int), e->stream);
         if (err == cudaSuccess)
             err = numa::launch_batch_lsrk(e->prec == NUMA_MIXED, e->d_inst, e->d_items,
-                                          (int)items.size(), e->d_counter, kCoef, steps, dt,
-                                          e->num_sms, e->stream);
+                                          (int)items.size(), e->d_counter, kCoef, launch_steps,
+                                          dt, e->num_sms, e->stream);
         // the host vectors are sources of in-flight copies: wait before they go
         if (err == cudaSuccess) err = cudaStreamSynchronize(e->stream);
         if (err != cudaSuccess) return efail_cuda(err, "numa_engine_progress: step");
@@ -350,7 +371,7 @@ int numa_engine_progress(numa_engine *e, int64_t *done_ids, int max_done, int *n
     std::vector<Request> done;
     for (size_t k = 0; k < e->resident.size();) {
         Request &r = e->resident[k];
-        r.remaining -= steps;
+        r.remaining -= steps_of(r);
         if (r.remaining == 0) {
             err = cudaMemcpyAsync(r.q_out, e->arena.base + r.off, r.bytes, cudaMemcpyDeviceToHost,
                                   e->stream);
@@ -380,6 +401,13 @@ int numa_engine_progress(numa_engine *e, int64_t *done_ids, int max_done, int *n
 int numa_engine_set_round_steps(numa_engine *e, int max_steps) {
     if (!e || max_steps < 1) return efail(NUMA_EINVAL, "numa_engine_set_round_steps: need max_steps >= 1");
     e->max_round_steps = max_steps;
+    return NUMA_OK;
+}
+
+int numa_engine_set_round_policy(numa_engine *e, int policy) {
+    if (!e || (policy != NUMA_ROUND_LOCKSTEP && policy != NUMA_ROUND_PER_MEMBER))
+        return efail(NUMA_EINVAL, "numa_engine_set_round_policy: NULL engine or unknown policy");
+    e->round_policy = policy;
     return NUMA_OK;
 }
 

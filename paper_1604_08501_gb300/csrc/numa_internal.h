@@ -168,6 +168,7 @@ struct BatchInstance {
     NativeParams np;
     MixedGeometry mgeo;
     MixedParams mp;
+    int nsteps;   // steps of this instance in the launch; 0: the launch's step count
 };
 
 // One work item: elements [e0, e0 + count) of an instance.

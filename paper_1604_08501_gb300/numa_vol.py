@@ -279,8 +279,10 @@ class Engine:
 
     STATUS = {0: "queued", 1: "running", 2: "done", 3: "cancelled"}
 
+    ROUND_POLICIES = {"lockstep": 0, "per_member": 1}   # NUMA_ROUND_*
+
     def __init__(self, precision: str = "fp64", budget_bytes: int = 1 << 30,
-                 max_members: int = 256, round_steps: int = 1):
+                 max_members: int = 256, round_steps: int = 1, round_policy: str = "lockstep"):
         self.precision = precision
         h = C.c_void_p()
         prec = {"fp64": NUMA_FP64, "mixed": NUMA_MIXED}[precision]
@@ -290,6 +292,9 @@ class Engine:
         self._bufs = {}          # request id -> (mesh, q0, out) kept alive while in flight
         if round_steps != 1:
             check_engine(_lib.load().numa_engine_set_round_steps(self.handle, int(round_steps)))
+        if round_policy != "lockstep":
+            check_engine(_lib.load().numa_engine_set_round_policy(
+                self.handle, self.ROUND_POLICIES[round_policy]))
 
     @property
     def handle(self) -> int:

@@ -144,6 +144,8 @@ def test_batch_engine_and_noalloc_reject_bad_arguments_without_a_gpu(lib):
     assert lib.numa_engine_query(None, 1, None) == _lib.NUMA_EINVAL
     assert lib.numa_engine_stats(None, None) == _lib.NUMA_EINVAL
     assert lib.numa_engine_checkpoint(None, 1, None, None) == _lib.NUMA_EINVAL
+    assert lib.numa_engine_set_round_steps(None, 2) == _lib.NUMA_EINVAL
+    assert lib.numa_engine_set_round_policy(None, 1) == _lib.NUMA_EINVAL
     assert b"NULL" in lib.numa_engine_last_error()
     lib.numa_engine_destroy(None)                        # no-op
     # the allocation-free advance: NULL arrays, counts out of range

@@ -10,6 +10,8 @@ ensemble-member requests.
 * Host-side failures return status codes and leave the engine usable:
   malformed requests, a state larger than the budget, cancellation of a queued
   and of a running request.
+* Rounds of several steps, lockstep and per member: the same bits as single
+  steps, in fewer rounds.
 """
 import numpy as np
 import pytest
@@ -225,5 +227,36 @@ def test_multi_step_rounds_give_the_same_bits(pool, precision):
     for a, b in zip(results[1][0], results[4][0]):
         assert np.array_equal(a, b)
     assert results[4][1] < results[1][1]
+    for vt in vts:
+        vt.close()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_per_member_rounds_give_the_same_bits_in_fewer_rounds(pool, precision):
+    # Rounds of up to 4 steps, a 13-step request beside a stream of 1-step
+    # requests (one arrives before every round).  Lockstep rounds then advance
+    # everyone one step at a time; per-member rounds advance the long request
+    # 4 + 4 + 4 + 1 steps, done in round 4.  Every final state is bitwise the
+    # same under both policies.
+    works, _ = pool
+    vts = [VolumeTerm.from_problem(w.problem(), precision=precision) for w in works]
+    q0s = [w.q_mixed() if precision == "mixed" else w.q for w in works]
+    outs, done_in = {}, {}
+    for policy in ("lockstep", "per_member"):
+        o = [np.empty_like(q0s[0])] + [np.empty_like(q0s[1 + n % 3]) for n in range(12)]
+        with Engine(precision, budget_bytes=1 << 28, round_steps=4, round_policy=policy) as eng:
+            long_id = eng.submit(vts[0], q0s[0], o[0], 13, DT)
+            done_in[policy] = None
+            for n in range(12):
+                eng.submit(vts[1 + n % 3], q0s[1 + n % 3], o[1 + n], 1, DT)
+                eng.progress()
+                if done_in[policy] is None and eng.query(long_id)["status"] == "done":
+                    done_in[policy] = n + 1
+            eng.run_until_idle()
+        outs[policy] = o
+    for a, b in zip(outs["lockstep"], outs["per_member"]):
+        assert np.array_equal(a, b)
+    assert done_in["per_member"] == 4
+    assert done_in["lockstep"] is None   # still running after 12 one-step rounds
     for vt in vts:
         vt.close()
