@@ -33,12 +33,19 @@ namespace {
 // (rho', U, Theta', tracers), FP32 geometry, p' from Theta' without
 // cancellation).
 
-// Threads: three per (i, j) column, each owning a slab of KS = ceil(Nq/3)
-// k-planes in the point phases and one line per field in the sweep phase
-// (3 directions x Nq^2 lines = 3 Nq^2 threads).
-template <int NQ>
+// Threads: TPC per (i, j) column, each owning a slab of KS = ceil(Nq/TPC)
+// k-planes in the point phases; the sweep phase deals the 3 Nq^2 lines of
+// each field of a group out to the threads.  TPC = 3 (one line per thread and
+// field); 4 for the FP32 instances at Nq >= 15, which fill the 1024 threads of
+// the one CTA their shared memory allows per SM.
+template <int NQ, typename T>
+__host__ __device__ constexpr int high_tpc() {
+    return (sizeof(T) == 4 && NQ >= 15 && 4 * NQ * NQ <= 1024) ? 4 : 3;
+}
+
+template <int NQ, typename T>
 __host__ __device__ constexpr int high_threads() {
-    return 3 * NQ * NQ;
+    return high_tpc<NQ, T>() * NQ * NQ;
 }
 
 // Fields per pass.  FP64: one (the flux arrays of one field already take
@@ -52,7 +59,7 @@ __host__ __device__ constexpr int high_group() {
     } else {
         constexpr size_t fixed = sizeof(T) * 4 * NQ * NQ * NQ;   // u_d and p'
         constexpr size_t per = sizeof(T) * 3 * NQ * NQ * 16;     // one field's fluxes
-        constexpr size_t budget = (2 * high_threads<NQ>() <= 1024 ? 113 : 226) * 1024;
+        constexpr size_t budget = (2 * 3 * NQ * NQ <= 1024 ? 113 : 226) * 1024;
         constexpr size_t g = budget > fixed ? (budget - fixed) / per : 1;
         return g < 1 ? 1 : (g > kMaxFields ? kMaxFields : (int)g);
     }
@@ -67,7 +74,7 @@ __host__ __device__ constexpr size_t high_smem_bytes() {
 // memory fits an SM and still leaves 64 registers per thread, else one.
 template <int NQ, typename T>
 __host__ __device__ constexpr int high_min_ctas() {
-    return (2 * (high_smem_bytes<NQ, T>() + 1024) <= 228 * 1024 && 2 * high_threads<NQ>() <= 1024)
+    return (2 * (high_smem_bytes<NQ, T>() + 1024) <= 228 * 1024 && 2 * high_threads<NQ, T>() <= 1024)
                ? 2
                : 1;
 }
@@ -77,14 +84,16 @@ template <> struct HighTypes<double> { using Geo = DeviceGeometry; using Params 
 template <> struct HighTypes<float> { using Geo = MixedGeometry; using Params = HighParams32; };
 
 template <int NQ, typename T>
-__global__ void __launch_bounds__(3 * NQ * NQ, (high_min_ctas<NQ, T>()))
+__global__ void __launch_bounds__((high_threads<NQ, T>()), (high_min_ctas<NQ, T>()))
 vol_rhs_high_kernel(typename HighTypes<T>::Geo geo, typename HighTypes<T>::Params P,
                     const T *__restrict__ q, T *__restrict__ rhs, int64_t M, int64_t e0, int nf) {
     constexpr bool MIXED = sizeof(T) == 4;
     constexpr int NL = NQ * NQ;      // columns; lines per direction
     constexpr int N3 = NQ * NL;
     constexpr int FB = NL * 16;      // one direction's flux block (padded lines)
-    constexpr int KS = (NQ + 2) / 3; // k-planes per slab
+    constexpr int TPC = high_tpc<NQ, T>();
+    constexpr int NT = TPC * NL;     // threads
+    constexpr int KS = (NQ + TPC - 1) / TPC; // k-planes per slab
     constexpr int G = high_group<NQ, T>();
     // k-loop unrolling: full in FP32 (registers to spare, more loads in
     // flight), two planes in FP64 (register budget)
@@ -178,8 +187,15 @@ vol_rhs_high_kernel(typename HighTypes<T>::Geo geo, typename HighTypes<T>::Param
         }
         __syncthreads();
         // ---- sweeps: line c of direction `slab`, for each field of the group
+        // (TPC = 3), or the group's 3 Nq^2 lines per field dealt out in turn
+        if constexpr (TPC == 3) {
 #pragma unroll 1
-        for (int gl = 0; gl < gn; ++gl) sweep_line<NQ>(sF + (gl * 3 + slab) * FB, c, P);
+            for (int gl = 0; gl < gn; ++gl) sweep_line<NQ>(sF + (gl * 3 + slab) * FB, c, P);
+        } else {
+#pragma unroll 1
+            for (int item = t; item < gn * 3 * NL; item += NT)
+                sweep_line<NQ>(sF + (item / NL) * FB, item % NL, P);
+        }
         __syncthreads();
         // ---- rhs of the group's fields: -Jinv (S_r + S_s + S_t), gravity on U3
 #pragma unroll(KU)
@@ -216,7 +232,7 @@ cudaError_t launch_high(ElemRange r, int nf, const Geo &geo, const Params &P, co
     cudaError_t e = cudaFuncSetAttribute(vol_rhs_high_kernel<NQ, T>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    vol_rhs_high_kernel<NQ, T><<<(unsigned)r.count, high_threads<NQ>(), smem, s>>>(geo, P, q, rhs,
+    vol_rhs_high_kernel<NQ, T><<<(unsigned)r.count, high_threads<NQ, T>(), smem, s>>>(geo, P, q, rhs,
                                                                                 r.M, r.e0, nf);
     return cudaGetLastError();
 }
