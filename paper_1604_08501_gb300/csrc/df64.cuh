@@ -18,7 +18,7 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
-#include "numa_internal.h"
+#include "kernel_params.h"
 
 namespace numa {
 

@@ -19,7 +19,7 @@
 // below 2^-26), expm1f(gamma log1pf(x)) beyond, chosen per warp.
 #pragma once
 
-#include "numa_internal.h"
+#include "kernel_params.h"
 
 namespace numa {
 

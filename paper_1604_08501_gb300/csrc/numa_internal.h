@@ -6,92 +6,10 @@
 
 #include <cuda_runtime.h>
 
+#include "kernel_params.h"
 #include "numa_vol.h"
 
 namespace numa {
-
-constexpr int kFields = 5;      // rho, U1, U2, U3, Theta
-constexpr int kMaxFields = 8;   // with three passive tracers
-
-// Elements [e0, e0 + count) of a mesh whose per-point planes hold M values.
-struct ElemRange {
-    int64_t e0, count, M;
-};
-
-// Device-side geometry of one handle. Every per-point array has M entries,
-// padded so that each starts on a 256-byte boundary.
-struct DeviceGeometry {
-    const double *g[9];      // metric terms g[3*d + a]
-    const double *Jinv;      // 1 / J
-    const double *rho_ref;   // reference density
-    const double *theta_ref; // reference Theta
-    const double *w;         // 1 / Theta_ref
-    const double *A;         // p(Theta_ref) / Theta_ref
-    const double *D;         // (N+1)^2, row-major D[i*Nq + n]
-};
-
-struct EosConstants {
-    double p0, R, gamma, grav;
-};
-
-// Parameters of the native kernel: EOS constants, c[k] = binom(gamma, k+1)
-// (k = 0..14, the coefficients of the p' series), and the even-odd pieces of D
-// for r, m < Nq/2: De = (D[r][m] + D[r][N-m])/2, Do = (D[r][m] - D[r][N-m])/2,
-// Dc[r] = D[r][c] and Dcr[m] = D[c][m] (centre column and row, odd Nq).
-// Uniform across threads, so the kernel reads them as constant-bank operands.
-struct NativeParams {
-    EosConstants eos;
-    double c[15];
-    double De[16], Do[16], Dc[4], Dcr[4];
-};
-
-// Parameters of the native kernel for orders N = 8..15 (Nq = 9..16): the same
-// quantities as NativeParams with even-odd tables up to (Nq/2)^2 = 64 entries.
-struct HighParams {
-    EosConstants eos;
-    double c[15];
-    double De[64], Do[64], Dc[8], Dcr[8];
-};
-
-// The same for the mixed-precision mode at N = 8..15: FP32 tables and the FP32
-// EOS constants of MixedParams (c[k] = binom(gamma, k+1)).
-struct HighParams32 {
-    float De[64], Do[64], Dc[8], Dcr[8];
-    float c[16];
-    float K, gm1, gamma, grav;
-};
-
-// Per-point arrays of the double-float path (N = 7): float2 (h, l) pairs, and
-// the reference state in FP64, so that rho - rho_ref and Theta - Theta_ref are
-// exact FP64 differences before they are split.
-struct DfGeometry {
-    const float2 *g[9];      // metric terms
-    const float2 *Jinv;      // 1 / J
-    const double *rho_ref;   // reference density
-    const double *theta_ref; // reference Theta
-    const float2 *w;         // 1 / Theta_ref
-    const float2 *A;         // p(Theta_ref) / Theta_ref
-};
-
-// Per-point arrays of the mixed-precision path, FP32.
-struct MixedGeometry {
-    const float *g[9];
-    const float *Jinv;
-    const float *rho_ref;
-    const float *theta_ref;
-};
-
-// Parameters of the mixed-precision kernel: even-odd pieces of D (as in
-// NativeParams), c[k] = binom(gamma, k+1) for k = 0..15, K = p0^(1-gamma) R^gamma
-// (so p(Theta) = K Theta^gamma), gamma - 1, gamma and gravity.
-struct MixedParams {
-    float De[16], Do[16], Dc[4], Dcr[4];
-    float c[16];
-    float K, gm1, gamma, grav;
-};
-
-// Kernel parameters of the double-float path.
-struct DfParams;  // defined below
 
 // Launchers (vol_fp64.cu). They return a cudaError_t from the launch.
 // reference_eos: w = 1/Theta_ref, A = p(Theta_ref)/Theta_ref per point.
@@ -137,21 +55,6 @@ int gll_diff_matrix(int N, double *D);
 // ((Nq/2)^2, row-major), Dc, Dcr (odd Nq).  Unused entries are zero.
 void sweep_tables(int N, const double *D, double De[16], double Do[16], double Dc[4],
                   double Dcr[4]);
-
-// Double-float value: the unevaluated sum h + l of two floats.
-struct df {
-    float h, l;
-};
-
-struct DfParams {
-    df De[4][4];       // (D[i][m] + D[i][7-m]) / 2, i, m < 4
-    df Do[4][4];       // (D[i][m] - D[i][7-m]) / 2
-    df c1, c2, c3;     // binom(gamma, k), k = 1..3
-    float ct[6];       // binom(gamma, k), k = 4..9
-    df grav_df;        // gravity
-    double grav, p0, R, gamma;
-    double D[64];      // D for the native fallback
-};
 
 // Native: vol_rhs_fp64_kernel (N <= 7); NativeHigh: vol_rhs_high_kernel<Nq, double>
 // (N = 8..15); DoubleFloat (N = 7); Mixed (N <= 7) and MixedHigh:

@@ -43,6 +43,7 @@
 
 #include "bulk_copy.cuh"
 #include "df64.cuh"
+#include "numa_internal.h"
 
 namespace numa {
 
