@@ -40,7 +40,8 @@ namespace {
 // the one CTA their shared memory allows per SM.
 template <int NQ, typename T>
 __host__ __device__ constexpr int high_tpc() {
-    return (sizeof(T) == 4 && NQ >= 15 && 4 * NQ * NQ <= 1024) ? 4 : 3;
+    if (sizeof(T) == 4 && NQ >= 15 && 4 * NQ * NQ <= 1024) return 4;
+    return 3;
 }
 
 template <int NQ, typename T>
@@ -59,7 +60,7 @@ __host__ __device__ constexpr int high_group() {
     } else {
         constexpr size_t fixed = sizeof(T) * 4 * NQ * NQ * NQ;   // u_d and p'
         constexpr size_t per = sizeof(T) * 3 * NQ * NQ * 16;     // one field's fluxes
-        constexpr size_t budget = (2 * 3 * NQ * NQ <= 1024 ? 113 : 226) * 1024;
+        constexpr size_t budget = (2 * high_tpc<NQ, T>() * NQ * NQ <= 1024 ? 113 : 226) * 1024;
         constexpr size_t g = budget > fixed ? (budget - fixed) / per : 1;
         return g < 1 ? 1 : (g > kMaxFields ? kMaxFields : (int)g);
     }
