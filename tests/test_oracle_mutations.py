@@ -55,6 +55,7 @@ PIN_CHECKS = [
     lambda: [pins.test_diff_matrix_exact_on_polynomials(N) for N in (1, 4, 7)],
     lambda: [pins.test_zero_perturbation_is_exactly_zero(N) for N in (1, 4)],
     lambda: [pins.test_free_stream_affine(N) for N in (1, 5)],
+    lambda: [pins.test_free_stream_warped_with_curl_form_metrics(N) for N in (2, 4)],
     lambda: [pins.test_manufactured_linear_velocity(N) for N in (2, 4)],
     lambda: [pins.test_manufactured_linear_pressure_and_gravity(N) for N in (1, 4)],
     lambda: pins.test_paper_units_by_hand_n1(),
