@@ -3,10 +3,11 @@
 //
 // Fluxes of one element are kept per (direction, field) in line-major order:
 // direction r has lines (k, j) with position i, s has lines (k, i) with
-// position j, t has lines (j, i) with position k.  For Nq > 8 every line has
-// 16 slots and slot(line, n) = 16 line + (n ^ (line & 15)): 16 consecutive
-// lines, or 16 consecutive points of a line, cover all banks with 8-byte
-// values (one half-warp wavefront).  For Nq = 8 an XOR swizzle
+// position j, t has lines (j, i) with position k.  For Nq > 8 and 8-byte
+// values every line has 16 slots and slot(line, n) = 16 line + (n ^ (line & 15)):
+// 16 consecutive lines, or 16 consecutive points of a line, cover all banks
+// (one half-warp wavefront).  For Nq > 8 and 4-byte values lines have an odd
+// number S of slots (Nq or Nq + 1) and slot(line, n) = S line + n.  For Nq = 8 an XOR swizzle
 // slot(line, n) = 8 line + (n ^ h(line)) keeps the accesses free of bank
 // conflicts when points write, lines read and write, and points read back:
 //   8-byte values: h(line) = (line & 6) | ((line >> 3) & 1)
@@ -26,9 +27,20 @@
 
 namespace numa {
 
+// Words between consecutive lines for Nq > 8: 16 slots with the XOR swizzle
+// for 8-byte values; for 4-byte values the smallest odd count >= Nq, whose
+// odd stride alone keeps 32 consecutive lines on distinct banks, and leaves a
+// line's addresses base + n, immediate offsets without per-access arithmetic.
+template <int NQ, typename T>
+__host__ __device__ constexpr int line_stride() {
+    return (NQ > 8 && sizeof(T) == 4) ? (NQ | 1) : 16;
+}
+
 template <int NQ, typename T>
 __device__ __forceinline__ int slot(int line, int n) {
-    if constexpr (NQ > 8)   // lines padded to 16 slots, XOR swizzle over 16
+    if constexpr (NQ > 8 && sizeof(T) == 4)   // lines of an odd number of slots
+        return line * line_stride<NQ, T>() + n;
+    else if constexpr (NQ > 8)   // lines padded to 16 slots, XOR swizzle over 16
         return line * 16 + (n ^ (line & 15));
     else if constexpr (NQ == 8 && sizeof(T) == 8)
         return line * 8 + (n ^ ((line & 6) | ((line >> 3) & 1)));

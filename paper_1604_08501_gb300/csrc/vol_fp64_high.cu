@@ -59,7 +59,7 @@ __host__ __device__ constexpr int high_group() {
         return 1;
     } else {
         constexpr size_t fixed = sizeof(T) * 4 * NQ * NQ * NQ;   // u_d and p'
-        constexpr size_t per = sizeof(T) * 3 * NQ * NQ * 16;     // one field's fluxes
+        constexpr size_t per = sizeof(T) * 3 * NQ * NQ * line_stride<NQ, T>();   // one field's fluxes
         constexpr size_t budget = (2 * high_tpc<NQ, T>() * NQ * NQ <= 1024 ? 113 : 226) * 1024;
         constexpr size_t g = budget > fixed ? (budget - fixed) / per : 1;
         return g < 1 ? 1 : (g > kMaxFields ? kMaxFields : (int)g);
@@ -68,7 +68,7 @@ __host__ __device__ constexpr int high_group() {
 
 template <int NQ, typename T>
 __host__ __device__ constexpr size_t high_smem_bytes() {
-    return sizeof(T) * (4 * NQ * NQ * NQ + high_group<NQ, T>() * 3 * NQ * NQ * 16);
+    return sizeof(T) * (4 * NQ * NQ * NQ + high_group<NQ, T>() * 3 * NQ * NQ * line_stride<NQ, T>());
 }
 
 // CTAs per SM the register budget is sized for: two where two CTAs' shared
@@ -91,7 +91,7 @@ vol_rhs_high_kernel(typename HighTypes<T>::Geo geo, typename HighTypes<T>::Param
     constexpr bool MIXED = sizeof(T) == 4;
     constexpr int NL = NQ * NQ;      // columns; lines per direction
     constexpr int N3 = NQ * NL;
-    constexpr int FB = NL * 16;      // one direction's flux block (padded lines)
+    constexpr int FB = NL * line_stride<NQ, T>();   // one direction's flux block (padded lines)
     constexpr int TPC = high_tpc<NQ, T>();
     constexpr int NT = TPC * NL;     // threads
     constexpr int KS = (NQ + TPC - 1) / TPC; // k-planes per slab
