@@ -22,10 +22,26 @@ constexpr int kThreads = 512;
 // binds).  Mixed: the fluxes, q and dq (10 values) and the point's geometry
 // (g and Jinv, 10 values) in shared memory, so that the kernel fits 64
 // registers and two CTAs share an SM, twice the warps to hide latency.
-constexpr int kMixedSmemWords = (3 * 5 + 2 * 5 + 10) * kThreads;
+// Flux words of one pass: 3 x 5 blocks of EPP elements; the largest over the
+// orders sizes the flux region (4-byte values at Nq = 8: lines of 9 slots).
+template <typename T, int NQ>
+constexpr int pass_flux_words() {
+    return 3 * 5 * (kThreads / (NQ * NQ * NQ)) * block_words<NQ, T>();
+}
+template <typename T>
+constexpr int tile_flux_words() {
+    constexpr int w[] = {pass_flux_words<T, 2>(), pass_flux_words<T, 3>(), pass_flux_words<T, 4>(),
+                         pass_flux_words<T, 5>(), pass_flux_words<T, 6>(), pass_flux_words<T, 7>(),
+                         pass_flux_words<T, 8>()};
+    int m = 0;
+    for (int x : w) m = x > m ? x : m;
+    return m;
+}
+constexpr int kMixedFluxWords = tile_flux_words<float>();
+constexpr int kMixedSmemWords = kMixedFluxWords + (2 * 5 + 10) * kThreads;
 template <bool MIXED>
 constexpr size_t tile_smem_bytes() {
-    return MIXED ? sizeof(float) * kMixedSmemWords : sizeof(double) * 3 * 5 * kThreads;
+    return MIXED ? sizeof(float) * kMixedSmemWords : sizeof(double) * tile_flux_words<double>();
 }
 template <bool MIXED>
 constexpr int tile_ctas_per_sm() {
@@ -90,7 +106,8 @@ __device__ void run_tile(const BatchInstance &I, int64_t e0, int64_t count,
     constexpr int N3 = NQ * NQ * NQ;
     constexpr int NL = NQ * NQ;
     constexpr int EPP = kThreads / N3;          // elements per pass
-    constexpr int BLK = EPP * N3;               // one (direction, field) block of sF
+    constexpr int EW = block_words<NQ, T>();    // one element's (direction, field) block
+    constexpr int BLK = EPP * EW;               // one (direction, field) block of sF
     constexpr int TASKS = 3 * kFields * EPP * NL;   // lines per stage
     T *sF = static_cast<T *>(smem);             // [(d*5 + b)*EPP + el][slot]
     const int l = threadIdx.x;
@@ -99,7 +116,7 @@ __device__ void run_tile(const BatchInstance &I, int64_t e0, int64_t count,
     // this thread's flux slot of field b in direction d: f[d] + b * BLK
     int f[3];
 #pragma unroll
-    for (int d = 0; d < 3; ++d) f[d] = d * kFields * BLK + el * N3 + dir_slot<NQ, T>(d, i, j, k);
+    for (int d = 0; d < 3; ++d) f[d] = d * kFields * BLK + el * EW + dir_slot<NQ, T>(d, i, j, k);
     const int64_t M = I.M;
     T *qv = static_cast<T *>(I.q);
     const T dtt = static_cast<T>(dt);
@@ -117,7 +134,7 @@ __device__ void run_tile(const BatchInstance &I, int64_t e0, int64_t count,
         // shared memory in the mixed mode), and the mixed mode's per-point
         // constants, kept for all stages
         T qr[kFields], dqr[kFields];
-        T *sQ = sF + 3 * kFields * kThreads + l;   // [b * kThreads], mixed only
+        T *sQ = sF + kMixedFluxWords + l;          // [b * kThreads], mixed only
         T *sD = sQ + kFields * kThreads;
         T *sG = sD + kFields * kThreads;           // g (9), Jinv
         auto Q = [&](int b) -> T & {
@@ -195,9 +212,9 @@ __device__ void run_tile(const BatchInstance &I, int64_t e0, int64_t count,
                     const int e = rem / NL, line = rem % NL;
                     if (e < npass) {
                         if constexpr (MIXED)
-                            sweep_line<NQ>(sF + bd * BLK + e * N3, line, c_sweep32[NQ]);
+                            sweep_line<NQ>(sF + bd * BLK + e * EW, line, c_sweep32[NQ]);
                         else
-                            sweep_line<NQ>(sF + bd * BLK + e * N3, line, c_sweep64[NQ]);
+                            sweep_line<NQ>(sF + bd * BLK + e * EW, line, c_sweep64[NQ]);
                     }
                 }
                 __syncthreads();

@@ -7,14 +7,12 @@
 // values every line has 16 slots and slot(line, n) = 16 line + (n ^ (line & 15)):
 // 16 consecutive lines, or 16 consecutive points of a line, cover all banks
 // (one half-warp wavefront).  For Nq > 8 and 4-byte values lines have an odd
-// number S of slots (Nq or Nq + 1) and slot(line, n) = S line + n.  For Nq = 8 an XOR swizzle
-// slot(line, n) = 8 line + (n ^ h(line)) keeps the accesses free of bank
-// conflicts when points write, lines read and write, and points read back:
-//   8-byte values: h(line) = (line & 6) | ((line >> 3) & 1)
-//     (a half-warp wavefront: the 16 lanes need distinct (line & 1, n ^ h) pairs);
-//   4-byte values: h(line) = bit2 << 2 | bit4 << 1 | bit3 of line
-//     (a warp wavefront: lanes of equal line % 4 need distinct n ^ h, and h must
-//     flip bit 2 with line bit 2 for the s-direction writes).
+// number S of slots (Nq or Nq + 1) and slot(line, n) = S line + n; that holds
+// for 4-byte values at Nq = 8 too (S = 9).  For 8-byte values at Nq = 8 an XOR
+// swizzle slot(line, n) = 8 line + (n ^ h(line)), h(line) = (line & 6) |
+// ((line >> 3) & 1), keeps the accesses free of bank conflicts when points
+// write, lines read and write, and points read back (a half-warp wavefront:
+// the 16 lanes need distinct (line & 1, n ^ h) pairs).
 //
 // The sweep uses the centro-antisymmetry of the GLL D, D[N-i][N-n] = -D[i][n]:
 // with E_m = F_m + F_{N-m} and O_m = F_m - F_{N-m} (m < Nq/2),
@@ -27,25 +25,30 @@
 
 namespace numa {
 
-// Words between consecutive lines for Nq > 8: 16 slots with the XOR swizzle
-// for 8-byte values; for 4-byte values the smallest odd count >= Nq, whose
-// odd stride alone keeps 32 consecutive lines on distinct banks, and leaves a
-// line's addresses base + n, immediate offsets without per-access arithmetic.
+// Words between consecutive lines: for 4-byte values at Nq >= 8 the smallest
+// odd count >= Nq (9 at Nq = 8, 13 at Nq = 12, 17 at Nq = 16), whose odd
+// stride alone keeps 32 consecutive lines on distinct banks and leaves a
+// line's addresses base + n, immediate offsets without per-access arithmetic;
+// 16 slots with an XOR swizzle for 8-byte values at Nq > 8; Nq otherwise.
 template <int NQ, typename T>
 __host__ __device__ constexpr int line_stride() {
-    return (NQ > 8 && sizeof(T) == 4) ? (NQ | 1) : 16;
+    return (NQ >= 8 && sizeof(T) == 4) ? (NQ | 1) : (NQ > 8 ? 16 : NQ);
+}
+
+// Words of one (direction, field) block of one element: Nq^2 lines.
+template <int NQ, typename T>
+__host__ __device__ constexpr int block_words() {
+    return NQ * NQ * line_stride<NQ, T>();
 }
 
 template <int NQ, typename T>
 __device__ __forceinline__ int slot(int line, int n) {
-    if constexpr (NQ > 8 && sizeof(T) == 4)   // lines of an odd number of slots
+    if constexpr (NQ >= 8 && sizeof(T) == 4)   // lines of an odd number of slots
         return line * line_stride<NQ, T>() + n;
     else if constexpr (NQ > 8)   // lines padded to 16 slots, XOR swizzle over 16
         return line * 16 + (n ^ (line & 15));
-    else if constexpr (NQ == 8 && sizeof(T) == 8)
+    else if constexpr (NQ == 8)
         return line * 8 + (n ^ ((line & 6) | ((line >> 3) & 1)));
-    else if constexpr (NQ == 8 && sizeof(T) == 4)
-        return line * 8 + (n ^ ((((line >> 2) & 1) << 2) | (((line >> 4) & 1) << 1) | ((line >> 3) & 1)));
     else
         return line * NQ + n;
 }

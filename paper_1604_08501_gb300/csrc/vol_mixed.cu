@@ -54,6 +54,7 @@ vol_rhs_mixed_kernel(MixedGeometry geo, MixedParams P, const float *__restrict__
                      float *__restrict__ rhs, int64_t M, int64_t e0, int nf_run) {
     constexpr int N3 = NQ * NQ * NQ;
     constexpr int NL = NQ * NQ;
+    constexpr int EW = block_words<NQ, float>();   // one (direction, field) block
     const int nf = TRACERS ? nf_run : kFields;
     extern __shared__ float sFm[];            // [direction*nf + field][slot]
 
@@ -82,23 +83,23 @@ vol_rhs_mixed_kernel(MixedGeometry geo, MixedParams P, const float *__restrict__
                     g3 = geo.g[3 * d + 2][node];
         const float v = fmaf(g3, U[2], fmaf(g2, U[1], g1 * U[0]));
         const float u = v * rinv;
-        float *F = sFm + d * nf * N3 + dir_slot<NQ, float>(d, i, j, k);
-        F[0 * N3] = v;
-        F[1 * N3] = fmaf(U[0], u, g1 * pp);
-        F[2 * N3] = fmaf(U[1], u, g2 * pp);
-        F[3 * N3] = fmaf(U[2], u, g3 * pp);
-        F[4 * N3] = Th * u;
+        float *F = sFm + d * nf * EW + dir_slot<NQ, float>(d, i, j, k);
+        F[0 * EW] = v;
+        F[1 * EW] = fmaf(U[0], u, g1 * pp);
+        F[2 * EW] = fmaf(U[1], u, g2 * pp);
+        F[3 * EW] = fmaf(U[2], u, g3 * pp);
+        F[4 * EW] = Th * u;
         if constexpr (TRACERS) {
 #pragma unroll
             for (int t = 0; t < kMaxFields - kFields; ++t)
-                if (kFields + t < nf) F[(kFields + t) * N3] = Q[t] * u;
+                if (kFields + t < nf) F[(kFields + t) * EW] = Q[t] * u;
         }
     }
     __syncthreads();
 
     // ---- phase 2: even-odd sweeps, one line per task, in place --------
     for (int item = l; item < 3 * nf * NL; item += N3)
-        sweep_line<NQ>(sFm + (item / NL) * N3, item % NL, P);
+        sweep_line<NQ>(sFm + (item / NL) * EW, item % NL, P);
     __syncthreads();
 
     // ---- phase 3: combine, scale, gravity, store ----------------------
@@ -106,9 +107,9 @@ vol_rhs_mixed_kernel(MixedGeometry geo, MixedParams P, const float *__restrict__
 #pragma unroll
     for (int b = 0; b < (TRACERS ? kMaxFields : kFields); ++b) {
         if (TRACERS && b >= nf) break;
-        const float R = sFm[(0 * nf + b) * N3 + dir_slot<NQ, float>(0, i, j, k)] +
-                        sFm[(1 * nf + b) * N3 + dir_slot<NQ, float>(1, i, j, k)] +
-                        sFm[(2 * nf + b) * N3 + dir_slot<NQ, float>(2, i, j, k)];
+        const float R = sFm[(0 * nf + b) * EW + dir_slot<NQ, float>(0, i, j, k)] +
+                        sFm[(1 * nf + b) * EW + dir_slot<NQ, float>(1, i, j, k)] +
+                        sFm[(2 * nf + b) * EW + dir_slot<NQ, float>(2, i, j, k)];
         float v = -Jinv * R;
         if (b == 3) v = fmaf(-rp, P.grav, v);
         rhs[b * M + node] = v;
@@ -125,7 +126,8 @@ constexpr uint32_t kSlabBytes = kPts * sizeof(float);  // one array of one eleme
 // 64 KB per CTA, so three CTAs of 512 threads share an SM (40 registers).
 constexpr int kBulkStages = 1;
 constexpr int kBulkCtasPerSm = kBulkStages == 1 ? 3 : 2;
-constexpr size_t kBulkSmem = sizeof(float) * (kBulkStages * kSlabArrays + 3 * kFields) * kPts;
+constexpr int kBlk = block_words<8, float>();            // one (direction, field) block
+constexpr size_t kBulkSmem = sizeof(float) * (kBulkStages * kSlabArrays * kPts + 3 * kFields * kBlk);
 
 __device__ __forceinline__ void issue_slab(int64_t e, int64_t M, const float *q,
                                            const MixedGeometry &geo, float *st, uint64_t *bar) {
@@ -201,12 +203,12 @@ vol_rhs_mixed_bulk_kernel(MixedGeometry geo, MixedParams P, const float *__restr
             const float g3 = st[(kFields + 3 * d + 2) * kPts + l];
             const float v = fmaf(g3, U[2], fmaf(g2, U[1], g1 * U[0]));
             const float u = v * rinv;
-            float *F = sF + d * kFields * kPts + dir_slot<NQ, float>(d, i, j, k);
-            F[0 * kPts] = v;
-            F[1 * kPts] = fmaf(U[0], u, g1 * pp);
-            F[2 * kPts] = fmaf(U[1], u, g2 * pp);
-            F[3 * kPts] = fmaf(U[2], u, g3 * pp);
-            F[4 * kPts] = Th * u;
+            float *F = sF + d * kFields * kBlk + dir_slot<NQ, float>(d, i, j, k);
+            F[0 * kBlk] = v;
+            F[1 * kBlk] = fmaf(U[0], u, g1 * pp);
+            F[2 * kBlk] = fmaf(U[1], u, g2 * pp);
+            F[3 * kBlk] = fmaf(U[2], u, g3 * pp);
+            F[4 * kBlk] = Th * u;
         }
         const float Jinv = st[14 * kPts + l];
         __syncthreads();
@@ -221,16 +223,16 @@ vol_rhs_mixed_bulk_kernel(MixedGeometry geo, MixedParams P, const float *__restr
 
         // ---- phase 2: even-odd sweeps ---------------------------------
         for (int item = l; item < 3 * kFields * 64; item += kPts)
-            sweep_line<NQ>(sF + (item >> 6) * kPts, item & 63, P);
+            sweep_line<NQ>(sF + (item >> 6) * kBlk, item & 63, P);
         __syncthreads();
 
         // ---- phase 3: combine, scale, gravity, store ------------------
         const int64_t node = e * kPts + l;
 #pragma unroll
         for (int b = 0; b < kFields; ++b) {
-            const float R = sF[(0 * kFields + b) * kPts + dir_slot<NQ, float>(0, i, j, k)] +
-                            sF[(1 * kFields + b) * kPts + dir_slot<NQ, float>(1, i, j, k)] +
-                            sF[(2 * kFields + b) * kPts + dir_slot<NQ, float>(2, i, j, k)];
+            const float R = sF[(0 * kFields + b) * kBlk + dir_slot<NQ, float>(0, i, j, k)] +
+                            sF[(1 * kFields + b) * kBlk + dir_slot<NQ, float>(1, i, j, k)] +
+                            sF[(2 * kFields + b) * kBlk + dir_slot<NQ, float>(2, i, j, k)];
             float v = -Jinv * R;
             if (b == 3) v = fmaf(-rp, P.grav, v);
             rhs[b * M + node] = v;
@@ -252,7 +254,7 @@ template <int NQ, bool TRACERS>
 cudaError_t launch_kernel(ElemRange r, int nf, const MixedGeometry &geo, const MixedParams &P,
                           const float *q, float *rhs, cudaStream_t s) {
     constexpr int N3 = NQ * NQ * NQ;
-    const size_t smem = sizeof(float) * nf * 3 * N3;
+    const size_t smem = sizeof(float) * nf * 3 * block_words<NQ, float>();
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(vol_rhs_mixed_kernel<NQ, TRACERS>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
