@@ -796,7 +796,7 @@ def main(argv=None):
     ap.add_argument("--budget-gb", type=int, default=120, help="serving: HBM budget of the states")
     ap.add_argument("--round-steps", type=int, default=4,
                     help="serving: steps per engine round at most (never past a completion)")
-    ap.add_argument("--round-policy", choices=["lockstep", "per_member"], default="lockstep",
+    ap.add_argument("--round-policy", choices=["lockstep", "per_member"], default="per_member",
                     help="serving: every member the same steps per round, or each its own")
     ap.add_argument("--orders", default="",
                     help="nq-sweep: comma-separated orders N to run (default 3,7,11,15)")
