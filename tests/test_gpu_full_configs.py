@@ -29,7 +29,7 @@ configurations bench.py times, checked by properties that hold at any size.
   the bound.
 * Serving: a seeded Poisson stream (200 requests/s) of requests drawn from the
   16-instance pool, through an engine with the bench's settings (120 GB budget,
-  256 members, rounds of up to 4 steps).  Each sampled request's result is bit
+  256 members, rounds of up to 4 steps, per-member rounds; lockstep too).  Each sampled request's result is bit
   for bit the batched integrator's on the same instance and step count.
 """
 import numpy as np
@@ -124,8 +124,9 @@ def test_batched_full_plan_on_sampled_elements(plan_works, precision):
         vt.close()
 
 
-@pytest.mark.parametrize("precision", ["mixed", "fp64"])
-def test_serving_stream_results_equal_the_batch(precision):
+@pytest.mark.parametrize("precision,policy", [("mixed", "per_member"), ("mixed", "lockstep"),
+                                              ("fp64", "per_member")])
+def test_serving_stream_results_equal_the_batch(precision, policy):
     plan = wl.batch_plan(count=16)
     works = [wl.integration_workload(N, n, seed) for N, n, seed in plan]
     vts = [VolumeTerm.from_problem(w.problem(), precision=precision) for w in works]
@@ -135,7 +136,8 @@ def test_serving_stream_results_equal_the_batch(precision):
     picks = rng.integers(0, len(works), size=count)
     ks = rng.choice(np.array([1, 5, 20]), size=count)
     outs = [np.empty_like(q0s[j]) for j in picks]
-    with Engine(precision, budget_bytes=120 << 30, max_members=256, round_steps=4) as eng:
+    with Engine(precision, budget_bytes=120 << 30, max_members=256, round_steps=4,
+                round_policy=policy) as eng:
         ids = []
         for n, (j, k) in enumerate(zip(picks, ks)):   # arrivals between rounds
             ids.append(eng.submit(vts[j], q0s[j], outs[n], int(k), DT))
