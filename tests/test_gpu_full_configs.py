@@ -29,8 +29,9 @@ configurations bench.py times, checked by properties that hold at any size.
   the bound.
 * Serving: a seeded Poisson stream (200 requests/s) of requests drawn from the
   16-instance pool, through an engine with the bench's settings (120 GB budget,
-  256 members, rounds of up to 4 steps, per-member rounds; lockstep too).  Each sampled request's result is bit
-  for bit the batched integrator's on the same instance and step count.
+  256 members, rounds of up to 4 steps, per-member rounds; lockstep too).  Each
+  sampled request's result is bit for bit the batched integrator's on the same
+  instance and step count.
 """
 import numpy as np
 import pytest
