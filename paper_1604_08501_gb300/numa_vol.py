@@ -275,7 +275,10 @@ class Engine:
     """Serving engine (numa_engine_*): continuous batching of ensemble-member
     requests.  Each request advances a copy of an initial state on a resident
     mesh (a VolumeTerm) by nsteps low-storage RK steps; the final state lands
-    in the request's host output buffer."""
+    in the request's host output buffer.  round_steps bounds the steps of one
+    round; round_policy "lockstep" advances every resident by the same count
+    (the smallest remaining), "per_member" each by its own (see
+    numa_engine_set_round_policy)."""
 
     STATUS = {0: "queued", 1: "running", 2: "done", 3: "cancelled"}
 
