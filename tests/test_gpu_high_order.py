@@ -99,7 +99,8 @@ def test_host_entry_point_and_rejections_at_high_order():
         VolumeTerm.from_problem(prob, precision="df64")
 
 
-@pytest.mark.parametrize("N,T", [(8, 0), (11, 0), (13, 2), (15, 0), (15, 3)])
+@pytest.mark.parametrize("N,T", [(8, 0), (9, 0), (10, 1), (11, 0), (11, 3), (12, 0), (13, 2),
+                                 (14, 0), (15, 0), (15, 3)])
 def test_mixed_precision_high_orders(N, T):
     # The FP32 instantiation of the high-order kernel: perturbation state,
     # FP32 sweeps, p' from Theta'; every field within 1e-5 of the FP64 oracle.
