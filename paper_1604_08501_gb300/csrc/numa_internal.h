@@ -42,7 +42,7 @@ cudaError_t launch_vol_rhs_df64(ElemRange r, const DfGeometry &geo, const DfPara
 
 // Launchers of the mixed-precision path (vol_mixed.cu).
 cudaError_t launch_to_f32(const double *src, float *dst, int64_t M, cudaStream_t s);
-// N = 7 launches the persistent bulk-copy kernel (2 CTAs per SM); it sets
+// N = 7 launches the persistent bulk-copy kernel (3 CTAs per SM); it sets
 // bit 0 of *err if a bounded wait on its copies times out.
 cudaError_t launch_vol_rhs_mixed(int N, int nf, ElemRange r, const MixedGeometry &geo,
                                  const MixedParams &P, const float *q, float *rhs, int *err,

@@ -122,8 +122,8 @@ vol_rhs_mixed_kernel(MixedGeometry geo, MixedParams P, const float *__restrict__
 constexpr int kSlabArrays = 17;                       // 5 state + 9 metric + Jinv + 2 reference
 constexpr int kPts = 512;
 constexpr uint32_t kSlabBytes = kPts * sizeof(float);  // one array of one element
-// Stages per CTA and CTAs per SM: one stage (34 KB) and 30 KB of fluxes make
-// 64 KB per CTA, so three CTAs of 512 threads share an SM (40 registers).
+// Stages per CTA and CTAs per SM: one stage (34 KB) and 34.6 KB of fluxes (lines
+// of 9 slots) make 69 KB per CTA, so three CTAs of 512 threads share an SM.
 constexpr int kBulkStages = 1;
 constexpr int kBulkCtasPerSm = kBulkStages == 1 ? 3 : 2;
 constexpr int kBlk = block_words<8, float>();            // one (direction, field) block
