@@ -134,6 +134,6 @@ struct numa_vol {
     // overlaps the next chunk's start), copy-in and copy-out streams
     cudaStream_t host_stream = nullptr, host_stream2 = nullptr, h2d_stream = nullptr,
                  d2h_stream = nullptr;
-    static constexpr int kChunks = 32;   // chunks of the host path: short pipeline fill and drain
+    static constexpr int kChunks = 64;   // host path: at most this many chunks (short fill and drain)
     cudaEvent_t ev_in[kChunks] = {}, ev_out[kChunks] = {};
 };

@@ -479,7 +479,10 @@ int numa_vol_rhs_host(numa_vol *h, const void *q, void *rhs) {
     const char *hq = static_cast<const char *>(q);
     char *hr = static_cast<char *>(rhs);
     const int64_t n3 = (int64_t)h->Nq * h->Nq * h->Nq;
-    const int chunks = (int)std::min<int64_t>(numa_vol::kChunks, h->Ne);
+    // FP64 states: 64 chunks (the kernel dominates; a shorter fill and drain);
+    // FP32 states: 32 (the copies dominate; fewer, larger copies).
+    const int64_t target = h->elem == sizeof(double) ? numa_vol::kChunks : numa_vol::kChunks / 2;
+    const int chunks = (int)std::min<int64_t>(target, h->Ne);
     const size_t plane = h->elem * h->M;
     // One 2D copy per chunk and direction moves the chunk's slice of every
     // field plane (pitch = the plane stride).
