@@ -6,19 +6,19 @@
 // study (Sec. 5, Nq up to 16).  An element of Nq = 16 has 4096 points: more
 // than a CTA has threads, and its fifteen FP64 flux arrays (491 KB) exceed
 // shared memory.  So:
-//  * one CTA of 3 Nq^2 threads per element: three per (i, j) column, each
-//    looping over a third of its k-planes, as the paper's kernels own (i, j)
-//    lanes and loop over k;
+//  * one CTA per element with three threads per (i, j) column (four in FP32
+//    at Nq >= 15), each looping over its share of the k-planes, as the
+//    paper's kernels own (i, j) lanes and loop over k;
 //  * a first pass forms the contravariant velocities u_d and p' of all points
 //    into shared memory (4 Nq^3 values);
 //  * then one pass per group of fields (one field in FP64; as many as
 //    shared memory holds in FP32): their flux arrays into shared memory
-//    (3 Nq^2 lines of 16 slots per field), the D sweeps in place (one line per
-//    thread and field, even-odd split), and the rhs of the thread's points
-//    straight to HBM.
-// Shared memory: (4 Nq^3 + 48 Nq^2) values, 224 KB at Nq = 16 in FP64 (every
-// operation FP64; bound by the FP64 pipe like the low orders) and 112 KB in
-// the mixed mode (FP32 perturbation state and arithmetic, as vol_mixed.cu).
+//    (3 Nq^2 lines per field: 16 slots in FP64, an odd number >= Nq in FP32),
+//    the D sweeps in place (even-odd split, lines dealt out to the threads),
+//    and the rhs of the thread's points straight to HBM.
+// Shared memory at Nq = 16: 224 KB in FP64 (every operation FP64; bound by the
+// FP64 pipe like the low orders), 222 KB in the mixed mode (FP32 perturbation
+// state and arithmetic as vol_mixed.cu; three fields per pass).
 #include <cuda_runtime.h>
 
 #include "element_sweep.cuh"
