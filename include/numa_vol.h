@@ -55,7 +55,7 @@ extern "C" {
 #define NUMA_ENOMEM (-2)        /* device allocation failed                               */
 #define NUMA_ECUDA (-3)         /* a CUDA call or kernel launch failed                    */
 #define NUMA_EUNSUPPORTED (-4)  /* a valid request the library does not implement          */
-#define NUMA_ETIMEOUT (-5)      /* a kernel's bounded wait on its own staged copies ran out */
+#define NUMA_ETIMEOUT (-5)      /* a kernel's bounded device-side wait ran out              */
 #define NUMA_ELIMIT (-6)        /* a count exceeds a fixed maximum of the call            */
 
 #define NUMA_MAX_N 7            /* orders N = 1 .. 7 (Nq = 2 .. 8): every mode, the batch
@@ -189,18 +189,18 @@ int numa_vol_rhs_host(numa_vol *h, const void *q, void *rhs);
 /*
  * Status of the kernels enqueued so far on a handle.  Reads and clears the
  * handle's device status word on `stream` and waits for the stream.  Returns
- * NUMA_ETIMEOUT if a kernel gave up a bounded wait on its own staged
- * shared-memory copies; that kernel returned early, so the rhs of the elements
- * it still owed is incomplete.  No timeout is expected in operation: each wait
- * is bounded far above its normal duration.  Returns NUMA_OK otherwise.
+ * NUMA_ETIMEOUT if a kernel of the handle gave up a bounded device-side wait
+ * (every wait in the library's kernels has a time limit far above its normal
+ * duration; the evaluation kernels themselves do not wait, and the self-test
+ * below makes one such wait run out).  Returns NUMA_OK otherwise.
  * numa_vol_rhs_host checks it itself.
  */
 int numa_vol_status(numa_vol *h, void *stream);
 
 /*
- * Failure-detection self-test: makes the staged kernels' bounded wait run out.
- * Enqueues on `stream` one CTA that waits, with the same bounded mbarrier wait
- * the staged kernels use, on a barrier nothing completes; after limit_us
+ * Failure-detection self-test: makes a bounded device-side wait run out.
+ * Enqueues on `stream` one CTA that waits, with the library's bounded
+ * mbarrier wait, on a barrier nothing completes; after limit_us
  * microseconds (1 .. 1,000,000) of GPU time the wait gives up and sets the
  * handle's status word, so that a following numa_vol_status on the same
  * stream returns NUMA_ETIMEOUT.  No copy or other asynchronous work is in

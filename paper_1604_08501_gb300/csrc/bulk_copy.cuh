@@ -1,10 +1,10 @@
-// Bulk asynchronous copies (cp.async.bulk, the untiled TMA path) and
-// mbarriers for staging element slabs in shared memory, in inline PTX for
-// sm_100-class GPUs.
+// The bulk L2 prefetch (cp.async.bulk.prefetch.L2, the untiled TMA path) that
+// the volume-term kernels issue for the element one wave ahead, and a bounded
+// mbarrier wait, in inline PTX for sm_100-class GPUs.  Rule of the untiled
+// bulk operations: address 16-byte aligned, size a multiple of 16 bytes.
 //
-// Every wait is bounded: bulk_wait() gives up after a time limit (and a
-// fixed number of polls) and returns false, so a kernel never spins forever.  Rules of the untiled
-// bulk copy: both addresses 16-byte aligned, size a multiple of 16 bytes.
+// Every device wait is bounded: bulk_wait() gives up after a time limit (and
+// a fixed number of polls) and returns false, so a kernel never spins forever.
 #pragma once
 
 #include <cstdint>
@@ -26,32 +26,11 @@ __device__ __forceinline__ void fence_mbar_init() {
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
 }
 
-__device__ __forceinline__ void fence_proxy_async() {
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-}
-
-// One arrival that also announces tx_bytes of incoming bulk-copy data.
-__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t tx_bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)),
-                 "r"(tx_bytes)
-                 : "memory");
-}
-
 // Bulk prefetch of [src, src + bytes) from global memory into L2 (no
 // completion to wait for; src 16-byte aligned, bytes a multiple of 16).
 __device__ __forceinline__ void prefetch_l2(const void *src_gmem, uint32_t bytes) {
     asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src_gmem), "r"(bytes)
                  : "memory");
-}
-
-// Global -> shared bulk copy completing on `bar`.
-__device__ __forceinline__ void bulk_g2s(void *dst_smem, const void *src_gmem, uint32_t bytes,
-                                         uint64_t *bar) {
-    asm volatile(
-        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-            smem_addr(dst_smem)),
-        "l"(src_gmem), "r"(bytes), "r"(smem_addr(bar))
-        : "memory");
 }
 
 // One poll of phase `parity` of `bar`; the thread may be suspended for up to

@@ -42,11 +42,11 @@ cudaError_t launch_vol_rhs_df64(ElemRange r, const DfGeometry &geo, const DfPara
 
 // Launchers of the mixed-precision path (vol_mixed.cu).
 cudaError_t launch_to_f32(const double *src, float *dst, int64_t M, cudaStream_t s);
-// N = 7 launches the persistent bulk-copy kernel (3 CTAs per SM); it sets
-// bit 0 of *err if a bounded wait on its copies times out.
+// One CTA per element (vol_rhs_mixed_kernel<Nq>), with an L2 prefetch of the
+// element one wave ahead; num_sms sizes that wave.
 cudaError_t launch_vol_rhs_mixed(int N, int nf, ElemRange r, const MixedGeometry &geo,
-                                 const MixedParams &P, const float *q, float *rhs, int *err,
-                                 int num_sms, cudaStream_t s);
+                                 const MixedParams &P, const float *q, float *rhs, int num_sms,
+                                 cudaStream_t s);
 
 // GLL points and differentiation matrix on the host (gll.cpp).
 int gll_diff_matrix(int N, double *D);

@@ -69,10 +69,9 @@ const char *numa_vol_kernel_name(const numa_vol *h) {
     static const char *mixed[] = {"", "vol_rhs_mixed_kernel<2>", "vol_rhs_mixed_kernel<3>",
                                   "vol_rhs_mixed_kernel<4>", "vol_rhs_mixed_kernel<5>",
                                   "vol_rhs_mixed_kernel<6>", "vol_rhs_mixed_kernel<7>",
-                                  "vol_rhs_mixed_bulk_kernel"};   // N = 7: the persistent staged kernel
+                                  "vol_rhs_mixed_kernel<8>"};
     if (h->kernel == numa::Kernel::DoubleFloat) return "vol_rhs_df64_kernel";
-    if (h->kernel == numa::Kernel::Mixed)
-        return h->N == 7 && h->nf > numa::kFields ? "vol_rhs_mixed_kernel<8>" : mixed[h->N];
+    if (h->kernel == numa::Kernel::Mixed) return mixed[h->N];
     if (h->kernel == numa::Kernel::MixedHigh) {
         static const char *mixed_high[] = {"vol_rhs_high_kernel<9, float>", "vol_rhs_high_kernel<10, float>",
                                            "vol_rhs_high_kernel<11, float>", "vol_rhs_high_kernel<12, float>",
@@ -413,7 +412,7 @@ cudaError_t launch(numa_vol *h, const void *q, void *rhs, int64_t e0, int64_t co
     if (h->kernel == numa::Kernel::Mixed)
         return numa::launch_vol_rhs_mixed(h->N, h->nf, r, h->mgeo, h->mparams,
                                           static_cast<const float *>(q), static_cast<float *>(rhs),
-                                          h->d_err, h->num_sms, s);
+                                          h->num_sms, s);
     if (h->kernel == numa::Kernel::DoubleFloat)
         return numa::launch_vol_rhs_df64(r, h->dgeo, h->dparams, static_cast<const double *>(q),
                                          static_cast<double *>(rhs), h->num_sms, s);
@@ -518,8 +517,8 @@ int numa_vol_status(numa_vol *h, void *stream) {
     if (e == cudaSuccess && flag) e = cudaMemsetAsync(h->d_err, 0, sizeof(int), s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return fail_cuda(e, "numa_vol_status");
-    if (flag) return fail(NUMA_ETIMEOUT, "numa_vol_rhs: a bounded wait on staged copies timed out; "
-                                         "the rhs of the affected elements is incomplete");
+    if (flag) return fail(NUMA_ETIMEOUT, "numa_vol_status: a kernel gave up a bounded device-side "
+                                         "wait; its results are incomplete");
     return NUMA_OK;
 }
 

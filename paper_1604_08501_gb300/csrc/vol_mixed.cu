@@ -18,17 +18,14 @@
 // HBM bandwidth, and the extra arithmetic is free.
 //
 // Structure as in vol_fp64.cu: fluxes by point into shared memory, even-odd D
-// sweeps by line in place, combination by point.  Two kernels:
-//  * vol_rhs_mixed_kernel<Nq>: one CTA of Nq^3 threads per element, direct loads.
-//  * vol_rhs_mixed_bulk_kernel (Nq = 8): persistent CTAs, 3 per SM.  The element
-//    slab (17 arrays x 2 KB, contiguous per array and element) is staged in
-//    shared memory by bulk asynchronous copies (cp.async.bulk) completing on an
-//    mbarrier.  One stage per CTA: once phase 1 has read an element's slab, the
-//    stage is refilled with the CTA's next element, whose copies stay in flight
-//    during the sweeps and stores.  (Two stages per CTA fit only two CTAs per
-//    SM; three CTAs with one stage each keep more warps resident, +2 %.)  Waits
-//    are bounded: on a timeout the kernel sets bit 0 of *err, drains its copies
-//    (again bounded) and returns.
+// sweeps by line in place, combination by point; one CTA of Nq^3 threads per
+// element, four CTAs of 512 threads per SM at Nq = 8 (32 registers, 35 KB of
+// shared memory each).  Thread 0 of each CTA prefetches to L2
+// (cp.async.bulk.prefetch.L2) the arrays of the element one wave of resident
+// CTAs ahead, so that CTA's loads hit L2 rather than DRAM.  At N = 7 this
+// replaced a persistent kernel that staged each element's arrays in shared
+// memory with cp.async.bulk on an mbarrier: the staging buffer limited that
+// kernel to three CTAs per SM, and it ran at 0.271 against 0.254 ms here.
 #include <cuda_runtime.h>
 
 #include "bulk_copy.cuh"
@@ -42,8 +39,25 @@ namespace {
 
 template <int NQ>
 constexpr int mixed_min_ctas() {
-    constexpr int n = 1536 / (NQ * NQ * NQ);
+    constexpr int n = 2048 / (NQ * NQ * NQ);
     return n < 1 ? 1 : (n > 32 ? 32 : n);
+}
+
+// Starts the 17 arrays element e reads toward L2, where an element's slab of
+// one array is a whole number of 16-byte units (the bulk prefetch's rule).
+template <int NQ>
+__device__ __forceinline__ void prefetch_element(const MixedGeometry &geo, const float *q,
+                                                 int64_t M, int nf, int64_t e) {
+    constexpr uint32_t B = NQ * NQ * NQ * sizeof(float);
+    if constexpr (B % 16 == 0) {
+        const int64_t off = e * (NQ * NQ * NQ);
+        for (int b = 0; b < nf; ++b) prefetch_l2(q + b * M + off, B);
+#pragma unroll
+        for (int a = 0; a < 9; ++a) prefetch_l2(geo.g[a] + off, B);
+        prefetch_l2(geo.Jinv + off, B);
+        prefetch_l2(geo.rho_ref + off, B);
+        prefetch_l2(geo.theta_ref + off, B);
+    }
 }
 
 // TRACERS: nf = 5 + tracers fields at run time (tracers Q in FP32 as they are,
@@ -51,7 +65,8 @@ constexpr int mixed_min_ctas() {
 template <int NQ, bool TRACERS>
 __global__ void __launch_bounds__(NQ * NQ * NQ, mixed_min_ctas<NQ>())
 vol_rhs_mixed_kernel(MixedGeometry geo, MixedParams P, const float *__restrict__ q,
-                     float *__restrict__ rhs, int64_t M, int64_t e0, int nf_run) {
+                     float *__restrict__ rhs, int64_t M, int64_t e0, int nf_run, int64_t e_end,
+                     int64_t ahead) {
     constexpr int N3 = NQ * NQ * NQ;
     constexpr int NL = NQ * NQ;
     constexpr int EW = block_words<NQ, float>();   // one (direction, field) block
@@ -61,6 +76,8 @@ vol_rhs_mixed_kernel(MixedGeometry geo, MixedParams P, const float *__restrict__
     const int l = threadIdx.x;
     const int i = l % NQ, j = (l / NQ) % NQ, k = l / (NQ * NQ);
     const int64_t node = (e0 + blockIdx.x) * N3 + l;
+    if (l == 0 && e0 + blockIdx.x + ahead < e_end)
+        prefetch_element<NQ>(geo, q, M, nf, e0 + blockIdx.x + ahead);
 
     // ---- phase 1: p', fluxes ----------------------------------------
     const float rp = q[node];
@@ -116,160 +133,29 @@ vol_rhs_mixed_kernel(MixedGeometry geo, MixedParams P, const float *__restrict__
     }
 }
 
-// ---------------------------------------------------------------------------
-// Nq = 8, persistent, bulk-copy staged.
-// ---------------------------------------------------------------------------
-constexpr int kSlabArrays = 17;                       // 5 state + 9 metric + Jinv + 2 reference
-constexpr int kPts = 512;
-constexpr uint32_t kSlabBytes = kPts * sizeof(float);  // one array of one element
-// Stages per CTA and CTAs per SM: one stage (34 KB) and 34.6 KB of fluxes (lines
-// of 9 slots) make 69 KB per CTA, so three CTAs of 512 threads share an SM.
-constexpr int kBulkStages = 1;
-constexpr int kBulkCtasPerSm = kBulkStages == 1 ? 3 : 2;
-constexpr int kBlk = block_words<8, float>();            // one (direction, field) block
-constexpr size_t kBulkSmem = sizeof(float) * (kBulkStages * kSlabArrays * kPts + 3 * kFields * kBlk);
-
-__device__ __forceinline__ void issue_slab(int64_t e, int64_t M, const float *q,
-                                           const MixedGeometry &geo, float *st, uint64_t *bar) {
-    mbar_arrive_expect_tx(bar, kSlabArrays * kSlabBytes);
-    const int64_t off = e * kPts;
-#pragma unroll
-    for (int a = 0; a < kFields; ++a) bulk_g2s(st + a * kPts, q + a * M + off, kSlabBytes, bar);
-#pragma unroll
-    for (int a = 0; a < 9; ++a) bulk_g2s(st + (kFields + a) * kPts, geo.g[a] + off, kSlabBytes, bar);
-    bulk_g2s(st + 14 * kPts, geo.Jinv + off, kSlabBytes, bar);
-    bulk_g2s(st + 15 * kPts, geo.rho_ref + off, kSlabBytes, bar);
-    bulk_g2s(st + 16 * kPts, geo.theta_ref + off, kSlabBytes, bar);
-}
-
-__global__ void __launch_bounds__(kPts, kBulkCtasPerSm)
-vol_rhs_mixed_bulk_kernel(MixedGeometry geo, MixedParams P, const float *__restrict__ q,
-                          float *__restrict__ rhs, int64_t M, int64_t e0, int64_t e_end,
-                          int *err) {
-    constexpr int NQ = 8;
-    constexpr int S = kBulkStages;
-    extern __shared__ __align__(128) float smem_f[];
-    __shared__ __align__(8) uint64_t bar[S];
-    float *sF = smem_f + S * kSlabArrays * kPts;
-
-    const int l = threadIdx.x;
-    const int i = l & 7, j = (l >> 3) & 7, k = l >> 6;
-    if (l == 0) {
-#pragma unroll
-        for (int b = 0; b < S; ++b) mbar_init(&bar[b], 1);
-        fence_mbar_init();
-    }
-    __syncthreads();
-
-    // Per stage b: bit b of `parity` is the phase to wait for; bit b of
-    // `pending` (thread 0 only) marks copies in flight.
-    uint32_t parity = 0u, pending = 0u;
-    const int64_t G = gridDim.x;
-    int64_t e = e0 + blockIdx.x;
-    // S elements in flight from the start: this CTA's first S into stages 0..S-1.
-    if (l == 0) {
-#pragma unroll
-        for (int b = 0; b < S; ++b)
-            if (e + b * G < e_end) {
-                issue_slab(e + b * G, M, q, geo, smem_f + b * kSlabArrays * kPts, &bar[b]);
-                pending |= 1u << b;
-            }
-    }
-    int buf = 0;
-    bool failed = false;
-    for (; e < e_end; e += G) {
-        const bool ok = bulk_wait(&bar[buf], (parity >> buf) & 1u);
-        if (__syncthreads_or(!ok)) {
-            failed = true;
-            break;
-        }
-        parity ^= 1u << buf;
-        pending &= ~(1u << buf);
-        float *const st = smem_f + buf * kSlabArrays * kPts;
-
-        // ---- phase 1: p', fluxes ------------------------------------
-        const float rp = st[0 * kPts + l];
-        const float U[3] = {st[1 * kPts + l], st[2 * kPts + l], st[3 * kPts + l]};
-        const float thp = st[4 * kPts + l];
-        const float th0 = st[16 * kPts + l];
-        const float rho = st[15 * kPts + l] + rp;
-        const float Th = th0 + thp;
-        const float pp = pressure_perturbation_f32(thp, th0, P);
-        const float rinv = __frcp_rn(rho);   // correctly rounded, as 1.0f / rho
-#pragma unroll
-        for (int d = 0; d < 3; ++d) {
-            const float g1 = st[(kFields + 3 * d) * kPts + l];
-            const float g2 = st[(kFields + 3 * d + 1) * kPts + l];
-            const float g3 = st[(kFields + 3 * d + 2) * kPts + l];
-            const float v = fmaf(g3, U[2], fmaf(g2, U[1], g1 * U[0]));
-            const float u = v * rinv;
-            float *F = sF + d * kFields * kBlk + dir_slot<NQ, float>(d, i, j, k);
-            F[0 * kBlk] = v;
-            F[1 * kBlk] = fmaf(U[0], u, g1 * pp);
-            F[2 * kBlk] = fmaf(U[1], u, g2 * pp);
-            F[3 * kBlk] = fmaf(U[2], u, g3 * pp);
-            F[4 * kBlk] = Th * u;
-        }
-        const float Jinv = st[14 * kPts + l];
-        __syncthreads();
-        // This stage is dead now (phase 1 read all of it, and phase 3 uses
-        // registers): refill it with the element S ahead, so that its copies
-        // are in flight during the sweeps and stores.
-        if (l == 0 && e + S * G < e_end) {
-            fence_proxy_async();   // order the generic reads above before the async writes
-            issue_slab(e + S * G, M, q, geo, st, &bar[buf]);
-            pending |= 1u << buf;
-        }
-
-        // ---- phase 2: even-odd sweeps ---------------------------------
-        for (int item = l; item < 3 * kFields * 64; item += kPts)
-            sweep_line<NQ>(sF + (item >> 6) * kBlk, item & 63, P);
-        __syncthreads();
-
-        // ---- phase 3: combine, scale, gravity, store ------------------
-        const int64_t node = e * kPts + l;
-#pragma unroll
-        for (int b = 0; b < kFields; ++b) {
-            const float R = sF[(0 * kFields + b) * kBlk + dir_slot<NQ, float>(0, i, j, k)] +
-                            sF[(1 * kFields + b) * kBlk + dir_slot<NQ, float>(1, i, j, k)] +
-                            sF[(2 * kFields + b) * kBlk + dir_slot<NQ, float>(2, i, j, k)];
-            float v = -Jinv * R;
-            if (b == 3) v = fmaf(-rp, P.grav, v);
-            rhs[b * M + node] = v;
-        }
-        // No barrier here: the barrier after the next wait orders this phase 3's
-        // reads of sF before the next phase 1 writes it.
-        buf = buf + 1 == S ? 0 : buf + 1;
-    }
-    if (failed && l == 0) {
-        atomicOr(err, 1);
-        // Drain the copies still in flight into this CTA's shared memory.
-#pragma unroll
-        for (int b = 0; b < S; ++b)
-            if ((pending >> b) & 1u) bulk_wait(&bar[b], (parity >> b) & 1u);
-    }
-}
-
 template <int NQ, bool TRACERS>
 cudaError_t launch_kernel(ElemRange r, int nf, const MixedGeometry &geo, const MixedParams &P,
-                          const float *q, float *rhs, cudaStream_t s) {
+                          const float *q, float *rhs, int num_sms, cudaStream_t s) {
     constexpr int N3 = NQ * NQ * NQ;
     const size_t smem = sizeof(float) * nf * 3 * block_words<NQ, float>();
-    if (smem > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(vol_rhs_mixed_kernel<NQ, TRACERS>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-    }
-    vol_rhs_mixed_kernel<NQ, TRACERS><<<(unsigned)r.count, N3, smem, s>>>(geo, P, q, rhs, r.M, r.e0,
-                                                                          nf);
+    cudaError_t e = cudaFuncSetAttribute(vol_rhs_mixed_kernel<NQ, TRACERS>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, vol_rhs_mixed_kernel<NQ, TRACERS>,
+                                                      N3, smem);
+    if (e != cudaSuccess) return e;
+    const int64_t ahead = (int64_t)num_sms * (per_sm > 0 ? per_sm : 1);
+    vol_rhs_mixed_kernel<NQ, TRACERS><<<(unsigned)r.count, N3, smem, s>>>(
+        geo, P, q, rhs, r.M, r.e0, nf, r.e0 + r.count, ahead);
     return cudaGetLastError();
 }
 
 template <int NQ>
 cudaError_t launch_nq(ElemRange r, int nf, const MixedGeometry &geo, const MixedParams &P,
-                      const float *q, float *rhs, cudaStream_t s) {
-    if (nf == kFields) return launch_kernel<NQ, false>(r, nf, geo, P, q, rhs, s);
-    return launch_kernel<NQ, true>(r, nf, geo, P, q, rhs, s);
+                      const float *q, float *rhs, int num_sms, cudaStream_t s) {
+    if (nf == kFields) return launch_kernel<NQ, false>(r, nf, geo, P, q, rhs, num_sms, s);
+    return launch_kernel<NQ, true>(r, nf, geo, P, q, rhs, num_sms, s);
 }
 
 __global__ void to_f32_kernel(const double *__restrict__ src, float *__restrict__ dst, int64_t M) {
@@ -287,29 +173,18 @@ cudaError_t launch_to_f32(const double *src, float *dst, int64_t M, cudaStream_t
 }
 
 cudaError_t launch_vol_rhs_mixed(int N, int nf, ElemRange r, const MixedGeometry &geo,
-                                 const MixedParams &P, const float *q, float *rhs, int *err,
-                                 int num_sms, cudaStream_t s) {
+                                 const MixedParams &P, const float *q, float *rhs, int num_sms,
+                                 cudaStream_t s) {
     if (r.count <= 0) return cudaSuccess;
     if (nf < kFields || nf > kMaxFields) return cudaErrorInvalidValue;
-    if (N == 7 && nf == kFields) {   // the staged kernel holds the five fields' slabs
-        cudaError_t e = cudaFuncSetAttribute(vol_rhs_mixed_bulk_kernel,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)kBulkSmem);
-        if (e != cudaSuccess) return e;
-        const int64_t per = kBulkCtasPerSm * (int64_t)num_sms;
-        const int64_t ctas = r.count < per ? r.count : per;
-        vol_rhs_mixed_bulk_kernel<<<(unsigned)ctas, kPts, kBulkSmem, s>>>(
-            geo, P, q, rhs, r.M, r.e0, r.e0 + r.count, err);
-        return cudaGetLastError();
-    }
     switch (N) {
-        case 1: return launch_nq<2>(r, nf, geo, P, q, rhs, s);
-        case 2: return launch_nq<3>(r, nf, geo, P, q, rhs, s);
-        case 3: return launch_nq<4>(r, nf, geo, P, q, rhs, s);
-        case 4: return launch_nq<5>(r, nf, geo, P, q, rhs, s);
-        case 5: return launch_nq<6>(r, nf, geo, P, q, rhs, s);
-        case 6: return launch_nq<7>(r, nf, geo, P, q, rhs, s);
-        case 7: return launch_nq<8>(r, nf, geo, P, q, rhs, s);
+        case 1: return launch_nq<2>(r, nf, geo, P, q, rhs, num_sms, s);
+        case 2: return launch_nq<3>(r, nf, geo, P, q, rhs, num_sms, s);
+        case 3: return launch_nq<4>(r, nf, geo, P, q, rhs, num_sms, s);
+        case 4: return launch_nq<5>(r, nf, geo, P, q, rhs, num_sms, s);
+        case 5: return launch_nq<6>(r, nf, geo, P, q, rhs, num_sms, s);
+        case 6: return launch_nq<7>(r, nf, geo, P, q, rhs, num_sms, s);
+        case 7: return launch_nq<8>(r, nf, geo, P, q, rhs, num_sms, s);
         default: return cudaErrorInvalidValue;
     }
 }

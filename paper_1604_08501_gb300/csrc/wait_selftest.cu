@@ -1,12 +1,11 @@
 // Failure-detection self-test of the bounded device wait.
 //
-// The staged mixed-precision kernel waits on mbarriers for its bulk copies;
-// each wait gives up after a time limit, and the kernel then sets the
-// handle's status word, which numa_vol_status reports as NUMA_ETIMEOUT.
-// numa_vol_selftest_wait makes that wait run out on purpose, without any
-// fault: one thread waits, with the same bulk_wait, on a barrier that nothing
-// arrives at and no copy targets, so nothing is left in flight when it gives
-// up.  The context stays usable.
+// A device-side wait of the library (bulk_wait, on an mbarrier) gives up
+// after a time limit; the kernel then sets the handle's status word, which
+// numa_vol_status reports as NUMA_ETIMEOUT.  numa_vol_selftest_wait makes
+// such a wait run out on purpose, without any fault: one thread waits on a
+// barrier that nothing arrives at and no copy targets, so nothing is left in
+// flight when it gives up.  The context stays usable.
 #include <cuda_runtime.h>
 
 #include <cstdint>

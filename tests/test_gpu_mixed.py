@@ -104,10 +104,10 @@ def test_mixed_host_entry_point_and_large_perturbation():
     assert np.array_equal(host.astype(np.float64), dev)
 
 
-def test_mixed_bulk_kernel_ranges_and_status():
-    # N = 7 runs the persistent bulk-copy kernel; element counts below, at and
-    # above its CTA count (a small multiple of the SM count), several elements
-    # per CTA, and the chunked host path all agree.
+def test_mixed_n7_ranges_prefetch_and_status():
+    # N = 7 runs one CTA per element with an L2 prefetch of the element one
+    # wave of resident CTAs ahead: element counts below, at and above that
+    # wave (a small multiple of the SM count) and the chunked host path agree.
     sms = torch.cuda.get_device_properties(0).multi_processor_count
     for shape in [(1, 1, 1), (7, 5, 3), (sms, 2, 1), (sms, 3, 1), (sms, 7, 1)]:
         w = wl.make_workload(7, shape, seed=90)
@@ -118,13 +118,13 @@ def test_mixed_bulk_kernel_ranges_and_status():
             vt.status()
             host = vt.rhs_host(q32)
         assert np.array_equal(host, dev.cpu().numpy())
-        check(host.astype(np.float64), oracle.vol_rhs_o2(prob, w.q), f"bulk {shape}")
+        check(host.astype(np.float64), oracle.vol_rhs_o2(prob, w.q), f"N=7 {shape}")
 
 
 def test_bounded_wait_runs_out_and_reports_a_status():
-    # The staged kernels' bounded mbarrier wait, made to run out on a barrier
-    # nothing completes (no fault): numa_vol_status reports NUMA_ETIMEOUT, the
-    # status word is cleared, and the handle still computes correct results.
+    # The library's bounded mbarrier wait, made to run out on a barrier nothing
+    # completes (no fault): numa_vol_status reports NUMA_ETIMEOUT, the status
+    # word is cleared, and the handle still computes correct results.
     import time
     w = wl.make_workload(7, (2, 1, 1), seed=91)
     prob = w.problem()
