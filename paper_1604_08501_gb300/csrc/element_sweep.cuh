@@ -53,11 +53,24 @@ __device__ __forceinline__ int slot(int line, int n) {
         return line * NQ + n;
 }
 
+// Slot of point (i, j, k) in direction d's block.  For 4-byte values at Nq = 8
+// (lines of 9 slots) the r and s lines are numbered so that a warp of points
+// (i = 0..7, four consecutive j, one k) touches 32 distinct banks in every
+// direction: r line k + 8 j gives bank 9 k + 8 j + i, s line 4 i + (k & 3) +
+// 32 (k >> 2) gives bank 4 i + j + 9 (k & 3), t line 8 j + i gives bank
+// 9 i + 8 j + k (mod 32).  With the natural numbering (r line 8 k + j, s line
+// 8 k + i) r and s conflict 2-way.  The sweep only needs a bijection of lines.
 template <int NQ, typename T>
 __device__ __forceinline__ int dir_slot(int d, int i, int j, int k) {
-    if (d == 0) return slot<NQ, T>(NQ * k + j, i);
-    if (d == 1) return slot<NQ, T>(NQ * k + i, j);
-    return slot<NQ, T>(NQ * j + i, k);
+    if constexpr (NQ == 8 && sizeof(T) == 4) {
+        if (d == 0) return slot<NQ, T>(k + 8 * j, i);
+        if (d == 1) return slot<NQ, T>(4 * i + (k & 3) + 32 * (k >> 2), j);
+        return slot<NQ, T>(8 * j + i, k);
+    } else {
+        if (d == 0) return slot<NQ, T>(NQ * k + j, i);
+        if (d == 1) return slot<NQ, T>(NQ * k + i, j);
+        return slot<NQ, T>(NQ * j + i, k);
+    }
 }
 
 // Sweep line `line` of buf in place.  De, Do: (Nq/2)^2 row-major; Dc[r] =
