@@ -25,7 +25,8 @@
 // CTAs ahead, so that CTA's loads hit L2 rather than DRAM.  At N = 7 this
 // replaced a persistent kernel that staged each element's arrays in shared
 // memory with cp.async.bulk on an mbarrier: the staging buffer limited that
-// kernel to three CTAs per SM, and it ran at 0.271 against 0.254 ms here.
+// kernel to three CTAs per SM, and it ran at 0.271 against 0.254 ms here
+// (0.242 ms with the line numbering of dir_slot at Nq = 8).
 #include <cuda_runtime.h>
 
 #include "bulk_copy.cuh"
