@@ -49,6 +49,25 @@ __host__ __device__ constexpr int high_threads() {
     return high_tpc<NQ, T>() * NQ * NQ;
 }
 
+// Flux slot of point (i, j, k) in direction d.  A warp of the point phases is
+// 32 consecutive (i, j) columns at one k.  For FP32 at Nq = 16 (lines of 17
+// slots) r line k + 16 j and s line 2 i + (k & 1) + 32 (k >> 1) put the warp on
+// 32 distinct banks in every direction, where the natural numbering of
+// dir_slot takes two wavefronts in r and s; the sweeps only need a bijection
+// of lines.  At Nq = 12 the s numbering 2 i + (k & 1) + 24 (k >> 1) cut the
+// counted wavefronts by a third but measured no faster (the kernel is bound by
+// global-load latency), so the other orders keep dir_slot's numbering.
+template <int NQ, typename T>
+__device__ __forceinline__ int high_slot(int d, int i, int j, int k) {
+    if constexpr (NQ == 16 && sizeof(T) == 4) {
+        if (d == 0) return slot<NQ, T>(k + 16 * j, i);
+        if (d == 1) return slot<NQ, T>(2 * i + (k & 1) + 32 * (k >> 1), j);
+        return slot<NQ, T>(16 * j + i, k);
+    } else {
+        return dir_slot<NQ, T>(d, i, j, k);
+    }
+}
+
 // Fields per pass.  FP64: one (the flux arrays of one field already take
 // 98 KB at Nq = 16).  FP32: as many as fit the shared memory of the CTAs per
 // SM the thread count allows (two CTAs up to 512 threads each), so that fewer
@@ -138,7 +157,7 @@ vol_rhs_high_kernel(typename HighTypes<T>::Geo geo, typename HighTypes<T>::Param
                 const T v = fma(g[2], U[2], fma(g[1], U[1], g[0] * U[0]));
                 const T u = v * rinv;
                 sU[d * N3 + k * NL + c] = u;
-                const int sl = dir_slot<NQ, T>(d, i, j, k);
+                const int sl = high_slot<NQ, T>(d, i, j, k);
 #pragma unroll
                 for (int b = 0; b < G; ++b) {
                     if (b >= nf) break;
@@ -180,7 +199,7 @@ vol_rhs_high_kernel(typename HighTypes<T>::Geo geo, typename HighTypes<T>::Param
                                                      : (b == 2 ? geo.g[3 * d + 1] : geo.g[3 * d + 2]);
                                 F = fma(qb, u, gp[node] * sP[k * NL + c]);
                             }
-                            sF[(gl * 3 + d) * FB + dir_slot<NQ, T>(d, i, j, k)] = F;
+                            sF[(gl * 3 + d) * FB + high_slot<NQ, T>(d, i, j, k)] = F;
                         }
                     }
                 }
@@ -205,8 +224,8 @@ vol_rhs_high_kernel(typename HighTypes<T>::Geo geo, typename HighTypes<T>::Param
             if (k < NQ) {
                 const int64_t node = node0 + k * NL;
                 const T jinv = geo.Jinv[node];
-                const int s0 = dir_slot<NQ, T>(0, i, j, k), s1 = dir_slot<NQ, T>(1, i, j, k),
-                          s2 = dir_slot<NQ, T>(2, i, j, k);
+                const int s0 = high_slot<NQ, T>(0, i, j, k), s1 = high_slot<NQ, T>(1, i, j, k),
+                          s2 = high_slot<NQ, T>(2, i, j, k);
 #pragma unroll
                 for (int gl = 0; gl < G; ++gl) {
                     if (gl >= gn) break;
