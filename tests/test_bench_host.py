@@ -73,3 +73,21 @@ def test_cpu_baseline_records_all_cores_and_one_core():
     assert d["single_core"]["cores"] == 1 and d["single_core"]["value"] > 0
     assert d["parity_workload"]["points"] == 8 * 8 and d["parity_workload"]["value"] > 0
     assert isinstance(d["cpu_model"], str) and d["cpu_model"]
+
+
+def test_traffic_record_is_dropped_once_a_source_changes(tmp_path, monkeypatch):
+    # A DRAM-traffic record counts only while the kernel's sources hash as they
+    # did when the counters were taken; comment edits do not count as changes.
+    src = tmp_path / "k.cu"
+    src.write_text("__global__ void k(float *x) { x[0] = 1.f; }  // first\n")
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    (tmp_path / "profiles").mkdir()
+    rec = {"k": {"dram_bytes_per_launch": 123.0, "sources": ["k.cu"],
+                 "sources_sha": bench.sources_sha(["k.cu"])}}
+    (tmp_path / "profiles" / "traffic.json").write_text(json.dumps(rec))
+    assert bench.load_traffic("k") == 123.0
+    src.write_text("/* a note */ __global__ void k(float *x) {\n x[0] = 1.f; }  // edited\n")
+    assert bench.load_traffic("k") == 123.0
+    assert bench.load_traffic("other") is None
+    src.write_text("__global__ void k(float *x) { x[0] = 2.f; }\n")
+    assert bench.load_traffic("k") is None
