@@ -479,8 +479,11 @@ def run_batched(args):
     works = [wl.integration_workload(N, n, seed) for N, n, seed in plan]
     nsteps, dt = 10, 0.01
     out = {}
-    for prec in args.precisions:
-        if prec not in ("fp64", "mixed"):
+    for name in args.precisions:
+        # "mixed-tc": the mixed batch with its D sums on the tensor cores
+        prec, sweep = {"fp64": ("fp64", "cuda_cores"), "mixed": ("mixed", "cuda_cores"),
+                       "mixed-tc": ("mixed", "tensor_tf32")}.get(name, (None, None))
+        if prec is None:
             continue
         vts, states, points = [], [], 0
         for w in works:
@@ -488,7 +491,7 @@ def run_batched(args):
             q0 = w.q_mixed() if prec == "mixed" else w.q
             states.append(torch.from_numpy(q0).to(dev))
             points += w.M
-        b = Batch(prec)
+        b = Batch(prec, sweep=sweep)
         for vt, q in zip(vts, states):
             b.add(vt, q)
         b.autotune()
@@ -523,8 +526,9 @@ def run_batched(args):
         ms = sum(t0.elapsed_time(t1) for t0, t1 in ev) / args.steps
         evals = points * 5 * nsteps
         value, tmax = aggregate(evals * args.steps, ms * 1e-3 * args.steps, dev)
-        out[prec] = {"value": value / 1e9, "ms_per_launch": tmax * 1e3 / args.steps,
-                     "points": points, "instances": len(plan),
+        b.status()
+        out[name] = {"value": value / 1e9, "ms_per_launch": tmax * 1e3 / args.steps,
+                     "points": points, "instances": len(plan), "sweep": sweep,
                      "tiles": {str(nq): b.tile(nq) for nq in (4, 5, 6, 8)}, "clocks": clocks}
         b.close()
         for vt in vts:
@@ -537,7 +541,8 @@ def run_batched(args):
                 "value": out[head]["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": out[head]["ms_per_launch"],
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-                "dtype": {"fp64": "f64", "mixed": "f32 (perturbation state)"}[head],
+                "dtype": {"fp64": "f64", "mixed": "f32 (perturbation state)",
+                          "mixed-tc": "f32 (perturbation state), TF32 split products"}[head],
                 "data": "synthetic",
                 "config": {"workload": f"{len(plan)} instances, N in {{3,4,5,7}}, 512..32768 elements "
                                        f"(log-uniform, cubes), smooth velocities (peak 10 m/s), "
@@ -617,7 +622,8 @@ def run_nq_sweep(args):
                 "value": per[ref_nq][head]["gdofs"], "unit": UNIT, "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": per[ref_nq][head]["ms"],
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-                "dtype": {"fp64": "f64", "mixed": "f32 (perturbation state)"}[head],
+                "dtype": {"fp64": "f64", "mixed": "f32 (perturbation state)",
+                          "mixed-tc": "f32 (perturbation state), TF32 split products"}[head],
                 "data": "synthetic",
                 "config": {"workload": "warped 10 km box, 3,538,944 points at Nq = 4, 8, 12, 16 "
                                        "(48x48x24, 24x24x12, 16x16x8, 12x12x6 elements), seed 1",
@@ -749,7 +755,8 @@ def run_serving(args):
                 "value": out[head]["value"], "unit": UNIT, "n_gpus": world, "steps": total,
                 "warmup": args.warmup, "ms_per_step": out[head]["span_s"] * 1e3 / total,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-                "dtype": {"fp64": "f64", "mixed": "f32 (perturbation state)"}[head],
+                "dtype": {"fp64": "f64", "mixed": "f32 (perturbation state)",
+                          "mixed-tc": "f32 (perturbation state), TF32 split products"}[head],
                 "data": "synthetic",
                 "config": {"workload": f"Poisson arrivals at {args.rate:g} req/s, {total} requests, "
                                        f"each one of {len(plan)} instances (N in {{3,4,5,7}}, "

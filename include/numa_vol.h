@@ -287,6 +287,36 @@ int numa_batch_autotune(numa_batch *b, void *stream);
 /* Elements per work item the batch uses for order Nq (2..8). */
 int numa_batch_tile(const numa_batch *b, int nq);
 
+/*
+ * How a NUMA_MIXED batch evaluates the three D sums of the volume term
+ * (Sec. 2, Eq. (2)):
+ *   NUMA_SWEEP_CUDA_CORES   FP32 FMAs on the CUDA cores, the even-odd split of
+ *                           D (the default; relative error about 2^-24 times
+ *                           the sums' condition number);
+ *   NUMA_SWEEP_TENSOR_TF32  TF32 split products on the tensor cores (tcgen05)
+ *                           with FP32 accumulation in tensor memory: each flux
+ *                           and each entry of D is a TF32 head plus an FP32
+ *                           tail, and the sums take head x head, head x tail
+ *                           and tail x head (relative error about 2^-21 times
+ *                           the condition number).
+ * The choice applies from the next numa_batch_advance.  NUMA_FP64 batches take
+ * NUMA_SWEEP_CUDA_CORES only (tcgen05 has no FP64 kind).
+ * Errors: NUMA_EINVAL (NULL batch or unknown value), NUMA_EUNSUPPORTED.
+ */
+typedef enum { NUMA_SWEEP_CUDA_CORES = 0, NUMA_SWEEP_TENSOR_TF32 = 1 } numa_sweep;
+int numa_batch_set_sweep(numa_batch *b, numa_sweep sweep);
+
+/* The batch's current sweep (a numa_sweep value), or -1 for a NULL batch. */
+int numa_batch_sweep(const numa_batch *b);
+
+/*
+ * Read and clear the batch's device status word, after the work on `stream`
+ * has finished (synchronous).  NUMA_ETIMEOUT: a launch's bounded wait for the
+ * tensor core ran out; that launch stopped early and the states it was
+ * advancing are not valid.  NUMA_OK otherwise.  Errors: NUMA_EINVAL, NUMA_ECUDA.
+ */
+int numa_batch_status(numa_batch *b, void *stream);
+
 /* Message for the last batch error on the calling thread. */
 const char *numa_batch_last_error(void);
 

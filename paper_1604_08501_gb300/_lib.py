@@ -15,6 +15,7 @@ NUMA_NOALLOC_MAX_INSTANCES = 64
 NUMA_MAX_N = 7
 NUMA_MAX_N_FP64 = 15
 NUMA_FP64, NUMA_MIXED, NUMA_DF64 = 0, 1, 2
+NUMA_SWEEP_CUDA_CORES, NUMA_SWEEP_TENSOR_TF32 = 0, 1
 
 _ERRNAMES = {NUMA_EINVAL: "NUMA_EINVAL", NUMA_ENOMEM: "NUMA_ENOMEM",
              NUMA_ECUDA: "NUMA_ECUDA", NUMA_EUNSUPPORTED: "NUMA_EUNSUPPORTED",
@@ -93,6 +94,9 @@ def load() -> C.CDLL:
     lib.numa_batch_advance.argtypes = [C.c_void_p, C.c_int, C.c_double, C.c_void_p]
     lib.numa_batch_autotune.argtypes = [C.c_void_p, C.c_void_p]
     lib.numa_batch_tile.argtypes = [C.c_void_p, C.c_int]
+    lib.numa_batch_set_sweep.argtypes = [C.c_void_p, C.c_int]
+    lib.numa_batch_sweep.argtypes = [C.c_void_p]
+    lib.numa_batch_status.argtypes = [C.c_void_p, C.c_void_p]
     lib.numa_batch_last_error.restype = C.c_char_p
     lib.numa_batch_destroy.argtypes = [C.c_void_p]
     lib.numa_batch_destroy.restype = None
@@ -121,7 +125,8 @@ def load() -> C.CDLL:
                                                C.c_int, C.c_double, C.c_void_p]
     lib.numa_batch_advance_noalloc.restype = C.c_int
     for name in ("numa_batch_create", "numa_batch_add", "numa_batch_clear", "numa_batch_size",
-                 "numa_batch_advance", "numa_batch_autotune", "numa_batch_tile"):
+                 "numa_batch_advance", "numa_batch_autotune", "numa_batch_tile",
+                 "numa_batch_set_sweep", "numa_batch_sweep", "numa_batch_status"):
         getattr(lib, name).restype = C.c_int
     _lib = lib
     return lib

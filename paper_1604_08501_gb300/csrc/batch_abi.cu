@@ -47,6 +47,7 @@ struct numa_batch {
     int num_sms = 0;
     std::vector<numa::BatchInstance> inst;
     int tile_mult[9] = {4, 4, 4, 4, 4, 4, 4, 4, 4};   // elements per item / elements per pass, by Nq
+    bool tensor = false;   // NUMA_SWEEP_TENSOR_TF32 (mixed only)
     // device scratch: instance table, work items, claim counter
     numa::BatchInstance *d_inst = nullptr;
     size_t inst_cap = 0;
@@ -150,6 +151,7 @@ int numa_batch_create(numa_precision prec, numa_batch **out) {
         e = cudaDeviceGetAttribute(&b->num_sms, cudaDevAttrMultiProcessorCount, b->device);
     if (e == cudaSuccess) e = numa::prepare_batch_lsrk();
     if (e == cudaSuccess) e = cudaMalloc(&b->d_counter, 256);
+    if (e == cudaSuccess) e = cudaMemset(b->d_counter, 0, 256);   // [0] claims, [1] status
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->launched, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventRecord(b->launched, b->cap_stream);
@@ -220,7 +222,8 @@ int numa_batch_advance(numa_batch *b, int nsteps, double dt, void *stream) {
         if (e == cudaSuccess) e = cudaMemsetAsync(b->d_counter, 0, sizeof(int), b->cap_stream);
         if (e == cudaSuccess)
             e = numa::launch_batch_lsrk(b->prec == NUMA_MIXED, b->d_inst, b->d_items, b->num_items,
-                                        b->d_counter, kLsrk, nsteps, dt, grid_of(b), b->cap_stream);
+                                        b->d_counter, kLsrk, nsteps, dt, grid_of(b), b->cap_stream,
+                                        b->tensor);
         cudaGraph_t g = nullptr;
         const cudaError_t e2 = cudaStreamEndCapture(b->cap_stream, &g);
         if (e == cudaSuccess) e = e2;
@@ -279,7 +282,7 @@ int numa_batch_autotune(numa_batch *b, void *stream) {
                 if (e == cudaSuccess)
                     e = numa::launch_batch_lsrk(b->prec == NUMA_MIXED, b->d_inst, b->d_items,
                                                 b->num_items, b->d_counter, kLsrk, 1, 1e-6,
-                                                grid_of(b), s);
+                                                grid_of(b), s, b->tensor);
                 if (e == cudaSuccess) e = cudaEventRecord(t1, s);
                 if (e == cudaSuccess) e = cudaEventRecord(b->launched, s);
                 if (e == cudaSuccess) e = cudaEventSynchronize(t1);
@@ -299,6 +302,42 @@ int numa_batch_autotune(numa_batch *b, void *stream) {
     if (t1) cudaEventDestroy(t1);
     b->dirty = true;   // the work list is rebuilt with the chosen tiles
     if (e != cudaSuccess) return bfail_cuda(e, "numa_batch_autotune");
+    return NUMA_OK;
+}
+
+int numa_batch_set_sweep(numa_batch *b, numa_sweep sweep) {
+    g_batch_error.clear();
+    if (!b) return bfail(NUMA_EINVAL, "numa_batch_set_sweep: NULL batch");
+    if (sweep != NUMA_SWEEP_CUDA_CORES && sweep != NUMA_SWEEP_TENSOR_TF32)
+        return bfail(NUMA_EINVAL, "numa_batch_set_sweep: unknown sweep");
+    if (sweep == NUMA_SWEEP_TENSOR_TF32 && b->prec != NUMA_MIXED)
+        return bfail(NUMA_EUNSUPPORTED,
+                     "numa_batch_set_sweep: the tensor-core sweep is for NUMA_MIXED batches");
+    const bool t = sweep == NUMA_SWEEP_TENSOR_TF32;
+    if (t != b->tensor) {
+        b->tensor = t;
+        drop_graph(b);   // the next advance captures the other kernel
+    }
+    return NUMA_OK;
+}
+
+int numa_batch_sweep(const numa_batch *b) {
+    if (!b) return -1;
+    return b->tensor ? NUMA_SWEEP_TENSOR_TF32 : NUMA_SWEEP_CUDA_CORES;
+}
+
+int numa_batch_status(numa_batch *b, void *stream) {
+    g_batch_error.clear();
+    if (!b) return bfail(NUMA_EINVAL, "numa_batch_status: NULL batch");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    int word = 0;
+    cudaError_t e = cudaMemcpyAsync(&word, b->d_counter + 1, sizeof(int), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e == cudaSuccess && word != 0) e = cudaMemsetAsync(b->d_counter + 1, 0, sizeof(int), s);
+    if (e == cudaSuccess && word != 0) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return bfail_cuda(e, "numa_batch_status");
+    if (word & 1)
+        return bfail(NUMA_ETIMEOUT, "numa_batch_status: a wait for the tensor core ran out");
     return NUMA_OK;
 }
 

@@ -26,6 +26,7 @@
 #include <mutex>
 
 #include "batch_tile.cuh"
+#include "batch_tile_tc.cuh"
 
 namespace numa {
 
@@ -69,6 +70,71 @@ batch_lsrk_kernel(const BatchInstance *__restrict__ inst, const BatchItem *__res
     }
 }
 
+
+// Mixed precision with the D contractions on the tensor cores (batch_tile_tc.cuh).
+// counter[1] is the batch's status word: bit 0 is set when a wait for the
+// tensor core ran out; the CTA then stops claiming work.
+__global__ void __launch_bounds__(kThreads, 2)
+batch_lsrk_tc_kernel(const BatchInstance *__restrict__ inst, const BatchItem *__restrict__ items,
+                     int num_items, int *counter, LsrkCoef co, int nsteps, double dt) {
+    extern __shared__ __align__(1024) unsigned char smem_tc[];
+    __shared__ BatchInstance sI;
+    __shared__ int s_item, s_nq;
+    __shared__ float sco[10];
+    __shared__ __align__(8) uint64_t bar;
+    __shared__ uint32_t s_tmem;
+    load_stage_coefficients<true>(co, sco);
+    if (threadIdx.x < 32) tc::tmem_alloc(&s_tmem, kTcCols);
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        fence_mbar_init();
+        s_nq = 0;
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tmem = s_tmem;
+    uint32_t phase = 0;
+    bool ok = true;
+    for (;;) {
+        if (threadIdx.x == 0) s_item = atomicAdd(counter, 1);
+        __syncthreads();
+        const int it = s_item;
+        if (it >= num_items) break;
+        const BatchItem item = items[it];
+        {
+            const int *src = reinterpret_cast<const int *>(inst + item.instance);
+            int *dst = reinterpret_cast<int *>(&sI);
+            for (int w = threadIdx.x; w < (int)(sizeof(BatchInstance) / sizeof(int)); w += kThreads)
+                dst[w] = src[w];
+        }
+        __syncthreads();
+        const int ns = sI.nsteps > 0 ? sI.nsteps : nsteps;
+        switch (item.nq) {
+            case 2: ok = run_tile_tc<2>(sI, item.e0, item.count, sco, ns, dt, smem_tc, tmem, &bar, phase, &s_nq); break;
+            case 3: ok = run_tile_tc<3>(sI, item.e0, item.count, sco, ns, dt, smem_tc, tmem, &bar, phase, &s_nq); break;
+            case 4: ok = run_tile_tc<4>(sI, item.e0, item.count, sco, ns, dt, smem_tc, tmem, &bar, phase, &s_nq); break;
+            case 5: ok = run_tile_tc<5>(sI, item.e0, item.count, sco, ns, dt, smem_tc, tmem, &bar, phase, &s_nq); break;
+            case 6: ok = run_tile_tc<6>(sI, item.e0, item.count, sco, ns, dt, smem_tc, tmem, &bar, phase, &s_nq); break;
+            case 7: ok = run_tile_tc<7>(sI, item.e0, item.count, sco, ns, dt, smem_tc, tmem, &bar, phase, &s_nq); break;
+            case 8: ok = run_tile_tc<8>(sI, item.e0, item.count, sco, ns, dt, smem_tc, tmem, &bar, phase, &s_nq); break;
+            default: break;
+        }
+        __syncthreads();   // sI and s_item are rewritten by the next claim
+        if (!ok) break;    // uniform: run_tile_tc decides it with a barrier
+    }
+    if (!ok) {
+        if (threadIdx.x == 0) atomicOr(counter + 1, 1);
+        bulk_wait(&bar, phase);   // the MMAs in flight, bounded again
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        tc::fence_after_sync();
+        tc::tmem_dealloc(tmem, kTcCols);
+    }
+}
+
 }  // namespace
 
 cudaError_t prepare_batch_lsrk() {
@@ -83,6 +149,7 @@ cudaError_t prepare_batch_lsrk() {
         std::lock_guard<std::mutex> lock(mu);
         if (!uploaded[dev]) {
             e = upload_sweep_tables();
+            if (e == cudaSuccess) e = upload_tc_tables();
             if (e != cudaSuccess) return e;
             uploaded[dev] = true;
         }
@@ -90,15 +157,21 @@ cudaError_t prepare_batch_lsrk() {
     e = cudaFuncSetAttribute(batch_lsrk_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)tile_smem_bytes<false>());
     if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(batch_lsrk_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)tile_smem_bytes<true>());
+    e = cudaFuncSetAttribute(batch_lsrk_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)tile_smem_bytes<true>());
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(batch_lsrk_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                kTcSmemBytes);
 }
 
 cudaError_t launch_batch_lsrk(bool mixed, const BatchInstance *inst, const BatchItem *items,
                               int num_items, int *counter, const LsrkCoef &co, int nsteps,
-                              double dt, int num_sms, cudaStream_t s) {
+                              double dt, int num_sms, cudaStream_t s, bool tensor) {
     if (num_items <= 0 || nsteps <= 0) return cudaSuccess;
-    if (mixed)
+    if (mixed && tensor)
+        batch_lsrk_tc_kernel<<<num_sms * 2, kThreads, kTcSmemBytes, s>>>(inst, items, num_items,
+                                                                         counter, co, nsteps, dt);
+    else if (mixed)
         batch_lsrk_kernel<true><<<num_sms * tile_ctas_per_sm<true>(), kThreads,
                                   tile_smem_bytes<true>(), s>>>(inst, items, num_items, counter,
                                                                 co, nsteps, dt);

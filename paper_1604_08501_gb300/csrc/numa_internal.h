@@ -92,10 +92,12 @@ struct LsrkCoef {
 // prepare_batch_lsrk() sets the kernels' shared-memory opt-in on the current
 // device; call it before the first launch (and outside stream capture).
 cudaError_t prepare_batch_lsrk();
-// The grid is num_sms times the CTAs per SM the kernel is built for.
+// The grid is num_sms times the CTAs per SM the kernel is built for.  tensor
+// (mixed only): the D contractions as TF32 split products on the tensor
+// cores (batch_tile_tc.cuh); counter[1] then receives its status bits.
 cudaError_t launch_batch_lsrk(bool mixed, const BatchInstance *inst, const BatchItem *items,
                               int num_items, int *counter, const LsrkCoef &co, int nsteps,
-                              double dt, int num_sms, cudaStream_t s);
+                              double dt, int num_sms, cudaStream_t s, bool tensor = false);
 
 // Elements one CTA pass holds for order Nq (512 threads, one per point).
 inline int elements_per_pass(int nq) { return 512 / (nq * nq * nq); }

@@ -16,7 +16,8 @@ import ctypes as C
 import numpy as np
 
 from . import _lib
-from ._lib import (NUMA_DF64, NUMA_FP64, NUMA_MIXED, NumaError, check, check_batch,
+from ._lib import (NUMA_DF64, NUMA_FP64, NUMA_MIXED, NUMA_SWEEP_CUDA_CORES,
+                   NUMA_SWEEP_TENSOR_TF32, NumaError, check, check_batch,
                    check_engine)
 
 NFIELDS = 5
@@ -192,13 +193,31 @@ class Batch:
     """Batched low-storage Runge-Kutta integration of many VolumeTerm instances
     (numa_batch_*).  States are CUDA tensors the batch updates in place."""
 
-    def __init__(self, precision: str = "fp64"):
+    SWEEPS = {"cuda_cores": NUMA_SWEEP_CUDA_CORES, "tensor_tf32": NUMA_SWEEP_TENSOR_TF32}
+
+    def __init__(self, precision: str = "fp64", sweep: str = "cuda_cores"):
         self.precision = precision
         h = C.c_void_p()
         prec = {"fp64": NUMA_FP64, "mixed": NUMA_MIXED}[precision]
         check_batch(_lib.load().numa_batch_create(prec, C.byref(h)))
         self._h = h
         self._keep = []          # (VolumeTerm, state) pairs the device table points to
+        if sweep != "cuda_cores":
+            self.sweep = sweep
+
+    @property
+    def sweep(self) -> str:
+        """How the D sums are evaluated: "cuda_cores" or "tensor_tf32" (mixed only)."""
+        v = _lib.load().numa_batch_sweep(self.handle)
+        return {NUMA_SWEEP_CUDA_CORES: "cuda_cores", NUMA_SWEEP_TENSOR_TF32: "tensor_tf32"}[v]
+
+    @sweep.setter
+    def sweep(self, name: str) -> None:
+        check_batch(_lib.load().numa_batch_set_sweep(self.handle, self.SWEEPS[name]))
+
+    def status(self, stream=None) -> None:
+        """Raise NumaError(NUMA_ETIMEOUT) if a launch's bounded device wait ran out."""
+        check_batch(_lib.load().numa_batch_status(self.handle, C.c_void_p(self._stream(stream))))
 
     @property
     def handle(self) -> int:

@@ -94,19 +94,21 @@ def element_problem(w, e):
     return prob, np.ascontiguousarray(w.q[:, sl]), sl
 
 
-@pytest.mark.parametrize("precision", ["fp64", "mixed"])
-def test_batched_full_plan_on_sampled_elements(plan_works, precision):
+@pytest.mark.parametrize("precision,sweep", [("fp64", "cuda_cores"), ("mixed", "cuda_cores"),
+                                             ("mixed", "tensor_tf32")])
+def test_batched_full_plan_on_sampled_elements(plan_works, precision, sweep):
     vts, states = [], []
     for w in plan_works:
         vts.append(VolumeTerm.from_problem(w.problem(), precision=precision))
         q0 = w.q_mixed() if precision == "mixed" else w.q
         states.append(torch.from_numpy(np.ascontiguousarray(q0)).cuda())
     assert sum(w.M for w in plan_works) == 106_757_616
-    with Batch(precision) as b:
+    with Batch(precision, sweep=sweep) as b:
         for vt, q in zip(vts, states):
             b.add(vt, q)
         b.autotune()
         b.advance(NSTEPS, DT)
+        b.status()
         torch.cuda.synchronize()
     mixed = precision == "mixed"
     u = 2.0 ** -24 if mixed else 2.0 ** -53
