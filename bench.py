@@ -481,8 +481,10 @@ def run_batched(args):
     out = {}
     for name in args.precisions:
         # "mixed-tc": the mixed batch with its D sums on the tensor cores
+        # "mixed-auto": the autotuner picks the sweep per order
         prec, sweep = {"fp64": ("fp64", "cuda_cores"), "mixed": ("mixed", "cuda_cores"),
-                       "mixed-tc": ("mixed", "tensor_tf32")}.get(name, (None, None))
+                       "mixed-tc": ("mixed", "tensor_tf32"),
+                       "mixed-auto": ("mixed", "auto")}.get(name, (None, None))
         if prec is None:
             continue
         vts, states, points = [], [], 0
@@ -527,9 +529,17 @@ def run_batched(args):
         evals = points * 5 * nsteps
         value, tmax = aggregate(evals * args.steps, ms * 1e-3 * args.steps, dev)
         b.status()
+        cfg = b.config()
+        present = sorted({w.N + 1 for w in works})
         out[name] = {"value": value / 1e9, "ms_per_launch": tmax * 1e3 / args.steps,
                      "points": points, "instances": len(plan), "sweep": sweep,
-                     "tiles": {str(nq): b.tile(nq) for nq in (4, 5, 6, 8)}, "clocks": clocks}
+                     "autotuned": {"tile_elements_by_nq": {str(nq): cfg["tile"][nq] for nq in present},
+                                   "sweep_by_nq": {str(nq): cfg["sweep"][nq] for nq in present},
+                                   "ctas_per_sm": cfg["ctas_per_sm"] or "max",
+                                   "costliest_first": cfg["costliest_first"],
+                                   "tuned_ms_per_step": round(cfg["tuned_ms_per_step"], 4),
+                                   "candidates_timed": cfg["tuned_candidates"]},
+                     "clocks": clocks}
         b.close()
         for vt in vts:
             vt.close()
@@ -542,7 +552,8 @@ def run_batched(args):
                 "warmup": args.warmup, "ms_per_step": out[head]["ms_per_launch"],
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
                 "dtype": {"fp64": "f64", "mixed": "f32 (perturbation state)",
-                          "mixed-tc": "f32 (perturbation state), TF32 split products"}[head],
+                          "mixed-tc": "f32 (perturbation state), TF32 split products",
+                          "mixed-auto": "f32 (perturbation state)"}[head],
                 "data": "synthetic",
                 "config": {"workload": f"{len(plan)} instances, N in {{3,4,5,7}}, 512..32768 elements "
                                        f"(log-uniform, cubes), smooth velocities (peak 10 m/s), "
@@ -623,7 +634,8 @@ def run_nq_sweep(args):
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": per[ref_nq][head]["ms"],
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
                 "dtype": {"fp64": "f64", "mixed": "f32 (perturbation state)",
-                          "mixed-tc": "f32 (perturbation state), TF32 split products"}[head],
+                          "mixed-tc": "f32 (perturbation state), TF32 split products",
+                          "mixed-auto": "f32 (perturbation state)"}[head],
                 "data": "synthetic",
                 "config": {"workload": "warped 10 km box, 3,538,944 points at Nq = 4, 8, 12, 16 "
                                        "(48x48x24, 24x24x12, 16x16x8, 12x12x6 elements), seed 1",
@@ -756,7 +768,8 @@ def run_serving(args):
                 "warmup": args.warmup, "ms_per_step": out[head]["span_s"] * 1e3 / total,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
                 "dtype": {"fp64": "f64", "mixed": "f32 (perturbation state)",
-                          "mixed-tc": "f32 (perturbation state), TF32 split products"}[head],
+                          "mixed-tc": "f32 (perturbation state), TF32 split products",
+                          "mixed-auto": "f32 (perturbation state)"}[head],
                 "data": "synthetic",
                 "config": {"workload": f"Poisson arrivals at {args.rate:g} req/s, {total} requests, "
                                        f"each one of {len(plan)} instances (N in {{3,4,5,7}}, "

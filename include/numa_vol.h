@@ -280,9 +280,40 @@ int numa_batch_size(const numa_batch *b);
  * NUMA_ENOMEM, NUMA_ECUDA. */
 int numa_batch_advance(numa_batch *b, int nsteps, double dt, void *stream);
 
-/* Choose the elements per work item for each order present by timing one
- * step on copies of the current states (synchronous; states unchanged). */
+/* Choose the launch configuration (numa_batch_config below) by timing
+ * launches of two steps on copies of the current states, best of three per
+ * candidate (synchronous; states unchanged).  First each order alone over its
+ * tiles (1, 2, 4, 8, 16 or 32 passes of 512 threads per work item), and under
+ * NUMA_SWEEP_AUTO over both sweeps; then, in the launch the batch actually
+ * runs (all orders together), one round of coordinate descent over each
+ * order's candidates, the CTAs per SM of the persistent grid and the order of
+ * the work items, keeping a change that saves at least 1 %. */
 int numa_batch_autotune(numa_batch *b, void *stream);
+
+/* Launch configuration of a batch.  Indices are Nq = N + 1 (2..8; 0 and 1
+ * unused). */
+typedef struct {
+    int tile[9];               /* elements per work item: a positive multiple of
+                                  512 / Nq^3 (the elements one pass of 512
+                                  threads holds) */
+    int sweep[9];              /* NUMA_SWEEP_CUDA_CORES or NUMA_SWEEP_TENSOR_TF32 */
+    int ctas_per_sm;           /* CTAs per SM of the persistent grid: 1 .. 2
+                                  (NUMA_MIXED) or 1 (NUMA_FP64); 0 = the most */
+    int costliest_first;       /* nonzero: work items sorted by points, largest
+                                  first (else instance by instance) */
+    double tuned_ms_per_step;  /* read only: the last autotune's time for one
+                                  step of the chosen configuration (0: none) */
+    int tuned_candidates;      /* read only: launches the last autotune timed */
+} numa_batch_config;
+
+/* Read the current configuration.  Errors: NUMA_EINVAL. */
+int numa_batch_get_config(const numa_batch *b, numa_batch_config *out);
+
+/* Set tiles, sweeps, CTAs per SM and item order (the read-only fields are
+ * ignored); applies from the next numa_batch_advance.  Errors: NUMA_EINVAL
+ * (a field out of range), NUMA_EUNSUPPORTED (a tensor-core sweep in a
+ * NUMA_FP64 batch). */
+int numa_batch_set_config(numa_batch *b, const numa_batch_config *c);
 
 /* Elements per work item the batch uses for order Nq (2..8). */
 int numa_batch_tile(const numa_batch *b, int nq);
@@ -298,16 +329,27 @@ int numa_batch_tile(const numa_batch *b, int nq);
  *                           and each entry of D is a TF32 head plus an FP32
  *                           tail, and the sums take head x head, head x tail
  *                           and tail x head (relative error about 2^-21 times
- *                           the condition number).
+ *                           the condition number), for every order;
+ *   NUMA_SWEEP_AUTO         numa_batch_autotune times both for each order
+ *                           present and keeps the faster (until it runs, the
+ *                           previous choice per order stands).
  * The choice applies from the next numa_batch_advance.  NUMA_FP64 batches take
  * NUMA_SWEEP_CUDA_CORES only (tcgen05 has no FP64 kind).
  * Errors: NUMA_EINVAL (NULL batch or unknown value), NUMA_EUNSUPPORTED.
  */
-typedef enum { NUMA_SWEEP_CUDA_CORES = 0, NUMA_SWEEP_TENSOR_TF32 = 1 } numa_sweep;
+typedef enum {
+    NUMA_SWEEP_CUDA_CORES = 0,
+    NUMA_SWEEP_TENSOR_TF32 = 1,
+    NUMA_SWEEP_AUTO = 2
+} numa_sweep;
 int numa_batch_set_sweep(numa_batch *b, numa_sweep sweep);
 
-/* The batch's current sweep (a numa_sweep value), or -1 for a NULL batch. */
+/* The sweep mode last set (a numa_sweep value), or -1 for a NULL batch. */
 int numa_batch_sweep(const numa_batch *b);
+
+/* The sweep order Nq (2..8) uses now: NUMA_SWEEP_CUDA_CORES or
+ * NUMA_SWEEP_TENSOR_TF32; -1 for a NULL batch or an Nq outside 2..8. */
+int numa_batch_sweep_of(const numa_batch *b, int nq);
 
 /*
  * Read and clear the batch's device status word, after the work on `stream`

@@ -15,7 +15,7 @@ NUMA_NOALLOC_MAX_INSTANCES = 64
 NUMA_MAX_N = 7
 NUMA_MAX_N_FP64 = 15
 NUMA_FP64, NUMA_MIXED, NUMA_DF64 = 0, 1, 2
-NUMA_SWEEP_CUDA_CORES, NUMA_SWEEP_TENSOR_TF32 = 0, 1
+NUMA_SWEEP_CUDA_CORES, NUMA_SWEEP_TENSOR_TF32, NUMA_SWEEP_AUTO = 0, 1, 2
 
 _ERRNAMES = {NUMA_EINVAL: "NUMA_EINVAL", NUMA_ENOMEM: "NUMA_ENOMEM",
              NUMA_ECUDA: "NUMA_ECUDA", NUMA_EUNSUPPORTED: "NUMA_EUNSUPPORTED",
@@ -46,6 +46,12 @@ class numa_engine_counters(C.Structure):
     _fields_ = [("queued", C.c_int), ("resident", C.c_int), ("bytes_used", C.c_size_t),
                 ("bytes_budget", C.c_size_t), ("completed", C.c_int64), ("rounds", C.c_int64),
                 ("point_stages", C.c_double)]
+
+
+class numa_batch_config(C.Structure):
+    _fields_ = [("tile", C.c_int * 9), ("sweep", C.c_int * 9), ("ctas_per_sm", C.c_int),
+                ("costliest_first", C.c_int), ("tuned_ms_per_step", C.c_double),
+                ("tuned_candidates", C.c_int)]
 
 
 NUMA_REQ_QUEUED, NUMA_REQ_RUNNING, NUMA_REQ_DONE, NUMA_REQ_CANCELLED = 0, 1, 2, 3
@@ -96,7 +102,10 @@ def load() -> C.CDLL:
     lib.numa_batch_tile.argtypes = [C.c_void_p, C.c_int]
     lib.numa_batch_set_sweep.argtypes = [C.c_void_p, C.c_int]
     lib.numa_batch_sweep.argtypes = [C.c_void_p]
+    lib.numa_batch_sweep_of.argtypes = [C.c_void_p, C.c_int]
     lib.numa_batch_status.argtypes = [C.c_void_p, C.c_void_p]
+    lib.numa_batch_get_config.argtypes = [C.c_void_p, C.POINTER(numa_batch_config)]
+    lib.numa_batch_set_config.argtypes = [C.c_void_p, C.POINTER(numa_batch_config)]
     lib.numa_batch_last_error.restype = C.c_char_p
     lib.numa_batch_destroy.argtypes = [C.c_void_p]
     lib.numa_batch_destroy.restype = None
@@ -126,7 +135,8 @@ def load() -> C.CDLL:
     lib.numa_batch_advance_noalloc.restype = C.c_int
     for name in ("numa_batch_create", "numa_batch_add", "numa_batch_clear", "numa_batch_size",
                  "numa_batch_advance", "numa_batch_autotune", "numa_batch_tile",
-                 "numa_batch_set_sweep", "numa_batch_sweep", "numa_batch_status"):
+                 "numa_batch_set_sweep", "numa_batch_sweep", "numa_batch_sweep_of",
+                 "numa_batch_status", "numa_batch_get_config", "numa_batch_set_config"):
         getattr(lib, name).restype = C.c_int
     _lib = lib
     return lib

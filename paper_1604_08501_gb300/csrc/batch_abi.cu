@@ -47,7 +47,12 @@ struct numa_batch {
     int num_sms = 0;
     std::vector<numa::BatchInstance> inst;
     int tile_mult[9] = {4, 4, 4, 4, 4, 4, 4, 4, 4};   // elements per item / elements per pass, by Nq
-    bool tensor = false;   // NUMA_SWEEP_TENSOR_TF32 (mixed only)
+    numa_sweep sweep = NUMA_SWEEP_CUDA_CORES;
+    unsigned tc_mask = 0;  // orders (bit Nq) whose D sums run on the tensor cores (mixed only)
+    int ctas_per_sm = 0;   // CTAs per SM of the persistent grid (0: the kernel's maximum)
+    bool costliest_first = false;   // work items sorted by points, largest first
+    double tuned_ms = 0.0;          // last autotune: ms per step of the chosen configuration
+    int tuned_candidates = 0;       // last autotune: configurations timed
     // device scratch: instance table, work items, claim counter
     numa::BatchInstance *d_inst = nullptr;
     size_t inst_cap = 0;
@@ -69,7 +74,8 @@ namespace numa {
 
 // Build the work list for `inst` with the given tiles; items of one instance
 // are contiguous and instances keep their order.
-std::vector<BatchItem> build_items(const std::vector<BatchInstance> &inst, const int *tile_mult) {
+std::vector<BatchItem> build_items(const std::vector<BatchInstance> &inst, const int *tile_mult,
+                                   bool costliest_first) {
     std::vector<BatchItem> items;
     for (size_t k = 0; k < inst.size(); ++k) {
         const int nq = inst[k].nq;
@@ -78,6 +84,10 @@ std::vector<BatchItem> build_items(const std::vector<BatchInstance> &inst, const
         for (int64_t e0 = 0; e0 < ne; e0 += tile)
             items.push_back(BatchItem{(int)k, nq, e0, std::min(tile, ne - e0)});
     }
+    if (costliest_first)
+        std::stable_sort(items.begin(), items.end(), [](const BatchItem &a, const BatchItem &b) {
+            return a.count * a.nq * a.nq * a.nq > b.count * b.nq * b.nq * b.nq;
+        });
     return items;
 }
 
@@ -212,7 +222,8 @@ int numa_batch_advance(numa_batch *b, int nsteps, double dt, void *stream) {
     cudaError_t e = cudaSuccess;
     if (b->dirty) {
         drop_graph(b);
-        e = upload(b, b->inst, numa::build_items(b->inst, b->tile_mult), b->cap_stream);
+        e = upload(b, b->inst, numa::build_items(b->inst, b->tile_mult, b->costliest_first),
+                   b->cap_stream);
         if (e != cudaSuccess) return bfail_cuda(e, "numa_batch_advance: upload of the work list");
         b->dirty = false;
     }
@@ -223,7 +234,7 @@ int numa_batch_advance(numa_batch *b, int nsteps, double dt, void *stream) {
         if (e == cudaSuccess)
             e = numa::launch_batch_lsrk(b->prec == NUMA_MIXED, b->d_inst, b->d_items, b->num_items,
                                         b->d_counter, kLsrk, nsteps, dt, grid_of(b), b->cap_stream,
-                                        b->tensor);
+                                        b->tc_mask, b->ctas_per_sm);
         cudaGraph_t g = nullptr;
         const cudaError_t e2 = cudaStreamEndCapture(b->cap_stream, &g);
         if (e == cudaSuccess) e = e2;
@@ -243,87 +254,235 @@ int numa_batch_advance(numa_batch *b, int nsteps, double dt, void *stream) {
     return NUMA_OK;
 }
 
+namespace {
+
+// One launch configuration of the batch.
+struct TuneCfg {
+    int mult[9];
+    unsigned mask;
+    int ctas;
+    bool costliest;
+};
+
+// Best of `reps` timed launches of `nsteps` steps over instances `sub` in
+// configuration c (the work list is uploaded first).
+cudaError_t time_cfg(numa_batch *b, const std::vector<numa::BatchInstance> &sub, const TuneCfg &c,
+                     int nsteps, int reps, cudaStream_t s, cudaEvent_t t0, cudaEvent_t t1,
+                     float *ms_out) {
+    cudaError_t e = upload(b, sub, numa::build_items(sub, c.mult, c.costliest), s);
+    float ms = 1e30f;
+    for (int rep = 0; rep < reps && e == cudaSuccess; ++rep) {
+        e = cudaMemsetAsync(b->d_counter, 0, sizeof(int), s);
+        if (e == cudaSuccess) e = cudaEventRecord(t0, s);
+        if (e == cudaSuccess)
+            e = numa::launch_batch_lsrk(b->prec == NUMA_MIXED, b->d_inst, b->d_items, b->num_items,
+                                        b->d_counter, kLsrk, nsteps, 1e-6, grid_of(b), s, c.mask,
+                                        c.ctas);
+        if (e == cudaSuccess) e = cudaEventRecord(t1, s);
+        if (e == cudaSuccess) e = cudaEventRecord(b->launched, s);
+        if (e == cudaSuccess) e = cudaEventSynchronize(t1);
+        float t = 0.f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&t, t0, t1);
+        ms = std::min(ms, t);
+    }
+    ++b->tuned_candidates;
+    *ms_out = ms;
+    return e;
+}
+
+}  // namespace
+
 int numa_batch_autotune(numa_batch *b, void *stream) {
     g_batch_error.clear();
     if (!b) return bfail(NUMA_EINVAL, "numa_batch_autotune: NULL batch");
     if (b->inst.empty()) return NUMA_OK;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    const size_t elem = b->prec == NUMA_MIXED ? sizeof(float) : sizeof(double);
-    const int cands[] = {1, 2, 4, 8, 16, 32};
+    const bool mixed = b->prec == NUMA_MIXED;
+    const size_t elem = mixed ? sizeof(float) : sizeof(double);
+    const int mults[] = {1, 2, 4, 8, 16, 32};
+    constexpr int kSteps = 2, kReps = 3;   // per timing: two steps (ten stages), best of three
+    b->tuned_candidates = 0;
     cudaEvent_t t0 = nullptr, t1 = nullptr;
     cudaError_t e = cudaEventCreate(&t0);
     if (e == cudaSuccess) e = cudaEventCreate(&t1);
-    for (int nq = 2; nq <= 8 && e == cudaSuccess; ++nq) {
-        // the instances of this order, on copies of their states
-        std::vector<numa::BatchInstance> sub;
-        std::vector<void *> copies;
-        for (const auto &I : b->inst) {
-            if (I.nq != nq) continue;
-            void *c = nullptr;
-            e = cudaMalloc(&c, elem * numa::kFields * I.M);
-            if (e != cudaSuccess) break;
-            copies.push_back(c);
-            e = cudaMemcpyAsync(c, I.q, elem * numa::kFields * I.M, cudaMemcpyDeviceToDevice, s);
-            numa::BatchInstance J = I;
-            J.q = c;
-            sub.push_back(J);
+    // every instance on a copy of its state
+    std::vector<numa::BatchInstance> all;
+    std::vector<void *> copies;
+    for (const auto &I : b->inst) {
+        if (e != cudaSuccess) break;
+        void *c = nullptr;
+        e = cudaMalloc(&c, elem * numa::kFields * I.M);
+        if (e != cudaSuccess) break;
+        copies.push_back(c);
+        e = cudaMemcpyAsync(c, I.q, elem * numa::kFields * I.M, cudaMemcpyDeviceToDevice, s);
+        numa::BatchInstance J = I;
+        J.q = c;
+        all.push_back(J);
+    }
+    TuneCfg cur{};
+    std::copy(b->tile_mult, b->tile_mult + 9, cur.mult);
+    cur.mask = b->tc_mask;
+    cur.ctas = b->ctas_per_sm;
+    cur.costliest = b->costliest_first;
+    // per-order candidates: (sweep, passes per item)
+    auto order_cands = [&](int nq) {
+        std::vector<std::pair<unsigned, int>> v;
+        const unsigned bit = 1u << nq;
+        std::vector<unsigned> masks;
+        if (b->sweep == NUMA_SWEEP_AUTO) {
+            masks = {0u, bit};
+        } else {
+            masks = {b->tc_mask & bit};
         }
+        for (unsigned mk : masks)
+            for (int m : mults) v.push_back({mk, m});
+        return v;
+    };
+    // 1. each order alone: the best candidate as the starting point
+    bool present[9] = {};
+    for (const auto &I : all) present[I.nq] = true;
+    for (int nq = 2; nq <= 8 && e == cudaSuccess; ++nq) {
+        if (!present[nq]) continue;
+        std::vector<numa::BatchInstance> sub;
+        for (const auto &I : all)
+            if (I.nq == nq) sub.push_back(I);
         float best = 1e30f;
-        int best_m = b->tile_mult[nq];
-        for (int m : cands) {
-            if (e != cudaSuccess || sub.empty()) break;
-            int mult[9];
-            std::fill(mult, mult + 9, m);
-            e = upload(b, sub, numa::build_items(sub, mult), s);
-            float ms = 1e30f;
-            for (int rep = 0; rep < 2 && e == cudaSuccess; ++rep) {
-                e = cudaMemsetAsync(b->d_counter, 0, sizeof(int), s);
-                if (e == cudaSuccess) e = cudaEventRecord(t0, s);
-                if (e == cudaSuccess)
-                    e = numa::launch_batch_lsrk(b->prec == NUMA_MIXED, b->d_inst, b->d_items,
-                                                b->num_items, b->d_counter, kLsrk, 1, 1e-6,
-                                                grid_of(b), s, b->tensor);
-                if (e == cudaSuccess) e = cudaEventRecord(t1, s);
-                if (e == cudaSuccess) e = cudaEventRecord(b->launched, s);
-                if (e == cudaSuccess) e = cudaEventSynchronize(t1);
-                float t = 0.f;
-                if (e == cudaSuccess) e = cudaEventElapsedTime(&t, t0, t1);
-                ms = std::min(ms, t);
-            }
+        for (auto [mk, m] : order_cands(nq)) {
+            if (e != cudaSuccess) break;
+            TuneCfg c = cur;
+            c.mult[nq] = m;
+            c.mask = (cur.mask & ~(1u << nq)) | mk;
+            float ms = 0.f;
+            e = time_cfg(b, sub, c, kSteps, kReps, s, t0, t1, &ms);
             if (e == cudaSuccess && ms < best) {
                 best = ms;
-                best_m = m;
+                cur.mult[nq] = m;
+                cur.mask = c.mask;
             }
         }
-        for (void *c : copies) cudaFree(c);
-        if (e == cudaSuccess) b->tile_mult[nq] = best_m;
     }
+    // 2. the launch the batch runs (all orders together): coordinate descent
+    // over each order's candidates, then CTAs per SM and the item order; a
+    // change is kept when it saves at least 1 %.
+    float best = 1e30f;
+    if (e == cudaSuccess) e = time_cfg(b, all, cur, kSteps, kReps, s, t0, t1, &best);
+    auto try_cfg = [&](const TuneCfg &c) {
+        float ms = 0.f;
+        if (e == cudaSuccess) e = time_cfg(b, all, c, kSteps, kReps, s, t0, t1, &ms);
+        if (e == cudaSuccess && ms < 0.99f * best) {
+            best = ms;
+            cur = c;
+        }
+    };
+    int present_count = 0;
+    for (int nq = 2; nq <= 8; ++nq) present_count += present[nq];
+    for (int nq = 2; nq <= 8 && present_count > 1; ++nq) {
+        if (!present[nq]) continue;
+        const TuneCfg base = cur;
+        for (auto [mk, m] : order_cands(nq)) {
+            TuneCfg c = base;
+            c.mult[nq] = m;
+            c.mask = (base.mask & ~(1u << nq)) | mk;
+            if (c.mult[nq] == base.mult[nq] && c.mask == base.mask) continue;
+            try_cfg(c);
+        }
+    }
+    for (int k = 1; k <= numa::batch_max_ctas_per_sm(mixed); ++k) {
+        TuneCfg c = cur;
+        c.ctas = k == numa::batch_max_ctas_per_sm(mixed) ? 0 : k;
+        if (c.ctas != cur.ctas) try_cfg(c);
+    }
+    {
+        TuneCfg c = cur;
+        c.costliest = !cur.costliest;
+        try_cfg(c);
+    }
+    for (void *c : copies) cudaFree(c);
     if (t0) cudaEventDestroy(t0);
     if (t1) cudaEventDestroy(t1);
-    b->dirty = true;   // the work list is rebuilt with the chosen tiles
     if (e != cudaSuccess) return bfail_cuda(e, "numa_batch_autotune");
+    std::copy(cur.mult, cur.mult + 9, b->tile_mult);
+    b->tc_mask = cur.mask;
+    b->ctas_per_sm = cur.ctas;
+    b->costliest_first = cur.costliest;
+    b->tuned_ms = best / kSteps;
+    b->dirty = true;   // the work list is rebuilt with the chosen tiles
+    drop_graph(b);     // and the launch recaptured with the chosen kernel and grid
+    return NUMA_OK;
+}
+
+int numa_batch_get_config(const numa_batch *b, numa_batch_config *out) {
+    if (!b || !out) return bfail(NUMA_EINVAL, "numa_batch_get_config: NULL argument");
+    numa_batch_config c{};
+    for (int nq = 0; nq < 9; ++nq) {
+        c.tile[nq] = nq >= 2 ? numa::elements_per_pass(nq) * b->tile_mult[nq] : 0;
+        c.sweep[nq] = ((b->tc_mask >> nq) & 1u) ? NUMA_SWEEP_TENSOR_TF32 : NUMA_SWEEP_CUDA_CORES;
+    }
+    c.ctas_per_sm = b->ctas_per_sm;
+    c.costliest_first = b->costliest_first ? 1 : 0;
+    c.tuned_ms_per_step = b->tuned_ms;
+    c.tuned_candidates = b->tuned_candidates;
+    *out = c;
+    return NUMA_OK;
+}
+
+int numa_batch_set_config(numa_batch *b, const numa_batch_config *c) {
+    g_batch_error.clear();
+    if (!b || !c) return bfail(NUMA_EINVAL, "numa_batch_set_config: NULL argument");
+    const bool mixed = b->prec == NUMA_MIXED;
+    if (c->ctas_per_sm < 0 || c->ctas_per_sm > numa::batch_max_ctas_per_sm(mixed))
+        return bfail(NUMA_EINVAL, "numa_batch_set_config: ctas_per_sm out of range");
+    unsigned mask = 0;
+    int mult[9];
+    for (int nq = 2; nq <= 8; ++nq) {
+        const int epp = numa::elements_per_pass(nq);
+        if (c->tile[nq] < epp || c->tile[nq] % epp != 0)
+            return bfail(NUMA_EINVAL, "numa_batch_set_config: a tile is not a positive multiple "
+                                      "of the elements per pass of its order");
+        mult[nq] = c->tile[nq] / epp;
+        if (c->sweep[nq] == NUMA_SWEEP_TENSOR_TF32) {
+            if (!mixed)
+                return bfail(NUMA_EUNSUPPORTED,
+                             "numa_batch_set_config: the tensor-core sweep is for NUMA_MIXED batches");
+            mask |= 1u << nq;
+        } else if (c->sweep[nq] != NUMA_SWEEP_CUDA_CORES) {
+            return bfail(NUMA_EINVAL, "numa_batch_set_config: a sweep is not CUDA_CORES or TENSOR_TF32");
+        }
+    }
+    for (int nq = 2; nq <= 8; ++nq) b->tile_mult[nq] = mult[nq];
+    b->tc_mask = mask;
+    b->ctas_per_sm = c->ctas_per_sm;
+    b->costliest_first = c->costliest_first != 0;
+    b->dirty = true;
+    drop_graph(b);
     return NUMA_OK;
 }
 
 int numa_batch_set_sweep(numa_batch *b, numa_sweep sweep) {
     g_batch_error.clear();
     if (!b) return bfail(NUMA_EINVAL, "numa_batch_set_sweep: NULL batch");
-    if (sweep != NUMA_SWEEP_CUDA_CORES && sweep != NUMA_SWEEP_TENSOR_TF32)
+    if (sweep != NUMA_SWEEP_CUDA_CORES && sweep != NUMA_SWEEP_TENSOR_TF32 &&
+        sweep != NUMA_SWEEP_AUTO)
         return bfail(NUMA_EINVAL, "numa_batch_set_sweep: unknown sweep");
-    if (sweep == NUMA_SWEEP_TENSOR_TF32 && b->prec != NUMA_MIXED)
+    if (sweep != NUMA_SWEEP_CUDA_CORES && b->prec != NUMA_MIXED)
         return bfail(NUMA_EUNSUPPORTED,
                      "numa_batch_set_sweep: the tensor-core sweep is for NUMA_MIXED batches");
-    const bool t = sweep == NUMA_SWEEP_TENSOR_TF32;
-    if (t != b->tensor) {
-        b->tensor = t;
+    const unsigned mask = sweep == NUMA_SWEEP_TENSOR_TF32 ? numa::kTcAllOrders
+                          : sweep == NUMA_SWEEP_AUTO      ? b->tc_mask
+                                                          : 0u;
+    b->sweep = sweep;
+    if (mask != b->tc_mask) {
+        b->tc_mask = mask;
         drop_graph(b);   // the next advance captures the other kernel
     }
     return NUMA_OK;
 }
 
-int numa_batch_sweep(const numa_batch *b) {
-    if (!b) return -1;
-    return b->tensor ? NUMA_SWEEP_TENSOR_TF32 : NUMA_SWEEP_CUDA_CORES;
+int numa_batch_sweep(const numa_batch *b) { return b ? (int)b->sweep : -1; }
+
+int numa_batch_sweep_of(const numa_batch *b, int nq) {
+    if (!b || nq < 2 || nq > 8) return -1;
+    return ((b->tc_mask >> nq) & 1u) ? NUMA_SWEEP_TENSOR_TF32 : NUMA_SWEEP_CUDA_CORES;
 }
 
 int numa_batch_status(numa_batch *b, void *stream) {

@@ -71,12 +71,48 @@ batch_lsrk_kernel(const BatchInstance *__restrict__ inst, const BatchItem *__res
 }
 
 
-// Mixed precision with the D contractions on the tensor cores (batch_tile_tc.cuh).
-// counter[1] is the batch's status word: bit 0 is set when a wait for the
-// tensor core ran out; the CTA then stops claiming work.
+// Mixed precision with the D contractions on the tensor cores (batch_tile_tc.cuh)
+// for the orders whose bit Nq is set in tc_mask, on the CUDA cores (run_tile)
+// for the others: the autotuner picks per order.  counter[1] is the batch's
+// status word: bit 0 is set when a wait for the tensor core ran out; the CTA
+// then stops claiming work.
+static_assert(sizeof(float) * kMixedSmemWords <= (size_t)kTcSmemBytes,
+              "the CUDA-core tile shares the tensor tile's shared memory");
+
+// Separate functions (not inlined), so that each tile is register-allocated on
+// its own: inlined together they spill.
+template <int NQ>
+__device__ __noinline__ bool run_tile_tc_call(const BatchInstance &I, int64_t e0, int64_t count,
+                                              const float *sco, int ns, double dt,
+                                              unsigned char *sm, uint32_t tmem, uint64_t *bar,
+                                              uint32_t &phase, int *s_nq) {
+    return run_tile_tc<NQ>(I, e0, count, sco, ns, dt, sm, tmem, bar, phase, s_nq);
+}
+template <int NQ>
+__device__ __noinline__ void run_tile_cc_call(const BatchInstance &I, int64_t e0, int64_t count,
+                                              const float *sco, int ns, double dt,
+                                              unsigned char *sm) {
+    run_tile<NQ, true>(I, e0, count, sco, ns, dt, sm);
+}
+
+template <int NQ>
+__device__ __forceinline__ bool run_tile_either(unsigned tc_mask, const BatchInstance &I,
+                                                int64_t e0, int64_t count, const float *sco,
+                                                int ns, double dt, unsigned char *sm,
+                                                uint32_t tmem, uint64_t *bar, uint32_t &phase,
+                                                int *s_nq) {
+    if ((tc_mask >> NQ) & 1u)
+        return run_tile_tc_call<NQ>(I, e0, count, sco, ns, dt, sm, tmem, bar, phase, s_nq);
+    run_tile_cc_call<NQ>(I, e0, count, sco, ns, dt, sm);
+    __syncthreads();
+    if (threadIdx.x == 0) *s_nq = 0;   // the operands were overwritten
+    return true;
+}
+
 __global__ void __launch_bounds__(kThreads, 2)
 batch_lsrk_tc_kernel(const BatchInstance *__restrict__ inst, const BatchItem *__restrict__ items,
-                     int num_items, int *counter, LsrkCoef co, int nsteps, double dt) {
+                     int num_items, int *counter, LsrkCoef co, int nsteps, double dt,
+                     unsigned tc_mask) {
     extern __shared__ __align__(1024) unsigned char smem_tc[];
     __shared__ BatchInstance sI;
     __shared__ int s_item, s_nq;
@@ -111,13 +147,13 @@ batch_lsrk_tc_kernel(const BatchInstance *__restrict__ inst, const BatchItem *__
         __syncthreads();
         const int ns = sI.nsteps > 0 ? sI.nsteps : nsteps;
         switch (item.nq) {
-            case 2: ok = run_tile_tc<2>(sI, item.e0, item.count, sco, ns, dt, smem_tc, tmem, &bar, phase, &s_nq); break;
-            case 3: ok = run_tile_tc<3>(sI, item.e0, item.count, sco, ns, dt, smem_tc, tmem, &bar, phase, &s_nq); break;
-            case 4: ok = run_tile_tc<4>(sI, item.e0, item.count, sco, ns, dt, smem_tc, tmem, &bar, phase, &s_nq); break;
-            case 5: ok = run_tile_tc<5>(sI, item.e0, item.count, sco, ns, dt, smem_tc, tmem, &bar, phase, &s_nq); break;
-            case 6: ok = run_tile_tc<6>(sI, item.e0, item.count, sco, ns, dt, smem_tc, tmem, &bar, phase, &s_nq); break;
-            case 7: ok = run_tile_tc<7>(sI, item.e0, item.count, sco, ns, dt, smem_tc, tmem, &bar, phase, &s_nq); break;
-            case 8: ok = run_tile_tc<8>(sI, item.e0, item.count, sco, ns, dt, smem_tc, tmem, &bar, phase, &s_nq); break;
+            case 2: ok = run_tile_either<2>(tc_mask, sI, item.e0, item.count, sco, ns, dt, smem_tc, tmem, &bar, phase, &s_nq); break;
+            case 3: ok = run_tile_either<3>(tc_mask, sI, item.e0, item.count, sco, ns, dt, smem_tc, tmem, &bar, phase, &s_nq); break;
+            case 4: ok = run_tile_either<4>(tc_mask, sI, item.e0, item.count, sco, ns, dt, smem_tc, tmem, &bar, phase, &s_nq); break;
+            case 5: ok = run_tile_either<5>(tc_mask, sI, item.e0, item.count, sco, ns, dt, smem_tc, tmem, &bar, phase, &s_nq); break;
+            case 6: ok = run_tile_either<6>(tc_mask, sI, item.e0, item.count, sco, ns, dt, smem_tc, tmem, &bar, phase, &s_nq); break;
+            case 7: ok = run_tile_either<7>(tc_mask, sI, item.e0, item.count, sco, ns, dt, smem_tc, tmem, &bar, phase, &s_nq); break;
+            case 8: ok = run_tile_either<8>(tc_mask, sI, item.e0, item.count, sco, ns, dt, smem_tc, tmem, &bar, phase, &s_nq); break;
             default: break;
         }
         __syncthreads();   // sI and s_item are rewritten by the next claim
@@ -164,21 +200,24 @@ cudaError_t prepare_batch_lsrk() {
                                 kTcSmemBytes);
 }
 
+int batch_max_ctas_per_sm(bool mixed) { return mixed ? 2 : tile_ctas_per_sm<false>(); }
+
 cudaError_t launch_batch_lsrk(bool mixed, const BatchInstance *inst, const BatchItem *items,
                               int num_items, int *counter, const LsrkCoef &co, int nsteps,
-                              double dt, int num_sms, cudaStream_t s, bool tensor) {
+                              double dt, int num_sms, cudaStream_t s, unsigned tc_mask,
+                              int ctas_per_sm) {
     if (num_items <= 0 || nsteps <= 0) return cudaSuccess;
-    if (mixed && tensor)
-        batch_lsrk_tc_kernel<<<num_sms * 2, kThreads, kTcSmemBytes, s>>>(inst, items, num_items,
-                                                                         counter, co, nsteps, dt);
+    const int kmax = batch_max_ctas_per_sm(mixed);
+    const int k = ctas_per_sm > 0 && ctas_per_sm < kmax ? ctas_per_sm : kmax;
+    if (mixed && tc_mask != 0)
+        batch_lsrk_tc_kernel<<<num_sms * k, kThreads, kTcSmemBytes, s>>>(
+            inst, items, num_items, counter, co, nsteps, dt, tc_mask);
     else if (mixed)
-        batch_lsrk_kernel<true><<<num_sms * tile_ctas_per_sm<true>(), kThreads,
-                                  tile_smem_bytes<true>(), s>>>(inst, items, num_items, counter,
-                                                                co, nsteps, dt);
+        batch_lsrk_kernel<true><<<num_sms * k, kThreads, tile_smem_bytes<true>(), s>>>(
+            inst, items, num_items, counter, co, nsteps, dt);
     else
-        batch_lsrk_kernel<false><<<num_sms * tile_ctas_per_sm<false>(), kThreads,
-                                   tile_smem_bytes<false>(), s>>>(inst, items, num_items, counter,
-                                                                  co, nsteps, dt);
+        batch_lsrk_kernel<false><<<num_sms * k, kThreads, tile_smem_bytes<false>(), s>>>(
+            inst, items, num_items, counter, co, nsteps, dt);
     return cudaGetLastError();
 }
 

@@ -19,9 +19,16 @@
 //
 // Layout.  A (heads and tails) and B live in shared memory in the canonical
 // K-major no-swizzle layout of tcgen05.cuh: 8-row groups contiguous (SBO = 128
-// bytes), K chunks of 4 values LBO = 16 ROWS + 64 bytes apart (the 64 bytes
-// put the two halves of a row's eight values on opposite halves of the
-// banks).  Each (direction, field) block has a whole number of 8-row groups,
+// bytes), K chunks of 4 values LBO = 16 ROWS + pad bytes apart.  A 4-byte
+// access by a warp is free of bank conflicts when its 32 (row, slot) pairs have
+// distinct (row + chunk shift) mod 8 within each class of slot mod 4; a warp of
+// points that all share the coordinate along a direction (one K slot) can only
+// reach 8 banks.  At Nq = 8 and 4 the thread of point (i, j, k) is chosen so
+// that the two low bits of i, j and k all vary within a warp (k1 = i0 ^ j0 ^
+// a warp bit), and each direction numbers its lines so that the threads of
+// one slot class land on 8 distinct rows mod 8: every access of phases 1 and
+// 3 is conflict-free.  Other orders keep the natural point order (about 2-way).
+// Each (direction, field) block has a whole number of 8-row groups,
 // so a thread's slot for field b is its field-0 slot plus b blocks (immediate
 // offsets).  The readback writes each output back into the slot its flux came
 // from, so phase 3 reads a point's three sweeps where phase 1 wrote its
@@ -77,7 +84,11 @@ struct TcShape {
     static constexpr int BROWS = BL / P;               // rows per block (a multiple of 8)
     static constexpr int ROWS = tc_round_up(15 * BROWS, 128);
     static constexpr int NBLK = ROWS / 128;
-    static constexpr int LBO_A = ROWS * 16 + 64;       // bytes between K chunks of A
+    // bytes between K chunks of A: ROWS 16 plus a pad that shifts the banks of
+    // successive chunks (chosen per order by counting bank conflicts of the
+    // phase-1 stores and phase-3 loads of every warp)
+    static constexpr int PAD = NQ == 3 || NQ == 5 ? 32 : NQ == 6 ? 16 : 64;
+    static constexpr int LBO_A = ROWS * 16 + PAD;
     static constexpr int REGION = 2 * KS * LBO_A;      // bytes of the heads (or the tails)
     static constexpr int LBO_B = NN * 16;
     static constexpr int BBYTES = 2 * KS * LBO_B;      // bytes of B1 (or B2)
@@ -95,7 +106,12 @@ constexpr int tc_smem_max() {
     for (int x : s) m = x > m ? x : m;
     return m;
 }
-constexpr int kTcSmemBytes = tc_smem_max();
+// Per-thread values kept in shared memory after the operands (the point's
+// reference state, EOS factors and flux offsets), read where they are used so
+// that they hold no registers across the stage: 8 words per thread.
+constexpr int kTcAuxWords = 8;
+constexpr int kTcOperandBytes = tc_smem_max();
+constexpr int kTcSmemBytes = kTcOperandBytes + kTcAuxWords * kThreads * 4;
 static_assert(kTcStateCol + 4 * kTcStateStride <= kTcCols, "TMEM columns");
 
 // Head and tail of D per order (index Nq), D[i][n] at [i Nq + n]: Dh is the
@@ -138,13 +154,63 @@ __device__ __forceinline__ int tc_slot(int R, int s, int lbo) {
     return (R >> 3) * 128 + (s >> 2) * lbo + (R & 7) * 16 + (s & 3) * 4;
 }
 
+// Point (el, i, j, k) of thread l.  Nq = 8 and 4: lane bits l0..l4 give
+// i0, i1, j0, j1, k0 and k1 = l0 ^ l2 ^ (a warp bit); the other bits come from
+// the warp index.  Other orders: l = el N3 + i + Nq j + Nq^2 k.
+template <int NQ>
+__device__ __forceinline__ void tc_thread_point(int l, int &el, int &i, int &j, int &k) {
+    if constexpr (NQ == 8) {
+        const int h = l >> 5;
+        el = 0;
+        i = (l & 3) | (h & 1) << 2;
+        j = ((l >> 2) & 3) | ((h >> 1) & 1) << 2;
+        k = ((l >> 4) & 1) | ((l ^ (l >> 2) ^ (h >> 3)) & 1) << 1 | ((h >> 2) & 1) << 2;
+    } else if constexpr (NQ == 4) {
+        const int h = l >> 5;
+        el = h >> 1;
+        i = l & 3;
+        j = (l >> 2) & 3;
+        k = ((l >> 4) & 1) | ((l ^ (l >> 2) ^ h) & 1) << 1;
+    } else {
+        constexpr int N3 = NQ * NQ * NQ;
+        el = l / N3;
+        const int p = l % N3;
+        i = p % NQ;
+        j = (p / NQ) % NQ;
+        k = p / (NQ * NQ);
+    }
+}
+
 // Byte offset, within a (direction, field) block, of the flux of point
-// (el, i, j, k) in direction d.
+// (el, i, j, k) in direction d: its line's row and its K slot.
 template <int NQ>
 __device__ __forceinline__ int tc_point_offset(int d, int el, int i, int j, int k) {
     using S = TcShape<NQ>;
     int line, pos;
-    if (d == 0) {
+    auto b = [](int x, int n) { return (x >> n) & 1; };
+    if constexpr (NQ == 8) {   // row bits of the line (P = 1)
+        if (d == 0) {
+            line = b(j, 0) | b(j, 1) << 1 | b(k, 0) << 2 | b(j, 2) << 3 | b(k, 1) << 4 | b(k, 2) << 5;
+            pos = i;
+        } else if (d == 1) {
+            line = b(i, 0) | b(i, 1) << 1 | b(k, 0) << 2 | b(i, 2) << 3 | b(k, 1) << 4 | b(k, 2) << 5;
+            pos = j;
+        } else {
+            line = b(i, 0) | b(i, 1) << 1 | b(j, 1) << 2 | b(i, 2) << 3 | b(j, 0) << 4 | b(j, 2) << 5;
+            pos = k;
+        }
+    } else if constexpr (NQ == 4) {   // two lines per row: row = line >> 1
+        if (d == 0) {
+            line = b(k, 1) | b(j, 0) << 1 | b(j, 1) << 2 | b(k, 0) << 3;
+            pos = i;
+        } else if (d == 1) {
+            line = b(k, 1) | b(i, 0) << 1 | b(i, 1) << 2 | b(k, 0) << 3;
+            pos = j;
+        } else {
+            line = b(j, 0) | b(i, 0) << 1 | b(i, 1) << 2 | b(j, 1) << 3;
+            pos = k;
+        }
+    } else if (d == 0) {
         line = j + NQ * k;
         pos = i;
     } else if (d == 1) {
@@ -181,6 +247,31 @@ __device__ void tc_prepare_operands(unsigned char *sm) {
     }
 }
 
+// Writes the sums of K step ks of row R (heads' and tails' accumulator
+// halves added) back into the row's flux slots; slots past the row's lines
+// keep their zeros.
+template <int NQ>
+__device__ __forceinline__ void tc_store_row(unsigned char *Ah, int R, int ks, const uint32_t (&hv)[8],
+                                             const uint32_t (&lv)[8]) {
+    using S = TcShape<NQ>;
+    unsigned char *row = Ah + (R >> 3) * 128 + (R & 7) * 16;
+    float o[8];
+#pragma unroll
+    for (int t = 0; t < 8; ++t) o[t] = __uint_as_float(hv[t]) + __uint_as_float(lv[t]);
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+        const int s0 = 8 * ks + 4 * c;   // first K slot of this chunk
+        float *dst = reinterpret_cast<float *>(row + (2 * ks + c) * S::LBO_A);
+        if (s0 + 3 < S::PQ) {
+            *reinterpret_cast<float4 *>(dst) = make_float4(o[4 * c], o[4 * c + 1], o[4 * c + 2], o[4 * c + 3]);
+        } else {
+#pragma unroll
+            for (int t = 0; t < 4; ++t)
+                if (s0 + t < S::PQ) dst[t] = o[4 * c + t];
+        }
+    }
+}
+
 // One tile: elements [e0, e0 + count) of instance I through nsteps steps.
 // Returns false if the wait for the tensor core ran out (the caller stops).
 template <int NQ>
@@ -195,13 +286,16 @@ __device__ bool run_tile_tc(const BatchInstance &I, int64_t e0, int64_t count, c
         if (threadIdx.x == 0) *s_nq = NQ;
     }
     const int l = threadIdx.x, w = l >> 5, lane = l & 31;
-    const int el = l / S::N3, p = l % S::N3;
-    const int i = p % NQ, j = (p / NQ) % NQ, k = p / S::NL;
+    int el, i, j, k;
+    tc_thread_point<NQ>(l, el, i, j, k);
+    const int p = i + NQ * j + S::NL * k;
     const bool has_point = l < S::EPP * S::N3;
     unsigned char *Ah = sm;
-    int off[3];
+    float *aux = reinterpret_cast<float *>(sm + kTcOperandBytes) + l;   // [word * kThreads]
+    int *auxi = reinterpret_cast<int *>(aux);
 #pragma unroll
-    for (int d = 0; d < 3; ++d) off[d] = d * 5 * S::BLK_BYTES + tc_point_offset<NQ>(d, el, i, j, k);
+    for (int d = 0; d < 3; ++d)
+        auxi[(4 + d) * kThreads] = d * 5 * S::BLK_BYTES + tc_point_offset<NQ>(d, el, i, j, k);
     const uint32_t lane_base = tmem + ((uint32_t)(32 * (w & 3)) << 16);
     const uint32_t st_col = lane_base + kTcStateCol + kTcStateStride * (uint32_t)(w >> 2);
     const int64_t M = I.M;
@@ -209,30 +303,38 @@ __device__ bool run_tile_tc(const BatchInstance &I, int64_t e0, int64_t count, c
     const float dtt = static_cast<float>(dt);
     const float grav = I.mp.grav;
 
-    for (int64_t base = e0; base < e0 + count; base += S::EPP) {
-        const int npass = (int)((e0 + count - base) < S::EPP ? (e0 + count - base) : S::EPP);
+    // passes in 32-bit counters (a work item holds far fewer than 2^31
+    // elements); the point's global index is formed where it is used
+    const int cnt = (int)count;
+    for (int b0 = 0; b0 < cnt; b0 += S::EPP) {
+        const int npass = cnt - b0 < S::EPP ? cnt - b0 : S::EPP;
         const bool active = has_point && el < npass;
-        const int64_t node = (base + (active ? el : 0)) * S::N3 + p;
-        float th0 = 0.f, rho0 = 0.f;
-        EosRef32 er{0.f, 0.f};
+        // v: q (0-4), g (5-13), J^-1 (14) of this thread's point.  It is kept
+        // in registers from phase 3 into the next stage's phase 1, and
+        // reloaded from TMEM for phase 3 (issued before the barrier that
+        // precedes it, so the load's latency hides behind the barrier).
+        uint32_t v[16];
+#pragma unroll
+        for (int t = 0; t < 16; ++t) v[t] = 0u;
+        if (active) {
+            const int64_t node = (e0 + b0 + el) * S::N3 + p;
+#pragma unroll
+            for (int b = 0; b < kFields; ++b) v[b] = __float_as_uint(qv[b * M + node]);
+#pragma unroll
+            for (int s2 = 0; s2 < 9; ++s2) v[5 + s2] = __float_as_uint(__ldg(I.mgeo.g[s2] + node));
+            v[14] = __float_as_uint(__ldg(I.mgeo.Jinv + node));
+            const float th0 = __ldg(I.mgeo.theta_ref + node);
+            EosRef32 er{0.f, 0.f};
+            if (th0 > 0.f) er = eos_reference_f32(th0, I.mp);
+            aux[0] = th0;
+            aux[kThreads] = __ldg(I.mgeo.rho_ref + node);
+            aux[2 * kThreads] = er.w;
+            aux[3 * kThreads] = er.A;
+        }
         {
-            uint32_t v[16];
-#pragma unroll
-            for (int t = 0; t < 16; ++t) v[t] = 0u;
-            if (active) {
-#pragma unroll
-                for (int b = 0; b < kFields; ++b) v[b] = __float_as_uint(qv[b * M + node]);
-#pragma unroll
-                for (int s2 = 0; s2 < 9; ++s2) v[5 + s2] = __float_as_uint(__ldg(I.mgeo.g[s2] + node));
-                v[14] = __float_as_uint(__ldg(I.mgeo.Jinv + node));
-                th0 = __ldg(I.mgeo.theta_ref + node);
-                rho0 = __ldg(I.mgeo.rho_ref + node);
-                if (th0 > 0.f) er = eos_reference_f32(th0, I.mp);
-            }
             uint32_t z[8] = {0u, 0u, 0u, 0u, 0u, 0u, 0u, 0u};
             tc::tmem_st16(st_col, v);
             tc::tmem_st8(st_col + 16, z);
-            tc::tmem_st_wait();
         }
 
         for (int step = 0; step < nsteps; ++step) {
@@ -240,34 +342,31 @@ __device__ bool run_tile_tc(const BatchInstance &I, int64_t e0, int64_t count, c
             for (int st = 0; st < 5; ++st) {
                 __syncthreads();   // previous phase-3 reads of A are done
                 // ---- phase 1: p', fluxes, heads and tails into A -------
-                {
-                    uint32_t v[16];
-                    tc::tmem_ld16(st_col, v);
-                    tc::tmem_ld_wait16(v);
-                    if (active) {
-                        float q[kFields], g[9];
+                if (active) {
+                    const float th0 = aux[0], rho0 = aux[kThreads];
+                    const EosRef32 er{aux[2 * kThreads], aux[3 * kThreads]};
+                    float q[kFields], g[9];
 #pragma unroll
-                        for (int b = 0; b < kFields; ++b) q[b] = __uint_as_float(v[b]);
+                    for (int b = 0; b < kFields; ++b) q[b] = __uint_as_float(v[b]);
 #pragma unroll
-                        for (int s2 = 0; s2 < 9; ++s2) g[s2] = __uint_as_float(v[5 + s2]);
-                        const float rho = rho0 + q[0];
-                        const float Th = th0 + q[4];
-                        const float pp = pressure_perturbation_f32(q[4], th0, er, I.mp);
-                        const float rinv = __frcp_rn(rho);   // the correctly rounded 1/rho
+                    for (int s2 = 0; s2 < 9; ++s2) g[s2] = __uint_as_float(v[5 + s2]);
+                    const float rho = rho0 + q[0];
+                    const float Th = th0 + q[4];
+                    const float pp = pressure_perturbation_f32(q[4], th0, er, I.mp);
+                    const float rinv = __frcp_rn(rho);   // the correctly rounded 1/rho
 #pragma unroll
-                        for (int d = 0; d < 3; ++d) {
-                            const float g1 = g[3 * d], g2 = g[3 * d + 1], g3 = g[3 * d + 2];
-                            const float vv = fmaf(g3, q[3], fmaf(g2, q[2], g1 * q[1]));
-                            const float u = vv * rinv;
-                            const float F[kFields] = {vv, fmaf(q[1], u, g1 * pp),
-                                                      fmaf(q[2], u, g2 * pp),
-                                                      fmaf(q[3], u, g3 * pp), Th * u};
+                    for (int d = 0; d < 3; ++d) {
+                        const float g1 = g[3 * d], g2 = g[3 * d + 1], g3 = g[3 * d + 2];
+                        const float vv = fmaf(g3, q[3], fmaf(g2, q[2], g1 * q[1]));
+                        const float u = vv * rinv;
+                        const float F[kFields] = {vv, fmaf(q[1], u, g1 * pp), fmaf(q[2], u, g2 * pp),
+                                                  fmaf(q[3], u, g3 * pp), Th * u};
+                        unsigned char *ad = Ah + auxi[(4 + d) * kThreads];
 #pragma unroll
-                            for (int b = 0; b < kFields; ++b) {
-                                unsigned char *a = Ah + off[d] + b * S::BLK_BYTES;
-                                *reinterpret_cast<float *>(a) = F[b];
-                                *reinterpret_cast<float *>(a + S::REGION) = F[b] - tf32_head_dev(F[b]);
-                            }
+                        for (int b = 0; b < kFields; ++b) {
+                            unsigned char *a = ad + b * S::BLK_BYTES;
+                            *reinterpret_cast<float *>(a) = F[b];
+                            *reinterpret_cast<float *>(a + S::REGION) = F[b] - tf32_head_dev(F[b]);
                         }
                     }
                 }
@@ -298,76 +397,65 @@ __device__ bool run_tile_tc(const BatchInstance &I, int64_t e0, int64_t count, c
                 phase ^= 1u;
                 tc::fence_after_sync();
                 // ---- readback: C[:, 0:H] + C[:, H:2H] into the flux slots ----
+                // A warp reads the blocks m = warp / 4 + 4 t of its lane quarter.
+                // (Issuing a warp's loads of two blocks before one wait needs
+                // 32 more live registers and spills at this kernel's 64.)
 #pragma unroll 1
                 for (int m = w >> 2; m < S::NBLK; m += 4) {
                     const int R = m * 128 + 32 * (w & 3) + lane;
-                    unsigned char *row = Ah + (R >> 3) * 128 + (R & 7) * 16;
 #pragma unroll
                     for (int ks = 0; ks < S::KS; ++ks) {
                         uint32_t hv[8], lv[8];
                         tc::tmem_ld8(lane_base + m * S::NN + 8 * ks, hv);
                         tc::tmem_ld8(lane_base + m * S::NN + S::H + 8 * ks, lv);
                         tc::tmem_ld_wait8x2(hv, lv);
-                        float o[8];
-#pragma unroll
-                        for (int t = 0; t < 8; ++t) o[t] = __uint_as_float(hv[t]) + __uint_as_float(lv[t]);
-#pragma unroll
-                        for (int c = 0; c < 2; ++c) {
-                            const int s0 = 8 * ks + 4 * c;   // first K slot of this chunk
-                            float *dst = reinterpret_cast<float *>(row + (2 * ks + c) * S::LBO_A);
-                            if (s0 + 3 < S::PQ) {
-                                *reinterpret_cast<float4 *>(dst) =
-                                    make_float4(o[4 * c], o[4 * c + 1], o[4 * c + 2], o[4 * c + 3]);
-                            } else {
-#pragma unroll
-                                for (int t = 0; t < 4; ++t)
-                                    if (s0 + t < S::PQ) dst[t] = o[4 * c + t];
-                            }
-                        }
+                        tc_store_row<NQ>(Ah, R, ks, hv, lv);
                     }
                 }
+                // the state for phase 3 (its stores of the last stage are complete first)
+                uint32_t dv[8];
+                tc::tmem_st_wait();
+                tc::tmem_ld16(st_col, v);
+                tc::tmem_ld8(st_col + 16, dv);
                 tc::fence_before_sync();
                 __syncthreads();
                 // ---- phase 3: rhs, stage update ------------------------
-                {
-                    uint32_t v[16], dv[8];
-                    tc::tmem_ld16(st_col, v);
-                    tc::tmem_ld8(st_col + 16, dv);
-                    tc::tmem_ld_wait16(v);
-                    tc::tmem_ld_wait(dv);
-                    if (active) {
-                        const float a = sco[st], bcoef = sco[5 + st];
-                        const float jinv = __uint_as_float(v[14]);
-                        const float drho = __uint_as_float(v[0]);   // rho - rho_ref before the update
+                tc::tmem_ld_wait16(v);
+                tc::tmem_ld_wait(dv);
+                if (active) {
+                    const float a = sco[st], bcoef = sco[5 + st];
+                    const float jinv = __uint_as_float(v[14]);
+                    const float drho = __uint_as_float(v[0]);   // rho - rho_ref before the update
+                    const unsigned char *a0 = Ah + auxi[4 * kThreads], *a1 = Ah + auxi[5 * kThreads],
+                                        *a2 = Ah + auxi[6 * kThreads];
 #pragma unroll
-                        for (int b = 0; b < kFields; ++b) {
-                            const float Rb = *reinterpret_cast<const float *>(Ah + off[0] + b * S::BLK_BYTES) +
-                                             *reinterpret_cast<const float *>(Ah + off[1] + b * S::BLK_BYTES) +
-                                             *reinterpret_cast<const float *>(Ah + off[2] + b * S::BLK_BYTES);
-                            float rhs = -jinv * Rb;
-                            if (b == 3) rhs = fmaf(-drho, grav, rhs);
-                            const float dq = fmaf(a, __uint_as_float(dv[b]), dtt * rhs);
-                            dv[b] = __float_as_uint(dq);
-                            v[b] = __float_as_uint(fmaf(bcoef, dq, __uint_as_float(v[b])));
-                        }
+                    for (int b = 0; b < kFields; ++b) {
+                        const float Rb = *reinterpret_cast<const float *>(a0 + b * S::BLK_BYTES) +
+                                         *reinterpret_cast<const float *>(a1 + b * S::BLK_BYTES) +
+                                         *reinterpret_cast<const float *>(a2 + b * S::BLK_BYTES);
+                        float rhs = -jinv * Rb;
+                        if (b == 3) rhs = fmaf(-drho, grav, rhs);
+                        const float dq = fmaf(a, __uint_as_float(dv[b]), dtt * rhs);
+                        dv[b] = __float_as_uint(dq);
+                        v[b] = __float_as_uint(fmaf(bcoef, dq, __uint_as_float(v[b])));
                     }
+                }
+                {
                     uint32_t q8[8];
 #pragma unroll
                     for (int t = 0; t < 8; ++t) q8[t] = v[t];
                     tc::tmem_st8(st_col, q8);
                     tc::tmem_st8(st_col + 16, dv);
-                    tc::tmem_st_wait();
                 }
             }
         }
-        {
-            uint32_t q8[8];
-            tc::tmem_ld8(st_col, q8);
-            tc::tmem_ld_wait(q8);
-            if (active) {
+        tc::tmem_st_wait();
+        if (active) {
+            const int64_t node = (e0 + b0 + el) * S::N3 + p;
+            float *q_out = static_cast<float *>(I.q);
+            const int64_t Mo = I.M;
 #pragma unroll
-                for (int b = 0; b < kFields; ++b) qv[b * M + node] = __uint_as_float(q8[b]);
-            }
+            for (int b = 0; b < kFields; ++b) q_out[b * Mo + node] = __uint_as_float(v[b]);
         }
     }
     return true;

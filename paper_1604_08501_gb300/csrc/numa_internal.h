@@ -92,18 +92,26 @@ struct LsrkCoef {
 // prepare_batch_lsrk() sets the kernels' shared-memory opt-in on the current
 // device; call it before the first launch (and outside stream capture).
 cudaError_t prepare_batch_lsrk();
-// The grid is num_sms times the CTAs per SM the kernel is built for.  tensor
-// (mixed only): the D contractions as TF32 split products on the tensor
-// cores (batch_tile_tc.cuh); counter[1] then receives its status bits.
+// The grid is num_sms times the CTAs per SM the kernel is built for.  tc_mask
+// (mixed only): bit Nq set = order Nq takes its D contractions as TF32 split
+// products on the tensor cores (batch_tile_tc.cuh); counter[1] then receives
+// the kernel's status bits.
+constexpr unsigned kTcAllOrders = 0x1FCu;   // bits 2..8
+// ctas_per_sm: CTAs per SM of the persistent grid, 1 .. the kernel's maximum
+// (batch_max_ctas_per_sm); 0 takes the maximum.
 cudaError_t launch_batch_lsrk(bool mixed, const BatchInstance *inst, const BatchItem *items,
                               int num_items, int *counter, const LsrkCoef &co, int nsteps,
-                              double dt, int num_sms, cudaStream_t s, bool tensor = false);
+                              double dt, int num_sms, cudaStream_t s, unsigned tc_mask = 0,
+                              int ctas_per_sm = 0);
+int batch_max_ctas_per_sm(bool mixed);
 
 // Elements one CTA pass holds for order Nq (512 threads, one per point).
 inline int elements_per_pass(int nq) { return 512 / (nq * nq * nq); }
 
-// Work list for instances with tile_mult[nq] passes per item (batch_abi.cu).
-std::vector<BatchItem> build_items(const std::vector<BatchInstance> &inst, const int *tile_mult);
+// Work list for instances with tile_mult[nq] passes per item (batch_abi.cu);
+// costliest_first: items sorted by points, largest first (stable).
+std::vector<BatchItem> build_items(const std::vector<BatchInstance> &inst, const int *tile_mult,
+                                   bool costliest_first = false);
 
 }  // namespace numa
 

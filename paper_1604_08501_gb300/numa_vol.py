@@ -16,7 +16,7 @@ import ctypes as C
 import numpy as np
 
 from . import _lib
-from ._lib import (NUMA_DF64, NUMA_FP64, NUMA_MIXED, NUMA_SWEEP_CUDA_CORES,
+from ._lib import (NUMA_DF64, NUMA_FP64, NUMA_MIXED, NUMA_SWEEP_AUTO, NUMA_SWEEP_CUDA_CORES,
                    NUMA_SWEEP_TENSOR_TF32, NumaError, check, check_batch,
                    check_engine)
 
@@ -193,7 +193,8 @@ class Batch:
     """Batched low-storage Runge-Kutta integration of many VolumeTerm instances
     (numa_batch_*).  States are CUDA tensors the batch updates in place."""
 
-    SWEEPS = {"cuda_cores": NUMA_SWEEP_CUDA_CORES, "tensor_tf32": NUMA_SWEEP_TENSOR_TF32}
+    SWEEPS = {"cuda_cores": NUMA_SWEEP_CUDA_CORES, "tensor_tf32": NUMA_SWEEP_TENSOR_TF32,
+              "auto": NUMA_SWEEP_AUTO}
 
     def __init__(self, precision: str = "fp64", sweep: str = "cuda_cores"):
         self.precision = precision
@@ -207,13 +208,44 @@ class Batch:
 
     @property
     def sweep(self) -> str:
-        """How the D sums are evaluated: "cuda_cores" or "tensor_tf32" (mixed only)."""
+        """How the D sums are evaluated: "cuda_cores", "tensor_tf32" (mixed only)
+        or "auto" (the autotuner picks per order)."""
         v = _lib.load().numa_batch_sweep(self.handle)
+        return {v2: k for k, v2 in self.SWEEPS.items()}[v]
+
+    def sweep_of(self, nq: int) -> str:
+        """The sweep order Nq uses now: "cuda_cores" or "tensor_tf32"."""
+        v = _lib.load().numa_batch_sweep_of(self.handle, int(nq))
         return {NUMA_SWEEP_CUDA_CORES: "cuda_cores", NUMA_SWEEP_TENSOR_TF32: "tensor_tf32"}[v]
 
     @sweep.setter
     def sweep(self, name: str) -> None:
         check_batch(_lib.load().numa_batch_set_sweep(self.handle, self.SWEEPS[name]))
+
+    def config(self) -> dict:
+        """The launch configuration: tile (elements per work item) and sweep by
+        Nq, CTAs per SM, item order, and the last autotune's ms per step and
+        candidates timed."""
+        c = _lib.numa_batch_config()
+        check_batch(_lib.load().numa_batch_get_config(self.handle, C.byref(c)))
+        names = {NUMA_SWEEP_CUDA_CORES: "cuda_cores", NUMA_SWEEP_TENSOR_TF32: "tensor_tf32"}
+        return {"tile": {nq: c.tile[nq] for nq in range(2, 9)},
+                "sweep": {nq: names[c.sweep[nq]] for nq in range(2, 9)},
+                "ctas_per_sm": c.ctas_per_sm, "costliest_first": bool(c.costliest_first),
+                "tuned_ms_per_step": c.tuned_ms_per_step,
+                "tuned_candidates": c.tuned_candidates}
+
+    def set_config(self, tile=None, sweep=None, ctas_per_sm=None, costliest_first=None) -> None:
+        """Set any of the configuration fields of config() (the others stay)."""
+        cur = self.config()
+        c = _lib.numa_batch_config()
+        for nq in range(2, 9):
+            c.tile[nq] = int((tile or {}).get(nq, cur["tile"][nq]))
+            c.sweep[nq] = self.SWEEPS[(sweep or {}).get(nq, cur["sweep"][nq])]
+        c.ctas_per_sm = int(cur["ctas_per_sm"] if ctas_per_sm is None else ctas_per_sm)
+        c.costliest_first = int(cur["costliest_first"] if costliest_first is None
+                                else bool(costliest_first))
+        check_batch(_lib.load().numa_batch_set_config(self.handle, C.byref(c)))
 
     def status(self, stream=None) -> None:
         """Raise NumaError(NUMA_ETIMEOUT) if a launch's bounded device wait ran out."""

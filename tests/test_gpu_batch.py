@@ -204,3 +204,59 @@ def test_batch_across_the_eos_branches(precision, tol):
     for f, (mx, _) in enumerate(errs):
         assert mx <= tol, (precision, wl.FIELD_NAMES[f], mx)
     vt.close()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_every_candidate_configuration_keeps_parity(precision):
+    """Every configuration the autotuner can choose (tiles of 1..32 passes,
+    CTAs per SM, item order and, in the mixed mode, either sweep per order)
+    gives a result within the bar."""
+    runs = [make(sp, precision) for sp in SPECS]
+    refs = []
+    for w, _, _ in runs:
+        refs.append(oracle.lsrk(w.problem(), w.q, DT, NSTEPS))
+    saved = [q.clone() for _, _, q in runs]
+    sweeps = ["cuda_cores", "tensor_tf32"] if precision == "mixed" else ["cuda_cores"]
+    ctas = [1, 2] if precision == "mixed" else [1]
+    tol = 1e-5 if precision == "mixed" else 3e-12
+    with Batch(precision) as b:
+        for w, vt, q in runs:
+            b.add(vt, q)
+        for passes in (1, 2, 4, 8, 16, 32):
+            for sweep in sweeps:
+                for k in ctas:
+                    for costliest in (False, True):
+                        for (_, _, q), q0 in zip(runs, saved):
+                            q.copy_(q0)
+                        b.set_config(tile={nq: passes * (512 // nq ** 3) for nq in range(2, 9)},
+                                     sweep={nq: sweep for nq in range(2, 9)}, ctas_per_sm=k,
+                                     costliest_first=costliest)
+                        b.advance(NSTEPS, DT)
+                        b.status()
+                        torch.cuda.synchronize()
+                        for (w, _, q), ref, sp in zip(runs, refs, SPECS):
+                            got = q.cpu().numpy().astype(np.float64)
+                            if precision == "mixed":
+                                ref_s = np.concatenate([(ref[0] - w.rho_ref)[None], ref[1:4],
+                                                        (ref[4] - w.rhotheta_ref)[None]])
+                                errs = rel_err(got, ref_s)
+                            else:
+                                errs = rel_err(got - w.q, ref - w.q)
+                            for f, (mx, _) in enumerate(errs):
+                                assert mx <= tol, (passes, sweep, k, costliest, sp, f, mx)
+
+
+def test_autotune_reports_configuration():
+    runs = [make(sp, "mixed") for sp in SPECS]
+    with Batch("mixed", sweep="auto") as b:
+        for w, vt, q in runs:
+            b.add(vt, q)
+        b.autotune()
+        c = b.config()
+        assert c["tuned_ms_per_step"] > 0 and c["tuned_candidates"] > 0
+        for nq in (2, 4, 5, 6, 8):
+            assert c["tile"][nq] % (512 // nq ** 3) == 0
+        with pytest.raises(NumaError):
+            b.set_config(tile={4: 12})   # not a multiple of the 8 elements per pass at Nq = 4
+        with pytest.raises(NumaError):
+            b.set_config(ctas_per_sm=3)

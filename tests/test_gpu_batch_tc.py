@@ -146,3 +146,23 @@ def test_tensor_sweep_autotune_leaves_states():
         for f, (mx, _) in enumerate(state_errors(w, q.cpu().numpy())):
             assert mx <= 1e-5, (sp, f, mx)
         vt.close()
+
+
+def test_auto_sweep_picks_per_order_and_keeps_parity():
+    runs = [make(sp) for sp in SPECS]
+    with Batch("mixed", sweep="auto") as b:
+        assert b.sweep == "auto"
+        for w, vt, q in runs:
+            b.add(vt, q)
+        b.autotune()
+        chosen = {nq: b.sweep_of(nq) for nq in range(2, 9)}
+        assert set(chosen.values()) <= {"cuda_cores", "tensor_tf32"}
+        print(chosen)
+        b.advance(NSTEPS, DT)
+        b.status()
+        torch.cuda.synchronize()
+        for (w, vt, q), sp in zip(runs, SPECS):
+            for f, (mx, _) in enumerate(state_errors(w, q.cpu().numpy())):
+                assert mx <= 1e-5, (sp, chosen, f, mx)
+    for _, vt, _ in runs:
+        vt.close()
