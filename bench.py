@@ -48,8 +48,10 @@ def flops_per_node_fp64(Nq: int) -> int:
     return 5 + 51 + 30 * Nq + 8
 
 
-# FP64 CUDA-core peak of one GB300, used only when the FP64 pipe binds.
+# FP64 CUDA-core peak of one GB300, used only when the FP64 pipe binds: the
+# unit-count figure, and the rate a DFMA microbenchmark measured on the pool.
 FP64_PEAK_TFLOPS = 1.25
+FP64_DFMA_MEASURED_TFLOPS = 1.056
 FALLBACK_HBM_GBS = 6800.0
 
 
@@ -384,10 +386,38 @@ def roofline_entries(kname, kernel_ms, w):
     alu = {"bound": "alu", "achieved": fp64_tfs, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
            "frac": fp64_tfs / FP64_PEAK_TFLOPS, "traffic": load_traffic(kname), "kernel": kname,
            "flops_per_point": flops_per_node_fp64(w.N + 1),
-           "peak_source": "FP64 pipe of one GB300, nominal 1.25 TFLOP/s "
-                          "(microbenchmark: 1.056 TFLOP/s)",
+           "peak_source": "FP64 pipe of one GB300 from its unit counts and clock: 152 SMs x 2 "
+                          "DFMA/clk x 2 flop x 2.07 GHz = 1.26, quoted as the nominal 1.25 TFLOP/s",
+           "peak_measured_dfma": FP64_DFMA_MEASURED_TFLOPS,
+           "frac_of_measured_dfma": fp64_tfs / FP64_DFMA_MEASURED_TFLOPS,
+           "peak_measured_source": "FMA-chain microbenchmark on this pool's GB300 (8 independent "
+                                   "DFMA chains per thread): 528 G DFMA/s",
            "kernel_ms": kernel_ms}
     return (alu, hbm) if kname.startswith("vol_rhs_fp64") else (hbm, alu)
+
+
+_ORACLE_RHS = {}
+
+
+def oracle_rhs(w):
+    """Oracle O2's volume term of workload w (computed once per process)."""
+    import oracle
+    key = (w.N, w.Ne, w.seed)
+    if key not in _ORACLE_RHS:
+        _ORACLE_RHS[key] = oracle.vol_rhs_o2(w.problem(), w.q)
+    return _ORACLE_RHS[key]
+
+
+def error_vs_oracle(x, ref):
+    """Per-field normwise error of x against the FP64 oracle: max|x - ref| /
+    max|ref| and ||x - ref||_2 / ||ref||_2."""
+    names = ("rho", "rho_u", "rho_v", "rho_w", "rho_theta")
+    out = {}
+    for b in range(5):
+        d = np.asarray(x[b], dtype=np.float64) - ref[b]
+        out[names[b]] = {"max": float(np.max(np.abs(d)) / np.max(np.abs(ref[b]))),
+                         "rms": float(np.linalg.norm(d) / np.linalg.norm(ref[b]))}
+    return out
 
 
 def run_gpu(args):
@@ -418,6 +448,12 @@ def run_gpu(args):
         r = time_variant(vt, q, q_host, dev, K, W, rank, e2e=not args.no_e2e,
                          min_region_s=0.0 if prec == args.precisions[0] else 0.3)
         r["kernel"] = vt.kernel_name
+        if rank == 0 and not args.no_error:
+            # one more evaluation (outside the timed regions) against the oracle
+            out = vt.rhs(q)
+            torch.cuda.synchronize(dev)
+            r["error_vs_oracle"] = error_vs_oracle(out.cpu().numpy(), oracle_rhs(w))
+            del out
         vt.close()
         Kv = r["steps"]
         value, tmax = aggregate(Kv * w.M, r["region_ms"] * 1e-3, dev)
@@ -454,6 +490,29 @@ def run_gpu(args):
                               "roofline": vr, "roofline_other": vo, "e2e": r["e2e"],
                               "gpu_launches": r["steps"], "clocks": r["clocks"],
                               "launch_ms": r["launch_ms"]}
+        if "error_vs_oracle" in head:
+            line["error_vs_oracle"] = head["error_vs_oracle"]
+        for prec in args.precisions[1:]:
+            if "error_vs_oracle" in results[prec]:
+                variants[prec]["error_vs_oracle"] = results[prec]["error_vs_oracle"]
+        if world == 1 and not args.no_batched and args.n == 32:
+            # the batched workload, compact: both precisions, 3 timed launches
+            bres, bplan = batched_results(rank, dev, world, ["mixed", "fp64"], 64, 3, 3)
+            variants["batched"] = {"metric": "batched volume-RHS GDOF/s (points x RK stages / s)",
+                                   "workload": BATCHED_WORKLOAD.format(n=len(bplan)), **bres}
+        if world == 1 and not args.no_serving and args.n == 32:
+            # the serving workload at 200 req/s: 600 requests in the mixed
+            # mode; FP64 (overloaded about 9x at this rate) the first 100 of
+            # the same stream, so that the run stays short
+            sres, splan = serving_results(rank, dev, world, ["mixed", "fp64"], 200.0, 600, 16,
+                                          120, 4, "per_member", 3, {"fp64": 100})
+            variants["serving"] = {
+                "metric": "serving GDOF/s (points x RK stages / s) with p50/p99 request latency",
+                "workload": f"Poisson arrivals at 200 req/s (mixed: 600 requests, fp64: the first "
+                            f"100 of the same stream), each one of {len(splan)} instances "
+                            f"(N in {{3,4,5,7}}, 512..32768 elements) advancing k in {{1,5,20}} "
+                            f"LSRK(5,4) steps at dt = 0.01 s; budget 120 GB, <= 256 members, "
+                            f"rounds of up to 4 steps, per-member round policy", **sres}
         if variants:
             line["variants"] = variants
         if world == 1 and not args.no_cpu_baseline and args.n == 32:
@@ -462,25 +521,21 @@ def run_gpu(args):
     return 0
 
 
-def run_batched(args):
-    """The batched workload: 64 independent instances (N from {3,4,5,7},
-    512..32768 elements) advanced by 10 low-storage RK steps at dt = 0.01 s in one
-    graph-captured persistent launch.  Metric: volume-term evaluations per
-    second, in GDOF/s (points x 5 stages x steps / time)."""
+def batched_results(rank, dev, world, precisions, instances, steps, warmup, orders=None):
+    """The batched workload (run_batched's docstring) for each precision mode:
+    rate, launch time and the autotuned configuration.  orders: keep only the
+    plan's instances of these orders N."""
     import torch
-    rank, local, world = dist_setup("nccl")
-    torch.cuda.set_device(local)
-    dev = torch.device("cuda", local)
-    from paper_1604_08501_gb300 import build as lib_build
     from paper_1604_08501_gb300 import workload as wl
     from paper_1604_08501_gb300.numa_vol import Batch, VolumeTerm
-    lib_build.build()
-    plan = wl.batch_plan(count=args.instances)
+    plan = wl.batch_plan(count=instances)
+    if orders:
+        plan = [p for p in plan if p[0] in orders]
     works = [wl.integration_workload(N, n, seed) for N, n, seed in plan]
     nsteps, dt = 10, 0.01
     out = {}
-    for name in args.precisions:
-        # "mixed-tc": the mixed batch with its D sums on the tensor cores
+    for name in precisions:
+        # "mixed-tc": the mixed batch with its D sums on the tensor cores;
         # "mixed-auto": the autotuner picks the sweep per order
         prec, sweep = {"fp64": ("fp64", "cuda_cores"), "mixed": ("mixed", "cuda_cores"),
                        "mixed-tc": ("mixed", "tensor_tf32"),
@@ -507,15 +562,15 @@ def run_batched(args):
             for q, q0 in zip(states, saved):
                 q.copy_(q0)
 
-        for _ in range(args.warmup):
+        for _ in range(warmup):
             restore()
             b.advance(nsteps, dt, stream)
         torch.cuda.synchronize(dev)
-        sampler = ClockSampler(gpu_id_for(local)) if rank == 0 else None
+        sampler = ClockSampler(gpu_id_for(dev.index)) if rank == 0 else None
         if sampler:
             sampler.start()
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-              for _ in range(args.steps)]
+              for _ in range(steps)]
         barrier(dev)
         for t0, t1 in ev:
             restore()
@@ -525,14 +580,16 @@ def run_batched(args):
         torch.cuda.synchronize(dev)
         barrier(dev)
         clocks = sampler.stop() if sampler else None
-        ms = sum(t0.elapsed_time(t1) for t0, t1 in ev) / args.steps
+        ms = sum(t0.elapsed_time(t1) for t0, t1 in ev) / steps
         evals = points * 5 * nsteps
-        value, tmax = aggregate(evals * args.steps, ms * 1e-3 * args.steps, dev)
+        value, tmax = aggregate(evals * steps, ms * 1e-3 * steps, dev)
         b.status()
         cfg = b.config()
         present = sorted({w.N + 1 for w in works})
-        out[name] = {"value": value / 1e9, "ms_per_launch": tmax * 1e3 / args.steps,
+        out[name] = {"value": value / 1e9, "unit": UNIT, "ms_per_launch": tmax * 1e3 / steps,
+                     "steps": steps, "warmup": warmup, "gpu_launches": steps,
                      "points": points, "instances": len(plan), "sweep": sweep,
+                     "dtype": {"fp64": "f64", "mixed": "f32 (perturbation state)"}[prec],
                      "autotuned": {"tile_elements_by_nq": {str(nq): cfg["tile"][nq] for nq in present},
                                    "sweep_by_nq": {str(nq): cfg["sweep"][nq] for nq in present},
                                    "ctas_per_sm": cfg["ctas_per_sm"] or "max",
@@ -545,6 +602,28 @@ def run_batched(args):
             vt.close()
         del states, saved
         torch.cuda.empty_cache()
+    return out, plan
+
+
+BATCHED_WORKLOAD = ("{n} instances, N in {{3,4,5,7}}, 512..32768 elements (log-uniform, cubes), "
+                    "smooth velocities (peak 10 m/s), 10 LSRK(5,4) steps at dt = 0.01 s per launch "
+                    "from the initial states")
+
+
+def run_batched(args):
+    """The batched workload: 64 independent instances (N from {3,4,5,7},
+    512..32768 elements) advanced by 10 low-storage RK steps at dt = 0.01 s in one
+    graph-captured persistent launch.  Metric: volume-term evaluations per
+    second, in GDOF/s (points x 5 stages x steps / time)."""
+    import torch
+    rank, local, world = dist_setup("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    from paper_1604_08501_gb300 import build as lib_build
+    lib_build.build()
+    orders = [int(x) for x in args.orders.split(",") if x] if args.orders else None
+    out, plan = batched_results(rank, dev, world, args.precisions, args.instances, args.steps,
+                                args.warmup, orders)
     if rank == 0:
         head = args.precisions[0]
         line = {"metric": "batched volume-RHS GDOF/s (points x RK stages / s)",
@@ -555,13 +634,12 @@ def run_batched(args):
                           "mixed-tc": "f32 (perturbation state), TF32 split products",
                           "mixed-auto": "f32 (perturbation state)"}[head],
                 "data": "synthetic",
-                "config": {"workload": f"{len(plan)} instances, N in {{3,4,5,7}}, 512..32768 elements "
-                                       f"(log-uniform, cubes), smooth velocities (peak 10 m/s), "
-                                       f"10 LSRK(5,4) steps at dt = 0.01 s per launch from the "
-                                       f"initial states",
+                "config": {"workload": BATCHED_WORKLOAD.format(n=len(plan))
+                           + (f" (the plan's instances of orders N = {args.orders})" if orders else ""),
                            "points": out[head]["points"],
                            "l2": "states restored before each launch (a copy larger than L2)"},
                 "gpu_launches": args.steps, "clocks": out[head]["clocks"], "precision": head,
+                "autotuned": out[head]["autotuned"],
                 "variants": {k: v for k, v in out.items() if k != head}}
         print(json.dumps(line))
     return 0
@@ -645,37 +723,29 @@ def run_nq_sweep(args):
     return 0
 
 
-def run_serving(args):
-    """The serving workload: a Poisson stream of ensemble-member requests (mean
-    args.rate per second), each an instance drawn from a pool of meshes sized as
-    in the batched workload (N in {3,4,5,7}, 512..32768 elements), advancing
-    k in {1, 5, 20} LSRK steps at dt = 0.01 s on device-resident state.  The
-    engine admits by a 120 GB HBM budget with up to 256 members resident and
-    advances the resident members by up to --round-steps steps per round
-    (continuous batching), under the chosen round policy.
-    Latency of a request: from its scheduled arrival to the moment its final
-    state is in host memory.  Throughput: point x stage evaluations of all
-    requests over the span from the first arrival to the last completion."""
+def serving_results(rank, dev, world, precisions, rate, requests, pool, budget_gb, round_steps,
+                    round_policy, warmup, requests_by_prec=None):
+    """The serving workload (run_serving's docstring) for each precision mode:
+    delivered rate, offered load and request latencies."""
     import torch
-    rank, local, world = dist_setup("nccl")
-    torch.cuda.set_device(local)
-    dev = torch.device("cuda", local)
-    from paper_1604_08501_gb300 import build as lib_build
     from paper_1604_08501_gb300 import workload as wl
     from paper_1604_08501_gb300.numa_vol import Engine, VolumeTerm
-    lib_build.build()
-    plan = wl.batch_plan(count=args.pool)
+    local = dev.index
+    plan = wl.batch_plan(count=pool)
     works = [wl.integration_workload(N, n, seed) for N, n, seed in plan]
     rng = np.random.Generator(np.random.PCG64(2024 + rank))
-    total = args.requests
-    gaps = rng.exponential(1.0 / args.rate, size=total)
-    pick = rng.integers(0, len(works), size=total)
-    ks = rng.choice(np.array([1, 5, 20]), size=total)
+    total_max = max([requests] + list((requests_by_prec or {}).values()))
+    gaps_all = rng.exponential(1.0 / rate, size=total_max)
+    pick_all = rng.integers(0, len(works), size=total_max)
+    ks_all = rng.choice(np.array([1, 5, 20]), size=total_max)
     dt = 0.01
     out = {}
-    for prec in args.precisions:
+    for prec in precisions:
         if prec not in ("fp64", "mixed"):
             continue
+        # the first `total` requests of one seeded stream
+        total = int((requests_by_prec or {}).get(prec, requests))
+        gaps, pick, ks = gaps_all[:total], pick_all[:total], ks_all[:total]
         vts = [VolumeTerm.from_problem(w.problem(), precision=prec) for w in works]
         q0s = []
         for w in works:
@@ -703,10 +773,10 @@ def run_serving(args):
             late[0] += 1
             return torch.empty(q0s[j].shape, dtype=q0s[j].dtype, pin_memory=True)
 
-        with Engine(prec, budget_bytes=args.budget_gb << 30, max_members=256,
-                    round_steps=args.round_steps, round_policy=args.round_policy) as eng:
+        with Engine(prec, budget_bytes=budget_gb << 30, max_members=256,
+                    round_steps=round_steps, round_policy=round_policy) as eng:
             # warm-up: a few requests through the same path, not timed
-            for j in range(min(args.warmup, len(works))):
+            for j in range(min(warmup, len(works))):
                 o = take(j)
                 eng.submit(vts[j], q0s[j], o, 1, dt)
                 eng.run_until_idle()
@@ -749,18 +819,43 @@ def run_serving(args):
             stages = st["point_stages"] - base["point_stages"]
             span = last - t0
             value, tmax = aggregate(int(stages), span, dev)
-            offered = float(np.mean([works[int(j)].M for j in pick]) * 5 * np.mean(ks) * args.rate)
+            offered = float(np.mean([works[int(j)].M for j in pick]) * 5 * np.mean(ks) * rate)
             out[prec] = {"value": value / 1e9, "span_s": tmax,
                          "latency_ms": {"p50": float(np.percentile(lat, 50) * 1e3),
                                         "p99": float(np.percentile(lat, 99) * 1e3),
                                         "max": float(lat.max() * 1e3)},
                          "offered_gdofs": offered / 1e9, "rounds": st["rounds"] - base["rounds"],
-                         "requests": total, "late_pinned_allocations": late[0],
+                         "requests": total, "rate_per_s": rate,
+                         "late_pinned_allocations": late[0],
                          "clocks": clocks}
         for vt in vts:
             vt.close()
         del q0s, free
         torch.cuda.empty_cache()
+    return out, plan
+
+
+def run_serving(args):
+    """The serving workload: a Poisson stream of ensemble-member requests (mean
+    args.rate per second), each an instance drawn from a pool of meshes sized as
+    in the batched workload (N in {3,4,5,7}, 512..32768 elements), advancing
+    k in {1, 5, 20} LSRK steps at dt = 0.01 s on device-resident state.  The
+    engine admits by a 120 GB HBM budget with up to 256 members resident and
+    advances the resident members by up to --round-steps steps per round
+    (continuous batching), under the chosen round policy.
+    Latency of a request: from its scheduled arrival to the moment its final
+    state is in host memory.  Throughput: point x stage evaluations of all
+    requests over the span from the first arrival to the last completion."""
+    import torch
+    rank, local, world = dist_setup("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    from paper_1604_08501_gb300 import build as lib_build
+    lib_build.build()
+    out, plan = serving_results(rank, dev, world, args.precisions, args.rate, args.requests,
+                                args.pool, args.budget_gb, args.round_steps, args.round_policy,
+                                args.warmup)
+    total = args.requests
     if rank == 0:
         head = args.precisions[0]
         line = {"metric": "serving GDOF/s (points x RK stages / s) with p50/p99 request latency",
@@ -798,6 +893,12 @@ def main(argv=None):
                     help="skip the timed oracle sample (for profiling runs)")
     ap.add_argument("--no-e2e", action="store_true",
                     help="skip the host-buffer end-to-end leg (for profiling runs)")
+    ap.add_argument("--no-error", action="store_true",
+                    help="skip the comparison with the oracle (for profiling runs)")
+    ap.add_argument("--no-batched", action="store_true",
+                    help="single workload: skip the compact batched entry (for profiling runs)")
+    ap.add_argument("--no-serving", action="store_true",
+                    help="single workload: skip the compact serving entry (for profiling runs)")
     ap.add_argument("--n", type=int, default=32,
                     help="elements per axis; 32 is the timed workload, smaller is for ncu")
     ap.add_argument("--precision", default=None,
@@ -819,7 +920,8 @@ def main(argv=None):
     ap.add_argument("--round-policy", choices=["lockstep", "per_member"], default="per_member",
                     help="serving: every member the same steps per round, or each its own")
     ap.add_argument("--orders", default="",
-                    help="nq-sweep: comma-separated orders N to run (default 3,7,11,15)")
+                    help="nq-sweep: comma-separated orders N to run (default 3,7,11,15); "
+                         "batched: keep only the plan's instances of these orders")
     args = ap.parse_args(argv)
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

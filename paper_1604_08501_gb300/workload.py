@@ -48,6 +48,8 @@ from __future__ import annotations
 import math
 from dataclasses import dataclass, field
 
+import os
+
 import numpy as np
 
 NFIELDS = 5
@@ -197,12 +199,29 @@ def _bumps(rng: np.random.Generator, L: float, count: int = 4):
     return centres, widths, amps
 
 
-def _eval_bumps(x: np.ndarray, bumps) -> np.ndarray:
+def _eval_bumps_into(out: np.ndarray, x: np.ndarray, bumps) -> None:
     centres, widths, amps = bumps
-    out = np.zeros(x.shape[1])
     for c, w, a in zip(centres, widths, amps):
         r2 = (x[0] - c[0]) ** 2 + (x[1] - c[1]) ** 2 + (x[2] - c[2]) ** 2
         out += a * np.exp(-r2 / (w * w))
+
+
+def _eval_bumps(x: np.ndarray, bumps) -> np.ndarray:
+    """Sum of the Gaussian bumps at the points x (3, M).  Large meshes are
+    evaluated in chunks of points on a thread pool (NumPy releases the GIL in
+    its element-wise loops); every point sees the same operations in the same
+    order, so the result does not depend on the chunking."""
+    out = np.zeros(x.shape[1])
+    M = x.shape[1]
+    chunk = 1 << 19
+    if M <= 2 * chunk:
+        _eval_bumps_into(out, x, bumps)
+        return out
+    from concurrent.futures import ThreadPoolExecutor
+    starts = range(0, M, chunk)
+    with ThreadPoolExecutor(max_workers=min(16, os.cpu_count() or 1)) as ex:
+        list(ex.map(lambda s0: _eval_bumps_into(out[s0:s0 + chunk], x[:, s0:s0 + chunk], bumps),
+                    starts))
     return out
 
 
