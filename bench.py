@@ -444,7 +444,7 @@ def run_gpu(args):
         step_bytes = q_np.nbytes
         vt = VolumeTerm.from_problem(w.problem(), precision=prec)
         # The headline times exactly K launches; the other modes at least K
-        # and at least 0.3 s of launches (the paper's timing loop, Sec. 5).
+        # and at least 0.3 s of launches (the paper's timing loop, Sec. 4).
         r = time_variant(vt, q, q_host, dev, K, W, rank, e2e=not args.no_e2e,
                          min_region_s=0.0 if prec == args.precisions[0] else 0.3)
         r["kernel"] = vt.kernel_name
@@ -645,7 +645,7 @@ def run_batched(args):
     return 0
 
 
-# The paper's Nq study: 3,538,944 points at Nq = 4, 8, 12 and 16 (Sec. 5).
+# The paper's Nq study: 3,538,944 points at Nq = 4, 8, 12 and 16 (Sec. 4, Table 2).
 NQ_STUDY = {3: (48, 48, 24), 7: (24, 24, 12), 11: (16, 16, 8), 15: (12, 12, 6)}
 
 

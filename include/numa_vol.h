@@ -494,21 +494,23 @@ void numa_engine_destroy(numa_engine *e);
  * array of the library (about 57 KB, held by every GPU that loads the library
  * until the process exits).  The first call on a device does a one-time
  * set-up there: it looks up the array's device address and sets the kernel's
- * shared-memory limit.  Make that first call before any stream capture.
- * Every call overwrites the same array, so calls whose kernels may overlap on
- * the GPU (other streams, other host threads) race.  Serialise them on one
- * stream.
+ * shared-memory limit.  Every call overwrites the same array, so calls whose
+ * kernels may overlap on the GPU (other streams, other host threads) race.
+ * Serialise them on one stream.
  *
  * The call builds the table on its own stack, copies it into the array,
- * zeroes the counter and launches, all on `stream` (asynchronous; the table
- * copy from the stack is staged before the call returns).  It calls no
- * allocator: no cudaMalloc or cudaFree, no host heap, and it records no error
- * message.
+ * zeroes the counter and launches, all on `stream` (asynchronous).  The copy
+ * reads the stack frame while the call runs, which holds only when the
+ * stream is executing, not when it is being captured into a CUDA graph: a
+ * stream under capture is refused with NUMA_EINVAL before anything is
+ * enqueued (the capture itself stays valid).  It calls no allocator: no
+ * cudaMalloc or cudaFree, no host heap, and it records no error message.
  * Returns NUMA_OK; NUMA_ELIMIT if count > NUMA_NOALLOC_MAX_INSTANCES (or the
  * total work exceeds 2^31 - 1 items); NUMA_EINVAL for a NULL or misaligned
  * pointer, count < 1, nsteps < 0, handles of mixed kinds or of another device,
- * or a double-float handle; NUMA_EUNSUPPORTED for a handle of order
- * N > NUMA_MAX_N or with tracers; NUMA_ECUDA if a CUDA call fails.
+ * a double-float handle, or a stream under capture; NUMA_EUNSUPPORTED for a
+ * handle of order N > NUMA_MAX_N or with tracers; NUMA_ECUDA if a CUDA call
+ * fails.
  */
 #define NUMA_NOALLOC_MAX_INSTANCES 64
 int numa_batch_advance_noalloc(const numa_vol *const *handles, void *const *states, int count,

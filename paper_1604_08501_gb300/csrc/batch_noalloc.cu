@@ -146,6 +146,14 @@ extern "C" int numa_batch_advance_noalloc(const numa_vol *const *handles, void *
     if (count > kMaxInst) return NUMA_ELIMIT;
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return NUMA_ECUDA;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    // The table is copied from this call's stack frame: a captured copy would
+    // keep a pointer into a frame that is gone by the time the graph runs.
+    // So a stream that is being captured is refused before anything is
+    // enqueued (the capture stays valid).
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cap) != cudaSuccess) return NUMA_ECUDA;
+    if (cap != cudaStreamCaptureStatusNone) return NUMA_EINVAL;
     const bool mixed = handles[0] && handles[0]->kernel == Kernel::Mixed;
     NoallocTable tab;   // on the stack: no heap
     tab.count = count;
@@ -177,7 +185,6 @@ extern "C" int numa_batch_advance_noalloc(const numa_vol *const *handles, void *
 
     DeviceSetup ds;
     if (setup(dev, &ds) != cudaSuccess) return NUMA_ECUDA;
-    cudaStream_t s = static_cast<cudaStream_t>(stream);
     // The table's used part, from this stack frame (a pageable source is staged
     // before cudaMemcpyAsync returns), and a zeroed claim counter.
     const size_t used = offsetof(NoallocTable, inst) + sizeof(BatchInstance) * (size_t)count;

@@ -3,7 +3,7 @@
 //
 // The operation of vol_fp64.cu (Sec. 2, Eq. (2); sign and flux form of the
 // paper's r/s subroutines, Sec. 3), for the high orders of the paper's Nq
-// study (Sec. 5, Nq up to 16).  An element of Nq = 16 has 4096 points: more
+// study (Sec. 4, Table 2, Nq up to 16).  An element of Nq = 16 has 4096 points: more
 // than a CTA has threads, and its fifteen FP64 flux arrays (491 KB) exceed
 // shared memory.  So:
 //  * one CTA per element with three threads per (i, j) column (four in FP32

@@ -1,5 +1,5 @@
 """GPU parity of the native FP64 volume term at orders N = 8..15 (Nq up to 16,
-the range of the paper's Nq study, Sec. 5), through the C ABI.
+the range of the paper's Nq study, Sec. 4, Table 2), through the C ABI.
 
 Same bar as the low orders: per-field normwise max relative error <= 1e-12
 against the oracle's O2 form (and, at the study's sizes, against its pointwise

@@ -5,9 +5,13 @@ in a fixed device array of the library, so the call itself allocates nothing.
 
 Checked through the C ABI against the allocating entry point
 (numa_batch_advance) on the same states, after each of two calls in a row,
-within the tolerances the batch tests use: 1e-13 relative on the FP64 state
-increments, 1e-5 on the mixed-precision states.  This file is collected last,
-and it also passes alone in a fresh process.
+with one and with three steps per call (the several-step loop inside one
+persistent launch), within the tolerances the batch tests use: 1e-13 relative
+on the FP64 state increments, 1e-5 on the mixed-precision states.  Across the
+second call neither the device's free memory nor the PyTorch allocator's
+reserved bytes change (the first call does the one-time set-up).  A stream
+under capture is refused.  This file is collected last, and it also passes
+alone in a fresh process.
 """
 import ctypes as C
 
@@ -39,8 +43,9 @@ def _arrays(vts, states):
     return handles, ptrs
 
 
+@pytest.mark.parametrize("nsteps", [1, 3])
 @pytest.mark.parametrize("precision,tol", [("fp64", 1e-13), ("mixed", 1e-5)])
-def test_noalloc_advance_matches_batch_advance_on_two_calls(precision, tol):
+def test_noalloc_advance_matches_batch_advance_on_two_calls(precision, tol, nsteps):
     lib = _lib.load()
     works = [wl.make_workload(N, shape, seed=seed) for N, shape, seed in SPECS]
     vts = [VolumeTerm.from_problem(w.problem(), precision=precision) for w in works]
@@ -53,10 +58,16 @@ def test_noalloc_advance_matches_batch_advance_on_two_calls(precision, tol):
         for vt, q in zip(vts, qa):
             b.add(vt, q)
         for call in range(2):
-            b.advance(1, DT)
-            rc = lib.numa_batch_advance_noalloc(handles, ptrs, len(vts), 1, DT, C.c_void_p(stream))
+            b.advance(nsteps, DT)
+            torch.cuda.synchronize()
+            free0, reserved0 = torch.cuda.mem_get_info()[0], torch.cuda.memory_reserved()
+            rc = lib.numa_batch_advance_noalloc(handles, ptrs, len(vts), nsteps, DT,
+                                                C.c_void_p(stream))
             assert rc == _lib.NUMA_OK
             torch.cuda.synchronize()
+            if call == 1:   # after the first call's one-time set-up: nothing allocated
+                assert torch.cuda.mem_get_info()[0] == free0
+                assert torch.cuda.memory_reserved() == reserved0
             for k, (a, bq) in enumerate(zip(qa, qb)):
                 a_np, b_np = a.cpu().numpy().astype(np.float64), bq.cpu().numpy().astype(np.float64)
                 if precision == "fp64":
@@ -93,3 +104,28 @@ def test_noalloc_rejects_counts_beyond_its_maximum_and_bad_arguments():
     assert np.array_equal(q.cpu().numpy(), w.q)
     vt.close()
     vm.close()
+
+
+def test_noalloc_refuses_a_stream_under_capture():
+    lib = _lib.load()
+    w = wl.make_workload(3, (2, 1, 1), seed=5)
+    vt = VolumeTerm.from_problem(w.problem())
+    q = torch.from_numpy(w.q).cuda()
+    handles, ptrs = _arrays([vt], [q])
+    side = torch.cuda.Stream()
+    # the one-time set-up happens outside any capture
+    assert lib.numa_batch_advance_noalloc(handles, ptrs, 1, 1, DT,
+                                          C.c_void_p(side.cuda_stream)) == _lib.NUMA_OK
+    torch.cuda.synchronize()
+    before = q.clone()
+    scratch = torch.zeros(4, device="cuda")
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=side):
+        scratch.add_(1.0)   # the graph captures something of its own
+        rc = lib.numa_batch_advance_noalloc(handles, ptrs, 1, 1, DT, C.c_void_p(side.cuda_stream))
+    assert rc == _lib.NUMA_EINVAL
+    # the graph is never replayed; nothing of the refused call ran
+    torch.cuda.synchronize()
+    assert torch.equal(q, before)
+    del g
+    vt.close()
