@@ -375,12 +375,17 @@ void numa_batch_destroy(numa_batch *b);
  * host memory, a number of low-storage RK steps and a step size.  The engine
  * reserves its HBM budget once, as an arena for members' states, and admits
  * requests in arrival order while a member slot is free and the arena has room.
- * Each numa_engine_progress call is one round: admit, advance every resident
- * member by one step (or several, numa_engine_set_round_steps) in one
- * persistent launch (one per distinct dt), return the finished members'
- * states to their host buffers.  Requests submitted
- * while others run join at the next round.  A member's result is bitwise the
- * same whichever members share its rounds.  Engines are not thread-safe.
+ * Each numa_engine_progress call enqueues one round without waiting for the
+ * GPU: upload newly admitted states (on a copy stream), advance every
+ * resident member by one step (or several, numa_engine_set_round_steps) in one
+ * persistent launch (one per distinct dt) queued behind the previous round,
+ * and copy the states of members that finish with it to their host buffers
+ * (on a second copy stream).  Uploads and downloads overlap the launches, and
+ * requests submitted while a round runs join the next one.  A request is done
+ * when its final state is in host memory; progress reports it then, in the
+ * same or a later call.  Work tables are reserved at create time: no round
+ * allocates memory.  A member's result is bitwise the same whichever members
+ * share its rounds.  Engines are not thread-safe.
  */
 typedef struct numa_engine numa_engine;
 
@@ -424,9 +429,19 @@ int numa_engine_submit(numa_engine *e, const numa_vol *mesh, const void *q0_host
  * round (its state is discarded).  Errors: NUMA_EINVAL (unknown or finished). */
 int numa_engine_cancel(numa_engine *e, int64_t id);
 
-/* One round (synchronous).  Up to max_done ids of requests finished in this
- * round go to done_ids, their count to *num_done.  Errors: NUMA_ECUDA. */
+/* One round, enqueued on the device (see above).  Up to max_done ids of
+ * requests whose final state has reached host memory since the last call go
+ * to done_ids, their count to *num_done.  The call waits only when two
+ * launches are already in flight (for the older one), when a cancelled member's
+ * last launch has to finish before its memory is freed, and, with no member
+ * to advance, for the oldest result still being copied out.
+ * Errors: NUMA_ECUDA. */
 int numa_engine_progress(numa_engine *e, int64_t *done_ids, int max_done, int *num_done);
+
+/* Wait for everything enqueued (launches and copies) and report the requests
+ * that finished, like numa_engine_progress, without starting a round.
+ * Errors: NUMA_EINVAL, NUMA_ECUDA. */
+int numa_engine_drain(numa_engine *e, int64_t *done_ids, int max_done, int *num_done);
 
 /* Status and timestamps of a request.  The engine keeps the records of its
  * 2^20 most recently finished (done or cancelled) requests; an older finished

@@ -117,6 +117,8 @@ def load() -> C.CDLL:
     lib.numa_engine_cancel.argtypes = [C.c_void_p, C.c_int64]
     lib.numa_engine_progress.argtypes = [C.c_void_p, C.POINTER(C.c_int64), C.c_int,
                                          C.POINTER(C.c_int)]
+    lib.numa_engine_drain.argtypes = [C.c_void_p, C.POINTER(C.c_int64), C.c_int,
+                                      C.POINTER(C.c_int)]
     lib.numa_engine_query.argtypes = [C.c_void_p, C.c_int64, C.POINTER(numa_request_info)]
     lib.numa_engine_checkpoint.argtypes = [C.c_void_p, C.c_int64, C.c_void_p, C.POINTER(C.c_int)]
     lib.numa_engine_set_round_steps.argtypes = [C.c_void_p, C.c_int]
@@ -126,7 +128,8 @@ def load() -> C.CDLL:
     lib.numa_engine_destroy.argtypes = [C.c_void_p]
     lib.numa_engine_destroy.restype = None
     for name in ("numa_engine_create", "numa_engine_submit", "numa_engine_cancel",
-                 "numa_engine_progress", "numa_engine_query", "numa_engine_stats",
+                 "numa_engine_progress", "numa_engine_drain", "numa_engine_query",
+                 "numa_engine_stats",
                  "numa_engine_checkpoint", "numa_engine_set_round_steps",
                  "numa_engine_set_round_policy"):
         getattr(lib, name).restype = C.c_int

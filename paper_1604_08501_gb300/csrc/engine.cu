@@ -3,21 +3,34 @@
 //
 // A request names a resident mesh (a numa_vol handle the caller created), an
 // initial state and a number of RK steps.  The engine keeps members' states
-// in an arena it reserves once (the HBM budget), so admission never calls
-// cudaMalloc.  Each call of numa_engine_progress is one round:
-//   1. retire cancelled members;
-//   2. admit queued requests in arrival order while a member slot is free and
+// in an arena it reserves once (the HBM budget), and the work tables of its
+// launches in buffers reserved at create time, so no round allocates memory.
+// Each call of numa_engine_progress is one round, enqueued without waiting for
+// the GPU:
+//   1. report members whose final state has reached host memory and free
+//      their arena blocks;
+//   2. retire cancelled members (their blocks are freed once the last launch
+//      that used them has finished);
+//   3. admit queued requests in arrival order while a member slot is free and
 //      the arena has room (first fit); the head of the queue waits if it does
-//      not fit yet, so later requests cannot starve it;
-//   3. advance every resident member by s steps, all in one persistent launch
-//      (members of different dt in one launch each): s = 1 by default, or up
-//      to a set limit but never past the next member's completion; or, under
-//      the per-member policy, each member by its own min(limit, remaining);
-//   4. copy finished members' states to their host buffers and free them.
-// Requests that arrive during a round join at the next round while the others
-// are still resident.  That is the continuous batching.  Elements evolve
-// independently in the volume term, so a member's result is bitwise the same
-// whichever members share its rounds.
+//      not fit yet, so later requests cannot starve it.  Their states upload
+//      on a copy stream; the round's launch waits for them on the device;
+//   4. advance every resident member by s steps, all in one persistent launch
+//      (members of different dt in one launch each) on the compute stream:
+//      s = 1 by default, or up to a set limit but never past the next member's
+//      completion; or, under the per-member policy, each member by its own
+//      min(limit, remaining);
+//   5. members that finish with this round copy their states out on a second
+//      copy stream once its launch has run; they are reported (step 1) by
+//      this or a later call, when the copy has completed.
+// So the uploads of newly admitted members and the downloads of finished ones
+// overlap the launches, and requests that arrive while a round runs join the
+// next round, whose launch is queued behind it: the continuous batching.  At
+// most two launches are in flight (their work tables are double-buffered);
+// a call waits only for a free table buffer, for the last launch of a
+// cancelled member, or, when it has nothing to enqueue, for the oldest copy
+// still in flight.  Elements evolve independently in the volume term, so a
+// member's result is bitwise the same whichever members share its rounds.
 //
 // Checkpoint and resume: a step of the 2N-storage scheme starts from the state
 // alone (its register restarts at zero), so the state after a member's last
@@ -128,17 +141,44 @@ double now_s() {
 
 }  // namespace
 
+namespace {
+
+// Work tables of one launch: device copies and their pinned host staging.
+// `done` is recorded after the launch; the buffers are reused once it has
+// completed.
+struct LaunchSlot {
+    numa::BatchInstance *d_inst = nullptr, *h_inst = nullptr;
+    numa::BatchItem *d_items = nullptr, *h_items = nullptr;
+    int *d_counter = nullptr;
+    cudaEvent_t done = nullptr;
+    bool used = false;
+};
+
+// A finished member whose state is being copied to its host buffer.
+struct PendingResult {
+    Request r;
+    cudaEvent_t copied;
+};
+
+}  // namespace
+
 struct numa_engine {
     numa_precision prec = NUMA_FP64;
     int device = 0, num_sms = 0, max_members = 0;
     size_t elem = 8;
     Arena arena;
     void *d_arena = nullptr;
-    numa::BatchInstance *d_inst = nullptr;
-    numa::BatchItem *d_items = nullptr;
+    static constexpr int kSlots = 2;
+    LaunchSlot slot[kSlots];
+    int next_slot = 0;
     size_t items_cap = 0;
-    int *d_counter = nullptr;
-    cudaStream_t stream = nullptr;
+    cudaStream_t stream = nullptr;            // launches
+    cudaStream_t h2d = nullptr, d2h = nullptr;   // admissions, results
+    cudaEvent_t admitted = nullptr;           // after this call's admission uploads
+    cudaEvent_t last_launch = nullptr;        // after the most recent launch
+    bool launched_any = false;
+    std::vector<PendingResult> pending;
+    std::vector<cudaEvent_t> free_events;     // for PendingResult::copied
     int64_t next_id = 1;
     std::deque<Request> queue;
     std::vector<Request> resident;
@@ -193,22 +233,46 @@ int numa_engine_create(numa_precision prec, size_t budget_bytes, int max_members
     e->prec = prec;
     e->elem = prec == NUMA_MIXED ? sizeof(float) : sizeof(double);
     e->max_members = max_members;
-    e->items_cap = (size_t)max_members * 8192;
+    // The most work items one launch can have: every point the budget holds,
+    // in items of the fewest points (tile_mult passes of one element at
+    // Nq = 7: 4 x 343 points), plus one partial item per member.
+    {
+        size_t min_item_points = SIZE_MAX;
+        for (int nq = 2; nq <= 8; ++nq)
+            min_item_points = std::min(min_item_points, (size_t)numa::elements_per_pass(nq) *
+                                                            e->tile_mult * nq * nq * nq);
+        e->items_cap = budget_bytes / (e->elem * numa::kFields) / min_item_points +
+                       (size_t)max_members + 1;
+    }
     cudaError_t err = cudaGetDevice(&e->device);
     if (err == cudaSuccess)
         err = cudaDeviceGetAttribute(&e->num_sms, cudaDevAttrMultiProcessorCount, e->device);
     if (err == cudaSuccess) err = numa::prepare_batch_lsrk();
     if (err == cudaSuccess) err = cudaMalloc(&e->d_arena, budget_bytes);
-    if (err == cudaSuccess) err = cudaMalloc(&e->d_inst, sizeof(numa::BatchInstance) * max_members);
-    if (err == cudaSuccess) err = cudaMalloc(&e->d_items, sizeof(numa::BatchItem) * e->items_cap);
-    if (err == cudaSuccess) err = cudaMalloc(&e->d_counter, 256);
+    for (auto &sl : e->slot) {
+        if (err == cudaSuccess)
+            err = cudaMalloc(&sl.d_inst, sizeof(numa::BatchInstance) * max_members);
+        if (err == cudaSuccess)
+            err = cudaMallocHost(&sl.h_inst, sizeof(numa::BatchInstance) * max_members);
+        if (err == cudaSuccess) err = cudaMalloc(&sl.d_items, sizeof(numa::BatchItem) * e->items_cap);
+        if (err == cudaSuccess)
+            err = cudaMallocHost(&sl.h_items, sizeof(numa::BatchItem) * e->items_cap);
+        if (err == cudaSuccess) err = cudaMalloc(&sl.d_counter, 256);
+        if (err == cudaSuccess) err = cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming);
+    }
     if (err == cudaSuccess) err = cudaStreamCreateWithFlags(&e->stream, cudaStreamNonBlocking);
+    if (err == cudaSuccess) err = cudaStreamCreateWithFlags(&e->h2d, cudaStreamNonBlocking);
+    if (err == cudaSuccess) err = cudaStreamCreateWithFlags(&e->d2h, cudaStreamNonBlocking);
+    if (err == cudaSuccess) err = cudaEventCreateWithFlags(&e->admitted, cudaEventDisableTiming);
+    if (err == cudaSuccess) err = cudaEventCreateWithFlags(&e->last_launch, cudaEventDisableTiming);
+    for (int k = 0; k < max_members && err == cudaSuccess; ++k) {
+        cudaEvent_t ev = nullptr;
+        err = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+        if (err == cudaSuccess) e->free_events.push_back(ev);
+    }
     if (err != cudaSuccess) {
-        cudaFree(e->d_arena);
-        cudaFree(e->d_inst);
-        cudaFree(e->d_items);
-        cudaFree(e->d_counter);
-        delete e;
+        numa_engine_destroy(e);
+        cudaGetLastError();
         return efail_cuda(err, "numa_engine_create: reserving device memory");
     }
     e->arena.reset(static_cast<char *>(e->d_arena), budget_bytes);
@@ -262,15 +326,64 @@ int numa_engine_cancel(numa_engine *e, int64_t id) {
             r.status = NUMA_REQ_CANCELLED;   // retired at the start of the next round
             return NUMA_OK;
         }
+    // (a member whose result is being copied out has finished: not cancellable)
     return efail(NUMA_EINVAL, "numa_engine_cancel: no queued or running request with this id");
 }
+
+namespace {
+
+// Step 1 of a round: members whose result copy has completed (all of them
+// with wait_all; with wait_oldest the oldest one is waited for first).
+cudaError_t collect_results(numa_engine *e, bool wait_all, bool wait_oldest,
+                            std::vector<int64_t> *done) {
+    cudaError_t err = cudaSuccess;
+    if (wait_oldest && !e->pending.empty()) err = cudaEventSynchronize(e->pending.front().copied);
+    if (err != cudaSuccess) return err;
+    for (size_t k = 0; k < e->pending.size();) {
+        PendingResult &p = e->pending[k];
+        cudaError_t q = wait_all ? cudaEventSynchronize(p.copied) : cudaEventQuery(p.copied);
+        if (q == cudaErrorNotReady) {
+            ++k;
+            continue;
+        }
+        if (q != cudaSuccess) return q;
+        e->arena.release(p.r.off, p.r.bytes);
+        set_status(e, p.r.id, NUMA_REQ_DONE, true);
+        ++e->completed;
+        done->push_back(p.r.id);
+        e->free_events.push_back(p.copied);
+        e->pending.erase(e->pending.begin() + k);
+    }
+    return cudaSuccess;
+}
+
+int report(const std::vector<int64_t> &done, int64_t *done_ids, int max_done, int *num_done) {
+    int n = 0;
+    for (int64_t id : done) {
+        if (done_ids && n < max_done) done_ids[n] = id;
+        ++n;
+    }
+    if (num_done) *num_done = std::min(n, std::max(max_done, 0));
+    return NUMA_OK;
+}
+
+}  // namespace
 
 int numa_engine_progress(numa_engine *e, int64_t *done_ids, int max_done, int *num_done) {
     g_engine_error.clear();
     if (num_done) *num_done = 0;
     if (!e) return efail(NUMA_EINVAL, "numa_engine_progress: NULL engine");
-    cudaError_t err = cudaSuccess;
-    // 1. retire cancelled members
+    std::vector<int64_t> done;
+    // 1. results that have reached host memory
+    cudaError_t err = collect_results(e, false, false, &done);
+    if (err != cudaSuccess) return efail_cuda(err, "numa_engine_progress: result copy");
+    // 2. retire cancelled members, once the last launch that used them is over
+    bool cancelled = false;
+    for (const auto &r : e->resident) cancelled = cancelled || r.status == NUMA_REQ_CANCELLED;
+    if (cancelled && e->launched_any) {
+        err = cudaEventSynchronize(e->last_launch);
+        if (err != cudaSuccess) return efail_cuda(err, "numa_engine_progress: retiring");
+    }
     for (size_t k = 0; k < e->resident.size();) {
         Request &r = e->resident[k];
         if (r.status == NUMA_REQ_CANCELLED) {
@@ -281,22 +394,39 @@ int numa_engine_progress(numa_engine *e, int64_t *done_ids, int max_done, int *n
             ++k;
         }
     }
-    // 2. admit in arrival order
-    while (!e->queue.empty() && (int)e->resident.size() < e->max_members) {
+    // 3. admit in arrival order; members whose results are still being copied
+    //    out hold their slots and blocks
+    bool admitted = false;
+    while (!e->queue.empty() &&
+           (int)(e->resident.size() + e->pending.size()) < e->max_members) {
         Request r = e->queue.front();
         const size_t off = e->arena.alloc(r.bytes);
         if (off == SIZE_MAX) break;   // the head waits for room
         e->queue.pop_front();
         r.off = off;
         r.status = NUMA_REQ_RUNNING;
-        err = cudaMemcpyAsync(e->arena.base + off, r.q0, r.bytes, cudaMemcpyHostToDevice, e->stream);
+        err = cudaMemcpyAsync(e->arena.base + off, r.q0, r.bytes, cudaMemcpyHostToDevice, e->h2d);
         if (err != cudaSuccess) return efail_cuda(err, "numa_engine_progress: state upload");
         e->info[r.id].status = NUMA_REQ_RUNNING;
         e->info[r.id].admit_s = now_s();
         e->resident.push_back(r);
+        admitted = true;
     }
-    if (e->resident.empty()) return NUMA_OK;
-    // 3. advance the residents, one launch per distinct dt.  Lockstep: every
+    if (admitted) {
+        err = cudaEventRecord(e->admitted, e->h2d);
+        if (err == cudaSuccess) err = cudaStreamWaitEvent(e->stream, e->admitted, 0);
+        if (err != cudaSuccess) return efail_cuda(err, "numa_engine_progress: state upload");
+    }
+    if (e->resident.empty()) {
+        // nothing to launch: wait for the oldest result still in flight
+        // rather than return at once to a caller that polls
+        if (done.empty() && !e->pending.empty()) {
+            err = collect_results(e, false, true, &done);
+            if (err != cudaSuccess) return efail_cuda(err, "numa_engine_progress: result copy");
+        }
+        return report(done, done_ids, max_done, num_done);
+    }
+    // 4. advance the residents, one launch per distinct dt.  Lockstep: every
     //    member by s, the smallest remaining step count up to max_round_steps,
     //    so every member that finishes does so in the round it would with
     //    single steps.  Per member: each by min(max_round_steps, remaining).
@@ -342,60 +472,76 @@ int numa_engine_progress(numa_engine *e, int64_t *done_ids, int max_done, int *n
                                  return cost(a) > cost(b);
                              });
         }
-        if (items.size() > e->items_cap) {
-            cudaFree(e->d_items);
-            e->items_cap = items.size();
-            err = cudaMalloc(&e->d_items, sizeof(numa::BatchItem) * e->items_cap);
-            if (err != cudaSuccess) {
-                e->d_items = nullptr;
-                e->items_cap = 0;
-                return efail_cuda(err, "numa_engine_progress: work list");
-            }
+        if (items.size() > e->items_cap || inst.size() > (size_t)e->max_members)
+            return efail(NUMA_ECUDA, "numa_engine_progress: work list beyond the reserved tables");
+        // the table buffers of the launch two back are free once it has run
+        LaunchSlot &sl = e->slot[e->next_slot];
+        e->next_slot = (e->next_slot + 1) % numa_engine::kSlots;
+        if (sl.used) {
+            err = cudaEventSynchronize(sl.done);
+            if (err != cudaSuccess) return efail_cuda(err, "numa_engine_progress: step");
         }
-        err = cudaMemcpyAsync(e->d_inst, inst.data(), sizeof(numa::BatchInstance) * inst.size(),
+        std::memcpy(sl.h_inst, inst.data(), sizeof(numa::BatchInstance) * inst.size());
+        std::memcpy(sl.h_items, items.data(), sizeof(numa::BatchItem) * items.size());
+        err = cudaMemcpyAsync(sl.d_inst, sl.h_inst, sizeof(numa::BatchInstance) * inst.size(),
                               cudaMemcpyHostToDevice, e->stream);
         if (err == cudaSuccess)
-            err = cudaMemcpyAsync(e->d_items, items.data(), sizeof(numa::BatchItem) * items.size(),
+            err = cudaMemcpyAsync(sl.d_items, sl.h_items, sizeof(numa::BatchItem) * items.size(),
                                   cudaMemcpyHostToDevice, e->stream);
-        if (err == cudaSuccess) err = cudaMemsetAsync(e->d_counter, 0, sizeof(int), e->stream);
+        if (err == cudaSuccess) err = cudaMemsetAsync(sl.d_counter, 0, sizeof(int), e->stream);
         if (err == cudaSuccess)
-            err = numa::launch_batch_lsrk(e->prec == NUMA_MIXED, e->d_inst, e->d_items,
-                                          (int)items.size(), e->d_counter, kCoef, launch_steps,
+            err = numa::launch_batch_lsrk(e->prec == NUMA_MIXED, sl.d_inst, sl.d_items,
+                                          (int)items.size(), sl.d_counter, kCoef, launch_steps,
                                           dt, e->num_sms, e->stream);
-        // the host vectors are sources of in-flight copies: wait before they go
-        if (err == cudaSuccess) err = cudaStreamSynchronize(e->stream);
+        if (err == cudaSuccess) err = cudaEventRecord(sl.done, e->stream);
+        if (err == cudaSuccess) err = cudaEventRecord(e->last_launch, e->stream);
         if (err != cudaSuccess) return efail_cuda(err, "numa_engine_progress: step");
+        sl.used = true;
+        e->launched_any = true;
     }
     ++e->rounds;
-    // 4. retire finished members
-    std::vector<Request> done;
+    // 5. members that finish with this round: their states go to their host
+    //    buffers on the result stream once the round has run
+    bool any_done = false;
     for (size_t k = 0; k < e->resident.size();) {
         Request &r = e->resident[k];
         r.remaining -= steps_of(r);
         if (r.remaining == 0) {
+            if (!any_done) {
+                err = cudaStreamWaitEvent(e->d2h, e->last_launch, 0);
+                if (err != cudaSuccess) return efail_cuda(err, "numa_engine_progress: result copy");
+                any_done = true;
+            }
+            if (e->free_events.empty())
+                return efail(NUMA_ECUDA, "numa_engine_progress: no event left for a result copy");
+            PendingResult p{r, e->free_events.back()};
+            e->free_events.pop_back();
             err = cudaMemcpyAsync(r.q_out, e->arena.base + r.off, r.bytes, cudaMemcpyDeviceToHost,
-                                  e->stream);
+                                  e->d2h);
+            if (err == cudaSuccess) err = cudaEventRecord(p.copied, e->d2h);
             if (err != cudaSuccess) return efail_cuda(err, "numa_engine_progress: result copy");
-            done.push_back(r);
+            e->pending.push_back(p);
             e->resident.erase(e->resident.begin() + k);
         } else {
             ++k;
         }
     }
-    if (!done.empty()) {
-        err = cudaStreamSynchronize(e->stream);
-        if (err != cudaSuccess) return efail_cuda(err, "numa_engine_progress: result copy");
-        int n = 0;
-        for (const auto &r : done) {
-            e->arena.release(r.off, r.bytes);
-            set_status(e, r.id, NUMA_REQ_DONE, true);
-            ++e->completed;
-            if (done_ids && n < max_done) done_ids[n] = r.id;
-            ++n;
-        }
-        if (num_done) *num_done = std::min(n, max_done);
-    }
-    return NUMA_OK;
+    err = collect_results(e, false, false, &done);
+    if (err != cudaSuccess) return efail_cuda(err, "numa_engine_progress: result copy");
+    return report(done, done_ids, max_done, num_done);
+}
+
+int numa_engine_drain(numa_engine *e, int64_t *done_ids, int max_done, int *num_done) {
+    g_engine_error.clear();
+    if (num_done) *num_done = 0;
+    if (!e) return efail(NUMA_EINVAL, "numa_engine_drain: NULL engine");
+    cudaError_t err = cudaStreamSynchronize(e->stream);
+    if (err == cudaSuccess) err = cudaStreamSynchronize(e->h2d);
+    if (err == cudaSuccess) err = cudaStreamSynchronize(e->d2h);
+    std::vector<int64_t> done;
+    if (err == cudaSuccess) err = collect_results(e, true, false, &done);
+    if (err != cudaSuccess) return efail_cuda(err, "numa_engine_drain");
+    return report(done, done_ids, max_done, num_done);
 }
 
 int numa_engine_set_round_steps(numa_engine *e, int max_steps) {
@@ -422,13 +568,23 @@ int numa_engine_checkpoint(numa_engine *e, int64_t id, void *state_host, int *st
         }
     for (const auto &r : e->resident)
         if (r.id == id && r.status == NUMA_REQ_RUNNING) {
-            // progress() ends every round with the stream idle, so the arena
-            // holds the state after the member's last completed step
-            const cudaError_t err = cudaMemcpyAsync(state_host, e->arena.base + r.off, r.bytes,
-                                                    cudaMemcpyDeviceToHost, e->stream);
-            const cudaError_t err2 = err == cudaSuccess ? cudaStreamSynchronize(e->stream) : err;
-            if (err2 != cudaSuccess) return efail_cuda(err2, "numa_engine_checkpoint");
+            // after the launches already enqueued, the arena holds the state
+            // after the member's last enqueued step
+            cudaError_t err = cudaStreamSynchronize(e->stream);
+            if (err == cudaSuccess)
+                err = cudaMemcpyAsync(state_host, e->arena.base + r.off, r.bytes,
+                                      cudaMemcpyDeviceToHost, e->stream);
+            if (err == cudaSuccess) err = cudaStreamSynchronize(e->stream);
+            if (err != cudaSuccess) return efail_cuda(err, "numa_engine_checkpoint");
             if (steps_done) *steps_done = r.nsteps - r.remaining;
+            return NUMA_OK;
+        }
+    for (const auto &p : e->pending)
+        if (p.r.id == id) {   // finished, its result still being copied out
+            cudaError_t err = cudaEventSynchronize(p.copied);
+            if (err == cudaSuccess) std::memcpy(state_host, p.r.q_out, p.r.bytes);
+            if (err != cudaSuccess) return efail_cuda(err, "numa_engine_checkpoint");
+            if (steps_done) *steps_done = p.r.nsteps;
             return NUMA_OK;
         }
     return efail(NUMA_EINVAL, "numa_engine_checkpoint: no queued or running request with this id");
@@ -445,7 +601,7 @@ int numa_engine_query(const numa_engine *e, int64_t id, numa_request_info *out) 
 int numa_engine_stats(const numa_engine *e, numa_engine_counters *out) {
     if (!e || !out) return efail(NUMA_EINVAL, "numa_engine_stats: NULL argument");
     out->queued = (int)e->queue.size();
-    out->resident = (int)e->resident.size();
+    out->resident = (int)(e->resident.size() + e->pending.size());
     out->bytes_used = e->arena.used;
     out->bytes_budget = e->arena.size;
     out->completed = e->completed;
@@ -456,14 +612,24 @@ int numa_engine_stats(const numa_engine *e, numa_engine_counters *out) {
 
 void numa_engine_destroy(numa_engine *e) {
     if (!e) return;
-    if (e->stream) {
-        cudaStreamSynchronize(e->stream);
-        cudaStreamDestroy(e->stream);
+    for (cudaStream_t st : {e->stream, e->h2d, e->d2h})
+        if (st) {
+            cudaStreamSynchronize(st);
+            cudaStreamDestroy(st);
+        }
+    for (auto &sl : e->slot) {
+        cudaFree(sl.d_inst);
+        cudaFreeHost(sl.h_inst);
+        cudaFree(sl.d_items);
+        cudaFreeHost(sl.h_items);
+        cudaFree(sl.d_counter);
+        if (sl.done) cudaEventDestroy(sl.done);
     }
+    for (auto &p : e->pending) e->free_events.push_back(p.copied);
+    for (cudaEvent_t ev : e->free_events) cudaEventDestroy(ev);
+    if (e->admitted) cudaEventDestroy(e->admitted);
+    if (e->last_launch) cudaEventDestroy(e->last_launch);
     cudaFree(e->d_arena);
-    cudaFree(e->d_inst);
-    cudaFree(e->d_items);
-    cudaFree(e->d_counter);
     delete e;
 }
 

@@ -368,9 +368,21 @@ class Engine:
         check_engine(_lib.load().numa_engine_cancel(self.handle, C.c_int64(rid)))
 
     def progress(self, max_done: int = 4096):
+        """Enqueue one round; returns the ids of requests whose final state has
+        reached host memory since the last call."""
         ids = (C.c_int64 * max_done)()
         n = C.c_int()
         check_engine(_lib.load().numa_engine_progress(self.handle, ids, max_done, C.byref(n)))
+        done = [ids[k] for k in range(n.value)]
+        for rid in done:
+            self._bufs.pop(rid, None)
+        return done
+
+    def drain(self, max_done: int = 4096):
+        """Wait for everything enqueued; returns the ids of requests that finished."""
+        ids = (C.c_int64 * max_done)()
+        n = C.c_int()
+        check_engine(_lib.load().numa_engine_drain(self.handle, ids, max_done, C.byref(n)))
         done = [ids[k] for k in range(n.value)]
         for rid in done:
             self._bufs.pop(rid, None)

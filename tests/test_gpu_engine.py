@@ -250,6 +250,7 @@ def test_per_member_rounds_give_the_same_bits_in_fewer_rounds(pool, precision):
             for n in range(12):
                 eng.submit(vts[1 + n % 3], q0s[1 + n % 3], o[1 + n], 1, DT)
                 eng.progress()
+                eng.drain()   # the round has run and its results are in host memory
                 if done_in[policy] is None and eng.query(long_id)["status"] == "done":
                     done_in[policy] = n + 1
             eng.run_until_idle()
@@ -260,3 +261,32 @@ def test_per_member_rounds_give_the_same_bits_in_fewer_rounds(pool, precision):
     assert done_in["lockstep"] is None   # still running after 12 one-step rounds
     for vt in vts:
         vt.close()
+
+
+@pytest.mark.parametrize("policy", ["lockstep", "per_member"])
+def test_rounds_allocate_no_device_memory(pool, policy):
+    """After the first round (the kernel's one-time set-up), rounds with
+    admissions, launches and result copies leave the device's free memory and
+    the PyTorch allocator's reserve unchanged: the arena and the work tables
+    are reserved at create time."""
+    works, vts = pool
+    outs = [np.empty_like(works[n % len(works)].q) for n in range(12)]
+    with Engine("fp64", budget_bytes=1 << 28, max_members=8, round_steps=2,
+                round_policy=policy) as eng:
+        eng.submit(vts[0], works[0].q, np.empty_like(works[0].q), 1, DT)
+        eng.run_until_idle()
+        torch.cuda.synchronize()
+        free0, reserved0 = torch.cuda.mem_get_info()[0], torch.cuda.memory_reserved()
+        ids = []
+        for n, o in enumerate(outs):
+            j = n % len(works)
+            ids.append(eng.submit(vts[j], works[j].q, o, 1 + n % 5, DT))
+            eng.progress()
+            assert torch.cuda.mem_get_info()[0] == free0
+        eng.run_until_idle()
+        assert torch.cuda.mem_get_info()[0] == free0
+        assert torch.cuda.memory_reserved() == reserved0
+        assert all(eng.query(r)["status"] == "done" for r in ids)
+    for n, o in enumerate(outs):
+        j = n % len(works)
+        assert np.array_equal(o, batch_reference(vts[j], works[j].q, 1 + n % 5))
