@@ -9,9 +9,13 @@ Table 2), aggregated over all ranks.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl numa|reference]
 
-Under torchrun every rank evaluates its own copy of the workload: elements are
-independent in the volume term, so ranks need no data-path collective (weak
-scaling).  Rank 0 prints one JSON line.
+Under torchrun the ranks share one mesh of 32 x 32 x (32 ranks) elements by
+contiguous element ranges (--shard elements, the default; each rank 32^3
+elements) or each evaluates a replica of the workload (--shard replicas):
+elements are independent in the volume term, so ranks need no data-path
+collective (weak scaling).  Rank 0 prints one JSON line, with compact entries
+for the batched and serving workloads and each mode's error against the
+oracle.
 
 --impl reference times the FP64 CPU oracle on the host cores instead (each step
 a bounded sample of the same workload); only rank 0 runs it.
@@ -62,6 +66,30 @@ def workload_full(n: int = 32):
         return wl.bench_full(), wl.BENCH_FULL["name"]
     w = wl.make_workload(N=wl.BENCH_FULL["N"], n=n, seed=wl.BENCH_FULL["seed"])
     return w, f"N=7 (Nq=8), {n}^3={n ** 3} elements, warped 10 km box (profiling size)"
+
+
+def shard_ranges(n: int, world: int):
+    """Element layers of each rank when `world` ranks share one mesh of
+    n x n x (n world) elements: rank r takes layers [n r, n (r + 1)), the
+    contiguous elements [n^3 r, n^3 (r + 1)), an equal share Ne Nq^3 / world of
+    the points."""
+    return [(n * r, n * (r + 1)) for r in range(world)]
+
+
+def workload_for_rank(n: int, rank: int, world: int, shard: str):
+    """This rank's workload: under element sharding the rank's contiguous
+    element range of one n x n x (n world)-element mesh (point for point the
+    values of those elements in the whole mesh, so the ranks together evaluate
+    the volume term of that mesh with no exchange: elements are independent);
+    as replicas the whole n^3-element workload on every rank."""
+    from paper_1604_08501_gb300 import workload as wl
+    if world == 1 or shard == "replicas":
+        return workload_full(n)
+    z0, z1 = shard_ranges(n, world)[rank]
+    w = wl.make_workload(N=wl.BENCH_FULL["N"], n=(n, n, n * world), seed=wl.BENCH_FULL["seed"],
+                         z_range=(z0, z1))
+    return w, (f"N=7 (Nq=8), one warped 10 km box of {n}x{n}x{n * world} elements shared by "
+               f"{world} ranks by element layers ({n ** 3} elements, {w.M} points per rank)")
 
 
 def workload_config(w, name):
@@ -431,7 +459,7 @@ def run_gpu(args):
     barrier(dev)
     from paper_1604_08501_gb300.numa_vol import VolumeTerm
 
-    w, name = workload_full(args.n)
+    w, name = workload_for_rank(args.n, rank, world, args.shard)
     K, W = args.steps, args.warmup
 
     results = {}
@@ -472,11 +500,16 @@ def run_gpu(args):
         roof, other = roofline_entries(head["kernel"], head["kernel_ms"], w)
         dtypes = {"fp64": "f64", "df64": "df64 (FP32 hi+lo pairs, 48-bit)",
                   "mixed": "f32 (perturbation state)"}
+        cfg = workload_config(w, name)
+        if world > 1:
+            cfg["parallelism"] = (f"{world} ranks, " + ("contiguous element ranges of one mesh, "
+                                  "no collective" if args.shard == "elements"
+                                  else "a replica of the workload per rank, no collective"))
         line = {"metric": METRIC, "value": head["value"], "unit": UNIT, "n_gpus": world,
                 "steps": K, "warmup": W, "ms_per_step": head["ms_per_step"],
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
                 "dtype": dtypes.get(head_prec, head_prec), "data": "synthetic",
-                "config": workload_config(w, name), "roofline": roof, "roofline_other": other,
+                "config": cfg, "roofline": roof, "roofline_other": other,
                 "e2e": head["e2e"], "gpu_launches": K, "clocks": head["clocks"],
                 "precision": head_prec, "launch_ms": head["launch_ms"],
                 "field_dof_rate": {"value": head["value"] * 5, "unit": "G field-DOF/s",
@@ -899,6 +932,10 @@ def main(argv=None):
                     help="single workload: skip the compact batched entry (for profiling runs)")
     ap.add_argument("--no-serving", action="store_true",
                     help="single workload: skip the compact serving entry (for profiling runs)")
+    ap.add_argument("--shard", choices=["elements", "replicas"], default="elements",
+                    help="under torchrun: share one mesh by contiguous element ranges (each "
+                         "rank n^3 elements of an n x n x (n ranks) mesh), or evaluate a "
+                         "replica of the n^3-element workload per rank")
     ap.add_argument("--n", type=int, default=32,
                     help="elements per axis; 32 is the timed workload, smaller is for ncu")
     ap.add_argument("--precision", default=None,

@@ -111,18 +111,20 @@ class Mesh:
         return self.Ne * self.Nq ** 3
 
 
-def _node_axes(N: int, shape, L: float):
-    """Unwarped coordinates, broadcastable to (nz, ny, nx, Nq, Nq, Nq)."""
+def _node_axes(N: int, shape, L: float, z_range=None):
+    """Unwarped coordinates, broadcastable to (nz, ny, nx, Nq, Nq, Nq); with
+    z_range = (z0, z1) only the element layers z0 <= ez < z1."""
     nx, ny, nz = shape
+    z0, z1 = (0, nz) if z_range is None else z_range
     Nq = N + 1
     r = (gll_points(N) + 1.0) * 0.5
     hx, hy, hz = L / nx, L / ny, L / nz
     xh = (np.arange(nx)[:, None] + r[None, :]) * hx   # (nx, Nq)
     yh = (np.arange(ny)[:, None] + r[None, :]) * hy
-    zh = (np.arange(nz)[:, None] + r[None, :]) * hz
+    zh = (np.arange(z0, z1)[:, None] + r[None, :]) * hz
     xh = xh.reshape(1, 1, nx, 1, 1, Nq)
     yh = yh.reshape(1, ny, 1, 1, Nq, 1)
-    zh = zh.reshape(nz, 1, 1, Nq, 1, 1)
+    zh = zh.reshape(z1 - z0, 1, 1, Nq, 1, 1)
     return xh, yh, zh, (hx, hy, hz)
 
 
@@ -154,9 +156,15 @@ def _finish(N, shape, L, X, a_r, a_s, a_t) -> Mesh:
                 Jinv=np.ascontiguousarray(1.0 / J).reshape(M))
 
 
-def warped_box(N: int, shape=(8, 8, 8), L: float = 10_000.0, warp: float = 0.05) -> Mesh:
-    """The benchmark mesh: the sine-warped box described in the module docstring."""
-    xh, yh, zh, (hx, hy, hz) = _node_axes(N, shape, L)
+def warped_box(N: int, shape=(8, 8, 8), L: float = 10_000.0, warp: float = 0.05,
+               z_range=None) -> Mesh:
+    """The benchmark mesh: the sine-warped box described in the module docstring.
+    z_range = (z0, z1): only the element layers z0 <= ez < z1 (elements
+    e = ex + nx (ey + ny ez), so a contiguous range of elements), point for
+    point the same values as those elements of the whole mesh."""
+    xh, yh, zh, (hx, hy, hz) = _node_axes(N, shape, L, z_range)
+    if z_range is not None:
+        shape = (shape[0], shape[1], z_range[1] - z_range[0])
     A = warp * L
     k = math.pi / L
     sx, sy, sz = np.sin(k * xh), np.sin(k * yh), np.sin(k * zh)
@@ -227,18 +235,34 @@ def _eval_bumps(x: np.ndarray, bumps) -> np.ndarray:
 
 def perturbed_state(mesh: Mesh, rho_ref, rhotheta_ref, seed: int,
                     eps: float = 1e-3, vmax: float = 10.0,
-                    smooth_velocity: bool = False) -> np.ndarray:
+                    smooth_velocity: bool = False, point_range=None) -> np.ndarray:
     """Seeded state (5, M): Gaussian-bump perturbations of rho and theta and
     per-point uniform random velocities, or smooth bump velocities of peak vmax
-    (see module docstring)."""
+    (see module docstring).  point_range = (p0, M_all): the mesh is the points
+    p0 .. p0 + M - 1 of a mesh of M_all points, and the state is those points'
+    state in that mesh (the velocity draws are taken from the generator's
+    stream at their positions; smooth velocities, normalised over the whole
+    mesh, are not available then)."""
     rng = np.random.Generator(np.random.PCG64(seed))
     b_rho = _bumps(rng, mesh.L)
     b_theta = _bumps(rng, mesh.L)
     if smooth_velocity:
+        if point_range is not None:
+            raise ValueError("smooth velocities are normalised over the whole mesh")
         vel = np.empty((3, mesh.M))
         for a in range(3):
             B = _eval_bumps(mesh.x, _bumps(rng, mesh.L))
             vel[a] = vmax * B / max(np.max(np.abs(B)), 1e-300)
+    elif point_range is not None:
+        # the draws of the whole mesh are 40 for the bumps, then 3 M_all
+        # uniforms (velocity a of point p at 40 + a M_all + p), one 64-bit
+        # output each: jump the stream to this range's draws
+        p0, m_all = point_range
+        vel = np.empty((3, mesh.M))
+        for a in range(3):
+            bg = np.random.PCG64(seed)
+            bg.advance(40 + a * m_all + p0)
+            vel[a] = np.random.Generator(bg).uniform(-vmax, vmax, size=mesh.M)
     else:
         vel = rng.uniform(-vmax, vmax, size=(3, mesh.M))
     rho = rho_ref * (1.0 + eps * _eval_bumps(mesh.x, b_rho))
@@ -313,15 +337,24 @@ def tracer_state(mesh: Mesh, rho: np.ndarray, seed: int, count: int) -> np.ndarr
 def make_workload(N: int, n, seed: int, L: float = 10_000.0, warp: float = 0.05,
                   consts: Constants = DRY_AIR, T: float = 300.0, eps: float = 1e-3,
                   vmax: float = 10.0, name: str = "", tracers: int = 0,
-                  smooth_velocity: bool = False) -> Workload:
+                  smooth_velocity: bool = False, z_range=None) -> Workload:
     """Warped box of order N with the seeded perturbed hydrostatic state and
     ``tracers`` (0..3) passive tracers after Theta.
-    ``n`` is the number of elements per axis, or a tuple (nx, ny, nz)."""
+    ``n`` is the number of elements per axis, or a tuple (nx, ny, nz).
+    z_range = (z0, z1): only the element layers z0 <= ez < z1, a contiguous
+    range of elements, with the same geometry and state as those elements of
+    the whole workload (rough velocities, no tracers)."""
     shape = (n, n, n) if np.isscalar(n) else tuple(int(v) for v in n)
-    mesh = warped_box(N, shape, L=L, warp=warp)
+    mesh = warped_box(N, shape, L=L, warp=warp, z_range=z_range)
     rho_ref, rt_ref = hydrostatic_reference(mesh.x[2], consts, T)
+    point_range = None
+    if z_range is not None:
+        if tracers:
+            raise ValueError("element ranges are generated without tracers")
+        per_layer = shape[0] * shape[1] * (N + 1) ** 3
+        point_range = (z_range[0] * per_layer, shape[2] * per_layer)
     q = perturbed_state(mesh, rho_ref, rt_ref, seed, eps=eps, vmax=vmax,
-                        smooth_velocity=smooth_velocity)
+                        smooth_velocity=smooth_velocity, point_range=point_range)
     if tracers:
         q = np.concatenate([q, tracer_state(mesh, q[0], seed, tracers)])
     return Workload(mesh=mesh, consts=consts, rho_ref=rho_ref, rhotheta_ref=rt_ref,

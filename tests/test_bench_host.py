@@ -37,6 +37,42 @@ def test_aggregate_over_two_gloo_ranks(tmp_path):
         assert d["max"] == 10.0
 
 
+def _shard_main(rank, world, port, out):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank),
+                      WORLD_SIZE=str(world), LOCAL_RANK=str(rank))
+    import numpy as np
+    import torch.distributed as dist
+    bench.dist_setup("gloo")
+    w, _ = bench.workload_for_rank(2, rank, world, "elements")
+    np.savez(os.path.join(out, f"s{rank}.npz"), q=w.q, g=w.mesh.g, Jinv=w.mesh.Jinv,
+             rho_ref=w.rho_ref, rhotheta_ref=w.rhotheta_ref)
+    bench.barrier()
+    dist.destroy_process_group()
+
+
+def test_element_sharding_partitions_one_mesh(tmp_path):
+    """Two gloo ranks take contiguous element ranges that cover the mesh once,
+    and their workloads are, point for point, the whole mesh's."""
+    import numpy as np
+    import torch.multiprocessing as mp
+    from paper_1604_08501_gb300 import workload as wl
+    ranges = bench.shard_ranges(2, 2)
+    assert ranges == [(0, 2), (2, 4)]
+    for world in (1, 3, 4):
+        r = bench.shard_ranges(5, world)
+        assert r[0][0] == 0 and r[-1][1] == 5 * world
+        assert all(a[1] == b[0] for a, b in zip(r, r[1:]))
+        assert len({b - a for a, b in r}) == 1
+    port = 29600 + os.getpid() % 1000
+    mp.spawn(_shard_main, args=(2, port, str(tmp_path)), nprocs=2, join=True)
+    whole = wl.make_workload(7, (2, 2, 4), seed=1)
+    parts = [np.load(tmp_path / f"s{r}.npz") for r in range(2)]
+    assert sum(p["q"].shape[1] for p in parts) == whole.M
+    for name, ref in (("q", whole.q), ("g", whole.mesh.g), ("Jinv", whole.mesh.Jinv),
+                      ("rho_ref", whole.rho_ref), ("rhotheta_ref", whole.rhotheta_ref)):
+        assert np.array_equal(np.concatenate([p[name] for p in parts], axis=-1), ref), name
+
+
 def test_single_process_aggregate_is_identity():
     thr, tmax = bench.aggregate(500, 2.0)
     assert (thr, tmax) == (250.0, 2.0)
