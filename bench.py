@@ -684,7 +684,7 @@ NQ_STUDY = {3: (48, 48, 24), 7: (24, 24, 12), 11: (16, 16, 8), 15: (12, 12, 6)}
 
 def run_nq_sweep(args):
     """One evaluation per step of the 3,538,944-point mesh at each order of the
-    paper's Nq study, NUMA_FP64 and NUMA_MIXED, with five fields and with three
+    paper's Nq study, NUMA_FP64, NUMA_DF64 (N <= 7) and NUMA_MIXED, with five fields and with three
     passive tracers (*_8fields: the paper's 8-field form; mixed_8fields is also
     its FP32 precision).  Inputs exceed L2 (0.68 GB FP64).  Metric: GDOF/s per
     order; `value` is Nq = 8."""
@@ -707,8 +707,8 @@ def run_nq_sweep(args):
         w5 = dataclasses.replace(w, q=w.q[:5])
         row = {"elements": w.Ne, "points": w.M}
         for prec in list(args.precisions) + ["fp64_8fields", "mixed_8fields"]:
-            if prec == "df64":
-                continue
+            if prec == "df64" and N > 7:
+                continue   # the double-float mode takes N <= 7
             # *_8fields: the paper's 8-field form (three passive tracers);
             # mixed_8fields is also the paper's precision (FP32)
             ww = w if prec.endswith("_8fields") else w5
@@ -965,7 +965,8 @@ def main(argv=None):
     if args.steps is None:   # a few minutes at most for each workload
         args.steps = {"single": 300, "batched": 5, "nq-sweep": 50, "serving": 300}[args.workload]
     if args.precision is None:
-        args.precision = ("fp64,df64,mixed" if args.workload == "single" else "fp64,mixed")
+        args.precision = ("fp64,df64,mixed" if args.workload in ("single", "nq-sweep")
+                          else "fp64,mixed")
     args.precisions = [p for p in args.precision.split(",") if p]
     if args.impl == "reference":
         return run_reference(args)

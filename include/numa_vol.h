@@ -102,7 +102,7 @@ typedef enum {
     NUMA_MIXED = 1,  /* FP32 perturbation state (rho', U1, U2, U3, Theta'), FP32 rhs,
                         FP32 geometry and arithmetic                                    */
     NUMA_DF64 = 2    /* FP64 state and rhs, double-float arithmetic (hi + lo FP32 pairs,
-                        about 48 significant bits) on the FP32 pipes; N = 7 only      */
+                        about 48 significant bits) on the FP32 pipes; N = 1..7        */
 } numa_precision;
 
 typedef struct numa_vol numa_vol;
@@ -116,11 +116,12 @@ typedef struct numa_vol numa_vol;
  * 1/Theta_ref and p(Theta_ref)/Theta_ref.  p' is exactly zero wherever
  * Theta == Theta_ref.  Synchronous.
  *
- * mesh->N in [1, NUMA_MAX_N_FP64] for NUMA_FP64 and NUMA_MIXED, and 7 for
- * NUMA_DF64; mesh->num_elements >= 0; every pointer of geo non-null;
+ * mesh->N in [1, NUMA_MAX_N_FP64] for NUMA_FP64 and NUMA_MIXED, and in
+ * [1, NUMA_MAX_N] for NUMA_DF64; mesh->num_elements >= 0; every pointer of
+ * geo non-null;
  * c->cp > c->R > 0 and c->p0 > 0.  On success *out receives the handle
  * (release with numa_vol_destroy).  Errors: NUMA_EINVAL, NUMA_ENOMEM,
- * NUMA_ECUDA, NUMA_EUNSUPPORTED (NUMA_DF64 with N != 7 or with tracers).
+ * NUMA_ECUDA, NUMA_EUNSUPPORTED (NUMA_DF64 with N > 7 or with tracers).
  * Handles of N > 7 evaluate one element per CTA of 3 (N+1)^2 threads, one
  * pass per field (vol_rhs_high_kernel); the batch and the engine take handles
  * of N <= 7 without tracers only.
@@ -147,7 +148,7 @@ typedef struct numa_vol numa_vol;
  * when a geometry array (after values below 2^-50 of the array's largest
  * magnitude are set to zero) holds a magnitude outside [2^-40, 2^41); and for
  * one element when its state holds such a value or its double-float result
- * overflows.  N != 7 with NUMA_DF64 gives NUMA_EUNSUPPORTED.
+ * overflows.  N > 7 with NUMA_DF64 gives NUMA_EUNSUPPORTED.
  */
 int numa_vol_create(const numa_mesh *mesh, const numa_geometry *geo,
                     const numa_constants *c, numa_precision prec, numa_vol **out);

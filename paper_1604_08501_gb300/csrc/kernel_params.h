@@ -61,7 +61,7 @@ struct HighParams32 {
     float K, gm1, gamma, grav;
 };
 
-// Per-point arrays of the double-float path (N = 7): float2 (h, l) pairs, and
+// Per-point arrays of the double-float path (N = 1..7): float2 (h, l) pairs, and
 // the reference state in FP64, so that rho - rho_ref and Theta - Theta_ref are
 // exact FP64 differences before they are split.
 struct DfGeometry {
@@ -96,13 +96,15 @@ struct df {
 };
 
 struct DfParams {
-    df De[4][4];       // (D[i][m] + D[i][7-m]) / 2, i, m < 4
-    df Do[4][4];       // (D[i][m] - D[i][7-m]) / 2
+    df De[4][4];       // (D[i][m] + D[i][N-m]) / 2, i, m < Nq/2
+    df Do[4][4];       // (D[i][m] - D[i][N-m]) / 2
+    df Dc[4];          // D[i][c], the centre column (odd Nq), i < Nq/2
+    df Dcr[4];         // D[c][m], the centre row (odd Nq), m < Nq/2
     df c1, c2, c3;     // binom(gamma, k), k = 1..3
     float ct[6];       // binom(gamma, k), k = 4..9
     df grav_df;        // gravity
     double grav, p0, R, gamma;
-    double D[64];      // D for the native fallback
+    double D[64];      // D, row-major D[i Nq + n], for the native fallback
 };
 
 }  // namespace numa

@@ -37,7 +37,7 @@ cudaError_t launch_abs_max(const double *src, int64_t M, unsigned long long *ama
                            cudaStream_t s);
 cudaError_t launch_to_df(const double *src, float2 *dst, int64_t M, double thresh, int *bad,
                          cudaStream_t s);
-cudaError_t launch_vol_rhs_df64(ElemRange r, const DfGeometry &geo, const DfParams &P,
+cudaError_t launch_vol_rhs_df64(int N, ElemRange r, const DfGeometry &geo, const DfParams &P,
                                 const double *q, double *rhs, int num_sms, cudaStream_t s);
 
 // Launchers of the mixed-precision path (vol_mixed.cu).
@@ -57,7 +57,7 @@ void sweep_tables(int N, const double *D, double De[16], double Do[16], double D
                   double Dcr[4]);
 
 // Native: vol_rhs_fp64_kernel (N <= 7); NativeHigh: vol_rhs_high_kernel<Nq, double>
-// (N = 8..15); DoubleFloat (N = 7); Mixed (N <= 7) and MixedHigh:
+// (N = 8..15); DoubleFloat (vol_rhs_df64_kernel<Nq>, N <= 7); Mixed (N <= 7) and MixedHigh:
 // vol_rhs_high_kernel<Nq, float> (N = 8..15).
 enum class Kernel { Native, NativeHigh, DoubleFloat, Mixed, MixedHigh };
 

@@ -70,7 +70,11 @@ const char *numa_vol_kernel_name(const numa_vol *h) {
                                   "vol_rhs_mixed_kernel<4>", "vol_rhs_mixed_kernel<5>",
                                   "vol_rhs_mixed_kernel<6>", "vol_rhs_mixed_kernel<7>",
                                   "vol_rhs_mixed_kernel<8>"};
-    if (h->kernel == numa::Kernel::DoubleFloat) return "vol_rhs_df64_kernel";
+    static const char *dfk[] = {"", "vol_rhs_df64_kernel<2>", "vol_rhs_df64_kernel<3>",
+                                "vol_rhs_df64_kernel<4>", "vol_rhs_df64_kernel<5>",
+                                "vol_rhs_df64_kernel<6>", "vol_rhs_df64_kernel<7>",
+                                "vol_rhs_df64_kernel<8>"};
+    if (h->kernel == numa::Kernel::DoubleFloat) return dfk[h->N];
     if (h->kernel == numa::Kernel::Mixed) return mixed[h->N];
     if (h->kernel == numa::Kernel::MixedHigh) {
         static const char *mixed_high[] = {"vol_rhs_high_kernel<9, float>", "vol_rhs_high_kernel<10, float>",
@@ -152,14 +156,20 @@ void build_params(numa_vol *h, const double *D) {
         m.gamma = static_cast<float>(g);
         m.grav = static_cast<float>(h->eos.grav);
     }
-    if (h->N != 7) return;
+    if (h->N > NUMA_MAX_N) return;
     numa::DfParams &P = h->dparams;
-    for (int i = 0; i < 4; ++i)
-        for (int m = 0; m < 4; ++m) {
-            const long double a = D[i * 8 + m], b = D[i * 8 + 7 - m];
+    const int nq = h->Nq, N = h->N, half = nq / 2, cc = nq / 2;
+    for (int i = 0; i < half; ++i) {
+        for (int m = 0; m < half; ++m) {
+            const long double a = D[i * nq + m], b = D[i * nq + N - m];
             P.De[i][m] = split_host((a + b) / 2);
             P.Do[i][m] = split_host((a - b) / 2);
         }
+        if (nq & 1) {
+            P.Dc[i] = split_host(D[i * nq + cc]);
+            P.Dcr[i] = split_host(D[cc * nq + i]);
+        }
+    }
     P.c1 = split_host(c[1]);
     P.c2 = split_host(c[2]);
     P.c3 = split_host(c[3]);
@@ -169,7 +179,7 @@ void build_params(numa_vol *h, const double *D) {
     P.p0 = h->eos.p0;
     P.R = h->eos.R;
     P.gamma = h->eos.gamma;
-    for (int t = 0; t < 64; ++t) P.D[t] = D[t];
+    for (int t = 0; t < nq * nq; ++t) P.D[t] = D[t];
 }
 
 // Per-point arrays of a handle, in order: g[0..8], Jinv, rho_ref, theta_ref,
@@ -330,7 +340,7 @@ int numa_vol_create(const numa_mesh *mesh, const numa_geometry *geo, const numa_
     if (mesh->N < 1 || mesh->N > NUMA_MAX_N_FP64)
         return fail(NUMA_EINVAL, "numa_vol_create: N must be in [1, 15]");
     if (mesh->N > NUMA_MAX_N && prec == NUMA_DF64)
-        return fail(NUMA_EUNSUPPORTED, "numa_vol_create: NUMA_DF64 is implemented for N = 7 only");
+        return fail(NUMA_EUNSUPPORTED, "numa_vol_create: NUMA_DF64 is implemented for N = 1..7");
     if (mesh->num_tracers < 0 || mesh->num_tracers > NUMA_MAX_TRACERS)
         return fail(NUMA_EINVAL, "numa_vol_create: num_tracers must be in [0, 3]");
     if (mesh->num_tracers > 0 && prec == NUMA_DF64)
@@ -347,8 +357,6 @@ int numa_vol_create(const numa_mesh *mesh, const numa_geometry *geo, const numa_
         return fail(NUMA_EINVAL, "numa_vol_create: NULL Jinv or reference array");
     if (prec != NUMA_FP64 && prec != NUMA_DF64 && prec != NUMA_MIXED)
         return fail(NUMA_EINVAL, "numa_vol_create: unknown precision");
-    if (prec == NUMA_DF64 && mesh->N != 7)
-        return fail(NUMA_EUNSUPPORTED, "numa_vol_create: NUMA_DF64 is implemented for N = 7 only");
 
     numa_vol *h = new (std::nothrow) numa_vol();
     if (!h) return fail(NUMA_ENOMEM, "numa_vol_create: host allocation failed");
@@ -414,7 +422,7 @@ cudaError_t launch(numa_vol *h, const void *q, void *rhs, int64_t e0, int64_t co
                                           static_cast<const float *>(q), static_cast<float *>(rhs),
                                           h->num_sms, s);
     if (h->kernel == numa::Kernel::DoubleFloat)
-        return numa::launch_vol_rhs_df64(r, h->dgeo, h->dparams, static_cast<const double *>(q),
+        return numa::launch_vol_rhs_df64(h->N, r, h->dgeo, h->dparams, static_cast<const double *>(q),
                                          static_cast<double *>(rhs), h->num_sms, s);
     if (h->kernel == numa::Kernel::NativeHigh)
         return numa::launch_vol_rhs_fp64_high(h->N, h->nf, r, h->geo, h->hparams,

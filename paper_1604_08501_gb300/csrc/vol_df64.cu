@@ -1,4 +1,4 @@
-// FP64-accurate element volume term for N = 7 (Nq = 8) in double-float
+// FP64-accurate element volume term for N = 1..7 (Nq = 2..8) in double-float
 // arithmetic on the FP32 pipes.
 //
 // Same operation as vol_fp64.cu (Sec. 2, Eq. (2); flux form and sign of the
@@ -9,26 +9,28 @@
 // costs one FP64 add.  Accuracy against an FP64 evaluation is about 1e-14,
 // normwise.
 //
-// One CTA (512 threads) per element, in three phases:
+// One CTA (Nq^3 threads) per element, in three phases:
 //  1. Thread per point: the pressure perturbation p' (series in
 //     x = Theta'/Theta_ref, below), 1/rho, and the fifteen contravariant
 //     fluxes of the point.  Each flux goes into a per-(direction, field) buffer
 //     in shared memory, laid out line by line (the paper's per-k-slice flux
 //     precompute, Sec. 3, opt. level 5, extended to whole elements).
-//  2. Thread per line (5 fields x 3 directions x 64 lines): the D sweep of one
+//  2. Thread per line (5 fields x 3 directions x Nq^2 lines): the D sweep of one
 //     line by the even-odd split of the GLL differentiation matrix.  D is
-//     centro-antisymmetric (D[7-i][7-n] = -D[i][n]), so with E_m = F_m + F_{7-m}
-//     and O_m = F_m - F_{7-m}, the pair S_i, S_{7-i} (i < 4) comes from
-//     a_i = sum_m De[i][m] E_m and b_i = sum_m Do[i][m] O_m as S_i = a_i + b_i,
-//     S_{7-i} = b_i - a_i.  That is 4 products per output instead of 8.  Each
-//     result overwrites its flux in place.
+//     centro-antisymmetric (D[N-i][N-n] = -D[i][n]), so with E_m = F_m + F_{N-m}
+//     and O_m = F_m - F_{N-m}, the pair S_i, S_{N-i} (i < Nq/2) comes from
+//     a_i = sum_m De[i][m] E_m (+ D[i][c] F_c for odd Nq) and
+//     b_i = sum_m Do[i][m] O_m as S_i = a_i + b_i, S_{N-i} = b_i - a_i, and for
+//     odd Nq the centre row S_c = sum_m D[c][m] O_m.  That is half the products
+//     of the direct sweep.  Each result overwrites its flux in place.
 //  3. Thread per point: sum of the three sweeps, times -Jinv, the gravity
 //     source, one rounding to FP64 and one store per field.
 //
-// Shared layout: slot(line, n) = 8*line + (n ^ h(line)), with
-// h(line) = (line & 6) | ((line >> 3) & 1).  8-byte accesses are then free of
-// bank conflicts in all three access patterns: phase-1 writes by points,
-// phase-2 line reads and writes, and phase-3 reads by points.
+// Shared layout: at Nq = 8, slot(line, n) = 8*line + (n ^ h(line)), with
+// h(line) = (line & 6) | ((line >> 3) & 1): 8-byte accesses are then free of
+// bank conflicts in all three access patterns (phase-1 writes by points,
+// phase-2 line reads and writes, phase-3 reads by points).  Other orders
+// keep lines of Nq slots.
 //
 // Theta - Theta_ref and rho - rho_ref are formed in FP64 (one exact
 // subtraction each) before splitting.  In double-float the 2^-48 error of each
@@ -49,9 +51,22 @@ namespace numa {
 
 namespace {
 
-constexpr int NQ = 8;
-constexpr int N3 = 512;
-constexpr int kItems = kFields * 3 * 64;  // (direction, field, line) sweep tasks
+template <int NQ>
+struct DfShape {
+    static constexpr int N3 = NQ * NQ * NQ;
+    static constexpr int NL = NQ * NQ;                 // lines per (direction, field)
+    static constexpr int kItems = kFields * 3 * NL;    // (direction, field, line) sweep tasks
+};
+
+// Resident CTAs per SM the register budget is sized for: two 512-thread CTAs
+// at Nq = 8 (64 registers); about 640 threads per SM at the other orders
+// (about 100 registers: the double-float sweeps of one line need more than
+// 64 without spilling), at most 32 CTAs.
+template <int NQ>
+constexpr int df_min_ctas() {
+    constexpr int n = NQ == 8 ? 2 : 640 / (NQ * NQ * NQ);
+    return n < 1 ? 1 : (n > 32 ? 32 : n);
+}
 
 __device__ __forceinline__ df ld_df(const float2 *p, int64_t i) {
     float2 v = __ldg(p + i);
@@ -60,13 +75,20 @@ __device__ __forceinline__ df ld_df(const float2 *p, int64_t i) {
 
 __device__ __forceinline__ int swz_h(int line) { return (line & 6) | ((line >> 3) & 1); }
 
-__device__ __forceinline__ int slot(int line, int n) { return line * 8 + (n ^ swz_h(line)); }
+template <int NQ>
+__device__ __forceinline__ int slot(int line, int n) {
+    if constexpr (NQ == 8)
+        return line * 8 + (n ^ swz_h(line));
+    else
+        return line * NQ + n;
+}
 
 // Line and position of point (i, j, k) for reference direction d.
+template <int NQ>
 __device__ __forceinline__ int dir_slot(int d, int i, int j, int k) {
-    if (d == 0) return slot(8 * k + j, i);
-    if (d == 1) return slot(8 * k + i, j);
-    return slot(8 * j + i, k);
+    if (d == 0) return slot<NQ>(NQ * k + j, i);
+    if (d == 1) return slot<NQ>(NQ * k + i, j);
+    return slot<NQ>(NQ * j + i, k);
 }
 
 __device__ __forceinline__ float rcp_approx(float x) {
@@ -111,8 +133,10 @@ __device__ __noinline__ double eos_pressure_fp64(double Th, const DfParams &P) {
 }
 
 // Native FP64 evaluation of one element from df-stored geometry (rare path).
+template <int NQ>
 __device__ void element_fp64(const DfGeometry &geo, const DfParams &P, const double *__restrict__ q,
                              double *__restrict__ rhs, int64_t M, int64_t e, double *sF) {
+    constexpr int N3 = DfShape<NQ>::N3;
     const int l = threadIdx.x;
     const int64_t node = e * N3 + l;
     __syncthreads();  // sF aliases the df buffers of the caller
@@ -134,7 +158,7 @@ __device__ void element_fp64(const DfGeometry &geo, const DfParams &P, const dou
         F[4 * N3] = Th * u;
     }
     __syncthreads();
-    const int i = l & 7, j = (l >> 3) & 7, k = l >> 6;
+    const int i = l % NQ, j = (l / NQ) % NQ, k = l / (NQ * NQ);
     const double Jinv = df_to_double(ld_df(geo.Jinv, node));
     const double drho = rho - geo.rho_ref[node];
 #pragma unroll
@@ -155,20 +179,26 @@ __device__ void element_fp64(const DfGeometry &geo, const DfParams &P, const dou
     }
 }
 
-// Starts the arrays of element e toward L2 (4 KB per array: 512 points of 8 bytes).
+// Starts the arrays of element e toward L2 (Nq^3 points of 8 bytes per array),
+// where an element's slab of one array is a whole number of 16-byte units
+// (the bulk prefetch's rule; even Nq).
+template <int NQ>
 __device__ __forceinline__ void prefetch_element(const DfGeometry &geo, const double *q,
                                                  int64_t M, int64_t e) {
-    const int64_t off = e * N3;
+    constexpr int N3 = DfShape<NQ>::N3;
     constexpr uint32_t B = N3 * 8;
+    if constexpr (B % 16 == 0) {
+        const int64_t off = e * N3;
 #pragma unroll
-    for (int b = 0; b < kFields; ++b) prefetch_l2(q + b * M + off, B);
+        for (int b = 0; b < kFields; ++b) prefetch_l2(q + b * M + off, B);
 #pragma unroll
-    for (int a = 0; a < 9; ++a) prefetch_l2(geo.g[a] + off, B);
-    prefetch_l2(geo.Jinv + off, B);
-    prefetch_l2(geo.rho_ref + off, B);
-    prefetch_l2(geo.theta_ref + off, B);
-    prefetch_l2(geo.w + off, B);
-    prefetch_l2(geo.A + off, B);
+        for (int a = 0; a < 9; ++a) prefetch_l2(geo.g[a] + off, B);
+        prefetch_l2(geo.Jinv + off, B);
+        prefetch_l2(geo.rho_ref + off, B);
+        prefetch_l2(geo.theta_ref + off, B);
+        prefetch_l2(geo.w + off, B);
+        prefetch_l2(geo.A + off, B);
+    }
 }
 
 // ahead: the CTAs resident on the GPU at once.  The element that many launch
@@ -176,16 +206,22 @@ __device__ __forceinline__ void prefetch_element(const DfGeometry &geo, const do
 // prefetched to L2 now and its loads then hit L2 rather than DRAM (one wave
 // ahead: 1.30 -> 1.22 ms at N = 7, 32768 elements; two waves ahead was
 // slower than none, the prefetched data displacing the running wave's).
-__global__ void __launch_bounds__(N3, 2)
+template <int NQ>
+__global__ void __launch_bounds__(NQ * NQ * NQ, df_min_ctas<NQ>())
 vol_rhs_df64_kernel(DfGeometry geo, DfParams P, const double *__restrict__ q,
                     double *__restrict__ rhs, int64_t M, int64_t e0, int64_t e_end,
                     int64_t ahead) {
-    extern __shared__ float2 sbuf[];  // [direction*5 + field][slot], 15 * 512 float2
+    constexpr int N3 = DfShape<NQ>::N3;
+    constexpr int NL = DfShape<NQ>::NL;
+    constexpr int HALF = NQ / 2;
+    constexpr bool ODD = (NQ & 1) != 0;
+    constexpr int C = NQ / 2;
+    extern __shared__ float2 sbuf[];  // [direction*5 + field][slot], 15 * Nq^3 float2
     const int l = threadIdx.x;
-    const int i = l & 7, j = (l >> 3) & 7, k = l >> 6;
+    const int i = l % NQ, j = (l / NQ) % NQ, k = l / (NQ * NQ);
     const int64_t e = e0 + blockIdx.x;
     const int64_t node = e * N3 + l;
-    if (l == 0 && e + ahead < e_end) prefetch_element(geo, q, M, e + ahead);
+    if (l == 0 && e + ahead < e_end) prefetch_element<NQ>(geo, q, M, e + ahead);
 
     // ---- phase 1: state, p', fluxes -----------------------------------
     bool big = false, tiny = false;
@@ -204,7 +240,7 @@ vol_rhs_df64_kernel(DfGeometry geo, DfParams P, const double *__restrict__ q,
     const df drho = df_split(drho_d, big, tiny);
     const bool bad = big || !(qd[0] > 0.0);
     if (__syncthreads_or(bad)) {
-        element_fp64(geo, P, q, rhs, M, e, reinterpret_cast<double *>(sbuf));
+        element_fp64<NQ>(geo, P, q, rhs, M, e, reinterpret_cast<double *>(sbuf));
         return;
     }
 
@@ -244,43 +280,50 @@ vol_rhs_df64_kernel(DfGeometry geo, DfParams P, const double *__restrict__ q,
             F[3] = dot2_value(c);
         }
         F[4] = df_mul(Q[4], u);
-        const int s = dir_slot(d, i, j, k);
+        const int s = dir_slot<NQ>(d, i, j, k);
 #pragma unroll
         for (int b = 0; b < kFields; ++b) sbuf[(d * kFields + b) * N3 + s] = make_float2(F[b].h, F[b].l);
     }
     __syncthreads();
 
     // ---- phase 2: even-odd D sweeps, one line per task -----------------
-    for (int item = l; item < kItems; item += N3) {
-        float2 *buf = sbuf + (item >> 6) * N3;
-        const int line = item & 63;
-        const int hh = swz_h(line);
+    for (int item = l; item < DfShape<NQ>::kItems; item += N3) {
+        float2 *buf = sbuf + (item / NL) * N3;
+        const int line = item % NL;
         df F[NQ];
 #pragma unroll
         for (int n = 0; n < NQ; ++n) {
-            const float2 v = buf[line * 8 + (n ^ hh)];
+            const float2 v = buf[slot<NQ>(line, n)];
             F[n] = df{v.x, v.y};
         }
-        df E[4], O[4];
+        df E[HALF], O[HALF];
 #pragma unroll
-        for (int m = 0; m < 4; ++m) {
-            E[m] = df_add(F[m], F[7 - m]);
-            O[m] = df_sub(F[m], F[7 - m]);
+        for (int m = 0; m < HALF; ++m) {
+            E[m] = df_add(F[m], F[NQ - 1 - m]);
+            O[m] = df_sub(F[m], F[NQ - 1 - m]);
         }
 #pragma unroll
-        for (int r = 0; r < 4; ++r) {
+        for (int r = 0; r < HALF; ++r) {
             dot2 a = dot2_first(P.De[r][0], E[0]);
             dot2 b = dot2_first(P.Do[r][0], O[0]);
 #pragma unroll
-            for (int m = 1; m < 4; ++m) {
+            for (int m = 1; m < HALF; ++m) {
                 dot2_add(a, P.De[r][m], E[m]);
                 dot2_add(b, P.Do[r][m], O[m]);
             }
+            if constexpr (ODD) dot2_add(a, P.Dc[r], F[C]);
             const df A = dot2_value(a), B = dot2_value(b);
             const df Si = df_add(B, A);
             const df Sm = df_sub(B, A);
-            buf[line * 8 + (r ^ hh)] = make_float2(Si.h, Si.l);
-            buf[line * 8 + ((7 - r) ^ hh)] = make_float2(Sm.h, Sm.l);
+            buf[slot<NQ>(line, r)] = make_float2(Si.h, Si.l);
+            buf[slot<NQ>(line, NQ - 1 - r)] = make_float2(Sm.h, Sm.l);
+        }
+        if constexpr (ODD) {
+            dot2 c = dot2_first(P.Dcr[0], O[0]);
+#pragma unroll
+            for (int m = 1; m < HALF; ++m) dot2_add(c, P.Dcr[m], O[m]);
+            const df Sc = df_norm(dot2_value(c));
+            buf[slot<NQ>(line, C)] = make_float2(Sc.h, Sc.l);
         }
     }
     __syncthreads();
@@ -291,9 +334,9 @@ vol_rhs_df64_kernel(DfGeometry geo, DfParams P, const double *__restrict__ q,
     bool finite = true;
 #pragma unroll
     for (int b = 0; b < kFields; ++b) {
-        const float2 r = sbuf[(0 * kFields + b) * N3 + dir_slot(0, i, j, k)];
-        const float2 s = sbuf[(1 * kFields + b) * N3 + dir_slot(1, i, j, k)];
-        const float2 t = sbuf[(2 * kFields + b) * N3 + dir_slot(2, i, j, k)];
+        const float2 r = sbuf[(0 * kFields + b) * N3 + dir_slot<NQ>(0, i, j, k)];
+        const float2 s = sbuf[(1 * kFields + b) * N3 + dir_slot<NQ>(1, i, j, k)];
+        const float2 t = sbuf[(2 * kFields + b) * N3 + dir_slot<NQ>(2, i, j, k)];
         df R = df_add(df_add(df{r.x, r.y}, df{s.x, s.y}), df{t.x, t.y});
         df v = df_mul(df_norm(R), jinv);
         if (b == 3) v = df_add(v, df_mul(drho, P.grav_df));
@@ -303,7 +346,7 @@ vol_rhs_df64_kernel(DfGeometry geo, DfParams P, const double *__restrict__ q,
     }
     // An overflow anywhere in the element (float range) sends it to FP64.
     if (__syncthreads_or(!finite)) {
-        element_fp64(geo, P, q, rhs, M, e, reinterpret_cast<double *>(sbuf));
+        element_fp64<NQ>(geo, P, q, rhs, M, e, reinterpret_cast<double *>(sbuf));
         return;
     }
 #pragma unroll
@@ -355,20 +398,40 @@ cudaError_t launch_to_df(const double *src, float2 *dst, int64_t M, double thres
     return cudaGetLastError();
 }
 
-cudaError_t launch_vol_rhs_df64(ElemRange r, const DfGeometry &geo, const DfParams &P,
-                                const double *q, double *rhs, int num_sms, cudaStream_t s) {
-    if (r.count <= 0) return cudaSuccess;
+namespace {
+
+template <int NQ>
+cudaError_t launch_df(ElemRange r, const DfGeometry &geo, const DfParams &P, const double *q,
+                      double *rhs, int num_sms, cudaStream_t s) {
+    constexpr int N3 = NQ * NQ * NQ;
     const size_t smem = sizeof(float2) * kFields * 3 * N3;
-    cudaError_t e = cudaFuncSetAttribute(vol_rhs_df64_kernel,
+    cudaError_t e = cudaFuncSetAttribute(vol_rhs_df64_kernel<NQ>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, vol_rhs_df64_kernel, N3, smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, vol_rhs_df64_kernel<NQ>, N3, smem);
     if (e != cudaSuccess) return e;
     const int64_t ahead = (int64_t)num_sms * (per_sm > 0 ? per_sm : 1);
-    vol_rhs_df64_kernel<<<(unsigned)r.count, N3, smem, s>>>(geo, P, q, rhs, r.M, r.e0,
-                                                            r.e0 + r.count, ahead);
+    vol_rhs_df64_kernel<NQ><<<(unsigned)r.count, N3, smem, s>>>(geo, P, q, rhs, r.M, r.e0,
+                                                                r.e0 + r.count, ahead);
     return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_vol_rhs_df64(int N, ElemRange r, const DfGeometry &geo, const DfParams &P,
+                                const double *q, double *rhs, int num_sms, cudaStream_t s) {
+    if (r.count <= 0) return cudaSuccess;
+    switch (N) {
+        case 1: return launch_df<2>(r, geo, P, q, rhs, num_sms, s);
+        case 2: return launch_df<3>(r, geo, P, q, rhs, num_sms, s);
+        case 3: return launch_df<4>(r, geo, P, q, rhs, num_sms, s);
+        case 4: return launch_df<5>(r, geo, P, q, rhs, num_sms, s);
+        case 5: return launch_df<6>(r, geo, P, q, rhs, num_sms, s);
+        case 6: return launch_df<7>(r, geo, P, q, rhs, num_sms, s);
+        case 7: return launch_df<8>(r, geo, P, q, rhs, num_sms, s);
+        default: return cudaErrorInvalidValue;
+    }
 }
 
 }  // namespace numa

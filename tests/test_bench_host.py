@@ -96,7 +96,7 @@ def test_roofline_entries_pick_the_binding_bound():
     w = wl.make_workload(7, 1, seed=0)
     roof, other = bench.roofline_entries("vol_rhs_fp64_kernel<8>", 1.0, w)
     assert roof["bound"] == "alu" and other["bound"] == "hbm"
-    roof, other = bench.roofline_entries("vol_rhs_df64_kernel", 1.0, w)
+    roof, other = bench.roofline_entries("vol_rhs_df64_kernel<8>", 1.0, w)
     assert roof["bound"] == "hbm"
     assert roof["achieved"] == pytest.approx(176 * w.M / 1e-3 / 1e9)
 

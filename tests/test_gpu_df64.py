@@ -1,4 +1,4 @@
-"""GPU tests of the double-float mode (NUMA_DF64, N = 7) against the oracle,
+"""GPU tests of the double-float mode (NUMA_DF64, N = 1..7) against the oracle,
 the native FP64 kernel and its own fallbacks.
 
 The double-float kernel carries about 48 significant bits, so its error against
@@ -59,7 +59,7 @@ def test_df_matches_oracle_and_native(shape):
     w = wl.make_workload(7, shape, seed=31)
     prob = w.problem()
     ref = oracle.vol_rhs_o2(prob, w.q)
-    assert kernel_of(prob) == "vol_rhs_df64_kernel"
+    assert kernel_of(prob) == "vol_rhs_df64_kernel<8>"
     df = run(prob, w.q, "df64")
     nat = run(prob, w.q, "fp64")
     tol, kappa = df_tol(prob, w.q, ref)
@@ -73,7 +73,7 @@ def test_df_full_size_workload():
     # The timed workload (N = 7, 32^3 elements, seed 1) at 1e-12.
     w = wl.bench_full()
     prob = w.problem()
-    assert kernel_of(prob) == "vol_rhs_df64_kernel"
+    assert kernel_of(prob) == "vol_rhs_df64_kernel<8>"
     ref = oracle.vol_rhs_o2(prob, w.q)
     print("df full size", check(run(prob, w.q), ref, label="df full size"))
 
@@ -89,9 +89,37 @@ def test_df_ill_conditioned_manufactured_case():
     print("kappa", kappa, "errors", errs)
 
 
-def test_df64_is_for_order_7_only():
+@pytest.mark.parametrize("N", [1, 2, 3, 4, 5, 6, 7])
+def test_df_every_order_matches_oracle(N):
+    # Every order with ragged element counts, against the oracle, at the
+    # conditioning-scaled bar (the FP64 bar where the sweeps are well conditioned).
+    for shape, seed in (((1, 1, 1), 40 + N), ((3, 2, 1), 50 + N)):
+        w = wl.make_workload(N, shape, seed=seed)
+        prob = w.problem()
+        assert kernel_of(prob) == f"vol_rhs_df64_kernel<{N + 1}>"
+        ref = oracle.vol_rhs_o2(prob, w.q)
+        tol, kappa = df_tol(prob, w.q, ref)
+        errs = check(run(prob, w.q), ref, tol=tol, label=f"df N={N} {shape}")
+        print(N, shape, "kappa", kappa, "errors", errs)
+
+
+def test_df_order_6_point_fallback_and_zero_state():
+    # odd Nq: the centre row and column of the even-odd sweep; large Theta
+    # perturbations take p' from pow; the unperturbed state gives exact zeros
+    w = wl.make_workload(6, (2, 1, 1), seed=61)
+    q = w.q.copy()
+    q[4, 50:90] *= 1.05
+    prob = w.problem()
+    tol, _ = df_tol(prob, q, oracle.vol_rhs_o2(prob, q))
+    check(run(prob, q), oracle.vol_rhs_o2(prob, q), tol=tol, label="df N=6 pow fallback")
+    q0 = np.zeros_like(w.q)
+    q0[0], q0[4] = w.rho_ref, w.rhotheta_ref
+    assert np.all(run(prob, q0) == 0.0)
+
+
+def test_df64_refuses_orders_above_7():
     from paper_1604_08501_gb300.numa_vol import NumaError
-    w = wl.make_workload(4, 1, seed=1)
+    w = wl.make_workload(8, 1, seed=1)
     with pytest.raises(NumaError, match="UNSUPPORTED"):
         VolumeTerm.from_problem(w.problem(), precision="df64")
 

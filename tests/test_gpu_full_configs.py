@@ -113,6 +113,7 @@ def test_batched_full_plan_on_sampled_elements(plan_works, precision, sweep):
     mixed = precision == "mixed"
     u = 2.0 ** -24 if mixed else 2.0 ** -53
     rng = np.random.default_rng(7)
+    ratios = []
     for w, q in zip(plan_works, states):
         got_all = q.cpu().numpy()
         for e in (0, w.Ne - 1, int(rng.integers(w.Ne))):
@@ -124,17 +125,24 @@ def test_batched_full_plan_on_sampled_elements(plan_works, precision, sweep):
                 err = np.max(np.abs(got[f] - ref[f]))
                 assert err <= bound[f], (precision, w.N, w.Ne, e, wl.FIELD_NAMES[f], err, bound[f])
             if not mixed:
-                # The FP64 increment q(T) - q(0) against the oracle's, at the
-                # small-batch bar 3e-12, plus the stored state's rounding: each
-                # of the 50 stages rounds q to FP64, and a value whose exact
-                # update falls near a rounding boundary can round to
-                # neighbouring doubles on the two sides (ulp(q) ~ 2e-10 of
-                # these smooth 10-step increments).
+                # The FP64 increment q(T) - q(0) against the oracle's: the
+                # small-batch bar 3e-12 of the increment, plus the oracle's own
+                # response to one rounding of its inputs (S_f: it holds the
+                # oracle's cancellation in p(Theta) - p(Theta_ref), about
+                # ulp(p) ~ 1.5e-11 Pa per evaluation, which reaches the
+                # momentum increments of these smooth states, ~1e-4 over the
+                # 10 steps, at ~1e-13), plus one rounding of the stored state
+                # per stage.  The 3e-12 alone holds for the rough states of the
+                # small-batch tests, whose increments are far larger.
                 inc, inc_ref = got - q0, ref - q0
                 for f in range(5):
                     err = np.max(np.abs(inc[f] - inc_ref[f]))
-                    ibound = 3e-12 * np.max(np.abs(inc_ref[f])) + 50 * u * np.max(np.abs(ref[f]))
+                    ibound = (3e-12 * np.max(np.abs(inc_ref[f])) + 4 * S[f]
+                              + 50 * u * np.max(np.abs(ref[f])))
+                    ratios.append(err / ibound)
                     assert err <= ibound, (w.N, w.Ne, e, wl.FIELD_NAMES[f], err, ibound)
+    if ratios:
+        print("FP64 increment: largest error / bound", max(ratios))
     for vt in vts:
         vt.close()
 
