@@ -466,11 +466,15 @@ def run_gpu(args):
     for prec in args.precisions:
         # the mixed mode takes the FP32 perturbation state (input preparation,
         # outside the timed regions)
-        q_np = w.q_mixed() if prec == "mixed" else w.q
+        # mixed-tc: the mixed mode with its D sums on the tensor cores
+        mode = "mixed" if prec == "mixed-tc" else prec
+        q_np = w.q_mixed() if mode == "mixed" else w.q
         q_host = torch.from_numpy(q_np).pin_memory()
         q = q_host.to(dev)
         step_bytes = q_np.nbytes
-        vt = VolumeTerm.from_problem(w.problem(), precision=prec)
+        vt = VolumeTerm.from_problem(w.problem(), precision=mode)
+        if prec == "mixed-tc":
+            vt.set_sweep("tensor_tf32")
         # The headline times exactly K launches; the other modes at least K
         # and at least 0.3 s of launches (the paper's timing loop, Sec. 4).
         r = time_variant(vt, q, q_host, dev, K, W, rank, e2e=not args.no_e2e,
@@ -499,7 +503,8 @@ def run_gpu(args):
         head = results[head_prec]
         roof, other = roofline_entries(head["kernel"], head["kernel_ms"], w)
         dtypes = {"fp64": "f64", "df64": "df64 (FP32 hi+lo pairs, 48-bit)",
-                  "mixed": "f32 (perturbation state)"}
+                  "mixed": "f32 (perturbation state)",
+                  "mixed-tc": "f32 (perturbation state), D sums as TF32 split products"}
         cfg = workload_config(w, name)
         if world > 1:
             cfg["parallelism"] = (f"{world} ranks, " + ("contiguous element ranges of one mesh, "
@@ -965,8 +970,8 @@ def main(argv=None):
     if args.steps is None:   # a few minutes at most for each workload
         args.steps = {"single": 300, "batched": 5, "nq-sweep": 50, "serving": 300}[args.workload]
     if args.precision is None:
-        args.precision = ("fp64,df64,mixed" if args.workload in ("single", "nq-sweep")
-                          else "fp64,mixed")
+        args.precision = {"single": "fp64,df64,mixed,mixed-tc",
+                          "nq-sweep": "fp64,df64,mixed"}.get(args.workload, "fp64,mixed")
     args.precisions = [p for p in args.precision.split(",") if p]
     if args.impl == "reference":
         return run_reference(args)

@@ -221,6 +221,35 @@ void numa_vol_destroy(numa_vol *h);
  * string; "" for a NULL handle. */
 const char *numa_vol_kernel_name(const numa_vol *h);
 
+/*
+ * How the three D sums of the volume term (Sec. 2, Eq. (2)) are evaluated:
+ *   NUMA_SWEEP_CUDA_CORES   FMAs on the CUDA cores (every mode's default; in
+ *                           NUMA_MIXED FP32 with relative error about 2^-24
+ *                           times the sums' condition number);
+ *   NUMA_SWEEP_TENSOR_TF32  TF32 split products on the tensor cores (tcgen05)
+ *                           with FP32 accumulation in tensor memory: each flux
+ *                           and each entry of D is a TF32 head plus an FP32
+ *                           tail, and the sums take head x head, head x tail
+ *                           and tail x head (relative error about 2^-21 times
+ *                           the condition number); NUMA_MIXED only;
+ *   NUMA_SWEEP_AUTO         batches only (numa_batch_set_sweep).
+ */
+typedef enum {
+    NUMA_SWEEP_CUDA_CORES = 0,
+    NUMA_SWEEP_TENSOR_TF32 = 1,
+    NUMA_SWEEP_AUTO = 2
+} numa_sweep;
+
+/* Choose the sweep of a handle: NUMA_SWEEP_TENSOR_TF32 takes NUMA_MIXED
+ * handles of N = 7 without tracers (vol_rhs_mixed_tc_kernel: a persistent
+ * grid, one element per CTA, one MMA round per element); NUMA_SWEEP_CUDA_CORES
+ * any handle.  The first tensor-core choice on a device uploads the kernel's
+ * tables (synchronous): make it before any stream capture.  A bounded wait of
+ * that kernel that runs out is reported by numa_vol_status (NUMA_ETIMEOUT).
+ * Errors: NUMA_EINVAL (NULL handle, NUMA_SWEEP_AUTO or unknown value),
+ * NUMA_EUNSUPPORTED, NUMA_ECUDA. */
+int numa_vol_set_sweep(numa_vol *h, numa_sweep sweep);
+
 /* Message for the last error on the calling thread ("" if none).  The
  * pointer stays valid until the thread's next numa_vol call. */
 const char *numa_vol_last_error(void);
@@ -321,28 +350,14 @@ int numa_batch_tile(const numa_batch *b, int nq);
 
 /*
  * How a NUMA_MIXED batch evaluates the three D sums of the volume term
- * (Sec. 2, Eq. (2)):
- *   NUMA_SWEEP_CUDA_CORES   FP32 FMAs on the CUDA cores, the even-odd split of
- *                           D (the default; relative error about 2^-24 times
- *                           the sums' condition number);
- *   NUMA_SWEEP_TENSOR_TF32  TF32 split products on the tensor cores (tcgen05)
- *                           with FP32 accumulation in tensor memory: each flux
- *                           and each entry of D is a TF32 head plus an FP32
- *                           tail, and the sums take head x head, head x tail
- *                           and tail x head (relative error about 2^-21 times
- *                           the condition number), for every order;
- *   NUMA_SWEEP_AUTO         numa_batch_autotune times both for each order
- *                           present and keeps the faster (until it runs, the
- *                           previous choice per order stands).
- * The choice applies from the next numa_batch_advance.  NUMA_FP64 batches take
+ * (numa_sweep, declared with numa_vol_set_sweep above): NUMA_SWEEP_CUDA_CORES
+ * (the default), NUMA_SWEEP_TENSOR_TF32 at every order, or NUMA_SWEEP_AUTO:
+ * numa_batch_autotune times both for each order present and keeps the faster
+ * (until it runs, the previous choice per order stands).  The choice applies
+ * from the next numa_batch_advance.  NUMA_FP64 batches take
  * NUMA_SWEEP_CUDA_CORES only (tcgen05 has no FP64 kind).
  * Errors: NUMA_EINVAL (NULL batch or unknown value), NUMA_EUNSUPPORTED.
  */
-typedef enum {
-    NUMA_SWEEP_CUDA_CORES = 0,
-    NUMA_SWEEP_TENSOR_TF32 = 1,
-    NUMA_SWEEP_AUTO = 2
-} numa_sweep;
 int numa_batch_set_sweep(numa_batch *b, numa_sweep sweep);
 
 /* The sweep mode last set (a numa_sweep value), or -1 for a NULL batch. */

@@ -90,6 +90,8 @@ def load() -> C.CDLL:
     lib.numa_vol_last_error.argtypes = []
     lib.numa_vol_last_error.restype = C.c_char_p
     lib.numa_vol_kernel_name.argtypes = [C.c_void_p]
+    lib.numa_vol_set_sweep.argtypes = [C.c_void_p, C.c_int]
+    lib.numa_vol_set_sweep.restype = C.c_int
     lib.numa_vol_kernel_name.restype = C.c_char_p
     lib.numa_vol_diff_matrix.argtypes = [C.c_int, _DP]
     lib.numa_vol_diff_matrix.restype = C.c_int

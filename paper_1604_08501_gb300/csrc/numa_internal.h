@@ -48,6 +48,15 @@ cudaError_t launch_vol_rhs_mixed(int N, int nf, ElemRange r, const MixedGeometry
                                  const MixedParams &P, const float *q, float *rhs, int num_sms,
                                  cudaStream_t s);
 
+// The mixed-precision kernel at N = 7 with the D sums on the tensor cores
+// (vol_mixed_tc.cu): a persistent grid; a bounded wait that runs out sets
+// bit 0 of *err.  prepare_vol_rhs_mixed_tc() once per device first (outside
+// stream capture).
+cudaError_t prepare_vol_rhs_mixed_tc();
+cudaError_t launch_vol_rhs_mixed_tc(ElemRange r, const MixedGeometry &geo, const MixedParams &P,
+                                    const float *q, float *rhs, int num_sms, int *err,
+                                    cudaStream_t s);
+
 // GLL points and differentiation matrix on the host (gll.cpp).
 int gll_diff_matrix(int N, double *D);
 
@@ -125,6 +134,7 @@ struct numa_vol {
     int num_sms = 0;
     int *d_err = nullptr;           // device status word: bit 0 = a bounded wait timed out
     numa_precision prec = NUMA_FP64;
+    bool tc_sweep = false;          // NUMA_MIXED, N = 7: the D sums on the tensor cores
     numa::EosConstants eos{};
     void *d_block = nullptr;        // one allocation: geometry, reference state, D
     size_t block_bytes = 0;

@@ -75,6 +75,7 @@ const char *numa_vol_kernel_name(const numa_vol *h) {
                                 "vol_rhs_df64_kernel<6>", "vol_rhs_df64_kernel<7>",
                                 "vol_rhs_df64_kernel<8>"};
     if (h->kernel == numa::Kernel::DoubleFloat) return dfk[h->N];
+    if (h->kernel == numa::Kernel::Mixed && h->tc_sweep) return "vol_rhs_mixed_tc_kernel<8>";
     if (h->kernel == numa::Kernel::Mixed) return mixed[h->N];
     if (h->kernel == numa::Kernel::MixedHigh) {
         static const char *mixed_high[] = {"vol_rhs_high_kernel<9, float>", "vol_rhs_high_kernel<10, float>",
@@ -84,6 +85,24 @@ const char *numa_vol_kernel_name(const numa_vol *h) {
         return mixed_high[h->N - 8];
     }
     return native[h->N];
+}
+
+int numa_vol_set_sweep(numa_vol *h, numa_sweep sweep) {
+    g_last_error.clear();
+    if (!h) return fail(NUMA_EINVAL, "numa_vol_set_sweep: NULL handle");
+    if (sweep != NUMA_SWEEP_CUDA_CORES && sweep != NUMA_SWEEP_TENSOR_TF32)
+        return fail(NUMA_EINVAL, "numa_vol_set_sweep: NUMA_SWEEP_CUDA_CORES or NUMA_SWEEP_TENSOR_TF32");
+    if (sweep == NUMA_SWEEP_CUDA_CORES) {
+        h->tc_sweep = false;
+        return NUMA_OK;
+    }
+    if (h->kernel != numa::Kernel::Mixed || h->N != 7 || h->nf != numa::kFields)
+        return fail(NUMA_EUNSUPPORTED, "numa_vol_set_sweep: the tensor-core sweep takes NUMA_MIXED "
+                                       "handles of N = 7 without tracers");
+    const cudaError_t e = numa::prepare_vol_rhs_mixed_tc();
+    if (e != cudaSuccess) return fail_cuda(e, "numa_vol_set_sweep");
+    h->tc_sweep = true;
+    return NUMA_OK;
 }
 
 int numa_vol_diff_matrix(int N, double *D_out) {
@@ -417,6 +436,9 @@ cudaError_t launch(numa_vol *h, const void *q, void *rhs, int64_t e0, int64_t co
         return numa::launch_vol_rhs_mixed_high(h->N, h->nf, r, h->mgeo, h->hmparams,
                                                static_cast<const float *>(q),
                                                static_cast<float *>(rhs), s);
+    if (h->kernel == numa::Kernel::Mixed && h->tc_sweep)
+        return numa::launch_vol_rhs_mixed_tc(r, h->mgeo, h->mparams, static_cast<const float *>(q),
+                                             static_cast<float *>(rhs), h->num_sms, h->d_err, s);
     if (h->kernel == numa::Kernel::Mixed)
         return numa::launch_vol_rhs_mixed(h->N, h->nf, r, h->mgeo, h->mparams,
                                           static_cast<const float *>(q), static_cast<float *>(rhs),

@@ -98,6 +98,12 @@ class VolumeTerm:
             raise RuntimeError("VolumeTerm is closed")
         return self._h.value
 
+    def set_sweep(self, sweep: str) -> None:
+        """The D sums on the CUDA cores ("cuda_cores") or as TF32 split products
+        on the tensor cores ("tensor_tf32": NUMA_MIXED handles of N = 7)."""
+        code = {"cuda_cores": NUMA_SWEEP_CUDA_CORES, "tensor_tf32": NUMA_SWEEP_TENSOR_TF32}[sweep]
+        check(_lib.load().numa_vol_set_sweep(C.c_void_p(self.handle), code))
+
     @property
     def kernel_name(self) -> str:
         """The kernel numa_vol_rhs launches for this handle."""
