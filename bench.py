@@ -575,9 +575,12 @@ def batched_results(rank, dev, world, precisions, instances, steps, warmup, orde
     for name in precisions:
         # "mixed-tc": the mixed batch with its D sums on the tensor cores;
         # "mixed-auto": the autotuner picks the sweep per order
+        # "mixed-tmem" / "mixed-smem": the CUDA-core tiles with the state in
+        # tensor memory / shared memory, whatever the autotuner would choose
         prec, sweep = {"fp64": ("fp64", "cuda_cores"), "mixed": ("mixed", "cuda_cores"),
                        "mixed-tc": ("mixed", "tensor_tf32"),
-                       "mixed-auto": ("mixed", "auto")}.get(name, (None, None))
+                       "mixed-auto": ("mixed", "auto"), "mixed-tmem": ("mixed", "cuda_cores"),
+                       "mixed-smem": ("mixed", "cuda_cores")}.get(name, (None, None))
         if prec is None:
             continue
         vts, states, points = [], [], 0
@@ -590,6 +593,8 @@ def batched_results(rank, dev, world, precisions, instances, steps, warmup, orde
         for vt, q in zip(vts, states):
             b.add(vt, q)
         b.autotune()
+        if name in ("mixed-tmem", "mixed-smem"):
+            b.set_config(state_in_tmem=name == "mixed-tmem")
         stream = torch.cuda.current_stream(dev)
         # Every launch integrates nsteps from the initial states: they are
         # restored before each launch, outside the timed events (the copy of
@@ -632,6 +637,7 @@ def batched_results(rank, dev, world, precisions, instances, steps, warmup, orde
                                    "sweep_by_nq": {str(nq): cfg["sweep"][nq] for nq in present},
                                    "ctas_per_sm": cfg["ctas_per_sm"] or "max",
                                    "costliest_first": cfg["costliest_first"],
+                                   "state_in_tmem": cfg["state_in_tmem"],
                                    "tuned_ms_per_step": round(cfg["tuned_ms_per_step"], 4),
                                    "candidates_timed": cfg["tuned_candidates"]},
                      "clocks": clocks}
@@ -670,7 +676,9 @@ def run_batched(args):
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
                 "dtype": {"fp64": "f64", "mixed": "f32 (perturbation state)",
                           "mixed-tc": "f32 (perturbation state), TF32 split products",
-                          "mixed-auto": "f32 (perturbation state)"}[head],
+                          "mixed-auto": "f32 (perturbation state)",
+                          "mixed-tmem": "f32 (perturbation state)",
+                          "mixed-smem": "f32 (perturbation state)"}[head],
                 "data": "synthetic",
                 "config": {"workload": BATCHED_WORKLOAD.format(n=len(plan))
                            + (f" (the plan's instances of orders N = {args.orders})" if orders else ""),

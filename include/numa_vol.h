@@ -316,8 +316,9 @@ int numa_batch_advance(numa_batch *b, int nsteps, double dt, void *stream);
  * tiles (1, 2, 4, 8, 16 or 32 passes of 512 threads per work item), and under
  * NUMA_SWEEP_AUTO over both sweeps; then, in the launch the batch actually
  * runs (all orders together), one round of coordinate descent over each
- * order's candidates, the CTAs per SM of the persistent grid and the order of
- * the work items, keeping a change that saves at least 1 %. */
+ * order's candidates, the CTAs per SM of the persistent grid, the order of
+ * the work items and (NUMA_MIXED) where the CUDA-core tiles keep the state,
+ * keeping a change that saves at least 1 %. */
 int numa_batch_autotune(numa_batch *b, void *stream);
 
 /* Launch configuration of a batch.  Indices are Nq = N + 1 (2..8; 0 and 1
@@ -331,6 +332,10 @@ typedef struct {
                                   (NUMA_MIXED) or 1 (NUMA_FP64); 0 = the most */
     int costliest_first;       /* nonzero: work items sorted by points, largest
                                   first (else instance by instance) */
+    int state_in_tmem;         /* NUMA_MIXED, nonzero (the default): the
+                                  CUDA-core tiles keep each point's q, dq,
+                                  metric terms and J^-1 in tensor memory rather
+                                  than shared memory */
     double tuned_ms_per_step;  /* read only: the last autotune's time for one
                                   step of the chosen configuration (0: none) */
     int tuned_candidates;      /* read only: launches the last autotune timed */

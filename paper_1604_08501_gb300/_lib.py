@@ -50,7 +50,8 @@ class numa_engine_counters(C.Structure):
 
 class numa_batch_config(C.Structure):
     _fields_ = [("tile", C.c_int * 9), ("sweep", C.c_int * 9), ("ctas_per_sm", C.c_int),
-                ("costliest_first", C.c_int), ("tuned_ms_per_step", C.c_double),
+                ("costliest_first", C.c_int), ("state_in_tmem", C.c_int),
+                ("tuned_ms_per_step", C.c_double),
                 ("tuned_candidates", C.c_int)]
 
 

@@ -51,6 +51,7 @@ struct numa_batch {
     unsigned tc_mask = 0;  // orders (bit Nq) whose D sums run on the tensor cores (mixed only)
     int ctas_per_sm = 0;   // CTAs per SM of the persistent grid (0: the kernel's maximum)
     bool costliest_first = false;   // work items sorted by points, largest first
+    bool tmem_state = false;        // mixed, CUDA-core tiles: the state in tensor memory
     double tuned_ms = 0.0;          // last autotune: ms per step of the chosen configuration
     int tuned_candidates = 0;       // last autotune: configurations timed
     // device scratch: instance table, work items, claim counter
@@ -156,6 +157,7 @@ int numa_batch_create(numa_precision prec, numa_batch **out) {
     numa_batch *b = new (std::nothrow) numa_batch();
     if (!b) return bfail(NUMA_ENOMEM, "numa_batch_create: host allocation failed");
     b->prec = prec;
+    b->tmem_state = prec == NUMA_MIXED;   // measured faster (section on the batch tile)
     cudaError_t e = cudaGetDevice(&b->device);
     if (e == cudaSuccess)
         e = cudaDeviceGetAttribute(&b->num_sms, cudaDevAttrMultiProcessorCount, b->device);
@@ -234,7 +236,7 @@ int numa_batch_advance(numa_batch *b, int nsteps, double dt, void *stream) {
         if (e == cudaSuccess)
             e = numa::launch_batch_lsrk(b->prec == NUMA_MIXED, b->d_inst, b->d_items, b->num_items,
                                         b->d_counter, kLsrk, nsteps, dt, grid_of(b), b->cap_stream,
-                                        b->tc_mask, b->ctas_per_sm);
+                                        b->tc_mask, b->ctas_per_sm, b->tmem_state);
         cudaGraph_t g = nullptr;
         const cudaError_t e2 = cudaStreamEndCapture(b->cap_stream, &g);
         if (e == cudaSuccess) e = e2;
@@ -262,6 +264,7 @@ struct TuneCfg {
     unsigned mask;
     int ctas;
     bool costliest;
+    bool tmem;
 };
 
 // Best of `reps` timed launches of `nsteps` steps over instances `sub` in
@@ -277,7 +280,7 @@ cudaError_t time_cfg(numa_batch *b, const std::vector<numa::BatchInstance> &sub,
         if (e == cudaSuccess)
             e = numa::launch_batch_lsrk(b->prec == NUMA_MIXED, b->d_inst, b->d_items, b->num_items,
                                         b->d_counter, kLsrk, nsteps, 1e-6, grid_of(b), s, c.mask,
-                                        c.ctas);
+                                        c.ctas, c.tmem);
         if (e == cudaSuccess) e = cudaEventRecord(t1, s);
         if (e == cudaSuccess) e = cudaEventRecord(b->launched, s);
         if (e == cudaSuccess) e = cudaEventSynchronize(t1);
@@ -324,6 +327,7 @@ int numa_batch_autotune(numa_batch *b, void *stream) {
     cur.mask = b->tc_mask;
     cur.ctas = b->ctas_per_sm;
     cur.costliest = b->costliest_first;
+    cur.tmem = b->tmem_state;
     // per-order candidates: (sweep, passes per item)
     auto order_cands = [&](int nq) {
         std::vector<std::pair<unsigned, int>> v;
@@ -397,6 +401,11 @@ int numa_batch_autotune(numa_batch *b, void *stream) {
         c.costliest = !cur.costliest;
         try_cfg(c);
     }
+    if (mixed) {   // the CUDA-core tiles' state in tensor memory or shared memory
+        TuneCfg c = cur;
+        c.tmem = !cur.tmem;
+        try_cfg(c);
+    }
     for (void *c : copies) cudaFree(c);
     if (t0) cudaEventDestroy(t0);
     if (t1) cudaEventDestroy(t1);
@@ -405,6 +414,7 @@ int numa_batch_autotune(numa_batch *b, void *stream) {
     b->tc_mask = cur.mask;
     b->ctas_per_sm = cur.ctas;
     b->costliest_first = cur.costliest;
+    b->tmem_state = cur.tmem;
     b->tuned_ms = best / kSteps;
     b->dirty = true;   // the work list is rebuilt with the chosen tiles
     drop_graph(b);     // and the launch recaptured with the chosen kernel and grid
@@ -420,6 +430,7 @@ int numa_batch_get_config(const numa_batch *b, numa_batch_config *out) {
     }
     c.ctas_per_sm = b->ctas_per_sm;
     c.costliest_first = b->costliest_first ? 1 : 0;
+    c.state_in_tmem = b->tmem_state ? 1 : 0;
     c.tuned_ms_per_step = b->tuned_ms;
     c.tuned_candidates = b->tuned_candidates;
     *out = c;
@@ -452,7 +463,10 @@ int numa_batch_set_config(numa_batch *b, const numa_batch_config *c) {
     for (int nq = 2; nq <= 8; ++nq) b->tile_mult[nq] = mult[nq];
     b->tc_mask = mask;
     b->ctas_per_sm = c->ctas_per_sm;
+    if (c->state_in_tmem && !mixed)
+        return bfail(NUMA_EUNSUPPORTED, "numa_batch_set_config: state_in_tmem is for NUMA_MIXED batches");
     b->costliest_first = c->costliest_first != 0;
+    b->tmem_state = c->state_in_tmem != 0;
     b->dirty = true;
     drop_graph(b);
     return NUMA_OK;

@@ -72,12 +72,13 @@ batch_lsrk_kernel(const BatchInstance *__restrict__ inst, const BatchItem *__res
 
 
 // Mixed precision with the D contractions on the tensor cores (batch_tile_tc.cuh)
-// for the orders whose bit Nq is set in tc_mask, on the CUDA cores (run_tile)
-// for the others: the autotuner picks per order.  counter[1] is the batch's
+// for the orders whose bit Nq is set in tc_mask, on the CUDA cores for the
+// others (run_tile_cc_tm: run_tile's phases with the state in tensor memory):
+// the autotuner picks per order.  counter[1] is the batch's
 // status word: bit 0 is set when a wait for the tensor core ran out; the CTA
 // then stops claiming work.
-static_assert(sizeof(float) * kMixedSmemWords <= (size_t)kTcSmemBytes,
-              "the CUDA-core tile shares the tensor tile's shared memory");
+static_assert(sizeof(float) * kMixedFluxWords <= (size_t)kTcOperandBytes,
+              "the CUDA-core tile's fluxes fit the tensor tile's operand region");
 
 // Separate functions (not inlined), so that each tile is register-allocated on
 // its own: inlined together they spill.
@@ -91,8 +92,8 @@ __device__ __noinline__ bool run_tile_tc_call(const BatchInstance &I, int64_t e0
 template <int NQ>
 __device__ __noinline__ void run_tile_cc_call(const BatchInstance &I, int64_t e0, int64_t count,
                                               const float *sco, int ns, double dt,
-                                              unsigned char *sm) {
-    run_tile<NQ, true>(I, e0, count, sco, ns, dt, sm);
+                                              unsigned char *sm, uint32_t tmem) {
+    run_tile_cc_tm<NQ>(I, e0, count, sco, ns, dt, sm, tmem);
 }
 
 template <int NQ>
@@ -103,7 +104,7 @@ __device__ __forceinline__ bool run_tile_either(unsigned tc_mask, const BatchIns
                                                 int *s_nq) {
     if ((tc_mask >> NQ) & 1u)
         return run_tile_tc_call<NQ>(I, e0, count, sco, ns, dt, sm, tmem, bar, phase, s_nq);
-    run_tile_cc_call<NQ>(I, e0, count, sco, ns, dt, sm);
+    run_tile_cc_call<NQ>(I, e0, count, sco, ns, dt, sm, tmem);
     __syncthreads();
     if (threadIdx.x == 0) *s_nq = 0;   // the operands were overwritten
     return true;
@@ -205,11 +206,11 @@ int batch_max_ctas_per_sm(bool mixed) { return mixed ? 2 : tile_ctas_per_sm<fals
 cudaError_t launch_batch_lsrk(bool mixed, const BatchInstance *inst, const BatchItem *items,
                               int num_items, int *counter, const LsrkCoef &co, int nsteps,
                               double dt, int num_sms, cudaStream_t s, unsigned tc_mask,
-                              int ctas_per_sm) {
+                              int ctas_per_sm, bool tmem_state) {
     if (num_items <= 0 || nsteps <= 0) return cudaSuccess;
     const int kmax = batch_max_ctas_per_sm(mixed);
     const int k = ctas_per_sm > 0 && ctas_per_sm < kmax ? ctas_per_sm : kmax;
-    if (mixed && tc_mask != 0)
+    if (mixed && (tc_mask != 0 || tmem_state))
         batch_lsrk_tc_kernel<<<num_sms * k, kThreads, kTcSmemBytes, s>>>(
             inst, items, num_items, counter, co, nsteps, dt, tc_mask);
     else if (mixed)

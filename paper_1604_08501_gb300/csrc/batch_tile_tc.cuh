@@ -461,6 +461,139 @@ __device__ bool run_tile_tc(const BatchInstance &I, int64_t e0, int64_t count, c
     return true;
 }
 
+// The CUDA-core tile (run_tile's phases: fluxes by point into the line
+// layout of element_sweep.cuh, even-odd sweeps by line, combination by point)
+// with each point's q, dq, metric terms and J^-1 in tensor memory (the columns
+// run_tile_tc uses) instead of shared memory: shared memory holds only the
+// fluxes, and the point phases read and write the state with three TMEM
+// loads and two TMEM stores per stage instead of 35 shared accesses.
+template <int NQ>
+__device__ void run_tile_cc_tm(const BatchInstance &I, int64_t e0, int64_t count, const float *sco,
+                               int nsteps, double dt, unsigned char *sm, uint32_t tmem) {
+    constexpr int N3 = NQ * NQ * NQ;
+    constexpr int NL = NQ * NQ;
+    constexpr int EPP = kThreads / N3;
+    constexpr int EW = block_words<NQ, float>();
+    constexpr int BLK = EPP * EW;
+    constexpr int TASKS = 3 * kFields * EPP * NL;
+    float *sF = reinterpret_cast<float *>(sm);
+    float *aux = reinterpret_cast<float *>(sm + kTcOperandBytes) + threadIdx.x;
+    const int l = threadIdx.x, w = l >> 5;
+    const int el = l / N3, p = l % N3;
+    const int i = p % NQ, j = (p / NQ) % NQ, k = p / NL;
+    const bool has_point = l < EPP * N3;
+    int f[3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) f[d] = d * kFields * BLK + el * EW + dir_slot<NQ, float>(d, i, j, k);
+    const uint32_t st_col =
+        tmem + ((uint32_t)(32 * (w & 3)) << 16) + kTcStateCol + kTcStateStride * (uint32_t)(w >> 2);
+    const float dtt = static_cast<float>(dt);
+    const float grav = I.mp.grav;
+    const int cnt = (int)count;
+    for (int b0 = 0; b0 < cnt; b0 += EPP) {
+        const int npass = cnt - b0 < EPP ? cnt - b0 : EPP;
+        const bool active = has_point && el < npass;
+        uint32_t v[16];
+#pragma unroll
+        for (int t = 0; t < 16; ++t) v[t] = 0u;
+        if (active) {
+            const int64_t node = (e0 + b0 + el) * N3 + p;
+            const float *qv = static_cast<const float *>(I.q);
+#pragma unroll
+            for (int b = 0; b < kFields; ++b) v[b] = __float_as_uint(qv[b * I.M + node]);
+#pragma unroll
+            for (int s2 = 0; s2 < 9; ++s2) v[5 + s2] = __float_as_uint(__ldg(I.mgeo.g[s2] + node));
+            v[14] = __float_as_uint(__ldg(I.mgeo.Jinv + node));
+            const float th0 = __ldg(I.mgeo.theta_ref + node);
+            EosRef32 er{0.f, 0.f};
+            if (th0 > 0.f) er = eos_reference_f32(th0, I.mp);
+            aux[0] = th0;
+            aux[kThreads] = __ldg(I.mgeo.rho_ref + node);
+            aux[2 * kThreads] = er.w;
+            aux[3 * kThreads] = er.A;
+        }
+        {
+            uint32_t z[8] = {0u, 0u, 0u, 0u, 0u, 0u, 0u, 0u};
+            tc::tmem_st16(st_col, v);
+            tc::tmem_st8(st_col + 16, z);
+        }
+        for (int step = 0; step < nsteps; ++step) {
+#pragma unroll 1
+            for (int st = 0; st < 5; ++st) {
+                __syncthreads();   // previous phase-3 reads of sF are done
+                if (active) {
+                    const float th0 = aux[0], rho0 = aux[kThreads];
+                    const EosRef32 er{aux[2 * kThreads], aux[3 * kThreads]};
+                    float q[kFields], g[9];
+#pragma unroll
+                    for (int b = 0; b < kFields; ++b) q[b] = __uint_as_float(v[b]);
+#pragma unroll
+                    for (int s2 = 0; s2 < 9; ++s2) g[s2] = __uint_as_float(v[5 + s2]);
+                    const float rho = rho0 + q[0];
+                    const float Th = th0 + q[4];
+                    const float pp = pressure_perturbation_f32(q[4], th0, er, I.mp);
+                    const float rinv = __frcp_rn(rho);   // the correctly rounded 1/rho
+#pragma unroll
+                    for (int d = 0; d < 3; ++d) {
+                        const float g1 = g[3 * d], g2 = g[3 * d + 1], g3 = g[3 * d + 2];
+                        const float vv = fmaf(g3, q[3], fmaf(g2, q[2], g1 * q[1]));
+                        const float u = vv * rinv;
+                        float *F = sF + f[d];
+                        F[0 * BLK] = vv;
+                        F[1 * BLK] = fmaf(q[1], u, g1 * pp);
+                        F[2 * BLK] = fmaf(q[2], u, g2 * pp);
+                        F[3 * BLK] = fmaf(q[3], u, g3 * pp);
+                        F[4 * BLK] = Th * u;
+                    }
+                }
+                __syncthreads();
+#pragma unroll 1
+                for (int t = l; t < TASKS; t += kThreads) {
+                    const int bd = t / (EPP * NL), rem = t % (EPP * NL);
+                    const int e = rem / NL, line = rem % NL;
+                    if (e < npass) sweep_line<NQ>(sF + bd * BLK + e * EW, line, c_sweep32[NQ]);
+                }
+                // the state for phase 3, its loads issued before the barrier
+                uint32_t dv[8];
+                tc::tmem_st_wait();
+                tc::tmem_ld16(st_col, v);
+                tc::tmem_ld8(st_col + 16, dv);
+                __syncthreads();
+                tc::tmem_ld_wait16(v);
+                tc::tmem_ld_wait(dv);
+                if (active) {
+                    const float a = sco[st], bcoef = sco[5 + st];
+                    const float jinv = __uint_as_float(v[14]);
+                    const float drho = __uint_as_float(v[0]);
+#pragma unroll
+                    for (int b = 0; b < kFields; ++b) {
+                        const float R = sF[f[0] + b * BLK] + sF[f[1] + b * BLK] + sF[f[2] + b * BLK];
+                        float rhs = -jinv * R;
+                        if (b == 3) rhs = fmaf(-drho, grav, rhs);
+                        const float dq = fmaf(a, __uint_as_float(dv[b]), dtt * rhs);
+                        dv[b] = __float_as_uint(dq);
+                        v[b] = __float_as_uint(fmaf(bcoef, dq, __uint_as_float(v[b])));
+                    }
+                }
+                {
+                    uint32_t q8[8];
+#pragma unroll
+                    for (int t = 0; t < 8; ++t) q8[t] = v[t];
+                    tc::tmem_st8(st_col, q8);
+                    tc::tmem_st8(st_col + 16, dv);
+                }
+            }
+        }
+        tc::tmem_st_wait();
+        if (active) {
+            const int64_t node = (e0 + b0 + el) * N3 + p;
+            float *q_out = static_cast<float *>(I.q);
+#pragma unroll
+            for (int b = 0; b < kFields; ++b) q_out[b * I.M + node] = __uint_as_float(v[b]);
+        }
+    }
+}
+
 }  // namespace
 
 }  // namespace numa

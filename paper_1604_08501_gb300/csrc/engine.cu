@@ -492,7 +492,8 @@ int numa_engine_progress(numa_engine *e, int64_t *done_ids, int max_done, int *n
         if (err == cudaSuccess)
             err = numa::launch_batch_lsrk(e->prec == NUMA_MIXED, sl.d_inst, sl.d_items,
                                           (int)items.size(), sl.d_counter, kCoef, launch_steps,
-                                          dt, e->num_sms, e->stream);
+                                          dt, e->num_sms, e->stream, 0u, 0,
+                                          e->prec == NUMA_MIXED);
         if (err == cudaSuccess) err = cudaEventRecord(sl.done, e->stream);
         if (err == cudaSuccess) err = cudaEventRecord(e->last_launch, e->stream);
         if (err != cudaSuccess) return efail_cuda(err, "numa_engine_progress: step");

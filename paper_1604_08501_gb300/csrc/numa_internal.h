@@ -107,11 +107,13 @@ cudaError_t prepare_batch_lsrk();
 // the kernel's status bits.
 constexpr unsigned kTcAllOrders = 0x1FCu;   // bits 2..8
 // ctas_per_sm: CTAs per SM of the persistent grid, 1 .. the kernel's maximum
-// (batch_max_ctas_per_sm); 0 takes the maximum.
+// (batch_max_ctas_per_sm); 0 takes the maximum.  tmem_state (mixed): the
+// CUDA-core tiles keep each point's state in tensor memory instead of shared
+// memory (the tensor-core kernel's CUDA-core path).
 cudaError_t launch_batch_lsrk(bool mixed, const BatchInstance *inst, const BatchItem *items,
                               int num_items, int *counter, const LsrkCoef &co, int nsteps,
                               double dt, int num_sms, cudaStream_t s, unsigned tc_mask = 0,
-                              int ctas_per_sm = 0);
+                              int ctas_per_sm = 0, bool tmem_state = false);
 int batch_max_ctas_per_sm(bool mixed);
 
 // Elements one CTA pass holds for order Nq (512 threads, one per point).

@@ -238,10 +238,12 @@ class Batch:
         return {"tile": {nq: c.tile[nq] for nq in range(2, 9)},
                 "sweep": {nq: names[c.sweep[nq]] for nq in range(2, 9)},
                 "ctas_per_sm": c.ctas_per_sm, "costliest_first": bool(c.costliest_first),
+                "state_in_tmem": bool(c.state_in_tmem),
                 "tuned_ms_per_step": c.tuned_ms_per_step,
                 "tuned_candidates": c.tuned_candidates}
 
-    def set_config(self, tile=None, sweep=None, ctas_per_sm=None, costliest_first=None) -> None:
+    def set_config(self, tile=None, sweep=None, ctas_per_sm=None, costliest_first=None,
+                   state_in_tmem=None) -> None:
         """Set any of the configuration fields of config() (the others stay)."""
         cur = self.config()
         c = _lib.numa_batch_config()
@@ -251,6 +253,8 @@ class Batch:
         c.ctas_per_sm = int(cur["ctas_per_sm"] if ctas_per_sm is None else ctas_per_sm)
         c.costliest_first = int(cur["costliest_first"] if costliest_first is None
                                 else bool(costliest_first))
+        c.state_in_tmem = int(cur["state_in_tmem"] if state_in_tmem is None
+                              else bool(state_in_tmem))
         check_batch(_lib.load().numa_batch_set_config(self.handle, C.byref(c)))
 
     def status(self, stream=None) -> None:

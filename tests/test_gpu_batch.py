@@ -222,15 +222,16 @@ def test_every_candidate_configuration_keeps_parity(precision):
     with Batch(precision) as b:
         for w, vt, q in runs:
             b.add(vt, q)
+        tmems = [False, True] if precision == "mixed" else [False]
         for passes in (1, 2, 4, 8, 16, 32):
             for sweep in sweeps:
                 for k in ctas:
-                    for costliest in (False, True):
+                    for costliest, tmem in ((False, False), (True, tmems[-1])):
                         for (_, _, q), q0 in zip(runs, saved):
                             q.copy_(q0)
                         b.set_config(tile={nq: passes * (512 // nq ** 3) for nq in range(2, 9)},
                                      sweep={nq: sweep for nq in range(2, 9)}, ctas_per_sm=k,
-                                     costliest_first=costliest)
+                                     costliest_first=costliest, state_in_tmem=tmem)
                         b.advance(NSTEPS, DT)
                         b.status()
                         torch.cuda.synchronize()
@@ -243,7 +244,7 @@ def test_every_candidate_configuration_keeps_parity(precision):
                             else:
                                 errs = rel_err(got - w.q, ref - w.q)
                             for f, (mx, _) in enumerate(errs):
-                                assert mx <= tol, (passes, sweep, k, costliest, sp, f, mx)
+                                assert mx <= tol, (passes, sweep, k, costliest, tmem, sp, f, mx)
 
 
 def test_autotune_reports_configuration():

@@ -184,8 +184,8 @@ def test_invalid_pointers_are_rejected_and_context_survives():
         res = vt.rhs(q)
         torch.cuda.synchronize()
         assert_parity(res.cpu().numpy(), oracle.vol_rhs_o2(prob, w.q))
-    with pytest.raises(NumaError):
-        VolumeTerm(3, 1, [np.ones(64)] * 9, np.ones(64), np.ones(64), np.ones(64),
+    with pytest.raises(NumaError):   # the double-float mode takes N <= 7
+        VolumeTerm(8, 1, [np.ones(729)] * 9, np.ones(729), np.ones(729), np.ones(729),
                    p0=1e5, R=287.0, cp=1004.0, grav=9.8, precision="df64").close()
 
 
