@@ -157,7 +157,7 @@ int numa_batch_create(numa_precision prec, numa_batch **out) {
     numa_batch *b = new (std::nothrow) numa_batch();
     if (!b) return bfail(NUMA_ENOMEM, "numa_batch_create: host allocation failed");
     b->prec = prec;
-    b->tmem_state = prec == NUMA_MIXED;   // measured faster (section on the batch tile)
+    b->tmem_state = prec == NUMA_MIXED;   // the state in tensor memory: the faster tile
     cudaError_t e = cudaGetDevice(&b->device);
     if (e == cudaSuccess)
         e = cudaDeviceGetAttribute(&b->num_sms, cudaDevAttrMultiProcessorCount, b->device);
