@@ -55,6 +55,14 @@ __device__ __forceinline__ void tmem_alloc(uint32_t *slot, uint32_t ncols) {
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
 }
 
+// Gives up the CTA's permit to allocate without allocating (all 32 threads of
+// one warp).  A kernel that contains tcgen05.alloc issues it in CTAs that do
+// not allocate: measured on GB300, such CTAs that kept the permit until they
+// exited were not co-scheduled with a second CTA on their SM.
+__device__ __forceinline__ void tmem_relinquish() {
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+
 // Frees the columns (all 32 threads of one warp).
 __device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols)
@@ -161,6 +169,27 @@ __device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t (&r)[16
         "r"(r[8]), "r"(r[9]), "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]),
         "r"(r[15])
         : "memory");
+}
+
+// One column of this thread's lane.  Neither asm clobbers memory: a TMEM
+// access touches no memory the compiler sees, so ordinary loads and stores
+// may be scheduled across it.
+__device__ __forceinline__ void tmem_st1(uint32_t taddr, uint32_t v) {
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x1.b32 [%0], {%1};" ::"r"(taddr), "r"(v));
+}
+__device__ __forceinline__ uint32_t tmem_ld1(uint32_t taddr) {
+    uint32_t v;
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x1.b32 {%0}, [%1];" : "=r"(v) : "r"(taddr));
+    return v;
+}
+// Waits for this thread's TMEM loads; after it, pass each loaded register
+// through after_wait() so that no use of it is scheduled before the wait.
+__device__ __forceinline__ void tmem_ld_wait_all() {
+    asm volatile("tcgen05.wait::ld.sync.aligned;");
+}
+__device__ __forceinline__ uint32_t after_wait(uint32_t v) {
+    asm volatile("" : "+r"(v));
+    return v;
 }
 
 __device__ __forceinline__ void tmem_st_wait() {

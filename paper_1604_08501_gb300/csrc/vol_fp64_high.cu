@@ -9,21 +9,31 @@
 //  * one CTA per element with three threads per (i, j) column (four in FP32
 //    at Nq >= 15), each looping over its share of the k-planes, as the
 //    paper's kernels own (i, j) lanes and loop over k;
-//  * a first pass forms the contravariant velocities u_d and p' of all points
-//    into shared memory (4 Nq^3 values);
-//  * then one pass per group of fields (one field in FP64; as many as
-//    shared memory holds in FP32): their flux arrays into shared memory
-//    (3 Nq^2 lines per field: 16 slots in FP64, an odd number >= Nq in FP32),
-//    the D sweeps in place (even-odd split, lines dealt out to the threads),
-//    and the rhs of the thread's points straight to HBM.
+//  * one pass per group of fields (one field in FP64; as many as shared
+//    memory holds in FP32): their flux arrays into shared memory (3 Nq^2
+//    lines per field: 16 slots in FP64, an odd number >= Nq in FP32), the D
+//    sweeps in place (even-odd split, lines dealt out to the threads), and the
+//    rhs of the thread's points straight to HBM;
+//  * FP64: the first pass also keeps the contravariant velocities u_d and p'
+//    of all points in shared memory (4 Nq^3 values), from which each later
+//    pass forms its field's fluxes;
+//  * FP32: the first pass forms the fluxes of every field; those beyond the
+//    first group wait in tensor memory (tcgen05.st, one TMEM lane per thread)
+//    until their pass copies them into shared memory (tcgen05.ld), so no later
+//    pass reads the state or the metrics again, and without u_d and p' the
+//    first group is as large as shared memory allows: every field in one pass
+//    up to Nq = 12 (five fields), four of five at Nq = 16.
 // Shared memory at Nq = 16: 224 KB in FP64 (every operation FP64; bound by the
-// FP64 pipe like the low orders), 222 KB in the mixed mode (FP32 perturbation
-// state and arithmetic as vol_mixed.cu; three fields per pass).
+// FP64 pipe like the low orders), 204 KB in the mixed mode (FP32 perturbation
+// state and arithmetic as vol_mixed.cu).
 #include <cuda_runtime.h>
+
+#include <type_traits>
 
 #include "element_sweep.cuh"
 #include "eos.cuh"
 #include "numa_internal.h"
+#include "tcgen05.cuh"
 
 namespace numa {
 
@@ -44,9 +54,12 @@ __host__ __device__ constexpr int high_tpc() {
     return 3;
 }
 
+// FP32: rounded up to whole warps, since tensor-memory accesses are
+// warp-wide; the extra threads own no points and sweep no lines.
 template <int NQ, typename T>
 __host__ __device__ constexpr int high_threads() {
-    return high_tpc<NQ, T>() * NQ * NQ;
+    return sizeof(T) == 4 ? (high_tpc<NQ, T>() * NQ * NQ + 31) / 32 * 32
+                          : high_tpc<NQ, T>() * NQ * NQ;
 }
 
 // Flux slot of point (i, j, k) in direction d.  A warp of the point phases is
@@ -69,25 +82,42 @@ __device__ __forceinline__ int high_slot(int d, int i, int j, int k) {
 }
 
 // Fields per pass.  FP64: one (the flux arrays of one field already take
-// 98 KB at Nq = 16).  FP32: as many as fit the shared memory of the CTAs per
-// SM the thread count allows (two CTAs up to 512 threads each), so that fewer
-// passes re-read the element and fewer barriers separate them.
+// 98 KB at Nq = 16).  FP32: as many as 100 KB of shared memory hold where two
+// CTAs of the thread count fit an SM (226 KB with one CTA per SM), but at
+// least as many as leave the other fields of an 8-field launch room in the
+// tensor memory of the CTAs of one SM (256 or 512 columns each).  Not the full
+// 113 KB of two CTAs: a group of all five fields at Nq = 12 (110 KB) measured
+// 24.1 GDOF/s against 27.5 for four (88 KB) with the fifth parked in tensor
+// memory, the larger shared-memory carveout leaving the L1 too little room for
+// the loads in flight.
+template <int NQ, typename T>
+__host__ __device__ constexpr int high_tmem_need(int g) {
+    const int ks = (NQ + high_tpc<NQ, T>() - 1) / high_tpc<NQ, T>();
+    const int need = (high_threads<NQ, T>() / 32 + 3) / 4 * ks * 3 * (kMaxFields - g);
+    int c = 32;
+    while (c < need) c *= 2;
+    return need <= 0 ? 0 : c;
+}
+
 template <int NQ, typename T>
 __host__ __device__ constexpr int high_group() {
     if constexpr (sizeof(T) == 8) {
         return 1;
     } else {
-        constexpr size_t fixed = sizeof(T) * 4 * NQ * NQ * NQ;   // u_d and p'
+        constexpr bool two = 2 * high_threads<NQ, T>() <= 1024;
         constexpr size_t per = sizeof(T) * 3 * NQ * NQ * line_stride<NQ, T>();   // one field's fluxes
-        constexpr size_t budget = (2 * high_tpc<NQ, T>() * NQ * NQ <= 1024 ? 113 : 226) * 1024;
-        constexpr size_t g = budget > fixed ? (budget - fixed) / per : 1;
-        return g < 1 ? 1 : (g > kMaxFields ? kMaxFields : (int)g);
+        constexpr size_t budget = (two ? 100 : 226) * 1024;
+        int g = (int)(budget / per);
+        g = g < 1 ? 1 : (g > kMaxFields ? kMaxFields : g);
+        while (g < kMaxFields && high_tmem_need<NQ, T>(g) > (two ? 256 : 512)) ++g;
+        return g;
     }
 }
 
 template <int NQ, typename T>
 __host__ __device__ constexpr size_t high_smem_bytes() {
-    return sizeof(T) * (4 * NQ * NQ * NQ + high_group<NQ, T>() * 3 * NQ * NQ * line_stride<NQ, T>());
+    return sizeof(T) * ((sizeof(T) == 8 ? 4 * NQ * NQ * NQ : 0) +
+                        high_group<NQ, T>() * 3 * NQ * NQ * line_stride<NQ, T>());
 }
 
 // CTAs per SM the register budget is sized for: two where two CTAs' shared
@@ -97,6 +127,32 @@ __host__ __device__ constexpr int high_min_ctas() {
     return (2 * (high_smem_bytes<NQ, T>() + 1024) <= 228 * 1024 && 2 * high_threads<NQ, T>() <= 1024)
                ? 2
                : 1;
+}
+
+// Tensor memory of the FP32 instance: per warp, the fluxes of the fields
+// beyond the first group for its threads' points, 3 (kMaxFields - G) per
+// point (column (f KS + kk) 3 + d for parked field f, k-plane kk of the slab,
+// direction d); the warps of one lane quarter (warp % 4) side by side.  The
+// allocation (a power of two >= 32 columns) is sized for eight fields and
+// made only when the launch has fields beyond the first group.
+template <int NQ, typename T>
+__host__ __device__ constexpr int high_park_cols() {
+    constexpr int KS = (NQ + high_tpc<NQ, T>() - 1) / high_tpc<NQ, T>();
+    return sizeof(T) == 4 ? KS * 3 * (kMaxFields - high_group<NQ, T>()) : 0;
+}
+
+template <int NQ, typename T>
+__host__ __device__ constexpr int high_tmem_cols() {
+    return sizeof(T) == 4 ? high_tmem_need<NQ, T>(high_group<NQ, T>()) : 0;
+}
+
+// Parked fluxes a thread may hold in registers over its k-planes before it
+// stores them (pass 0 below): one field's at Nq = 12, 13 and 16.  Two fields'
+// (24 values) at Nq = 16 with three fields per group measured slower (26.2
+// against 27.7 GDOF/s for four fields per group and one held).
+template <int NQ, typename T>
+__host__ __device__ constexpr int high_hold() {
+    return 16;
 }
 
 template <typename T> struct HighTypes;
@@ -112,64 +168,131 @@ vol_rhs_high_kernel(typename HighTypes<T>::Geo geo, typename HighTypes<T>::Param
     constexpr int N3 = NQ * NL;
     constexpr int FB = NL * line_stride<NQ, T>();   // one direction's flux block (padded lines)
     constexpr int TPC = high_tpc<NQ, T>();
-    constexpr int NT = TPC * NL;     // threads
+    constexpr int NT = high_threads<NQ, T>();
     constexpr int KS = (NQ + TPC - 1) / TPC; // k-planes per slab
     constexpr int G = high_group<NQ, T>();
+    constexpr int PC = high_park_cols<NQ, T>();     // TMEM columns per warp
+    constexpr int TC = high_tmem_cols<NQ, T>();
+    constexpr int PL = PC > 0 ? kMaxFields - G : 1;   // fields a point can park
+    static_assert(TC <= 512 / high_min_ctas<NQ, T>(), "tensor memory of the CTAs of one SM");
     // k-loop unrolling: full in FP32 (registers to spare, more loads in
     // flight), two planes in FP64 (register budget)
     constexpr int KU = MIXED ? KS : 2;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    T *sU = reinterpret_cast<T *>(smem_raw);   // u_d of every point: [d][k][j][i]
-    T *sP = sU + 3 * N3;                       // p' of every point: [k][j][i]
-    T *sF = sU + 4 * N3;                       // fluxes of a group: [field][d][line][slot]
+    __shared__ uint32_t s_tmem;
+    T *sU = reinterpret_cast<T *>(smem_raw);   // FP64: u_d of every point: [d][k][j][i]
+    T *sP = sU + 3 * N3;                       // FP64: p' of every point: [k][j][i]
+    T *sF = MIXED ? sU : sU + 4 * N3;          // fluxes of a group: [field][d][line][slot]
 
     const int t = threadIdx.x;
-    const int c = t % NL, slab = t / NL;
+    const int c = t % NL, slab = t / NL;   // slab == TPC: a padding thread
     const int i = c % NQ, j = c / NQ;
     const int kb = slab * KS;                          // first k-plane of the slab
     const int64_t node0 = (e0 + blockIdx.x) * N3 + c;  // point (i, j, 0); + k NL
 
+    // FP32 with fields beyond the first group: their fluxes wait in TMEM
+    const bool park = PC > 0 && nf > G;   // uniform over the CTA
+    uint32_t tpark = 0;                   // this thread's lane, its warp's first column
+    if constexpr (PC > 0) {
+        if (t < 32) {
+            if (park) tc::tmem_alloc(&s_tmem, TC);
+            else tc::tmem_relinquish();   // lets a second CTA onto the SM
+        }
+        if (park) {
+            tc::fence_before_sync();
+            __syncthreads();
+            tc::fence_after_sync();
+            const int w = t >> 5;
+            tpark = s_tmem + ((uint32_t)(32 * (w & 3)) << 16) + (uint32_t)((w >> 2) * PC);
+        }
+    }
+
     // Flux of field b in direction d at a point: F_d[rho] = g_d . U,
     // F_d[U_a] = U_a u_d + g_{ad} p', F_d[Theta] = Theta u_d, tracers Q u_d.
-    // ---- pass 0: u_d, p', and the fluxes of the first group ---------------
+    // ---- pass 0: the fluxes of the first group (FP64: and u_d, p'; FP32:
+    // and the fluxes of LP more fields, parked in TMEM).  Where they fit
+    // (high_hold) the parked fluxes of all the slab's planes stay in
+    // registers until after the planes, so that the compiler can still issue
+    // every plane's loads at once: a TMEM store between two planes keeps the
+    // later plane's loads behind it (measured: 22.7 against 25.7 GDOF/s at
+    // Nq = 16 with one parked field).  Otherwise they are stored plane by
+    // plane.
+    auto pass0 = [&](auto lp) {
+        constexpr int LP = decltype(lp)::value;
+        constexpr bool HOLD = LP > 0 && 3 * LP * KS <= high_hold<NQ, T>();
+        T hold[HOLD ? 3 * LP * KS : 1];
 #pragma unroll(KU)
-    for (int kk = 0; kk < KS; ++kk) {
-        const int k = kb + kk;
-        if (k < NQ) {
-            const int64_t node = node0 + k * NL;
-            const T U[3] = {q[M + node], q[2 * M + node], q[3 * M + node]};
-            T rinv, pp, Th;
-            if constexpr (MIXED) {
-                const float th0 = geo.theta_ref[node];
-                pp = pressure_perturbation_f32(q[4 * M + node], th0, P);
-                rinv = __frcp_rn(geo.rho_ref[node] + q[node]);
-                Th = th0 + q[4 * M + node];
-            } else {
-                pp = pressure_perturbation(q[4 * M + node], geo.theta_ref[node], geo.w[node],
-                                           geo.A[node], P);
-                rinv = __drcp_rn(q[node]);
-                Th = q[4 * M + node];
+        for (int kk = 0; kk < KS; ++kk) {
+            const int k = kb + kk;
+            T pk[3 * (LP > 0 ? LP : 1)];   // this point's parked fluxes
+#pragma unroll
+            for (int x = 0; x < 3 * (LP > 0 ? LP : 1); ++x) pk[x] = T(0);
+            if (k < NQ) {
+                const int64_t node = node0 + k * NL;
+                const T U[3] = {q[M + node], q[2 * M + node], q[3 * M + node]};
+                T rinv, pp, Th;
+                if constexpr (MIXED) {
+                    const float th0 = geo.theta_ref[node];
+                    pp = pressure_perturbation_f32(q[4 * M + node], th0, P);
+                    rinv = __frcp_rn(geo.rho_ref[node] + q[node]);
+                    Th = th0 + q[4 * M + node];
+                } else {
+                    pp = pressure_perturbation(q[4 * M + node], geo.theta_ref[node], geo.w[node],
+                                               geo.A[node], P);
+                    rinv = __drcp_rn(q[node]);
+                    Th = q[4 * M + node];
+                    sP[k * NL + c] = pp;
+                }
+#pragma unroll
+                for (int d = 0; d < 3; ++d) {
+                    const T g[3] = {geo.g[3 * d][node], geo.g[3 * d + 1][node],
+                                    geo.g[3 * d + 2][node]};
+                    const T v = fma(g[2], U[2], fma(g[1], U[1], g[0] * U[0]));
+                    const T u = v * rinv;
+                    if constexpr (!MIXED) sU[d * N3 + k * NL + c] = u;
+                    const int sl = high_slot<NQ, T>(d, i, j, k);
+#pragma unroll
+                    for (int b = 0; b < G + LP; ++b) {
+                        if (b >= nf) break;
+                        T F;
+                        if (b == 0) F = v;
+                        else if (b < 4) F = fma(U[b - 1], u, g[b - 1] * pp);
+                        else if (b == 4) F = Th * u;
+                        else F = q[b * M + node] * u;
+                        if (b < G) sF[(b * 3 + d) * FB + sl] = F;
+                        else pk[(b - G) * 3 + d] = F;
+                    }
+                }
             }
-            sP[k * NL + c] = pp;
+            if constexpr (HOLD) {
 #pragma unroll
-            for (int d = 0; d < 3; ++d) {
-                const T g[3] = {geo.g[3 * d][node], geo.g[3 * d + 1][node], geo.g[3 * d + 2][node]};
-                const T v = fma(g[2], U[2], fma(g[1], U[1], g[0] * U[0]));
-                const T u = v * rinv;
-                sU[d * N3 + k * NL + c] = u;
-                const int sl = high_slot<NQ, T>(d, i, j, k);
+                for (int x = 0; x < 3 * LP; ++x) hold[(x / 3) * 3 * KS + 3 * kk + x % 3] = pk[x];
+            } else if constexpr (LP > 0) {   // every lane: the stores are warp-wide
 #pragma unroll
-                for (int b = 0; b < G; ++b) {
-                    if (b >= nf) break;
-                    T F;
-                    if (b == 0) F = v;
-                    else if (b < 4) F = fma(U[b - 1], u, g[b - 1] * pp);
-                    else if (b == 4) F = Th * u;
-                    else F = q[b * M + node] * u;
-                    sF[(b * 3 + d) * FB + sl] = F;
+                for (int f = 0; f < LP; ++f) {
+                    if (G + f >= nf) break;
+#pragma unroll
+                    for (int d = 0; d < 3; ++d)
+                        tc::tmem_st1(tpark + (f * KS + kk) * 3 + d, __float_as_uint(pk[f * 3 + d]));
                 }
             }
         }
+        if constexpr (HOLD) {
+#pragma unroll
+            for (int x = 0; x < 3 * LP * KS; ++x) {
+                if (G + x / (3 * KS) >= nf) break;
+                tc::tmem_st1(tpark + x, __float_as_uint(hold[x]));
+            }
+        }
+        if constexpr (LP > 0) tc::tmem_st_wait();
+    };
+    if constexpr (PC > 0) {
+        if (!park) pass0(std::integral_constant<int, 0>{});
+        else if (nf == G + 1) pass0(std::integral_constant<int, 1>{});
+        else if (nf == G + 2) pass0(std::integral_constant<int, PL < 2 ? PL : 2>{});
+        else pass0(std::integral_constant<int, PL>{});
+    } else {
+        pass0(std::integral_constant<int, 0>{});
     }
 
 #pragma unroll 1
@@ -177,29 +300,57 @@ vol_rhs_high_kernel(typename HighTypes<T>::Geo geo, typename HighTypes<T>::Param
         const int gn = nf - b0 < G ? nf - b0 : G;
         if (b0 > 0) {
             __syncthreads();   // the previous group's combination has read sF
+            if constexpr (MIXED) {
+                // the group's parked fluxes from TMEM into the flux arrays
+                if constexpr (PC > 0) {
 #pragma unroll(KU)
-            for (int kk = 0; kk < KS; ++kk) {
-                const int k = kb + kk;
-                if (k < NQ) {
-                    const int64_t node = node0 + k * NL;
+                    for (int kk = 0; kk < KS; ++kk) {
+                        const int k = kb + kk;
+                        uint32_t v[3 * G];
 #pragma unroll
-                    for (int gl = 0; gl < G; ++gl) {
-                        if (gl >= gn) break;
-                        const int b = b0 + gl;
-                        T qb = q[b * M + node];
-                        if (MIXED && b == 4) qb += geo.theta_ref[node];   // Theta = Theta_ref + Theta'
+                        for (int gl = 0; gl < G; ++gl) {
+                            if (gl >= gn) break;
 #pragma unroll
-                        for (int d = 0; d < 3; ++d) {
-                            const T u = sU[d * N3 + k * NL + c];
-                            T F = qb * u;
-                            if (b < 4) {
-                                // g_{b,d} by selection: a run-time index into the
-                                // parameter's pointer array would copy it to local memory
-                                const T *gp = b == 1 ? geo.g[3 * d]
-                                                     : (b == 2 ? geo.g[3 * d + 1] : geo.g[3 * d + 2]);
-                                F = fma(qb, u, gp[node] * sP[k * NL + c]);
+                            for (int d = 0; d < 3; ++d)
+                                v[gl * 3 + d] = tc::tmem_ld1(tpark + ((b0 - G + gl) * KS + kk) * 3 + d);
+                        }
+                        tc::tmem_ld_wait_all();
+                        if (k < NQ) {
+#pragma unroll
+                            for (int gl = 0; gl < G; ++gl) {
+                                if (gl >= gn) break;
+#pragma unroll
+                                for (int d = 0; d < 3; ++d)
+                                    sF[(gl * 3 + d) * FB + high_slot<NQ, T>(d, i, j, k)] =
+                                        __uint_as_float(tc::after_wait(v[gl * 3 + d]));
                             }
-                            sF[(gl * 3 + d) * FB + high_slot<NQ, T>(d, i, j, k)] = F;
+                        }
+                    }
+                }
+            } else {
+#pragma unroll(KU)
+                for (int kk = 0; kk < KS; ++kk) {
+                    const int k = kb + kk;
+                    if (k < NQ) {
+                        const int64_t node = node0 + k * NL;
+#pragma unroll
+                        for (int gl = 0; gl < G; ++gl) {
+                            if (gl >= gn) break;
+                            const int b = b0 + gl;
+                            const T qb = q[b * M + node];
+#pragma unroll
+                            for (int d = 0; d < 3; ++d) {
+                                const T u = sU[d * N3 + k * NL + c];
+                                T F = qb * u;
+                                if (b < 4) {
+                                    // g_{b,d} by selection: a run-time index into the
+                                    // parameter's pointer array would copy it to local memory
+                                    const T *gp = b == 1 ? geo.g[3 * d]
+                                                         : (b == 2 ? geo.g[3 * d + 1] : geo.g[3 * d + 2]);
+                                    F = fma(qb, u, gp[node] * sP[k * NL + c]);
+                                }
+                                sF[(gl * 3 + d) * FB + high_slot<NQ, T>(d, i, j, k)] = F;
+                            }
                         }
                     }
                 }
@@ -209,8 +360,10 @@ vol_rhs_high_kernel(typename HighTypes<T>::Geo geo, typename HighTypes<T>::Param
         // ---- sweeps: line c of direction `slab`, for each field of the group
         // (TPC = 3), or the group's 3 Nq^2 lines per field dealt out in turn
         if constexpr (TPC == 3) {
+            if (slab < 3) {
 #pragma unroll 1
-            for (int gl = 0; gl < gn; ++gl) sweep_line<NQ>(sF + (gl * 3 + slab) * FB, c, P);
+                for (int gl = 0; gl < gn; ++gl) sweep_line<NQ>(sF + (gl * 3 + slab) * FB, c, P);
+            }
         } else {
 #pragma unroll 1
             for (int item = t; item < gn * 3 * NL; item += NT)
@@ -240,6 +393,16 @@ vol_rhs_high_kernel(typename HighTypes<T>::Geo geo, typename HighTypes<T>::Param
                     }
                     rhs[b * M + node] = v;
                 }
+            }
+        }
+    }
+    if constexpr (PC > 0) {
+        if (park) {   // every TMEM load has completed (waited above)
+            tc::fence_before_sync();
+            __syncthreads();
+            if (t < 32) {
+                tc::fence_after_sync();
+                tc::tmem_dealloc(s_tmem, TC);
             }
         }
     }
