@@ -24,7 +24,7 @@ cudaError_t launch_vol_rhs_fp64_high(int N, int nf, ElemRange r, const DeviceGeo
 // Mixed precision for N = 8..15 (vol_fp64_high.cu, FP32 instantiation).
 cudaError_t launch_vol_rhs_mixed_high(int N, int nf, ElemRange r, const MixedGeometry &geo,
                                       const HighParams32 &P, const float *q, float *rhs,
-                                      cudaStream_t s);
+                                      int num_sms, cudaStream_t s);
 cudaError_t launch_vol_rhs_fp64(int N, int nf, ElemRange r, const DeviceGeometry &geo,
                                 const NativeParams &P, const double *q, double *rhs,
                                 cudaStream_t s);

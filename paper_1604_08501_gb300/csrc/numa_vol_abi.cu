@@ -435,7 +435,7 @@ cudaError_t launch(numa_vol *h, const void *q, void *rhs, int64_t e0, int64_t co
     if (h->kernel == numa::Kernel::MixedHigh)
         return numa::launch_vol_rhs_mixed_high(h->N, h->nf, r, h->mgeo, h->hmparams,
                                                static_cast<const float *>(q),
-                                               static_cast<float *>(rhs), s);
+                                               static_cast<float *>(rhs), h->num_sms, s);
     if (h->kernel == numa::Kernel::Mixed && h->tc_sweep)
         return numa::launch_vol_rhs_mixed_tc(r, h->mgeo, h->mparams, static_cast<const float *>(q),
                                              static_cast<float *>(rhs), h->num_sms, h->d_err, s);

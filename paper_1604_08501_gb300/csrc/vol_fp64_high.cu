@@ -21,8 +21,9 @@
 //    first group wait in tensor memory (tcgen05.st, one TMEM lane per thread)
 //    until their pass copies them into shared memory (tcgen05.ld), so no later
 //    pass reads the state or the metrics again, and without u_d and p' the
-//    first group is as large as shared memory allows: every field in one pass
-//    up to Nq = 12 (five fields), four of five at Nq = 16.
+//    groups are large (four of five fields at Nq = 12 and 16, all five up to
+//    Nq = 11); after its first pass each CTA prefetches the element of the next
+//    wave to L2.
 // Shared memory at Nq = 16: 224 KB in FP64 (every operation FP64; bound by the
 // FP64 pipe like the low orders), 204 KB in the mixed mode (FP32 perturbation
 // state and arithmetic as vol_mixed.cu).
@@ -30,6 +31,7 @@
 
 #include <type_traits>
 
+#include "bulk_copy.cuh"
 #include "element_sweep.cuh"
 #include "eos.cuh"
 #include "numa_internal.h"
@@ -81,71 +83,22 @@ __device__ __forceinline__ int high_slot(int d, int i, int j, int k) {
     }
 }
 
+// The FP32 instance comes in two forms per order, chosen at launch by the
+// handle's field count: NF = 5 (five fields) and NF = 8 (six to eight:
+// tracers).  FP64 has one form, NF = 8.
+//
 // Fields per pass.  FP64: one (the flux arrays of one field already take
-// 98 KB at Nq = 16).  FP32: as many as 100 KB of shared memory hold where two
-// CTAs of the thread count fit an SM (226 KB with one CTA per SM), but at
-// least as many as leave the other fields of an 8-field launch room in the
-// tensor memory of the CTAs of one SM (256 or 512 columns each).  Not the full
-// 113 KB of two CTAs: a group of all five fields at Nq = 12 (110 KB) measured
-// 24.1 GDOF/s against 27.5 for four (88 KB) with the fifth parked in tensor
-// memory, the larger shared-memory carveout leaving the L1 too little room for
-// the loads in flight.
-template <int NQ, typename T>
-__host__ __device__ constexpr int high_tmem_need(int g) {
-    const int ks = (NQ + high_tpc<NQ, T>() - 1) / high_tpc<NQ, T>();
-    const int need = (high_threads<NQ, T>() / 32 + 3) / 4 * ks * 3 * (kMaxFields - g);
-    int c = 32;
-    while (c < need) c *= 2;
-    return need <= 0 ? 0 : c;
-}
-
-template <int NQ, typename T>
-__host__ __device__ constexpr int high_group() {
-    if constexpr (sizeof(T) == 8) {
-        return 1;
-    } else {
-        constexpr bool two = 2 * high_threads<NQ, T>() <= 1024;
-        constexpr size_t per = sizeof(T) * 3 * NQ * NQ * line_stride<NQ, T>();   // one field's fluxes
-        constexpr size_t budget = (two ? 100 : 226) * 1024;
-        int g = (int)(budget / per);
-        g = g < 1 ? 1 : (g > kMaxFields ? kMaxFields : g);
-        while (g < kMaxFields && high_tmem_need<NQ, T>(g) > (two ? 256 : 512)) ++g;
-        return g;
-    }
-}
-
-template <int NQ, typename T>
-__host__ __device__ constexpr size_t high_smem_bytes() {
-    return sizeof(T) * ((sizeof(T) == 8 ? 4 * NQ * NQ * NQ : 0) +
-                        high_group<NQ, T>() * 3 * NQ * NQ * line_stride<NQ, T>());
-}
-
-// CTAs per SM the register budget is sized for: two where two CTAs' shared
-// memory fits an SM and still leaves 64 registers per thread, else one.
-template <int NQ, typename T>
-__host__ __device__ constexpr int high_min_ctas() {
-    return (2 * (high_smem_bytes<NQ, T>() + 1024) <= 228 * 1024 && 2 * high_threads<NQ, T>() <= 1024)
-               ? 2
-               : 1;
-}
-
-// Tensor memory of the FP32 instance: per warp, the fluxes of the fields
-// beyond the first group for its threads' points, 3 (kMaxFields - G) per
-// point (column (f KS + kk) 3 + d for parked field f, k-plane kk of the slab,
-// direction d); the warps of one lane quarter (warp % 4) side by side.  The
-// allocation (a power of two >= 32 columns) is sized for eight fields and
-// made only when the launch has fields beyond the first group.
-template <int NQ, typename T>
-__host__ __device__ constexpr int high_park_cols() {
-    constexpr int KS = (NQ + high_tpc<NQ, T>() - 1) / high_tpc<NQ, T>();
-    return sizeof(T) == 4 ? KS * 3 * (kMaxFields - high_group<NQ, T>()) : 0;
-}
-
-template <int NQ, typename T>
-__host__ __device__ constexpr int high_tmem_cols() {
-    return sizeof(T) == 4 ? high_tmem_need<NQ, T>(high_group<NQ, T>()) : 0;
-}
-
+// 98 KB at Nq = 16).  FP32: as many as a shared-memory budget holds, but at
+// least as many as leave the other NF - G fields room in the tensor memory of
+// the CTAs of one SM (256 columns each with two CTAs per SM, 512 with one).
+// The budget is 226 KB with one CTA per SM; with two, 113 KB (all of it) for
+// NF = 8 but 100 KB for NF = 5, whose parked fields must also fit the
+// registers of pass 0 (high_hold).  At Nq = 12, five fields: one 110 KB group
+// measured 27.9 GDOF/s against 31.7 for four fields (88 KB) with the fifth
+// parked, the larger shared-memory carveout leaving the L1 too little room
+// for the loads in flight; eight fields: 25.4 against 19.8 for groups of
+// four and four (the second group's four parked fields waiting on global
+// loads: long-scoreboard stalls 4.2 against 7.4 per issue).
 // Parked fluxes a thread may hold in registers over its k-planes before it
 // stores them (pass 0 below): one field's at Nq = 12, 13 and 16.  Two fields'
 // (24 values) at Nq = 16 with three fields per group measured slower (26.2
@@ -155,14 +108,77 @@ __host__ __device__ constexpr int high_hold() {
     return 16;
 }
 
+template <int NQ, typename T, int NF>
+__host__ __device__ constexpr int high_tmem_need(int g) {
+    const int ks = (NQ + high_tpc<NQ, T>() - 1) / high_tpc<NQ, T>();
+    const int need = (high_threads<NQ, T>() / 32 + 3) / 4 * ks * 3 * (NF - g);
+    int c = 32;
+    while (c < need) c *= 2;
+    return need <= 0 ? 0 : c;
+}
+
+template <int NQ, typename T, int NF>
+__host__ __device__ constexpr int high_group() {
+    if constexpr (sizeof(T) == 8) {
+        return 1;
+    } else {
+        constexpr bool two = 2 * high_threads<NQ, T>() <= 1024;
+        constexpr size_t per = sizeof(T) * 3 * NQ * NQ * line_stride<NQ, T>();   // one field's fluxes
+        constexpr size_t budget = (two ? (NF > kFields ? 113 : 100) : 226) * 1024;
+        int g = (int)(budget / per);
+        g = g < 1 ? 1 : (g > NF ? NF : g);
+        while (g < NF && high_tmem_need<NQ, T, NF>(g) > (two ? 256 : 512)) ++g;
+        if (NF == kFields) {   // no more parked fields than registers hold (pass 0)
+            const int ks = (NQ + high_tpc<NQ, T>() - 1) / high_tpc<NQ, T>();
+            const int lo = NF - high_hold<NQ, T>() / (3 * ks);
+            g = g < lo ? lo : g;
+        }
+        return g;
+    }
+}
+
+template <int NQ, typename T, int NF>
+__host__ __device__ constexpr size_t high_smem_bytes() {
+    return sizeof(T) * ((sizeof(T) == 8 ? 4 * NQ * NQ * NQ : 0) +
+                        high_group<NQ, T, NF>() * 3 * NQ * NQ * line_stride<NQ, T>());
+}
+
+// CTAs per SM the register budget is sized for: two where two CTAs' shared
+// memory fits an SM and still leaves 64 registers per thread, else one.
+template <int NQ, typename T, int NF>
+__host__ __device__ constexpr int high_min_ctas() {
+    return (2 * (high_smem_bytes<NQ, T, NF>() + 1024) <= 228 * 1024 &&
+            2 * high_threads<NQ, T>() <= 1024)
+               ? 2
+               : 1;
+}
+
+// Tensor memory of the FP32 instance: per warp, the fluxes of the fields
+// beyond the first group for its threads' points, 3 (NF - G) per point
+// (column (f KS + kk) 3 + d for parked field f, k-plane kk of the slab,
+// direction d); the warps of one lane quarter (warp % 4) side by side.  The
+// allocation (a power of two >= 32 columns) is sized for NF fields and made
+// only when the launch has fields beyond the first group.
+template <int NQ, typename T, int NF>
+__host__ __device__ constexpr int high_park_cols() {
+    constexpr int KS = (NQ + high_tpc<NQ, T>() - 1) / high_tpc<NQ, T>();
+    return sizeof(T) == 4 ? KS * 3 * (NF - high_group<NQ, T, NF>()) : 0;
+}
+
+template <int NQ, typename T, int NF>
+__host__ __device__ constexpr int high_tmem_cols() {
+    return sizeof(T) == 4 ? high_tmem_need<NQ, T, NF>(high_group<NQ, T, NF>()) : 0;
+}
+
 template <typename T> struct HighTypes;
 template <> struct HighTypes<double> { using Geo = DeviceGeometry; using Params = HighParams; };
 template <> struct HighTypes<float> { using Geo = MixedGeometry; using Params = HighParams32; };
 
-template <int NQ, typename T>
-__global__ void __launch_bounds__((high_threads<NQ, T>()), (high_min_ctas<NQ, T>()))
+template <int NQ, typename T, int NF>
+__global__ void __launch_bounds__((high_threads<NQ, T>()), (high_min_ctas<NQ, T, NF>()))
 vol_rhs_high_kernel(typename HighTypes<T>::Geo geo, typename HighTypes<T>::Params P,
-                    const T *__restrict__ q, T *__restrict__ rhs, int64_t M, int64_t e0, int nf) {
+                    const T *__restrict__ q, T *__restrict__ rhs, int64_t M, int64_t e0, int nf,
+                    int64_t e_end, int64_t ahead) {
     constexpr bool MIXED = sizeof(T) == 4;
     constexpr int NL = NQ * NQ;      // columns; lines per direction
     constexpr int N3 = NQ * NL;
@@ -170,11 +186,11 @@ vol_rhs_high_kernel(typename HighTypes<T>::Geo geo, typename HighTypes<T>::Param
     constexpr int TPC = high_tpc<NQ, T>();
     constexpr int NT = high_threads<NQ, T>();
     constexpr int KS = (NQ + TPC - 1) / TPC; // k-planes per slab
-    constexpr int G = high_group<NQ, T>();
-    constexpr int PC = high_park_cols<NQ, T>();     // TMEM columns per warp
-    constexpr int TC = high_tmem_cols<NQ, T>();
-    constexpr int PL = PC > 0 ? kMaxFields - G : 1;   // fields a point can park
-    static_assert(TC <= 512 / high_min_ctas<NQ, T>(), "tensor memory of the CTAs of one SM");
+    constexpr int G = high_group<NQ, T, NF>();
+    constexpr int PC = high_park_cols<NQ, T, NF>();     // TMEM columns per warp
+    constexpr int TC = high_tmem_cols<NQ, T, NF>();
+    constexpr int PL = PC > 0 ? NF - G : 1;   // fields a point can park
+    static_assert(TC <= 512 / high_min_ctas<NQ, T, NF>(), "tensor memory of the CTAs of one SM");
     // k-loop unrolling: full in FP32 (registers to spare, more loads in
     // flight), two planes in FP64 (register budget)
     constexpr int KU = MIXED ? KS : 2;
@@ -189,6 +205,29 @@ vol_rhs_high_kernel(typename HighTypes<T>::Geo geo, typename HighTypes<T>::Param
     const int i = c % NQ, j = c / NQ;
     const int kb = slab * KS;                          // first k-plane of the slab
     const int64_t node0 = (e0 + blockIdx.x) * N3 + c;  // point (i, j, 0); + k NL
+
+    // FP32: the arrays of the element `ahead` CTAs later (the next wave of
+    // resident CTAs) toward L2, where its first pass then finds them.  Only
+    // where an element's array is whole 16-byte units (even Nq).
+    auto prefetch_next = [&]() {
+        if constexpr (MIXED && (N3 * sizeof(T)) % 16 == 0) {
+            const int64_t ea = e0 + blockIdx.x + ahead;
+            if (t == 0 && ahead > 0 && ea < e_end) {
+                const int64_t off = ea * N3;
+                constexpr uint32_t B = N3 * sizeof(T);
+                for (int b = 0; b < nf; ++b) prefetch_l2(q + b * M + off, B);
+#pragma unroll
+                for (int a = 0; a < 9; ++a) prefetch_l2(geo.g[a] + off, B);
+                prefetch_l2(geo.Jinv + off, B);
+                prefetch_l2(geo.rho_ref + off, B);
+                prefetch_l2(geo.theta_ref + off, B);
+            }
+        }
+    };
+    // Issued after the first pass, when the CTA's own loads are done: at the
+    // start it competed with them (Nq = 16, one CTA per SM: 24.7 GDOF/s
+    // against 26.8 without a prefetch and 30.7 after the first pass; Nq = 12:
+    // 30.3 against 27.4 and 31.7).
 
     // FP32 with fields beyond the first group: their fluxes wait in TMEM
     const bool park = PC > 0 && nf > G;   // uniform over the CTA
@@ -357,6 +396,7 @@ vol_rhs_high_kernel(typename HighTypes<T>::Geo geo, typename HighTypes<T>::Param
             }
         }
         __syncthreads();
+        if (b0 == 0) prefetch_next();
         // ---- sweeps: line c of direction `slab`, for each field of the group
         // (TPC = 3), or the group's 3 Nq^2 lines per field dealt out in turn
         if constexpr (TPC == 3) {
@@ -408,32 +448,54 @@ vol_rhs_high_kernel(typename HighTypes<T>::Geo geo, typename HighTypes<T>::Param
     }
 }
 
-template <int NQ, typename T, typename Geo, typename Params>
-cudaError_t launch_high(ElemRange r, int nf, const Geo &geo, const Params &P, const T *q, T *rhs,
-                        cudaStream_t s) {
-    constexpr size_t smem = high_smem_bytes<NQ, T>();
-    cudaError_t e = cudaFuncSetAttribute(vol_rhs_high_kernel<NQ, T>,
+template <int NQ, typename T, int NF, typename Geo, typename Params>
+cudaError_t launch_high_form(ElemRange r, int nf, const Geo &geo, const Params &P, const T *q,
+                             T *rhs, int num_sms, cudaStream_t s) {
+    constexpr size_t smem = high_smem_bytes<NQ, T, NF>();
+    cudaError_t e = cudaFuncSetAttribute(vol_rhs_high_kernel<NQ, T, NF>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    vol_rhs_high_kernel<NQ, T><<<(unsigned)r.count, high_threads<NQ, T>(), smem, s>>>(geo, P, q, rhs,
-                                                                                r.M, r.e0, nf);
+    int64_t ahead = 0;   // FP64: no prefetch (bound by the FP64 pipe)
+    if (sizeof(T) == 4 && num_sms > 0) {
+        int per_sm = 0;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, vol_rhs_high_kernel<NQ, T, NF>,
+                                                          high_threads<NQ, T>(), smem);
+        if (e != cudaSuccess) return e;
+        ahead = (int64_t)num_sms * (per_sm > 0 ? per_sm : 1);
+    }
+    vol_rhs_high_kernel<NQ, T, NF><<<(unsigned)r.count, high_threads<NQ, T>(), smem, s>>>(
+        geo, P, q, rhs, r.M, r.e0, nf, r.e0 + r.count, ahead);
     return cudaGetLastError();
+}
+
+// FP32: the five-field form for five fields where its group differs from
+// the eight-field form's, else the eight-field form (at Nq = 16 both have
+// groups of four, and the five-field form measured 29.1 against 30.7 GDOF/s);
+// FP64: the one form.
+template <int NQ, typename T, typename Geo, typename Params>
+cudaError_t launch_high(ElemRange r, int nf, const Geo &geo, const Params &P, const T *q, T *rhs,
+                        int num_sms, cudaStream_t s) {
+    if constexpr (sizeof(T) == 4 && high_group<NQ, T, kFields>() != high_group<NQ, T, kMaxFields>()) {
+        if (nf == kFields)
+            return launch_high_form<NQ, T, kFields>(r, nf, geo, P, q, rhs, num_sms, s);
+    }
+    return launch_high_form<NQ, T, kMaxFields>(r, nf, geo, P, q, rhs, num_sms, s);
 }
 
 template <typename T, typename Geo, typename Params>
 cudaError_t launch_high_order(int N, int nf, ElemRange r, const Geo &geo, const Params &P,
-                              const T *q, T *rhs, cudaStream_t s) {
+                              const T *q, T *rhs, int num_sms, cudaStream_t s) {
     if (r.count <= 0) return cudaSuccess;
     if (nf < kFields || nf > kMaxFields) return cudaErrorInvalidValue;
     switch (N) {
-        case 8: return launch_high<9>(r, nf, geo, P, q, rhs, s);
-        case 9: return launch_high<10>(r, nf, geo, P, q, rhs, s);
-        case 10: return launch_high<11>(r, nf, geo, P, q, rhs, s);
-        case 11: return launch_high<12>(r, nf, geo, P, q, rhs, s);
-        case 12: return launch_high<13>(r, nf, geo, P, q, rhs, s);
-        case 13: return launch_high<14>(r, nf, geo, P, q, rhs, s);
-        case 14: return launch_high<15>(r, nf, geo, P, q, rhs, s);
-        case 15: return launch_high<16>(r, nf, geo, P, q, rhs, s);
+        case 8: return launch_high<9>(r, nf, geo, P, q, rhs, num_sms, s);
+        case 9: return launch_high<10>(r, nf, geo, P, q, rhs, num_sms, s);
+        case 10: return launch_high<11>(r, nf, geo, P, q, rhs, num_sms, s);
+        case 11: return launch_high<12>(r, nf, geo, P, q, rhs, num_sms, s);
+        case 12: return launch_high<13>(r, nf, geo, P, q, rhs, num_sms, s);
+        case 13: return launch_high<14>(r, nf, geo, P, q, rhs, num_sms, s);
+        case 14: return launch_high<15>(r, nf, geo, P, q, rhs, num_sms, s);
+        case 15: return launch_high<16>(r, nf, geo, P, q, rhs, num_sms, s);
         default: return cudaErrorInvalidValue;
     }
 }
@@ -443,13 +505,13 @@ cudaError_t launch_high_order(int N, int nf, ElemRange r, const Geo &geo, const 
 cudaError_t launch_vol_rhs_fp64_high(int N, int nf, ElemRange r, const DeviceGeometry &geo,
                                      const HighParams &P, const double *q, double *rhs,
                                      cudaStream_t s) {
-    return launch_high_order<double>(N, nf, r, geo, P, q, rhs, s);
+    return launch_high_order<double>(N, nf, r, geo, P, q, rhs, 0, s);
 }
 
 cudaError_t launch_vol_rhs_mixed_high(int N, int nf, ElemRange r, const MixedGeometry &geo,
                                       const HighParams32 &P, const float *q, float *rhs,
-                                      cudaStream_t s) {
-    return launch_high_order<float>(N, nf, r, geo, P, q, rhs, s);
+                                      int num_sms, cudaStream_t s) {
+    return launch_high_order<float>(N, nf, r, geo, P, q, rhs, num_sms, s);
 }
 
 }  // namespace numa
