@@ -175,7 +175,7 @@ int numa_vol_rhs(numa_vol *h, const void *q, void *rhs, void *stream);
 /*
  * Evaluate the volume term from HOST memory: copies q to the device, runs the
  * kernel, copies rhs back and waits for completion.  The mesh is processed in
- * up to 64 chunks of elements (FP64 states; 32 for FP32 states) on four
+ * up to 64 chunks of elements (NUMA_FP64; 16 for NUMA_DF64 and NUMA_MIXED) on four
  * internal streams, so the copy-in of one
  * chunk, the kernel on the previous one and the copy-out of the one before
  * overlap; each chunk moves with one 2D copy per direction over all planes.  Device staging buffers
