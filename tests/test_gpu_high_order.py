@@ -129,3 +129,23 @@ def test_mixed_high_order_across_the_eos_forms():
     ref = oracle.vol_rhs_o2(prob, q)
     for f in range(5):
         assert np.max(np.abs(out[f] - ref[f])) <= 1e-5 * np.max(np.abs(ref[f])), f
+
+
+@pytest.mark.parametrize("N,shape,T", [(11, (5, 2, 2), 3), (11, (20, 16, 16), 0),
+                                       (15, (16, 16, 10), 0)])
+def test_mixed_high_order_host_path_is_bitwise(N, shape, T):
+    # The host entry point launches the mesh in 16 chunks (first element > 0,
+    # each launch with its own end), which bounds the kernel's L2 prefetch of
+    # the element one wave of resident CTAs later (304 CTAs at Nq = 12, 152 at
+    # Nq = 16); its result equals the device entry point's bit for bit.  The
+    # two large meshes make every chunk longer than a wave (320 and 160
+    # elements), so the prefetch runs inside each chunk; the small one has
+    # tracers and chunks of one or two elements.
+    w = wl.make_workload(N, shape, seed=700 + N, tracers=T)
+    q32 = np.ascontiguousarray(w.q_mixed())
+    with VolumeTerm.from_problem(w.problem(), precision="mixed") as vt:
+        dev = vt.rhs(torch.from_numpy(q32).cuda()).cpu().numpy()
+        host = np.empty_like(q32)
+        vt.rhs_host(q32, host)
+    assert np.array_equal(host, dev)
+    assert np.all(np.isfinite(dev))
