@@ -15,13 +15,15 @@ namespace numa {
 // reference_eos: w = 1/Theta_ref, A = p(Theta_ref)/Theta_ref per point.
 cudaError_t launch_reference_eos(const double *theta_ref, double *w, double *A, int64_t M,
                                  EosConstants c, cudaStream_t s);
-// Native FP64 for N = 8..15 (vol_fp64_high.cu): one CTA of Nq^2 threads per
-// element, one pass per field.
+// Native FP64 for N = 8..15 (vol_fp64_high.cu): one CTA of 3 Nq^2 threads
+// per element, one pass per field.
 // nf: 5 fields, or 5 + tracers (nf <= 8).
 cudaError_t launch_vol_rhs_fp64_high(int N, int nf, ElemRange r, const DeviceGeometry &geo,
                                      const HighParams &P, const double *q, double *rhs,
                                      cudaStream_t s);
-// Mixed precision for N = 8..15 (vol_fp64_high.cu, FP32 instantiation).
+// Mixed precision for N = 8..15 (vol_fp64_high.cu, FP32 instantiation: a
+// five-field and an eight-field form, chosen by nf; num_sms sets the
+// distance of its L2 prefetch, one wave of resident CTAs).
 cudaError_t launch_vol_rhs_mixed_high(int N, int nf, ElemRange r, const MixedGeometry &geo,
                                       const HighParams32 &P, const float *q, float *rhs,
                                       int num_sms, cudaStream_t s);
