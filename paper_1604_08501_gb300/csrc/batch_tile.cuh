@@ -165,7 +165,13 @@ __device__ void run_tile(const BatchInstance &I, int64_t e0, int64_t count,
         for (int step = 0; step < nsteps; ++step) {
 #pragma unroll 1
             for (int st = 0; st < 5; ++st) {
-                __syncthreads();   // previous phase-3 reads of sF are done
+                // Phase 3 reads and phase 1 writes only the thread's own
+                // point's flux slots (and its own state words), so within a
+                // pass the next stage's phase 1 needs no barrier after phase 3.
+                // The first stage of a pass takes one: the previous pass or
+                // work item (possibly another order) gave its slots to other
+                // threads.
+                if (step == 0 && st == 0) __syncthreads();
                 // ---- phase 1: p', fluxes ------------------------------
                 if (active) {
                     T q[kFields];
@@ -217,6 +223,15 @@ __device__ void run_tile(const BatchInstance &I, int64_t e0, int64_t count,
                             sweep_line<NQ>(sF + bd * BLK + e * EW, line, c_sweep64[NQ]);
                     }
                 }
+                // FP64: J^-1 and rho_ref loaded before the barrier, so that
+                // their latency passes while the last sweeps finish
+                T jinv_g = T(0), rho_ref_g = T(0);
+                if constexpr (!MIXED) {
+                    if (active) {
+                        jinv_g = __ldg(I.geo.Jinv + node);
+                        rho_ref_g = __ldg(I.geo.rho_ref + node);
+                    }
+                }
                 __syncthreads();
                 // ---- phase 3: rhs, stage update ------------------------
                 if (active) {
@@ -226,8 +241,8 @@ __device__ void run_tile(const BatchInstance &I, int64_t e0, int64_t count,
                         jinv = sG[9 * kThreads];
                         drho = Q(0);
                     } else {
-                        jinv = __ldg(I.geo.Jinv + node);
-                        drho = Q(0) - __ldg(I.geo.rho_ref + node);
+                        jinv = jinv_g;
+                        drho = Q(0) - rho_ref_g;
                     }
 #pragma unroll
                     for (int b = 0; b < kFields; ++b) {

@@ -520,7 +520,12 @@ __device__ void run_tile_cc_tm(const BatchInstance &I, int64_t e0, int64_t count
         for (int step = 0; step < nsteps; ++step) {
 #pragma unroll 1
             for (int st = 0; st < 5; ++st) {
-                __syncthreads();   // previous phase-3 reads of sF are done
+                // Phase 3 reads and phase 1 writes only the thread's own
+                // point's flux slots, so within a pass the next stage's phase 1
+                // needs no barrier after phase 3.  The first stage of a pass
+                // takes one: the previous pass or work item (possibly another
+                // order) gave its slots to other threads.
+                if (step == 0 && st == 0) __syncthreads();
                 if (active) {
                     const float th0 = aux[0], rho0 = aux[kThreads];
                     const EosRef32 er{aux[2 * kThreads], aux[3 * kThreads]};
