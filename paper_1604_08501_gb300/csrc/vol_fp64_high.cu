@@ -338,7 +338,9 @@ vol_rhs_high_kernel(typename HighTypes<T>::Geo geo, typename HighTypes<T>::Param
     for (int b0 = 0; b0 < nf; b0 += G) {   // groups of G fields: 5 fields, then the tracers
         const int gn = nf - b0 < G ? nf - b0 : G;
         if (b0 > 0) {
-            __syncthreads();   // the previous group's combination has read sF
+            // No barrier after the previous group's combination: it read, and
+            // this group's fluxes are written to, only the thread's own
+            // points' slots (a bijection per direction).
             if constexpr (MIXED) {
                 // the group's parked fluxes from TMEM into the flux arrays
                 if constexpr (PC > 0) {
