@@ -340,7 +340,11 @@ __device__ bool run_tile_tc(const BatchInstance &I, int64_t e0, int64_t count, c
         for (int step = 0; step < nsteps; ++step) {
 #pragma unroll 1
             for (int st = 0; st < 5; ++st) {
-                __syncthreads();   // previous phase-3 reads of A are done
+                // Phase 3 reads and phase 1 writes only the thread's own
+                // point's slots of A (the stage's MMAs completed before the
+                // readback); the first stage of a pass takes a barrier, since
+                // the previous pass or work item gave its slots to other threads.
+                if (step == 0 && st == 0) __syncthreads();
                 // ---- phase 1: p', fluxes, heads and tails into A -------
                 if (active) {
                     const float th0 = aux[0], rho0 = aux[kThreads];

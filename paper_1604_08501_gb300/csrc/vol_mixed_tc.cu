@@ -75,7 +75,9 @@ vol_rhs_mixed_tc_kernel(MixedGeometry geo, MixedParams P, const float *__restric
             prefetch_l2(geo.rho_ref + nx, 2048);
             prefetch_l2(geo.theta_ref + nx, 2048);
         }
-        __syncthreads();   // the previous element's phase-3 reads of A are done
+        // No barrier after the previous element's phase 3: it read, and this
+        // phase 1 writes, only the thread's own point's slots of A (the
+        // element's MMAs had completed before its readback).
         // ---- phase 1: p', fluxes, heads and tails into A -----------------
         const float rp = q[node];
         const float jinv = geo.Jinv[node];
