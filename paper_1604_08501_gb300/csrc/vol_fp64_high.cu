@@ -21,9 +21,9 @@
 //    first group wait in tensor memory (tcgen05.st, one TMEM lane per thread)
 //    until their pass copies them into shared memory (tcgen05.ld), so no later
 //    pass reads the state or the metrics again, and without u_d and p' the
-//    groups are large (four of five fields at Nq = 12 and 16, all five up to
-//    Nq = 11); after its first pass each CTA prefetches the element of the next
-//    wave to L2.
+//    groups are large (five fields: four per group at Nq = 12, 13 and 16, one
+//    pass at the other orders; a separate form for tracers); after its first
+//    pass each CTA prefetches the element of the next wave to L2.
 // Shared memory at Nq = 16: 224 KB in FP64 (every operation FP64; bound by the
 // FP64 pipe like the low orders), 204 KB in the mixed mode (FP32 perturbation
 // state and arithmetic as vol_mixed.cu).
