@@ -201,11 +201,12 @@ __device__ __forceinline__ void prefetch_element(const DfGeometry &geo, const do
     }
 }
 
-// ahead: the CTAs resident on the GPU at once.  The element that many launch
-// slots later is likely the next to start on this SM, so its arrays are
-// prefetched to L2 now and its loads then hit L2 rather than DRAM (one wave
-// ahead: 1.30 -> 1.22 ms at N = 7, 32768 elements; two waves ahead was
-// slower than none, the prefetched data displacing the running wave's).
+// ahead: half the CTAs resident on the GPU at once.  The element that many
+// launch slots later starts soon on some SM, so its arrays are prefetched to
+// L2 now and its loads then hit L2 rather than DRAM (one wave ahead: 1.30 ->
+// 1.22 ms at N = 7, 32768 elements; half a wave 14.06 against 13.91 GDOF/s
+// for one wave and 13.98 for a quarter; two waves ahead was slower than
+// none, the prefetched data displacing the running wave's).
 template <int NQ>
 __global__ void __launch_bounds__(NQ * NQ * NQ, df_min_ctas<NQ>())
 vol_rhs_df64_kernel(DfGeometry geo, DfParams P, const double *__restrict__ q,
@@ -413,7 +414,8 @@ cudaError_t launch_df(ElemRange r, const DfGeometry &geo, const DfParams &P, con
     int per_sm = 0;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, vol_rhs_df64_kernel<NQ>, N3, smem);
     if (e != cudaSuccess) return e;
-    const int64_t ahead = (int64_t)num_sms * (per_sm > 0 ? per_sm : 1);
+    const int64_t wave = (int64_t)num_sms * (per_sm > 0 ? per_sm : 1);
+    const int64_t ahead = wave / 2 > 0 ? wave / 2 : 1;
     vol_rhs_df64_kernel<NQ><<<(unsigned)r.count, N3, smem, s>>>(geo, P, q, rhs, r.M, r.e0,
                                                                 r.e0 + r.count, ahead);
     return cudaGetLastError();

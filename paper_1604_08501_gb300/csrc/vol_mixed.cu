@@ -21,8 +21,12 @@
 // sweeps by line in place, combination by point; one CTA of Nq^3 threads per
 // element, four CTAs of 512 threads per SM at Nq = 8 (32 registers, 35 KB of
 // shared memory each).  Thread 0 of each CTA prefetches to L2
-// (cp.async.bulk.prefetch.L2) the arrays of the element one wave of resident
-// CTAs ahead, so that CTA's loads hit L2 rather than DRAM.  At N = 7 this
+// (cp.async.bulk.prefetch.L2) the arrays of the element a quarter of a wave of
+// resident CTAs ahead (one CTA per SM at Nq = 8), so that CTA's loads hit L2
+// rather than DRAM.  Measured at N = 7 (GDOF/s): no prefetch 72.8, 1/8 of a
+// wave 74.2, 1/4 74.7, 3/8 74.7, 1/2 74.2, 3/4 72.4, one wave 69.7, 3/2 55.0,
+// two 48.3: a longer distance lets L2 evict the lines before their CTA
+// starts.  At N = 7 the prefetch
 // replaced a persistent kernel that staged each element's arrays in shared
 // memory with cp.async.bulk on an mbarrier: the staging buffer limited that
 // kernel to three CTAs per SM, and it ran at 0.271 against 0.254 ms here
@@ -148,7 +152,8 @@ cudaError_t launch_kernel(ElemRange r, int nf, const MixedGeometry &geo, const M
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, vol_rhs_mixed_kernel<NQ, TRACERS>,
                                                       N3, smem);
     if (e != cudaSuccess) return e;
-    const int64_t ahead = (int64_t)num_sms * (per_sm > 0 ? per_sm : 1);
+    const int64_t wave = (int64_t)num_sms * (per_sm > 0 ? per_sm : 1);
+    const int64_t ahead = wave / 4 > 0 ? wave / 4 : 1;   // a quarter of a wave
     vol_rhs_mixed_kernel<NQ, TRACERS><<<(unsigned)r.count, N3, smem, s>>>(
         geo, P, q, rhs, r.M, r.e0, nf, r.e0 + r.count, ahead);
     return cudaGetLastError();
