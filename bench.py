@@ -674,7 +674,8 @@ def run_batched(args):
                 "value": out[head]["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": out[head]["ms_per_launch"],
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-                "dtype": {"fp64": "f64", "mixed": "f32 (perturbation state)",
+                "dtype": {"fp64": "f64", "df64": "df64 (FP32 hi+lo pairs, 48-bit)",
+                          "mixed": "f32 (perturbation state)",
                           "mixed-tc": "f32 (perturbation state), TF32 split products",
                           "mixed-auto": "f32 (perturbation state)",
                           "mixed-tmem": "f32 (perturbation state)",
@@ -698,8 +699,8 @@ NQ_STUDY = {3: (48, 48, 24), 7: (24, 24, 12), 11: (16, 16, 8), 15: (12, 12, 6)}
 def run_nq_sweep(args):
     """One evaluation per step of the 3,538,944-point mesh at each order of the
     paper's Nq study, NUMA_FP64, NUMA_DF64 (N <= 7) and NUMA_MIXED, with five fields and with three
-    passive tracers (*_8fields: the paper's 8-field form; mixed_8fields is also
-    its FP32 precision).  Inputs exceed L2 (0.68 GB FP64).  Metric: GDOF/s per
+    passive tracers (*_8fields: the paper's 8-field form, df64_8fields with
+    df64 among the precisions; mixed_8fields is also its FP32 precision).  Inputs exceed L2 (0.68 GB FP64).  Metric: GDOF/s per
     order; `value` is Nq = 8."""
     import torch
     rank, local, world = dist_setup("nccl")
@@ -719,8 +720,10 @@ def run_nq_sweep(args):
         w = wl.make_workload(N, shape, seed=1, tracers=3)
         w5 = dataclasses.replace(w, q=w.q[:5])
         row = {"elements": w.Ne, "points": w.M}
-        for prec in list(args.precisions) + ["fp64_8fields", "mixed_8fields"]:
-            if prec == "df64" and N > 7:
+        extra = ["fp64_8fields", "mixed_8fields"] + (
+            ["df64_8fields"] if "df64" in args.precisions else [])
+        for prec in list(args.precisions) + extra:
+            if prec.startswith("df64") and N > 7:
                 continue   # the double-float mode takes N <= 7
             # *_8fields: the paper's 8-field form (three passive tracers);
             # mixed_8fields is also the paper's precision (FP32)

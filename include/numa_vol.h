@@ -70,8 +70,9 @@ typedef struct {
 } numa_constants;
 
 /* Mesh size: num_elements hexahedra of order N (Nq = N + 1 points per axis),
- * and num_tracers passive tracers (0 .. NUMA_MAX_TRACERS; NUMA_FP64 and
- * NUMA_MIXED, where tracers are FP32 values as they are): the
+ * and num_tracers passive tracers (0 .. NUMA_MAX_TRACERS; every precision,
+ * tracers FP64 in NUMA_FP64 and NUMA_DF64, FP32 values as they are in
+ * NUMA_MIXED; not in the batch or the engine): the
  * state and rhs then hold 5 + num_tracers planes, the tracers Q1.. after
  * Theta, each advected like Theta (flux Q u_d, no source; the paper's 8-field
  * form, Sec. 2).  Zero-initialise the struct so that num_tracers defaults to 0. */
@@ -121,10 +122,10 @@ typedef struct numa_vol numa_vol;
  * geo non-null;
  * c->cp > c->R > 0 and c->p0 > 0.  On success *out receives the handle
  * (release with numa_vol_destroy).  Errors: NUMA_EINVAL, NUMA_ENOMEM,
- * NUMA_ECUDA, NUMA_EUNSUPPORTED (NUMA_DF64 with N > 7 or with tracers).
- * Handles of N > 7 evaluate one element per CTA of 3 (N+1)^2 threads, one
- * pass per field (vol_rhs_high_kernel); the batch and the engine take handles
- * of N <= 7 without tracers only.
+ * NUMA_ECUDA, NUMA_EUNSUPPORTED (NUMA_DF64 with N > 7).
+ * Handles of N > 7 evaluate one element per CTA of 3 or 4 (N+1)^2 threads,
+ * the fields in groups (vol_rhs_high_kernel); the batch and the engine take
+ * handles of N <= 7 without tracers only.
  *
  * NUMA_MIXED takes the state as FP32 perturbations from the reference state:
  * plane 0 holds rho - rho_ref, plane 4 holds Theta - Theta_ref, planes 1-3

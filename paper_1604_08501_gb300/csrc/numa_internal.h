@@ -39,8 +39,10 @@ cudaError_t launch_abs_max(const double *src, int64_t M, unsigned long long *ama
                            cudaStream_t s);
 cudaError_t launch_to_df(const double *src, float2 *dst, int64_t M, double thresh, int *bad,
                          cudaStream_t s);
-cudaError_t launch_vol_rhs_df64(int N, ElemRange r, const DfGeometry &geo, const DfParams &P,
-                                const double *q, double *rhs, int num_sms, cudaStream_t s);
+// nf: 5 fields, or 5 + tracers (nf <= 8).
+cudaError_t launch_vol_rhs_df64(int N, int nf, ElemRange r, const DfGeometry &geo,
+                                const DfParams &P, const double *q, double *rhs, int num_sms,
+                                cudaStream_t s);
 
 // Launchers of the mixed-precision path (vol_mixed.cu).
 cudaError_t launch_to_f32(const double *src, float *dst, int64_t M, cudaStream_t s);

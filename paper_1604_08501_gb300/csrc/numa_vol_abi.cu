@@ -362,8 +362,6 @@ int numa_vol_create(const numa_mesh *mesh, const numa_geometry *geo, const numa_
         return fail(NUMA_EUNSUPPORTED, "numa_vol_create: NUMA_DF64 is implemented for N = 1..7");
     if (mesh->num_tracers < 0 || mesh->num_tracers > NUMA_MAX_TRACERS)
         return fail(NUMA_EINVAL, "numa_vol_create: num_tracers must be in [0, 3]");
-    if (mesh->num_tracers > 0 && prec == NUMA_DF64)
-        return fail(NUMA_EUNSUPPORTED, "numa_vol_create: NUMA_DF64 takes no tracers");
     if (mesh->num_elements < 0)
         return fail(NUMA_EINVAL, "numa_vol_create: num_elements must be >= 0");
     if (mesh->num_elements > (int64_t)INT32_MAX)
@@ -444,7 +442,8 @@ cudaError_t launch(numa_vol *h, const void *q, void *rhs, int64_t e0, int64_t co
                                           static_cast<const float *>(q), static_cast<float *>(rhs),
                                           h->num_sms, s);
     if (h->kernel == numa::Kernel::DoubleFloat)
-        return numa::launch_vol_rhs_df64(h->N, r, h->dgeo, h->dparams, static_cast<const double *>(q),
+        return numa::launch_vol_rhs_df64(h->N, h->nf, r, h->dgeo, h->dparams,
+                                         static_cast<const double *>(q),
                                          static_cast<double *>(rhs), h->num_sms, s);
     if (h->kernel == numa::Kernel::NativeHigh)
         return numa::launch_vol_rhs_fp64_high(h->N, h->nf, r, h->geo, h->hparams,

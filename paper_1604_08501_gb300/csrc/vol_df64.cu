@@ -133,10 +133,11 @@ __device__ __noinline__ double eos_pressure_fp64(double Th, const DfParams &P) {
 }
 
 // Native FP64 evaluation of one element from df-stored geometry (rare path).
-template <int NQ>
+template <int NQ, bool TR>
 __device__ void element_fp64(const DfGeometry &geo, const DfParams &P, const double *__restrict__ q,
-                             double *__restrict__ rhs, int64_t M, int64_t e, double *sF) {
+                             double *__restrict__ rhs, int64_t M, int64_t e, int nf, double *sF) {
     constexpr int N3 = DfShape<NQ>::N3;
+    const int NF = TR ? nf : kFields;   // flux blocks per direction
     const int l = threadIdx.x;
     const int64_t node = e * N3 + l;
     __syncthreads();  // sF aliases the df buffers of the caller
@@ -150,22 +151,25 @@ __device__ void element_fp64(const DfGeometry &geo, const DfParams &P, const dou
         const double g2 = df_to_double(ld_df(geo.g[3 * d + 1], node));
         const double g3 = df_to_double(ld_df(geo.g[3 * d + 2], node));
         const double u = (g1 * U1 + g2 * U2 + g3 * U3) / rho;
-        double *F = sF + d * kFields * N3 + l;
+        double *F = sF + d * NF * N3 + l;
         F[0 * N3] = rho * u;
         F[1 * N3] = U1 * u + g1 * pp;
         F[2 * N3] = U2 * u + g2 * pp;
         F[3 * N3] = U3 * u + g3 * pp;
         F[4 * N3] = Th * u;
+        if constexpr (TR) {
+            for (int b = kFields; b < nf; ++b) F[b * N3] = q[b * M + node] * u;   // tracers Q u_d
+        }
     }
     __syncthreads();
     const int i = l % NQ, j = (l / NQ) % NQ, k = l / (NQ * NQ);
     const double Jinv = df_to_double(ld_df(geo.Jinv, node));
     const double drho = rho - geo.rho_ref[node];
-#pragma unroll
-    for (int b = 0; b < kFields; ++b) {
-        const double *Fr = sF + (0 * kFields + b) * N3;
-        const double *Fs = sF + (1 * kFields + b) * N3;
-        const double *Ft = sF + (2 * kFields + b) * N3;
+#pragma unroll 1
+    for (int b = 0; b < NF; ++b) {
+        const double *Fr = sF + (0 * NF + b) * N3;
+        const double *Fs = sF + (1 * NF + b) * N3;
+        const double *Ft = sF + (2 * NF + b) * N3;
         double s = 0.0;
 #pragma unroll
         for (int n = 0; n < NQ; ++n) s += P.D[i * NQ + n] * Fr[(k * NQ + j) * NQ + n];
@@ -184,13 +188,12 @@ __device__ void element_fp64(const DfGeometry &geo, const DfParams &P, const dou
 // (the bulk prefetch's rule; even Nq).
 template <int NQ>
 __device__ __forceinline__ void prefetch_element(const DfGeometry &geo, const double *q,
-                                                 int64_t M, int64_t e) {
+                                                 int64_t M, int nf, int64_t e) {
     constexpr int N3 = DfShape<NQ>::N3;
     constexpr uint32_t B = N3 * 8;
     if constexpr (B % 16 == 0) {
         const int64_t off = e * N3;
-#pragma unroll
-        for (int b = 0; b < kFields; ++b) prefetch_l2(q + b * M + off, B);
+        for (int b = 0; b < nf; ++b) prefetch_l2(q + b * M + off, B);
 #pragma unroll
         for (int a = 0; a < 9; ++a) prefetch_l2(geo.g[a] + off, B);
         prefetch_l2(geo.Jinv + off, B);
@@ -207,22 +210,26 @@ __device__ __forceinline__ void prefetch_element(const DfGeometry &geo, const do
 // 1.22 ms at N = 7, 32768 elements; half a wave 14.06 against 13.91 GDOF/s
 // for one wave and 13.98 for a quarter; two waves ahead was slower than
 // none, the prefetched data displacing the running wave's).
-template <int NQ>
+// TR: the 8-field form (nf = 5 + tracers, 6..8): the tracers' state is split
+// like the other fields and their fluxes are Q u_d; nf blocks per direction.
+template <int NQ, bool TR>
 __global__ void __launch_bounds__(NQ * NQ * NQ, df_min_ctas<NQ>())
 vol_rhs_df64_kernel(DfGeometry geo, DfParams P, const double *__restrict__ q,
                     double *__restrict__ rhs, int64_t M, int64_t e0, int64_t e_end,
-                    int64_t ahead) {
+                    int64_t ahead, int nf) {
     constexpr int N3 = DfShape<NQ>::N3;
     constexpr int NL = DfShape<NQ>::NL;
     constexpr int HALF = NQ / 2;
     constexpr bool ODD = (NQ & 1) != 0;
     constexpr int C = NQ / 2;
-    extern __shared__ float2 sbuf[];  // [direction*5 + field][slot], 15 * Nq^3 float2
+    constexpr int NT = kMaxFields - kFields;   // tracers at most
+    const int NF = TR ? nf : kFields;          // flux blocks per direction
+    extern __shared__ float2 sbuf[];  // [direction*NF + field][slot], 3 NF Nq^3 float2
     const int l = threadIdx.x;
     const int i = l % NQ, j = (l / NQ) % NQ, k = l / (NQ * NQ);
     const int64_t e = e0 + blockIdx.x;
     const int64_t node = e * N3 + l;
-    if (l == 0 && e + ahead < e_end) prefetch_element<NQ>(geo, q, M, e + ahead);
+    if (l == 0 && e + ahead < e_end) prefetch_element<NQ>(geo, q, M, NF, e + ahead);
 
     // ---- phase 1: state, p', fluxes -----------------------------------
     bool big = false, tiny = false;
@@ -232,6 +239,13 @@ vol_rhs_df64_kernel(DfGeometry geo, DfParams P, const double *__restrict__ q,
     for (int b = 0; b < kFields; ++b) qd[b] = q[b * M + node];
 #pragma unroll
     for (int b = 0; b < kFields; ++b) Q[b] = df_split(qd[b], big, tiny);
+    df QT[TR ? NT : 1];   // the tracers
+    if constexpr (TR) {
+#pragma unroll
+        for (int t = 0; t < NT; ++t)
+            QT[t] = kFields + t < nf ? df_split(q[(kFields + t) * M + node], big, tiny)
+                                     : df{0.0f, 0.0f};
+    }
     // Exact FP64 differences (Sterbenz: the operands are within a factor 2 in
     // the fast path) before splitting, so the perturbations keep full accuracy.
     const double th0 = geo.theta_ref[node];
@@ -241,7 +255,7 @@ vol_rhs_df64_kernel(DfGeometry geo, DfParams P, const double *__restrict__ q,
     const df drho = df_split(drho_d, big, tiny);
     const bool bad = big || !(qd[0] > 0.0);
     if (__syncthreads_or(bad)) {
-        element_fp64<NQ>(geo, P, q, rhs, M, e, reinterpret_cast<double *>(sbuf));
+        element_fp64<NQ, TR>(geo, P, q, rhs, M, e, nf, reinterpret_cast<double *>(sbuf));
         return;
     }
 
@@ -286,12 +300,20 @@ vol_rhs_df64_kernel(DfGeometry geo, DfParams P, const double *__restrict__ q,
         F[4] = df_mul(Q[4], u);
         const int s = dir_slot<NQ>(d, i, j, k);
 #pragma unroll
-        for (int b = 0; b < kFields; ++b) sbuf[(d * kFields + b) * N3 + s] = make_float2(F[b].h, F[b].l);
+        for (int b = 0; b < kFields; ++b) sbuf[(d * NF + b) * N3 + s] = make_float2(F[b].h, F[b].l);
+        if constexpr (TR) {
+#pragma unroll
+            for (int t = 0; t < NT; ++t) {
+                if (kFields + t >= nf) break;
+                const df Ft = df_mul(QT[t], u);
+                sbuf[(d * NF + kFields + t) * N3 + s] = make_float2(Ft.h, Ft.l);
+            }
+        }
     }
     __syncthreads();
 
     // ---- phase 2: even-odd D sweeps, one line per task -----------------
-    for (int item = l; item < DfShape<NQ>::kItems; item += N3) {
+    for (int item = l; item < (TR ? 3 * NF * NL : DfShape<NQ>::kItems); item += N3) {
         float2 *buf = sbuf + (item / NL) * N3;
         const int line = item % NL;
         df F[NQ];
@@ -335,21 +357,28 @@ vol_rhs_df64_kernel(DfGeometry geo, DfParams P, const double *__restrict__ q,
     // ---- phase 3: combine, scale, gravity, store -----------------------
     double out[kFields];
     bool finite = true;
-#pragma unroll
-    for (int b = 0; b < kFields; ++b) {
-        const float2 r = sbuf[(0 * kFields + b) * N3 + dir_slot<NQ>(0, i, j, k)];
-        const float2 s = sbuf[(1 * kFields + b) * N3 + dir_slot<NQ>(1, i, j, k)];
-        const float2 t = sbuf[(2 * kFields + b) * N3 + dir_slot<NQ>(2, i, j, k)];
+    auto field = [&](int b) -> double {
+        const float2 r = sbuf[(0 * NF + b) * N3 + dir_slot<NQ>(0, i, j, k)];
+        const float2 s = sbuf[(1 * NF + b) * N3 + dir_slot<NQ>(1, i, j, k)];
+        const float2 t = sbuf[(2 * NF + b) * N3 + dir_slot<NQ>(2, i, j, k)];
         df R = df_add(df_add(df{r.x, r.y}, df{s.x, s.y}), df{t.x, t.y});
         df v = df_mul(df_norm(R), jinv);
         if (b == 3) v = df_add(v, df_mul(drho, P.grav_df));
         v = df_norm(v);
         finite = finite && isfinite(v.h) && isfinite(v.l);
-        out[b] = -df_to_double(v);
+        return -df_to_double(v);
+    };
+#pragma unroll
+    for (int b = 0; b < kFields; ++b) out[b] = field(b);
+    if constexpr (TR) {
+        // the tracers stored at once (the FP64 evaluation below rewrites
+        // every field of an element that overflowed)
+#pragma unroll 1
+        for (int b = kFields; b < nf; ++b) rhs[b * M + node] = field(b);
     }
     // An overflow anywhere in the element (float range) sends it to FP64.
     if (__syncthreads_or(!finite)) {
-        element_fp64<NQ>(geo, P, q, rhs, M, e, reinterpret_cast<double *>(sbuf));
+        element_fp64<NQ, TR>(geo, P, q, rhs, M, e, nf, reinterpret_cast<double *>(sbuf));
         return;
     }
 #pragma unroll
@@ -403,37 +432,46 @@ cudaError_t launch_to_df(const double *src, float2 *dst, int64_t M, double thres
 
 namespace {
 
-template <int NQ>
-cudaError_t launch_df(ElemRange r, const DfGeometry &geo, const DfParams &P, const double *q,
-                      double *rhs, int num_sms, cudaStream_t s) {
+template <int NQ, bool TR>
+cudaError_t launch_df_form(ElemRange r, int nf, const DfGeometry &geo, const DfParams &P,
+                           const double *q, double *rhs, int num_sms, cudaStream_t s) {
     constexpr int N3 = NQ * NQ * NQ;
-    const size_t smem = sizeof(float2) * kFields * 3 * N3;
-    cudaError_t e = cudaFuncSetAttribute(vol_rhs_df64_kernel<NQ>,
+    const size_t smem = sizeof(float2) * (TR ? nf : kFields) * 3 * N3;
+    cudaError_t e = cudaFuncSetAttribute(vol_rhs_df64_kernel<NQ, TR>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, vol_rhs_df64_kernel<NQ>, N3, smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, vol_rhs_df64_kernel<NQ, TR>, N3, smem);
     if (e != cudaSuccess) return e;
     const int64_t wave = (int64_t)num_sms * (per_sm > 0 ? per_sm : 1);
     const int64_t ahead = wave / 2 > 0 ? wave / 2 : 1;
-    vol_rhs_df64_kernel<NQ><<<(unsigned)r.count, N3, smem, s>>>(geo, P, q, rhs, r.M, r.e0,
-                                                                r.e0 + r.count, ahead);
+    vol_rhs_df64_kernel<NQ, TR><<<(unsigned)r.count, N3, smem, s>>>(geo, P, q, rhs, r.M, r.e0,
+                                                                    r.e0 + r.count, ahead, nf);
     return cudaGetLastError();
+}
+
+template <int NQ>
+cudaError_t launch_df(ElemRange r, int nf, const DfGeometry &geo, const DfParams &P,
+                      const double *q, double *rhs, int num_sms, cudaStream_t s) {
+    if (nf > kFields) return launch_df_form<NQ, true>(r, nf, geo, P, q, rhs, num_sms, s);
+    return launch_df_form<NQ, false>(r, nf, geo, P, q, rhs, num_sms, s);
 }
 
 }  // namespace
 
-cudaError_t launch_vol_rhs_df64(int N, ElemRange r, const DfGeometry &geo, const DfParams &P,
-                                const double *q, double *rhs, int num_sms, cudaStream_t s) {
+cudaError_t launch_vol_rhs_df64(int N, int nf, ElemRange r, const DfGeometry &geo,
+                                const DfParams &P, const double *q, double *rhs, int num_sms,
+                                cudaStream_t s) {
     if (r.count <= 0) return cudaSuccess;
+    if (nf < kFields || nf > kMaxFields) return cudaErrorInvalidValue;
     switch (N) {
-        case 1: return launch_df<2>(r, geo, P, q, rhs, num_sms, s);
-        case 2: return launch_df<3>(r, geo, P, q, rhs, num_sms, s);
-        case 3: return launch_df<4>(r, geo, P, q, rhs, num_sms, s);
-        case 4: return launch_df<5>(r, geo, P, q, rhs, num_sms, s);
-        case 5: return launch_df<6>(r, geo, P, q, rhs, num_sms, s);
-        case 6: return launch_df<7>(r, geo, P, q, rhs, num_sms, s);
-        case 7: return launch_df<8>(r, geo, P, q, rhs, num_sms, s);
+        case 1: return launch_df<2>(r, nf, geo, P, q, rhs, num_sms, s);
+        case 2: return launch_df<3>(r, nf, geo, P, q, rhs, num_sms, s);
+        case 3: return launch_df<4>(r, nf, geo, P, q, rhs, num_sms, s);
+        case 4: return launch_df<5>(r, nf, geo, P, q, rhs, num_sms, s);
+        case 5: return launch_df<6>(r, nf, geo, P, q, rhs, num_sms, s);
+        case 6: return launch_df<7>(r, nf, geo, P, q, rhs, num_sms, s);
+        case 7: return launch_df<8>(r, nf, geo, P, q, rhs, num_sms, s);
         default: return cudaErrorInvalidValue;
     }
 }

@@ -86,9 +86,9 @@ def test_create_rejects_invalid_arguments_without_a_gpu(lib):
         assert lib.numa_vol_create(C.byref(mesh), C.byref(geo), C.byref(consts), 0,
                                    C.byref(h)) == _lib.NUMA_EINVAL
         assert h.value is None
-    # tracers: 0..3, not in NUMA_DF64 (checked before any device work)
+    # tracers: 0..3 (checked before any device work)
     for T, prec, code in ((4, 0, _lib.NUMA_EINVAL), (-1, 0, _lib.NUMA_EINVAL),
-                          (3, _lib.NUMA_DF64, _lib.NUMA_EUNSUPPORTED)):
+                          (4, _lib.NUMA_DF64, _lib.NUMA_EINVAL)):
         mesh = _lib.numa_mesh(1, 7 if prec == _lib.NUMA_DF64 else 1, T)
         assert lib.numa_vol_create(C.byref(mesh), C.byref(geo), C.byref(consts), prec,
                                    C.byref(h)) == code
