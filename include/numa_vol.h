@@ -72,7 +72,7 @@ typedef struct {
 /* Mesh size: num_elements hexahedra of order N (Nq = N + 1 points per axis),
  * and num_tracers passive tracers (0 .. NUMA_MAX_TRACERS; every precision,
  * tracers FP64 in NUMA_FP64 and NUMA_DF64, FP32 values as they are in
- * NUMA_MIXED; not in the batch or the engine): the
+ * NUMA_MIXED; in the batch, not in the engine): the
  * state and rhs then hold 5 + num_tracers planes, the tracers Q1.. after
  * Theta, each advected like Theta (flux Q u_d, no source; the paper's 8-field
  * form, Sec. 2).  Zero-initialise the struct so that num_tracers defaults to 0. */
@@ -124,8 +124,9 @@ typedef struct numa_vol numa_vol;
  * (release with numa_vol_destroy).  Errors: NUMA_EINVAL, NUMA_ENOMEM,
  * NUMA_ECUDA, NUMA_EUNSUPPORTED (NUMA_DF64 with N > 7).
  * Handles of N > 7 evaluate one element per CTA of 3 or 4 (N+1)^2 threads,
- * the fields in groups (vol_rhs_high_kernel); the batch and the engine take
- * handles of N <= 7 without tracers only.
+ * the fields in groups (vol_rhs_high_kernel); the batch takes handles of
+ * N <= 7, the engine and numa_batch_advance_noalloc handles of N <= 7 without
+ * tracers.
  *
  * NUMA_MIXED takes the state as FP32 perturbations from the reference state:
  * plane 0 holds rho - rho_ref, plane 4 holds Theta - Theta_ref, planes 1-3
@@ -292,11 +293,13 @@ int numa_batch_create(numa_precision prec, numa_batch **out);
 
 /* Add an instance: handle h (created with the batch's precision on the same
  * device; the batch neither copies nor frees it, and it must outlive its use
- * in the batch) and its state q, a device pointer to 5 planes of M values of
- * the handle's state type, 16-byte aligned, that numa_batch_advance updates in
- * place.  *index (optional) receives the instance's position.
- * Errors: NUMA_EINVAL; NUMA_EUNSUPPORTED for a handle of order N > NUMA_MAX_N
- * or with tracers. */
+ * in the batch) and its state q, a device pointer to 5 (+ num_tracers) planes
+ * of M values of the handle's state type, 16-byte aligned, that
+ * numa_batch_advance updates in place.  *index (optional) receives the
+ * instance's position.  A batch holding an instance with tracers runs the
+ * shared-memory-state tiles' tracer forms for all its instances; its
+ * tensor-core sweep and tensor-memory state settings then have no effect.
+ * Errors: NUMA_EINVAL; NUMA_EUNSUPPORTED for a handle of order N > NUMA_MAX_N. */
 int numa_batch_add(numa_batch *b, const numa_vol *h, void *q, int *index);
 
 /* Remove every instance (the handles and states are untouched). */

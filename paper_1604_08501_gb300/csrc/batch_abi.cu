@@ -39,6 +39,13 @@ int bfail_cuda(cudaError_t e, const char *where) {
                            cudaGetErrorString(e) + ")");
 }
 
+// Some instance has tracers: the launch runs the tiles' tracer forms.
+bool has_tracers(const std::vector<numa::BatchInstance> &v) {
+    for (const auto &I : v)
+        if (I.nf > numa::kFields) return true;
+    return false;
+}
+
 }  // namespace
 
 struct numa_batch {
@@ -184,8 +191,6 @@ int numa_batch_add(numa_batch *b, const numa_vol *h, void *q, int *index) {
     const bool mixed = b->prec == NUMA_MIXED;
     if (h->N > NUMA_MAX_N)
         return bfail(NUMA_EUNSUPPORTED, "numa_batch_add: the batch takes orders N <= 7");
-    if (h->nf != numa::kFields)
-        return bfail(NUMA_EUNSUPPORTED, "numa_batch_add: the batch takes meshes without tracers");
     if (mixed ? h->kernel != numa::Kernel::Mixed : h->kernel != numa::Kernel::Native)
         return bfail(NUMA_EINVAL, "numa_batch_add: handle precision differs from the batch's "
                                   "(NUMA_FP64 batches take NUMA_FP64 handles)");
@@ -200,6 +205,7 @@ int numa_batch_add(numa_batch *b, const numa_vol *h, void *q, int *index) {
     I.np = h->nparams;
     I.mgeo = h->mgeo;
     I.mp = h->mparams;
+    I.nf = h->nf;
     b->inst.push_back(I);
     b->dirty = true;
     if (index) *index = (int)b->inst.size() - 1;
@@ -236,7 +242,8 @@ int numa_batch_advance(numa_batch *b, int nsteps, double dt, void *stream) {
         if (e == cudaSuccess)
             e = numa::launch_batch_lsrk(b->prec == NUMA_MIXED, b->d_inst, b->d_items, b->num_items,
                                         b->d_counter, kLsrk, nsteps, dt, grid_of(b), b->cap_stream,
-                                        b->tc_mask, b->ctas_per_sm, b->tmem_state);
+                                        b->tc_mask, b->ctas_per_sm, b->tmem_state,
+                                        has_tracers(b->inst));
         cudaGraph_t g = nullptr;
         const cudaError_t e2 = cudaStreamEndCapture(b->cap_stream, &g);
         if (e == cudaSuccess) e = e2;
@@ -280,7 +287,7 @@ cudaError_t time_cfg(numa_batch *b, const std::vector<numa::BatchInstance> &sub,
         if (e == cudaSuccess)
             e = numa::launch_batch_lsrk(b->prec == NUMA_MIXED, b->d_inst, b->d_items, b->num_items,
                                         b->d_counter, kLsrk, nsteps, 1e-6, grid_of(b), s, c.mask,
-                                        c.ctas, c.tmem);
+                                        c.ctas, c.tmem, has_tracers(sub));
         if (e == cudaSuccess) e = cudaEventRecord(t1, s);
         if (e == cudaSuccess) e = cudaEventRecord(b->launched, s);
         if (e == cudaSuccess) e = cudaEventSynchronize(t1);
@@ -314,10 +321,10 @@ int numa_batch_autotune(numa_batch *b, void *stream) {
     for (const auto &I : b->inst) {
         if (e != cudaSuccess) break;
         void *c = nullptr;
-        e = cudaMalloc(&c, elem * numa::kFields * I.M);
+        e = cudaMalloc(&c, elem * I.nf * I.M);
         if (e != cudaSuccess) break;
         copies.push_back(c);
-        e = cudaMemcpyAsync(c, I.q, elem * numa::kFields * I.M, cudaMemcpyDeviceToDevice, s);
+        e = cudaMemcpyAsync(c, I.q, elem * I.nf * I.M, cudaMemcpyDeviceToDevice, s);
         numa::BatchInstance J = I;
         J.q = c;
         all.push_back(J);

@@ -32,7 +32,8 @@ namespace numa {
 
 namespace {
 
-template <bool MIXED>
+// TR: the tiles' tracer forms, for batches that hold instances with tracers.
+template <bool MIXED, bool TR = false>
 __global__ void __launch_bounds__(kThreads, tile_ctas_per_sm<MIXED>())
 batch_lsrk_kernel(const BatchInstance *__restrict__ inst, const BatchItem *__restrict__ items,
                   int num_items, int *counter, LsrkCoef co, int nsteps, double dt) {
@@ -57,13 +58,13 @@ batch_lsrk_kernel(const BatchInstance *__restrict__ inst, const BatchItem *__res
         __syncthreads();
         const int ns = sI.nsteps > 0 ? sI.nsteps : nsteps;
         switch (item.nq) {
-            case 2: run_tile<2, MIXED>(sI, item.e0, item.count, sco, ns, dt, smem_d); break;
-            case 3: run_tile<3, MIXED>(sI, item.e0, item.count, sco, ns, dt, smem_d); break;
-            case 4: run_tile<4, MIXED>(sI, item.e0, item.count, sco, ns, dt, smem_d); break;
-            case 5: run_tile<5, MIXED>(sI, item.e0, item.count, sco, ns, dt, smem_d); break;
-            case 6: run_tile<6, MIXED>(sI, item.e0, item.count, sco, ns, dt, smem_d); break;
-            case 7: run_tile<7, MIXED>(sI, item.e0, item.count, sco, ns, dt, smem_d); break;
-            case 8: run_tile<8, MIXED>(sI, item.e0, item.count, sco, ns, dt, smem_d); break;
+            case 2: run_tile<2, MIXED, TR>(sI, item.e0, item.count, sco, ns, dt, smem_d); break;
+            case 3: run_tile<3, MIXED, TR>(sI, item.e0, item.count, sco, ns, dt, smem_d); break;
+            case 4: run_tile<4, MIXED, TR>(sI, item.e0, item.count, sco, ns, dt, smem_d); break;
+            case 5: run_tile<5, MIXED, TR>(sI, item.e0, item.count, sco, ns, dt, smem_d); break;
+            case 6: run_tile<6, MIXED, TR>(sI, item.e0, item.count, sco, ns, dt, smem_d); break;
+            case 7: run_tile<7, MIXED, TR>(sI, item.e0, item.count, sco, ns, dt, smem_d); break;
+            case 8: run_tile<8, MIXED, TR>(sI, item.e0, item.count, sco, ns, dt, smem_d); break;
             default: break;
         }
         __syncthreads();   // sI and s_item are rewritten by the next claim
@@ -197,6 +198,14 @@ cudaError_t prepare_batch_lsrk() {
     e = cudaFuncSetAttribute(batch_lsrk_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)tile_smem_bytes<true>());
     if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(batch_lsrk_kernel<false, true>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)tile_smem_bytes<false, true>());
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(batch_lsrk_kernel<true, true>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)tile_smem_bytes<true, true>());
+    if (e != cudaSuccess) return e;
     return cudaFuncSetAttribute(batch_lsrk_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 kTcSmemBytes);
 }
@@ -206,11 +215,17 @@ int batch_max_ctas_per_sm(bool mixed) { return mixed ? 2 : tile_ctas_per_sm<fals
 cudaError_t launch_batch_lsrk(bool mixed, const BatchInstance *inst, const BatchItem *items,
                               int num_items, int *counter, const LsrkCoef &co, int nsteps,
                               double dt, int num_sms, cudaStream_t s, unsigned tc_mask,
-                              int ctas_per_sm, bool tmem_state) {
+                              int ctas_per_sm, bool tmem_state, bool tracers) {
     if (num_items <= 0 || nsteps <= 0) return cudaSuccess;
     const int kmax = batch_max_ctas_per_sm(mixed);
     const int k = ctas_per_sm > 0 && ctas_per_sm < kmax ? ctas_per_sm : kmax;
-    if (mixed && (tc_mask != 0 || tmem_state))
+    if (tracers && mixed)   // the shared-memory-state tile's tracer form
+        batch_lsrk_kernel<true, true><<<num_sms * k, kThreads, tile_smem_bytes<true, true>(), s>>>(
+            inst, items, num_items, counter, co, nsteps, dt);
+    else if (tracers)
+        batch_lsrk_kernel<false, true><<<num_sms * k, kThreads, tile_smem_bytes<false, true>(), s>>>(
+            inst, items, num_items, counter, co, nsteps, dt);
+    else if (mixed && (tc_mask != 0 || tmem_state))
         batch_lsrk_tc_kernel<<<num_sms * k, kThreads, kTcSmemBytes, s>>>(
             inst, items, num_items, counter, co, nsteps, dt, tc_mask);
     else if (mixed)

@@ -169,6 +169,7 @@ extern "C" int numa_batch_advance_noalloc(const numa_vol *const *handles, void *
         I = BatchInstance{};
         I.N = h->N;
         I.nq = h->Nq;
+        I.nf = kFields;
         I.M = h->M;
         I.q = states[k];
         I.geo = h->geo;

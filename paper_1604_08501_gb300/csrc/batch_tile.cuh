@@ -22,26 +22,32 @@ constexpr int kThreads = 512;
 // binds).  Mixed: the fluxes, q and dq (10 values) and the point's geometry
 // (g and Jinv, 10 values) in shared memory, so that the kernel fits 64
 // registers and two CTAs share an SM, twice the warps to hide latency.
-// Flux words of one pass: 3 x 5 blocks of EPP elements; the largest over the
+// Flux words of one pass: 3 x NF blocks of EPP elements; the largest over the
 // orders sizes the flux region (4-byte values at Nq = 8: lines of 9 slots).
-template <typename T, int NQ>
-constexpr int pass_flux_words() {
-    return 3 * 5 * (kThreads / (NQ * NQ * NQ)) * block_words<NQ, T>();
+// NF = 5, or 8 in the tiles' tracer forms (TR), whose tracers' q and dq also
+// live in shared memory in FP64 (3 + 3 values per thread after the fluxes).
+template <typename T, int NQ, int NF = kFields>
+__host__ __device__ constexpr int pass_flux_words() {
+    return 3 * NF * (kThreads / (NQ * NQ * NQ)) * block_words<NQ, T>();
 }
-template <typename T>
-constexpr int tile_flux_words() {
-    constexpr int w[] = {pass_flux_words<T, 2>(), pass_flux_words<T, 3>(), pass_flux_words<T, 4>(),
-                         pass_flux_words<T, 5>(), pass_flux_words<T, 6>(), pass_flux_words<T, 7>(),
-                         pass_flux_words<T, 8>()};
+template <typename T, int NF = kFields>
+__host__ __device__ constexpr int tile_flux_words() {
+    constexpr int w[] = {pass_flux_words<T, 2, NF>(), pass_flux_words<T, 3, NF>(),
+                         pass_flux_words<T, 4, NF>(), pass_flux_words<T, 5, NF>(),
+                         pass_flux_words<T, 6, NF>(), pass_flux_words<T, 7, NF>(),
+                         pass_flux_words<T, 8, NF>()};
     int m = 0;
     for (int x : w) m = x > m ? x : m;
     return m;
 }
 constexpr int kMixedFluxWords = tile_flux_words<float>();
 constexpr int kMixedSmemWords = kMixedFluxWords + (2 * 5 + 10) * kThreads;
-template <bool MIXED>
+template <bool MIXED, bool TR = false>
 constexpr size_t tile_smem_bytes() {
-    return MIXED ? sizeof(float) * kMixedSmemWords : sizeof(double) * tile_flux_words<double>();
+    constexpr int NF = TR ? kMaxFields : kFields;
+    return MIXED ? sizeof(float) * (tile_flux_words<float, NF>() + (2 * NF + 10) * kThreads)
+                 : sizeof(double) * (tile_flux_words<double, NF>() +
+                                     (TR ? 2 * (kMaxFields - kFields) * kThreads : 0));
 }
 template <bool MIXED>
 constexpr int tile_ctas_per_sm() {
@@ -99,24 +105,29 @@ __device__ __forceinline__ void load_stage_coefficients(const LsrkCoef &co, tile
     }
 }
 
-template <int NQ, bool MIXED>
+// TR: the tracer form (instances of 5..8 fields, I.nf): flux blocks laid out
+// for 8 fields, the tracers' q and dq in shared memory in both precisions.
+template <int NQ, bool MIXED, bool TR = false>
 __device__ void run_tile(const BatchInstance &I, int64_t e0, int64_t count,
                          const tile_t<MIXED> *sco, int nsteps, double dt, void *smem) {
     using T = tile_t<MIXED>;
     constexpr int N3 = NQ * NQ * NQ;
     constexpr int NL = NQ * NQ;
+    constexpr int NF = TR ? kMaxFields : kFields;   // flux blocks per direction
+    constexpr int NTR = kMaxFields - kFields;       // tracers at most
     constexpr int EPP = kThreads / N3;          // elements per pass
     constexpr int EW = block_words<NQ, T>();    // one element's (direction, field) block
     constexpr int BLK = EPP * EW;               // one (direction, field) block of sF
-    constexpr int TASKS = 3 * kFields * EPP * NL;   // lines per stage
-    T *sF = static_cast<T *>(smem);             // [(d*5 + b)*EPP + el][slot]
+    constexpr int TASKS = 3 * NF * EPP * NL;    // lines per stage (TR: some blocks unused)
+    const int nf = TR ? I.nf : kFields;
+    T *sF = static_cast<T *>(smem);             // [(d*NF + b)*EPP + el][slot]
     const int l = threadIdx.x;
     const int el = l / N3, p = l % N3;
     const int i = p % NQ, j = (p / NQ) % NQ, k = p / NL;
     // this thread's flux slot of field b in direction d: f[d] + b * BLK
     int f[3];
 #pragma unroll
-    for (int d = 0; d < 3; ++d) f[d] = d * kFields * BLK + el * EW + dir_slot<NQ, T>(d, i, j, k);
+    for (int d = 0; d < 3; ++d) f[d] = d * NF * BLK + el * EW + dir_slot<NQ, T>(d, i, j, k);
     const int64_t M = I.M;
     T *qv = static_cast<T *>(I.q);
     const T dtt = static_cast<T>(dt);
@@ -134,9 +145,18 @@ __device__ void run_tile(const BatchInstance &I, int64_t e0, int64_t count,
         // shared memory in the mixed mode), and the mixed mode's per-point
         // constants, kept for all stages
         T qr[kFields], dqr[kFields];
-        T *sQ = sF + kMixedFluxWords + l;          // [b * kThreads], mixed only
-        T *sD = sQ + kFields * kThreads;
-        T *sG = sD + kFields * kThreads;           // g (9), Jinv
+        T *sQ = sF + tile_flux_words<T, NF>() + l;   // [b * kThreads], mixed: every field
+        T *sD = sQ + NF * kThreads;                  // FP64 (TR): the tracers
+        T *sG = sD + NF * kThreads;                  // g (9), Jinv; mixed only
+        // the tracers' q and dq (TR): shared memory in both precisions
+        auto QT = [&](int t) -> T & {
+            if constexpr (MIXED) return sQ[(kFields + t) * kThreads];
+            else return sF[tile_flux_words<T, NF>() + t * kThreads + l];
+        };
+        auto DQT = [&](int t) -> T & {
+            if constexpr (MIXED) return sD[(kFields + t) * kThreads];
+            else return sF[tile_flux_words<T, NF>() + (NTR + t) * kThreads + l];
+        };
         auto Q = [&](int b) -> T & {
             if constexpr (MIXED) return sQ[b * kThreads]; else return qr[b];
         };
@@ -149,6 +169,13 @@ __device__ void run_tile(const BatchInstance &I, int64_t e0, int64_t count,
             DQ(b) = T(0);
         }
         if (!active) Q(0) = MIXED ? T(0) : T(1);   // idle threads hold a harmless state
+        if constexpr (TR) {
+#pragma unroll
+            for (int t = 0; t < NTR; ++t) {
+                QT(t) = active && kFields + t < nf ? qv[(kFields + t) * M + node] : T(0);
+                DQT(t) = T(0);
+            }
+        }
         float th0 = 0.f, rho0 = 0.f;
         EosRef32 er{0.f, 0.f};
         if constexpr (MIXED) {
@@ -208,6 +235,11 @@ __device__ void run_tile(const BatchInstance &I, int64_t e0, int64_t count,
                         F[2 * BLK] = fma(q[2], u, g2 * pp);
                         F[3 * BLK] = fma(q[3], u, g3 * pp);
                         F[4 * BLK] = Th * u;
+                        if constexpr (TR) {
+#pragma unroll
+                            for (int t = 0; t < NTR; ++t)
+                                if (kFields + t < nf) F[(kFields + t) * BLK] = QT(t) * u;   // Q u_d
+                        }
                     }
                 }
                 __syncthreads();
@@ -216,7 +248,7 @@ __device__ void run_tile(const BatchInstance &I, int64_t e0, int64_t count,
                 for (int t = l; t < TASKS; t += kThreads) {
                     const int bd = t / (EPP * NL), rem = t % (EPP * NL);
                     const int e = rem / NL, line = rem % NL;
-                    if (e < npass) {
+                    if (e < npass && (!TR || bd % NF < nf)) {
                         if constexpr (MIXED)
                             sweep_line<NQ>(sF + bd * BLK + e * EW, line, c_sweep32[NQ]);
                         else
@@ -253,12 +285,28 @@ __device__ void run_tile(const BatchInstance &I, int64_t e0, int64_t count,
                         DQ(b) = d;
                         Q(b) = fma(bcoef, d, Q(b));
                     }
+                    if constexpr (TR) {
+#pragma unroll
+                        for (int t = 0; t < NTR; ++t) {
+                            if (kFields + t >= nf) break;
+                            const int b = kFields + t;
+                            const T R = sF[f[0] + b * BLK] + sF[f[1] + b * BLK] + sF[f[2] + b * BLK];
+                            const T d = fma(a, DQT(t), dtt * (-jinv * R));
+                            DQT(t) = d;
+                            QT(t) = fma(bcoef, d, QT(t));
+                        }
+                    }
                 }
             }
         }
         if (active) {
 #pragma unroll
             for (int b = 0; b < kFields; ++b) qv[b * M + node] = Q(b);
+            if constexpr (TR) {
+#pragma unroll
+                for (int t = 0; t < NTR; ++t)
+                    if (kFields + t < nf) qv[(kFields + t) * M + node] = QT(t);
+            }
         }
     }
 }

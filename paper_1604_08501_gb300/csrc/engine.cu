@@ -447,6 +447,7 @@ int numa_engine_progress(numa_engine *e, int64_t *done_ids, int max_done, int *n
             numa::BatchInstance I{};
             I.N = r.mesh->N;
             I.nq = r.mesh->Nq;
+            I.nf = numa::kFields;
             I.M = r.mesh->M;
             I.q = e->arena.base + r.off;
             I.geo = r.mesh->geo;

@@ -85,6 +85,7 @@ struct BatchInstance {
     MixedGeometry mgeo;
     MixedParams mp;
     int nsteps;   // steps of this instance in the launch; 0: the launch's step count
+    int nf;       // fields: 5, or 5 + tracers (the tracer forms of the tiles only)
 };
 
 // One work item: elements [e0, e0 + count) of an instance.
@@ -113,11 +114,14 @@ constexpr unsigned kTcAllOrders = 0x1FCu;   // bits 2..8
 // ctas_per_sm: CTAs per SM of the persistent grid, 1 .. the kernel's maximum
 // (batch_max_ctas_per_sm); 0 takes the maximum.  tmem_state (mixed): the
 // CUDA-core tiles keep each point's state in tensor memory instead of shared
-// memory (the tensor-core kernel's CUDA-core path).
+// memory (the tensor-core kernel's CUDA-core path).  tracers: some instance
+// has nf > 5; the launch then runs the shared-memory-state tiles' tracer forms
+// and tc_mask and tmem_state have no effect.
 cudaError_t launch_batch_lsrk(bool mixed, const BatchInstance *inst, const BatchItem *items,
                               int num_items, int *counter, const LsrkCoef &co, int nsteps,
                               double dt, int num_sms, cudaStream_t s, unsigned tc_mask = 0,
-                              int ctas_per_sm = 0, bool tmem_state = false);
+                              int ctas_per_sm = 0, bool tmem_state = false,
+                              bool tracers = false);
 int batch_max_ctas_per_sm(bool mixed);
 
 // Elements one CTA pass holds for order Nq (512 threads, one per point).

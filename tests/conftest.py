@@ -15,12 +15,17 @@ def pytest_configure(config):
 def rel_err(x, ref):
     """Per-field normwise errors: (max|x - ref| / max|ref|, ||x - ref||_2 / ||ref||_2).
 
-    Fields whose reference is identically zero report the absolute max error."""
+    Fields whose reference is identically zero report the absolute max error.
+    2-D arrays are (fields, points), any number of fields; flat arrays hold
+    five fields."""
     import numpy as np
-    x = np.asarray(x, dtype=np.float64).reshape(5, -1)
-    ref = np.asarray(ref, dtype=np.float64).reshape(5, -1)
+    x = np.asarray(x, dtype=np.float64)
+    ref = np.asarray(ref, dtype=np.float64)
+    x = x if x.ndim == 2 else x.reshape(5, -1)
+    ref = ref if ref.ndim == 2 else ref.reshape(5, -1)
+    assert x.shape == ref.shape, (x.shape, ref.shape)
     out = []
-    for b in range(5):
+    for b in range(x.shape[0]):
         d = x[b] - ref[b]
         scale = np.max(np.abs(ref[b])) if ref[b].size else 0.0
         mx = np.max(np.abs(d)) if d.size else 0.0

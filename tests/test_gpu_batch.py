@@ -62,6 +62,52 @@ def increment_errors(w, q_final, nsteps=NSTEPS, mixed=False):
 
 
 @pytest.mark.parametrize("precision,tol", [("fp64", 3e-12), ("mixed", 1e-5)])
+def test_batch_with_tracers_matches_oracle_integrator(precision, tol):
+    # A batch holding instances with tracers runs the tiles' tracer forms:
+    # instances of 5, 6 and 8 fields at three orders, every field against the
+    # oracle's integrator (tracers as they are in the mixed mode); an instance's
+    # five base fields bit for bit as the same instance without tracers in the
+    # same batch; in FP64 a tracer that starts equal to Theta stays equal.
+    specs = [(3, (3, 2, 1), 61, 3), (5, (2, 1, 2), 62, 1), (7, (2, 2, 1), 63, 3),
+             (4, (2, 2, 1), 64, 0)]
+    runs = []
+    for N, shape, seed, T in specs:
+        w = wl.make_workload(N, shape, seed=seed, tracers=T)
+        if T == 3 and precision == "fp64" and N == 7:
+            w.q[5] = w.q[4]   # Q1 = Theta
+        runs.append(w)
+    twin = wl.make_workload(3, (3, 2, 1), seed=61)   # the first instance without tracers
+    with Batch(precision) as b:
+        keep = []
+        for w in runs + [twin]:
+            vt = VolumeTerm.from_problem(w.problem(), precision=precision)
+            q0 = w.q_mixed() if precision == "mixed" else w.q
+            q = torch.from_numpy(np.ascontiguousarray(q0)).cuda()
+            b.add(vt, q)
+            keep.append((vt, q))
+        b.advance(NSTEPS, DT)
+        torch.cuda.synchronize()
+        outs = [q.cpu().numpy() for _, q in keep]
+        for w, got, sp in zip(runs, outs, specs):
+            ref = oracle.lsrk(w.problem(), w.q, DT, NSTEPS)
+            got = got.astype(np.float64)
+            if precision == "mixed":
+                ref_pert = np.concatenate([(ref[0] - w.rho_ref)[None], ref[1:4],
+                                           (ref[4] - w.rhotheta_ref)[None], ref[5:]])
+                errs = rel_err(got, ref_pert)
+            else:
+                errs = rel_err(got - w.q, ref - w.q)
+            assert len(errs) == w.q.shape[0]
+            for f, (mx, _) in enumerate(errs):
+                assert mx <= tol, (precision, sp, f, mx)
+        assert np.array_equal(outs[0][:5], outs[-1])
+        if precision == "fp64":
+            assert np.array_equal(outs[2][5], outs[2][4])
+        for vt, _ in keep:
+            vt.close()
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 3e-12), ("mixed", 1e-5)])
 def test_batch_matches_oracle_integrator(precision, tol):
     runs = [make(sp, precision) for sp in SPECS]
     with Batch(precision) as b:

@@ -13,7 +13,7 @@ import pytest
 import oracle
 from paper_1604_08501_gb300 import build
 from paper_1604_08501_gb300 import workload as wl
-from paper_1604_08501_gb300.numa_vol import Batch, Engine, NumaError, VolumeTerm
+from paper_1604_08501_gb300.numa_vol import Engine, NumaError, VolumeTerm
 
 pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
@@ -73,18 +73,11 @@ def test_tracer_host_path_full_paper_form():
 def test_tracer_handles_are_rejected_where_unsupported():
     w = wl.make_workload(3, (2, 1, 1), seed=430, tracers=2)
     prob = w.problem()
+    # the batch takes tracers (tests/test_gpu_batch.py); the engine does not
     with VolumeTerm.from_problem(prob) as vt:
-        q = torch.from_numpy(w.q).cuda()
-        with Batch("fp64") as b:
-            with pytest.raises(NumaError, match="EUNSUPPORTED"):
-                b.add(vt, q)
         with Engine("fp64", budget_bytes=1 << 24) as eng:
             with pytest.raises(NumaError, match="EUNSUPPORTED"):
                 eng.submit(vt, w.q, np.empty_like(w.q), 1, 0.01)
-    with VolumeTerm.from_problem(prob, precision="mixed") as vm:   # mixed takes tracers,
-        with Batch("mixed") as b:                                   # the mixed batch does not
-            with pytest.raises(NumaError, match="EUNSUPPORTED"):
-                b.add(vm, torch.from_numpy(w.q_mixed()).cuda())
 
 
 @pytest.mark.parametrize("N,T", [(2, 3), (4, 1), (7, 3)])
