@@ -72,7 +72,8 @@ typedef struct {
 /* Mesh size: num_elements hexahedra of order N (Nq = N + 1 points per axis),
  * and num_tracers passive tracers (0 .. NUMA_MAX_TRACERS; every precision,
  * tracers FP64 in NUMA_FP64 and NUMA_DF64, FP32 values as they are in
- * NUMA_MIXED; in the batch, not in the engine): the
+ * NUMA_MIXED; in the batch and the engine, not in the no-allocation
+ * advance): the
  * state and rhs then hold 5 + num_tracers planes, the tracers Q1.. after
  * Theta, each advected like Theta (flux Q u_d, no source; the paper's 8-field
  * form, Sec. 2).  Zero-initialise the struct so that num_tracers defaults to 0. */
@@ -124,8 +125,8 @@ typedef struct numa_vol numa_vol;
  * (release with numa_vol_destroy).  Errors: NUMA_EINVAL, NUMA_ENOMEM,
  * NUMA_ECUDA, NUMA_EUNSUPPORTED (NUMA_DF64 with N > 7).
  * Handles of N > 7 evaluate one element per CTA of 3 or 4 (N+1)^2 threads,
- * the fields in groups (vol_rhs_high_kernel); the batch takes handles of
- * N <= 7, the engine and numa_batch_advance_noalloc handles of N <= 7 without
+ * the fields in groups (vol_rhs_high_kernel); the batch and the engine take
+ * handles of N <= 7, numa_batch_advance_noalloc handles of N <= 7 without
  * tracers.
  *
  * NUMA_MIXED takes the state as FP32 perturbations from the reference state:
@@ -440,13 +441,15 @@ int numa_engine_create(numa_precision prec, size_t budget_bytes, int max_members
                        numa_engine **out);
 
 /* Queue a request.  mesh: a handle of the engine's precision on its device.
- * q0_host: the initial state (5 planes of M values of the handle's state type)
+ * q0_host: the initial state (5 + num_tracers planes of M values of the
+ * handle's state type; a round holding a member with tracers runs the batch's
+ * tracer tiles)
  * and q_out_host: where the final state goes; both host memory, read and
  * written during later progress calls, kept alive until the request is done or
  * cancelled.  nsteps >= 1, dt > 0.  *id receives the request id.
  * Errors: NUMA_EINVAL (malformed request; the engine is unchanged),
  * NUMA_ELIMIT (the state exceeds the whole budget: it can never be admitted),
- * NUMA_EUNSUPPORTED (a mesh of order N > NUMA_MAX_N or with tracers). */
+ * NUMA_EUNSUPPORTED (a mesh of order N > NUMA_MAX_N). */
 int numa_engine_submit(numa_engine *e, const numa_vol *mesh, const void *q0_host,
                        void *q_out_host, int nsteps, double dt, int64_t *id);
 

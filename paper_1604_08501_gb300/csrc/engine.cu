@@ -195,7 +195,7 @@ struct numa_engine {
 namespace {
 
 size_t state_bytes(const numa_engine *e, const numa_vol *h) {
-    return e->elem * numa::kFields * (size_t)h->M;
+    return e->elem * (size_t)h->nf * (size_t)h->M;
 }
 
 void set_status(numa_engine *e, int64_t id, int status, bool stamp_done = false) {
@@ -292,8 +292,6 @@ int numa_engine_submit(numa_engine *e, const numa_vol *mesh, const void *q0_host
     const bool mixed = e->prec == NUMA_MIXED;
     if (mesh->N > NUMA_MAX_N)
         return efail(NUMA_EUNSUPPORTED, "numa_engine_submit: the engine takes orders N <= 7");
-    if (mesh->nf != numa::kFields)
-        return efail(NUMA_EUNSUPPORTED, "numa_engine_submit: the engine takes meshes without tracers");
     if (mixed ? mesh->kernel != numa::Kernel::Mixed : mesh->kernel != numa::Kernel::Native)
         return efail(NUMA_EINVAL, "numa_engine_submit: mesh handle precision differs from the engine's");
     if (mesh->device != e->device)
@@ -442,12 +440,14 @@ int numa_engine_progress(numa_engine *e, int64_t *done_ids, int max_done, int *n
     for (double dt : dts) {
         std::vector<numa::BatchInstance> inst;
         int launch_steps = 1;
+        bool tracers = false;   // some member has tracers: the tiles' tracer forms
         for (const auto &r : e->resident) {
             if (r.dt != dt) continue;
             numa::BatchInstance I{};
             I.N = r.mesh->N;
             I.nq = r.mesh->Nq;
-            I.nf = numa::kFields;
+            I.nf = r.mesh->nf;
+            tracers = tracers || r.mesh->nf > numa::kFields;
             I.M = r.mesh->M;
             I.q = e->arena.base + r.off;
             I.geo = r.mesh->geo;
@@ -494,7 +494,7 @@ int numa_engine_progress(numa_engine *e, int64_t *done_ids, int max_done, int *n
             err = numa::launch_batch_lsrk(e->prec == NUMA_MIXED, sl.d_inst, sl.d_items,
                                           (int)items.size(), sl.d_counter, kCoef, launch_steps,
                                           dt, e->num_sms, e->stream, 0u, 0,
-                                          e->prec == NUMA_MIXED);
+                                          e->prec == NUMA_MIXED, tracers);
         if (err == cudaSuccess) err = cudaEventRecord(sl.done, e->stream);
         if (err == cudaSuccess) err = cudaEventRecord(e->last_launch, e->stream);
         if (err != cudaSuccess) return efail_cuda(err, "numa_engine_progress: step");

@@ -290,3 +290,37 @@ def test_rounds_allocate_no_device_memory(pool, policy):
     for n, o in enumerate(outs):
         j = n % len(works)
         assert np.array_equal(o, batch_reference(vts[j], works[j].q, 1 + n % 5))
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_members_with_tracers(precision):
+    # A member with three tracers beside one without: the rounds run the batch's
+    # tracer tiles.  Each result equals its own batch integration bit for bit
+    # and the oracle's integrator within the batch's bars.
+    w8 = wl.make_workload(3, (2, 2, 1), seed=470, tracers=3)
+    w5 = wl.make_workload(5, (2, 1, 1), seed=471)
+    ws = [w8, w5]
+    vts = [VolumeTerm.from_problem(w.problem(), precision=precision) for w in ws]
+    q0s = [w.q_mixed() if precision == "mixed" else w.q for w in ws]
+    outs = [np.empty_like(q) for q in q0s]
+    ks = [3, 2]
+    with Engine(precision, budget_bytes=1 << 30) as eng:
+        ids = [eng.submit(vt, q, o, k, DT) for vt, q, o, k in zip(vts, q0s, outs, ks)]
+        assert sorted(eng.run_until_idle()) == sorted(ids)
+    assert np.array_equal(outs[0], batch_reference(vts[0], q0s[0], ks[0], precision))
+    if precision == "fp64":
+        assert np.array_equal(outs[1], batch_reference(vts[1], q0s[1], ks[1], precision))
+    for w, o, k in zip(ws, outs, ks):
+        ref = oracle.lsrk(w.problem(), w.q, DT, k)
+        got = o.astype(np.float64)
+        if precision == "mixed":
+            ref = np.concatenate([(ref[0] - w.rho_ref)[None], ref[1:4],
+                                  (ref[4] - w.rhotheta_ref)[None], ref[5:]])
+            errs, tol = rel_err(got, ref), 1e-5
+        else:
+            errs, tol = rel_err(got - w.q, ref - w.q), 3e-12
+        assert len(errs) == w.q.shape[0]
+        for f, (mx, _) in enumerate(errs):
+            assert mx <= tol, (precision, w.N, f, mx)
+    for vt in vts:
+        vt.close()

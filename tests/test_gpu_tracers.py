@@ -13,7 +13,7 @@ import pytest
 import oracle
 from paper_1604_08501_gb300 import build
 from paper_1604_08501_gb300 import workload as wl
-from paper_1604_08501_gb300.numa_vol import Engine, NumaError, VolumeTerm
+from paper_1604_08501_gb300.numa_vol import VolumeTerm
 
 pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
@@ -73,11 +73,16 @@ def test_tracer_host_path_full_paper_form():
 def test_tracer_handles_are_rejected_where_unsupported():
     w = wl.make_workload(3, (2, 1, 1), seed=430, tracers=2)
     prob = w.problem()
-    # the batch takes tracers (tests/test_gpu_batch.py); the engine does not
+    # the batch and the engine take tracers (tests/test_gpu_batch.py,
+    # tests/test_gpu_engine.py); the no-allocation advance does not
+    import ctypes as C
+    from paper_1604_08501_gb300 import _lib
     with VolumeTerm.from_problem(prob) as vt:
-        with Engine("fp64", budget_bytes=1 << 24) as eng:
-            with pytest.raises(NumaError, match="EUNSUPPORTED"):
-                eng.submit(vt, w.q, np.empty_like(w.q), 1, 0.01)
+        q = torch.from_numpy(w.q).cuda()
+        rc = _lib.load().numa_batch_advance_noalloc((C.c_void_p * 1)(vt.handle),
+                                                    (C.c_void_p * 1)(q.data_ptr()), 1, 1, 0.01,
+                                                    None)
+        assert rc == _lib.NUMA_EUNSUPPORTED
 
 
 @pytest.mark.parametrize("N,T", [(2, 3), (4, 1), (7, 3)])
