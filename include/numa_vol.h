@@ -72,8 +72,7 @@ typedef struct {
 /* Mesh size: num_elements hexahedra of order N (Nq = N + 1 points per axis),
  * and num_tracers passive tracers (0 .. NUMA_MAX_TRACERS; every precision,
  * tracers FP64 in NUMA_FP64 and NUMA_DF64, FP32 values as they are in
- * NUMA_MIXED; in the batch and the engine, not in the no-allocation
- * advance): the
+ * NUMA_MIXED; in the batch, its no-allocation advance and the engine): the
  * state and rhs then hold 5 + num_tracers planes, the tracers Q1.. after
  * Theta, each advected like Theta (flux Q u_d, no source; the paper's 8-field
  * form, Sec. 2).  Zero-initialise the struct so that num_tracers defaults to 0. */
@@ -125,9 +124,8 @@ typedef struct numa_vol numa_vol;
  * (release with numa_vol_destroy).  Errors: NUMA_EINVAL, NUMA_ENOMEM,
  * NUMA_ECUDA, NUMA_EUNSUPPORTED (NUMA_DF64 with N > 7).
  * Handles of N > 7 evaluate one element per CTA of 3 or 4 (N+1)^2 threads,
- * the fields in groups (vol_rhs_high_kernel); the batch and the engine take
- * handles of N <= 7, numa_batch_advance_noalloc handles of N <= 7 without
- * tracers.
+ * the fields in groups (vol_rhs_high_kernel); the batch, the engine and
+ * numa_batch_advance_noalloc take handles of N <= 7.
  *
  * NUMA_MIXED takes the state as FP32 perturbations from the reference state:
  * plane 0 holds rho - rho_ref, plane 4 holds Theta - Theta_ref, planes 1-3
@@ -552,7 +550,7 @@ void numa_engine_destroy(numa_engine *e);
  * total work exceeds 2^31 - 1 items); NUMA_EINVAL for a NULL or misaligned
  * pointer, count < 1, nsteps < 0, handles of mixed kinds or of another device,
  * a double-float handle, or a stream under capture; NUMA_EUNSUPPORTED for a
- * handle of order N > NUMA_MAX_N or with tracers; NUMA_ECUDA if a CUDA call
+ * handle of order N > NUMA_MAX_N; NUMA_ECUDA if a CUDA call
  * fails.
  */
 #define NUMA_NOALLOC_MAX_INSTANCES 64

@@ -44,7 +44,8 @@ constexpr size_t kScratchBytes = kCounterBytes + (sizeof(NoallocTable) + 255) / 
 // setup() obtains with cudaGetSymbolAddress.
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 
-template <bool MIXED>
+// TR: the tiles' tracer forms, for a call that holds an instance with tracers.
+template <bool MIXED, bool TR>
 __global__ void __launch_bounds__(kThreads, tile_ctas_per_sm<MIXED>())
 batch_lsrk_noalloc_kernel(unsigned char *scratch, LsrkCoef co, int nsteps, double dt) {
     int *counter = reinterpret_cast<int *>(scratch);
@@ -76,13 +77,13 @@ batch_lsrk_noalloc_kernel(unsigned char *scratch, LsrkCoef co, int nsteps, doubl
         const int64_t count = ne - e0 < tile ? ne - e0 : tile;
         const int ns = sI.nsteps > 0 ? sI.nsteps : nsteps;
         switch (nq) {
-            case 2: run_tile<2, MIXED>(sI, e0, count, sco, ns, dt, smem_d); break;
-            case 3: run_tile<3, MIXED>(sI, e0, count, sco, ns, dt, smem_d); break;
-            case 4: run_tile<4, MIXED>(sI, e0, count, sco, ns, dt, smem_d); break;
-            case 5: run_tile<5, MIXED>(sI, e0, count, sco, ns, dt, smem_d); break;
-            case 6: run_tile<6, MIXED>(sI, e0, count, sco, ns, dt, smem_d); break;
-            case 7: run_tile<7, MIXED>(sI, e0, count, sco, ns, dt, smem_d); break;
-            case 8: run_tile<8, MIXED>(sI, e0, count, sco, ns, dt, smem_d); break;
+            case 2: run_tile<2, MIXED, TR>(sI, e0, count, sco, ns, dt, smem_d); break;
+            case 3: run_tile<3, MIXED, TR>(sI, e0, count, sco, ns, dt, smem_d); break;
+            case 4: run_tile<4, MIXED, TR>(sI, e0, count, sco, ns, dt, smem_d); break;
+            case 5: run_tile<5, MIXED, TR>(sI, e0, count, sco, ns, dt, smem_d); break;
+            case 6: run_tile<6, MIXED, TR>(sI, e0, count, sco, ns, dt, smem_d); break;
+            case 7: run_tile<7, MIXED, TR>(sI, e0, count, sco, ns, dt, smem_d); break;
+            case 8: run_tile<8, MIXED, TR>(sI, e0, count, sco, ns, dt, smem_d); break;
             default: break;
         }
         __syncthreads();   // sI and s_item are rewritten by the next claim
@@ -120,13 +121,21 @@ cudaError_t setup(int dev, DeviceSetup *out) {
         if (e != cudaSuccess) return e;
         e = upload_sweep_tables();
         if (e != cudaSuccess) return e;
-        e = cudaFuncSetAttribute(batch_lsrk_noalloc_kernel<false>,
+        e = cudaFuncSetAttribute(batch_lsrk_noalloc_kernel<false, false>,
                                  cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)tile_smem_bytes<false>());
         if (e != cudaSuccess) return e;
-        e = cudaFuncSetAttribute(batch_lsrk_noalloc_kernel<true>,
+        e = cudaFuncSetAttribute(batch_lsrk_noalloc_kernel<true, false>,
                                  cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)tile_smem_bytes<true>());
+        if (e != cudaSuccess) return e;
+        e = cudaFuncSetAttribute(batch_lsrk_noalloc_kernel<false, true>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)tile_smem_bytes<false, true>());
+        if (e != cudaSuccess) return e;
+        e = cudaFuncSetAttribute(batch_lsrk_noalloc_kernel<true, true>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)tile_smem_bytes<true, true>());
         if (e != cudaSuccess) return e;
         s.scratch = static_cast<unsigned char *>(p);
         s.done = true;
@@ -156,6 +165,7 @@ extern "C" int numa_batch_advance_noalloc(const numa_vol *const *handles, void *
     if (cap != cudaStreamCaptureStatusNone) return NUMA_EINVAL;
     const bool mixed = handles[0] && handles[0]->kernel == Kernel::Mixed;
     NoallocTable tab;   // on the stack: no heap
+    bool tracers = false;   // some instance has tracers: the tiles' tracer forms
     tab.count = count;
     tab.first_item[0] = 0;
     for (int k = 0; k < count; ++k) {
@@ -163,13 +173,14 @@ extern "C" int numa_batch_advance_noalloc(const numa_vol *const *handles, void *
         if (!h || !states[k] || (reinterpret_cast<uintptr_t>(states[k]) & 15u) != 0 ||
             h->device != dev)
             return NUMA_EINVAL;
-        if (h->N > NUMA_MAX_N || h->nf != kFields) return NUMA_EUNSUPPORTED;
+        if (h->N > NUMA_MAX_N) return NUMA_EUNSUPPORTED;
         if (mixed ? h->kernel != Kernel::Mixed : h->kernel != Kernel::Native) return NUMA_EINVAL;
         BatchInstance &I = tab.inst[k];
         I = BatchInstance{};
         I.N = h->N;
         I.nq = h->Nq;
-        I.nf = kFields;
+        I.nf = h->nf;
+        tracers = tracers || h->nf > kFields;
         I.M = h->M;
         I.q = states[k];
         I.geo = h->geo;
@@ -193,12 +204,19 @@ extern "C" int numa_batch_advance_noalloc(const numa_vol *const *handles, void *
             cudaSuccess ||
         cudaMemsetAsync(ds.scratch, 0, sizeof(int), s) != cudaSuccess)
         return NUMA_ECUDA;
-    if (mixed)
-        batch_lsrk_noalloc_kernel<true><<<ds.num_sms * tile_ctas_per_sm<true>(), kThreads,
-                                          tile_smem_bytes<true>(), s>>>(ds.scratch, kCoef, nsteps, dt);
+    const int g_mixed = ds.num_sms * tile_ctas_per_sm<true>();
+    const int g_fp64 = ds.num_sms * tile_ctas_per_sm<false>();
+    if (mixed && tracers)
+        batch_lsrk_noalloc_kernel<true, true><<<g_mixed, kThreads, tile_smem_bytes<true, true>(), s>>>(
+            ds.scratch, kCoef, nsteps, dt);
+    else if (mixed)
+        batch_lsrk_noalloc_kernel<true, false><<<g_mixed, kThreads, tile_smem_bytes<true>(), s>>>(
+            ds.scratch, kCoef, nsteps, dt);
+    else if (tracers)
+        batch_lsrk_noalloc_kernel<false, true><<<g_fp64, kThreads, tile_smem_bytes<false, true>(),
+                                                 s>>>(ds.scratch, kCoef, nsteps, dt);
     else
-        batch_lsrk_noalloc_kernel<false><<<ds.num_sms * tile_ctas_per_sm<false>(), kThreads,
-                                           tile_smem_bytes<false>(), s>>>(ds.scratch, kCoef, nsteps,
-                                                                          dt);
+        batch_lsrk_noalloc_kernel<false, false><<<g_fp64, kThreads, tile_smem_bytes<false>(), s>>>(
+            ds.scratch, kCoef, nsteps, dt);
     return cudaGetLastError() == cudaSuccess ? NUMA_OK : NUMA_ECUDA;
 }

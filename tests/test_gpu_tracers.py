@@ -70,21 +70,6 @@ def test_tracer_host_path_full_paper_form():
         assert np.max(np.abs(dev[f] - ref[f])) <= TOL * np.max(np.abs(ref[f])), f
 
 
-def test_tracer_handles_are_rejected_where_unsupported():
-    w = wl.make_workload(3, (2, 1, 1), seed=430, tracers=2)
-    prob = w.problem()
-    # the batch and the engine take tracers (tests/test_gpu_batch.py,
-    # tests/test_gpu_engine.py); the no-allocation advance does not
-    import ctypes as C
-    from paper_1604_08501_gb300 import _lib
-    with VolumeTerm.from_problem(prob) as vt:
-        q = torch.from_numpy(w.q).cuda()
-        rc = _lib.load().numa_batch_advance_noalloc((C.c_void_p * 1)(vt.handle),
-                                                    (C.c_void_p * 1)(q.data_ptr()), 1, 1, 0.01,
-                                                    None)
-        assert rc == _lib.NUMA_EUNSUPPORTED
-
-
 @pytest.mark.parametrize("N,T", [(2, 3), (4, 1), (7, 3)])
 def test_mixed_precision_tracers(N, T):
     # FP32 8-field form (the paper's benchmark precision and field count):

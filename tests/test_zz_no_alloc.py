@@ -80,6 +80,34 @@ def test_noalloc_advance_matches_batch_advance_on_two_calls(precision, tol, nste
         vt.close()
 
 
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-13), ("mixed", 1e-5)])
+def test_noalloc_advance_with_tracers_matches_batch_advance(precision, tol):
+    # Instances of 8, 6 and 5 fields: the call runs the tiles' tracer forms,
+    # as numa_batch_advance does for the same instances.
+    lib = _lib.load()
+    specs = [(3, (3, 2, 1), 31, 3), (7, (2, 1, 1), 32, 1), (5, (2, 2, 1), 33, 0)]
+    works = [wl.make_workload(N, shape, seed=seed, tracers=T) for N, shape, seed, T in specs]
+    vts = [VolumeTerm.from_problem(w.problem(), precision=precision) for w in works]
+    q0 = [w.q_mixed() if precision == "mixed" else w.q for w in works]
+    qa = [torch.from_numpy(np.ascontiguousarray(q)).cuda() for q in q0]
+    qb = [t.clone() for t in qa]
+    handles, ptrs = _arrays(vts, qb)
+    with Batch(precision) as b:
+        for vt, q in zip(vts, qa):
+            b.add(vt, q)
+        b.advance(3, DT)
+        assert lib.numa_batch_advance_noalloc(handles, ptrs, len(vts), 3, DT, None) == _lib.NUMA_OK
+        torch.cuda.synchronize()
+        for k, (a, bq) in enumerate(zip(qa, qb)):
+            a_np, b_np = a.cpu().numpy().astype(np.float64), bq.cpu().numpy().astype(np.float64)
+            errs = rel_err(b_np - q0[k], a_np - q0[k]) if precision == "fp64" else rel_err(b_np, a_np)
+            assert len(errs) == works[k].q.shape[0]
+            for f, (mx, _) in enumerate(errs):
+                assert mx <= tol, (precision, specs[k], f, mx)
+    for vt in vts:
+        vt.close()
+
+
 def test_noalloc_rejects_counts_beyond_its_maximum_and_bad_arguments():
     lib = _lib.load()
     w = wl.make_workload(2, 1, seed=3)
